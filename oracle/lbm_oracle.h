@@ -1,0 +1,54 @@
+/*
+ * FP64 CPU oracle for the iD3Q14 / iD3Q18 incompressible MRT lattice
+ * Boltzmann models (arXiv:1503.03337).  TEST INFRASTRUCTURE ONLY: nothing in
+ * the CUDA library includes, links or calls this.
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORACLE_PERIODIC = 0, ORACLE_WALL = 1, ORACLE_MOVING_WALL = 2 };
+
+typedef struct {
+  int Q;              /* 14 or 18 */
+  int nx, ny, nz;     /* fluid nodes per axis */
+  int face[6];        /* x-, x+, y-, y+, z-, z+ : ORACLE_* kinds */
+  double u_wall[6][3];/* wall velocity of each MOVING_WALL face */
+} oracle_grid;
+
+typedef struct {
+  double sc, se, sq, snu, spi, st; /* relaxation rates (spi unused for Q14) */
+} oracle_rates;
+
+typedef struct {
+  oracle_rates rates;
+  double force[3]; /* body force amplitude (lattice units) */
+  double period;   /* > 0: F(t_n) = force cos(2 pi n / period); else constant */
+} oracle_params;
+
+int oracle_velocities(int Q, int *c_out);           /* Q*3 ints */
+int oracle_weights(int Q, double *w_out, double *w0_out);
+int oracle_transform(int Q, int *T_out);            /* Q*Q ints, row-major */
+int oracle_moment_equilibrium(int Q, double p, const double *u, double *meq);
+int oracle_pressure(int Q, double P, const double *u, double *p);
+int oracle_feq(int Q, double p, const double *u, double *feq);
+int oracle_collide(int Q, const oracle_rates *r, const double *f,
+                   const double *F, double *fpost);
+int oracle_init_equilibrium(const oracle_grid *g, const double *u,
+                            const double *p, double *f);
+int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
+                const double *f_in, double *f_out, int nthreads);
+int oracle_run(const oracle_grid *g, const oracle_params *prm, int64_t n0,
+               int64_t nsteps, double *f, int nthreads);
+int oracle_macroscopic(const oracle_grid *g, const oracle_params *prm,
+                       int64_t n, const double *f, double *u, double *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
