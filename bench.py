@@ -1,0 +1,404 @@
+"""Throughput benchmark of the fused D3Q14/D3Q18 MRT step on one GB300.
+
+Workload (one bench step = one lattice update of the whole domain):
+lid-driven cube 128^3, D3Q18, FP32 populations, lid 0.05 along x on y+,
+Re = 1000 (nu = U L / Re), FP64 residual every 1000 steps, synthetic state
+from rest.  Between bench steps a 256 MiB buffer is written to flush L2;
+each step is timed with CUDA events on the stream the kernels run on, and
+the flush lies outside those events.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1503_03337_gb300 import inputs  # noqa: E402
+
+FLUSH_BYTES = 256 << 20
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--Q", type=int, default=18)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--storage", default="f32")
+    ap.add_argument("--Re", type=float, default=1000.0)
+    ap.add_argument("--residual-interval", type=int, default=1000)
+    ap.add_argument("--variant-steps", type=int, default=400,
+                    help="steps per extra (Q, storage) variant; 0 to skip")
+    ap.add_argument("--e2e-chunk", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return "lid-driven cavity %d^3 D3Q%d %s Re=%g lid=0.05" % (a.n, a.Q, a.storage.upper(), a.Re)
+
+
+# ---- clocks ------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                     "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                parts = [p.strip() for p in out.stdout.strip().split(",")]
+                if len(parts) >= 7:
+                    self.samples.append(parts)
+            except Exception:
+                pass
+            self._stop.wait(0.1)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---- ncu-derived traffic --------------------------------------------------------
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1503_03337_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(os.path.basename(p).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(Q, storage, n):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src_hash = kernel_source_hash()
+    key = "Q%d %s %d^3" % (Q, storage, n)
+    cur = None
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("source_hash:"):
+            cur = line.split(":", 1)[1].strip()
+        elif line.startswith(key + ":") and cur == src_hash:
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = json.load(fh).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except Exception:
+        pass
+    return 6800.0, "fallback"
+
+
+# ---- GPU leg -----------------------------------------------------------------------
+
+def run_gpu(a, rank, world, dist):
+    import torch
+
+    from paper_1503_03337_gb300 import lbm
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    lbm.load()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def open_case(Q, storage, residual_interval):
+        case = inputs.cavity(Q, a.n, a.Re, U=0.05, storage=storage)
+        h = lbm.lbm_create(Q, case.nx, case.ny, case.nz, storage, sp)
+        lbm.lbm_set_geometry(h, case.faces, case.u_wall)
+        lbm.lbm_set_params(h, nu=case.nu, residual_interval=residual_interval)
+        lbm.lbm_init_equilibrium(h)
+        return case, h
+
+    def timed_steps(h, K, interval):
+        """Per-step event times (ms); reduction steps reported separately."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        red = []
+        n0 = lbm.lbm_get_step(h)
+        for k in range(K):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            lbm.lbm_step(h, 1)
+            ev[k][1].record(stream)
+            if interval and (n0 + k + 1) % interval == 0:
+                red.append(k)
+        return ev, red
+
+    # --- main workload -------------------------------------------------------
+    case, h = open_case(a.Q, a.storage, a.residual_interval)
+    cells = case.cells
+    bytes_per_update = 2 * a.Q * STORAGE_BYTES[a.storage]
+    for _ in range(max(0, a.warmup)):
+        flush.fill_(0.0)
+        lbm.lbm_step(h, 1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        ev, red = timed_steps(h, a.steps, a.residual_interval)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = [s.elapsed_time(e) for s, e in ev]
+    red_set = set(red)
+    step_only = [t for k, t in enumerate(times) if k not in red_set] or times
+    total_ms = sum(times)
+    kernel_ms = statistics.mean(step_only)
+    stats = lbm.lbm_read_stats(h)
+    lbm.lbm_destroy(h)
+
+    if dist:
+        import torch.distributed as td
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    glups = world * cells * a.steps / (total_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bytes_per_update * cells / (kernel_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(a.Q, a.storage, a.n)
+
+    # --- e2e through the C-ABI with host buffers ---------------------------------
+    e2e = None
+    if True:
+        case_e, he = open_case(a.Q, a.storage, 0)
+        N = case_e.cells
+        u0 = torch.zeros(3 * N, dtype=torch.float64).pin_memory()
+        p0 = torch.zeros(N, dtype=torch.float64).pin_memory()
+        uout = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        lbm.lbm_init_equilibrium(he, u0, p0, 0)
+        lbm.lbm_step(he, 2)
+        lbm.lbm_read_fields(he, lbm.LBM_FIELD_U, uout, lbm.LBM_DTYPE_F64, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            lbm.lbm_init_equilibrium(he, u0, p0, 0)
+            lbm.lbm_step(he, a.e2e_chunk)
+            lbm.lbm_read_fields(he, lbm.LBM_FIELD_U, uout, lbm.LBM_DTYPE_F64, 0)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        lbm.lbm_destroy(he)
+        if dist:
+            import torch.distributed as td
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * N * a.e2e_chunk * a.e2e_steps / el / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": 4 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
+               "lattice_updates_per_step": a.e2e_chunk,
+               "calls": "lbm_init_equilibrium(host u,p) + lbm_step(%d) + lbm_read_fields(U -> host)"
+                        % a.e2e_chunk}
+
+    # --- other (Q, storage) variants, same workload shape ------------------------------
+    variants = {}
+    if a.variant_steps > 0 and rank == 0:
+        for Q in (14, 18):
+            for st in ("f32", "f16", "bf16"):
+                cv, hv = open_case(Q, st, 0)
+                for _ in range(10):
+                    flush.fill_(0.0)
+                    lbm.lbm_step(hv, 1)
+                evv, _ = timed_steps(hv, a.variant_steps, 0)
+                torch.cuda.synchronize()
+                tv = statistics.mean(s.elapsed_time(e) for s, e in evv)
+                lbm.lbm_destroy(hv)
+                bpu = 2 * Q * STORAGE_BYTES[st]
+                variants["D3Q%d_%s" % (Q, st)] = {
+                    "glups": round(cv.cells / (tv * 1e-3) / 1e9, 3),
+                    "hbm_gbs": round(bpu * cv.cells / (tv * 1e-3) / 1e9, 1),
+                    "frac_of_measured_hbm": round(bpu * cv.cells / (tv * 1e-3) / 1e9 / peak, 4)}
+
+    launches = a.steps + 2 * len(red)
+    res = {
+        "metric": "D3Q18 MRT fused-step GLUPS (lattice updates/s) and HBM-roofline fraction",
+        "value": round(glups, 4),
+        "unit": "GLUPS",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": round(total_ms / a.steps, 6),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (lid-driven cavity from rest)",
+        "config": {"workload": workload_name(a), "grid": [a.n, a.n, a.n], "Q": a.Q,
+                   "storage": a.storage, "Re": a.Re, "lid_velocity": 0.05,
+                   "residual_interval": a.residual_interval,
+                   "l2": "flushed between steps (256 MiB write), outside the event-timed region",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "wall_s_timed_region": round(wall, 4)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_per_update * cells,
+                     "kernel_ms": round(kernel_ms, 6)},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "residual_last": {"step": stats.step, "cavity": (lbm.residual_cavity(stats)
+                                                         if stats.prev_step >= 0 else None)},
+        "variants": variants,
+    }
+    return res
+
+
+# ---- CPU oracle ----------------------------------------------------------------------
+
+def oracle_rate(Q, n, Re, storage, budget_s=15.0, max_steps=50):
+    import oracle
+    case = inputs.cavity(Q, n, Re, U=0.05, storage=storage)
+    g = oracle.make_grid(Q, case.nx, case.ny, case.nz, case.faces, case.u_wall)
+    prm = oracle.make_params(oracle.rates(Q, case.s_nu))
+    f = oracle.init_equilibrium(g)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    f = oracle.run(g, prm, f, 0, 1, nthreads=threads)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(g, prm, f, 1, steps, nthreads=threads)
+    el = time.perf_counter() - t0
+    return {"value": case.cells * steps / el / 1e9, "unit": "GLUPS", "cores": min(threads, n),
+            "kind": "oracle",
+            "sample": "%d steps of the %d^3 D3Q%d cavity in FP64 (oracle, OpenMP over z)"
+                      % (steps, n, Q)}
+
+
+def oracle_reference_arm(a, budget_s=90.0):
+    """The oracle as it stands on the host cores: W + K steps of the cavity
+    workload, each step one lattice update of a 128 x 128 x nz_s slab of the
+    cube (same boundary kinds and per-cell work), nz_s sized so the whole
+    run fits in about budget_s."""
+    import oracle
+    threads = os.cpu_count() or 1
+    full = inputs.cavity(a.Q, a.n, a.Re, U=0.05, storage=a.storage)
+    # calibrate on one slab step
+    probe = inputs.cavity(a.Q, a.n, a.Re, U=0.05, storage=a.storage, nz=min(a.n, 8))
+    g = oracle.make_grid(a.Q, probe.nx, probe.ny, probe.nz, probe.faces, probe.u_wall)
+    prm = oracle.make_params(oracle.rates(a.Q, full.s_nu))
+    f = oracle.init_equilibrium(g)
+    t0 = time.perf_counter()
+    oracle.run(g, prm, f, 0, 1, nthreads=threads)
+    per_layer = (time.perf_counter() - t0) / probe.nz
+    total_steps = max(1, a.steps) + max(0, a.warmup)
+    nz_s = int(max(1, min(a.n, budget_s / (total_steps * max(per_layer, 1e-9)))))
+    case = inputs.cavity(a.Q, a.n, a.Re, U=0.05, storage=a.storage, nz=nz_s)
+    g = oracle.make_grid(a.Q, case.nx, case.ny, case.nz, case.faces, case.u_wall)
+    f = oracle.init_equilibrium(g)
+    f = oracle.run(g, prm, f, 0, max(0, a.warmup), nthreads=threads)
+    t0 = time.perf_counter()
+    oracle.run(g, prm, f, max(0, a.warmup), max(1, a.steps), nthreads=threads)
+    el = time.perf_counter() - t0
+    return {"value": case.cells * max(1, a.steps) / el / 1e9, "unit": "GLUPS",
+            "cores": min(threads, nz_s), "kind": "oracle",
+            "sample": "each step one FP64 oracle update of a %dx%dx%d slab of the %d^3 D3Q%d "
+                      "cavity (walls on all six faces of the slab, lid on y+)"
+                      % (a.n, a.n, nz_s, a.n, a.Q)}
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        cb = oracle_reference_arm(a)
+        steps_each = max(1, a.steps)
+        out = {"metric": "D3Q18 MRT fused-step GLUPS (lattice updates/s) and HBM-roofline fraction",
+               "value": cb["value"], "unit": "GLUPS", "n_gpus": 0, "steps": steps_each,
+               "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic (lid-driven cavity from rest)",
+               "config": {"workload": workload_name(a), "grid": [a.n] * 3, "Q": a.Q},
+               "impl": "reference", "cpu_baseline": cb,
+               "e2e": {"value": cb["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group("nccl")
+        dist = td
+    res = run_gpu(a, rank, world, dist)
+    if rank == 0:
+        if not a.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = oracle_rate(a.Q, a.n, a.Re, a.storage)
+        elif not a.no_cpu_baseline:
+            res["cpu_baseline"] = None
+        print(json.dumps(res))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * liblbm -- GB300 (sm_103a) fused streaming + MRT collision step of the
+ * incompressible 14- and 18-velocity lattice Boltzmann models of
+ * Zhang, Shi & Wang, "Incompressible MRT lattice Boltzmann models in three
+ * dimensions" (arXiv:1503.03337).
+ *
+ * Problem statement (Sec. 4): a box of nx*ny*nz fluid nodes; every face is
+ * periodic, a no-slip wall or a moving wall; viscosity nu (Eq. vis); an
+ * optional body force; output velocity u and pressure p (Eq. hgl).
+ *
+ * Conventions shared by every call:
+ *  - Nodes are ordered x fastest: cell = x + nx*(y + ny*z).
+ *  - Population arrays are [a][cell], a = 0..Q-1 being the paper's direction
+ *    a+1 (Sec. 3 velocity set for Q = 14, App. B for Q = 18).
+ *  - Walls sit halfway between the last fluid node and the ghost node beyond
+ *    it (halfway bounce-back); a moving wall adds 6 w_a (c_a . u_wall) to the
+ *    reflected population.
+ *  - Lattice units throughout (dx = dt = c = 1, c_s^2 = 1/3).
+ *  - Every call returns LBM_OK (0) or one of the LBM_E* codes below; no C++
+ *    exception crosses this boundary.  lbm_last_error() gives a message for
+ *    the calling thread's last failure.
+ *  - A handle is not thread-safe: one handle per host thread, or external
+ *    locking.  All GPU work of a handle is queued on the stream it was given.
+ *  - Device pointers passed in must be on the handle's device; host pointers
+ *    may be pageable or pinned.  The caller keeps ownership of every buffer
+ *    it passes; the library never frees a caller's buffer.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_EINVAL 1    /* bad argument, size or state                       */
+#define LBM_ENOMEM 2    /* device or pinned host allocation failed          */
+#define LBM_ECUDA 3     /* a CUDA runtime call or kernel launch failed      */
+#define LBM_EUNSTABLE 4 /* a reduction found a non-finite velocity          */
+#define LBM_ETIMEOUT 5  /* a bounded device-side wait gave up               */
+#define LBM_EBUSY 6     /* no free slot / memory budget exhausted           */
+
+/* ---- enumerations ------------------------------------------------------- */
+enum lbm_storage { /* how populations are held in device memory */
+  LBM_STORAGE_F64 = 0,  /* double; all arithmetic in double (parity build) */
+  LBM_STORAGE_F32 = 1,  /* float; arithmetic in float                      */
+  LBM_STORAGE_F16 = 2,  /* IEEE half; arithmetic in float                   */
+  LBM_STORAGE_BF16 = 3  /* bfloat16; arithmetic in float                    */
+};
+
+enum lbm_face_kind {
+  LBM_PERIODIC = 0,    /* wraps to the opposite face (both must say so)   */
+  LBM_WALL = 1,        /* halfway bounce-back, wall at rest               */
+  LBM_MOVING_WALL = 2  /* halfway bounce-back with wall velocity u_wall   */
+};
+
+enum lbm_face { LBM_XM = 0, LBM_XP = 1, LBM_YM = 2, LBM_YP = 3, LBM_ZM = 4, LBM_ZP = 5 };
+
+enum lbm_field_bits {
+  LBM_FIELD_U = 1u,          /* 3*N values: ux[N], uy[N], uz[N]            */
+  LBM_FIELD_P = 2u,          /* N values                                   */
+  LBM_FIELD_POPULATIONS = 4u /* Q*N values, canonical pre-collision f^n    */
+};
+
+enum lbm_dtype { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 };
+
+/* ---- descriptors -------------------------------------------------------- */
+typedef struct lbm_desc {
+  int32_t Q;       /* 14 (Sec. 3) or 18 (App. B)                           */
+  int32_t nx, ny, nz; /* fluid nodes per axis, each >= 1                   */
+  int32_t storage; /* enum lbm_storage                                     */
+} lbm_desc;
+
+/* Face order x-, x+, y-, y+, z-, z+.  A ghost node beyond several faces
+ * (an edge or corner) takes the velocity of the first MOVING_WALL face among
+ * them in that order, else zero. */
+typedef struct lbm_geom {
+  int32_t face[6];
+  double u_wall[6][3];
+} lbm_geom;
+
+/* Relaxation rates of the diagonal collision matrix, Eq. sD3Q15meaning
+ * (Q14) and Eq. sD3Q19 (Q18).  If nu > 0 then s_nu = 1/(3 nu + 1/2)
+ * (Eq. vis) and the s_nu field is ignored.  Sec. 4 uses s_c = 1, s_e = 1.19,
+ * s_q = 1.2, s_t = 0.98; s_pi (Q18 only) is not given by the paper.
+ * Body force F(t_n) = force * cos(2 pi n / force_period) if force_period > 0,
+ * else force; it enters as u = j + F/2 and a Guo source in moment space.
+ * p_ref shifts the reported pressure: stored populations are
+ * f_a - 3 w_a p_ref, and read-back p includes p_ref. */
+typedef struct lbm_params {
+  double nu;
+  double s_nu, s_c, s_e, s_q, s_pi, s_t;
+  double force[3];
+  double force_period;
+  double p_ref;
+  int32_t residual_interval; /* > 0: lbm_step runs the FP64 reductions every
+                                that many steps (stats via lbm_read_stats) */
+  int32_t reserved;
+} lbm_params;
+
+/* FP64 reductions over all nodes at step `step`, against the velocity
+ * snapshot of step `prev_step` (-1: none yet).  They give the convergence
+ * criteria of Eq. sc, Eq. cr and Eq. cavity_creterion:
+ *   sc     = sum_abs_du[k] / sum_abs_u_prev[k]   (one component k)
+ *   cr     = sum_abs_du[k] / sum_abs_u[k]
+ *   cavity = sum_k sum_abs_du[k] / sum_k sum_abs_u[k]. */
+typedef struct lbm_stats {
+  int64_t step, prev_step;
+  double sum_abs_du[3];
+  double sum_abs_u[3];
+  double sum_abs_u_prev[3];
+  double sum_P;     /* sum of P = sum_a f_a (mass-like invariant)        */
+  double sum_u[3];  /* sum of u (volume flux)                            */
+  double max_abs_u; /* largest |u_k| over nodes and components          */
+  int64_t nonfinite;/* nodes whose P or u is not finite                  */
+} lbm_stats;
+
+typedef struct lbm_handle lbm_handle;
+
+/* ---- single domain ------------------------------------------------------ */
+
+/* Allocate a domain on the current CUDA device: one population buffer of
+ * Q*nx*ny*nz storage values (single-buffer AA streaming) plus a small
+ * reduction workspace.  `cuda_stream` is a cudaStream_t (NULL = legacy
+ * default stream); it is borrowed, not owned.  Initial state: all walls at
+ * rest, Sec. 4 default rates with nu = 1/6, no force, f = 0, step 0.
+ * Errors: EINVAL (Q not 14/18, a size < 1, storage unknown, Q*N >= 2^31),
+ * ENOMEM, ECUDA. */
+int lbm_create(const lbm_desc *desc, void *cuda_stream, lbm_handle **out);
+
+/* Free everything the handle owns.  NULL is accepted. */
+void lbm_destroy(lbm_handle *h);
+
+/* Replace the stream later work is queued on. */
+int lbm_set_stream(lbm_handle *h, void *cuda_stream);
+
+/* Boundary kinds (Sec. 4 problem statement; halfway and moving-wall
+ * bounce-back stand in for the paper's extrapolation scheme).  EINVAL if a
+ * kind is unknown or only one of two opposite faces is periodic. */
+int lbm_set_geometry(lbm_handle *h, const lbm_geom *geom);
+
+/* Rates, force and reduction cadence.  EINVAL unless every rate is in
+ * (0, 2), nu > 0 or s_nu given, and all values are finite. */
+int lbm_set_params(lbm_handle *h, const lbm_params *params);
+
+/* f = f_eq(p, u) of Eq. edf at every node (u: 3*N FP64 ux,uy,uz; p: N FP64;
+ * either may be NULL meaning zero), step counter reset to 0, velocity
+ * snapshot cleared.  Pointers are device pointers if on_device != 0. */
+int lbm_init_equilibrium(lbm_handle *h, const double *u, const double *p, int on_device);
+
+/* Queue nsteps fused steps (stream + collide, Eq. mrteqvT) on the stream.
+ * Asynchronous.  Returns LBM_EUNSTABLE without queuing anything if an
+ * earlier reduction found non-finite values (until the next init or
+ * write_populations). */
+int lbm_step(lbm_handle *h, int64_t nsteps);
+
+/* Current step counter n (populations hold f^n). */
+int lbm_get_step(lbm_handle *h, int64_t *n);
+
+/* Set the step counter to n >= 0 without touching device memory (the force
+ * time level and the parity of the storage layout follow n).  Meant to be
+ * followed by lbm_write_populations when restoring a checkpoint taken at
+ * step n.  Clears the velocity snapshot. */
+int lbm_set_step(lbm_handle *h, int64_t n);
+
+/* Copy the fields selected by `mask` (LBM_FIELD_* bits), in the order U, P,
+ * POPULATIONS, back to back, into dst as FP64 or FP32 (dtype).  u is
+ * j + F(t_n)/2, p follows Eq. hgl plus p_ref.  Synchronises the stream. */
+int lbm_read_fields(lbm_handle *h, unsigned mask, void *dst, int dst_on_device, int dtype);
+
+/* Overwrite the state with canonical pre-collision populations (Q*N FP64)
+ * at the current step counter (checkpoint restore).  Synchronises. */
+int lbm_write_populations(lbm_handle *h, const double *src, int src_on_device);
+
+/* Run the FP64 reductions now (current populations against the last
+ * snapshot), make the current velocity the new snapshot, and return the
+ * statistics.  Synchronises. */
+int lbm_reductions(lbm_handle *h, lbm_stats *out);
+
+/* Statistics of the most recent reduction (queued by lbm_step's cadence or
+ * lbm_reductions).  Synchronises. */
+int lbm_read_stats(lbm_handle *h, lbm_stats *out);
+
+/* Device memory the handle holds, in bytes. */
+int lbm_memory_bytes(lbm_handle *h, int64_t *bytes);
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char *lbm_last_error(void);
+const char *lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,319 @@
+// Field I/O and FP64 reductions of a single domain: equilibrium
+// initialisation, canonical read-back (u, p, populations), checkpoint
+// restore, and the convergence / mass / flux reductions.
+#include <cmath>
+
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <typename R>
+Domain<R> to_domain(const DomainDesc& d, const double F[3]);
+
+namespace {
+
+// u and P of canonical populations fv (FP64), with the force half step.
+template <int Q>
+__device__ __forceinline__ void macro(const double* fv, const double F[3], double& P,
+                                      double u[3]) {
+  P = 0.0;
+  u[0] = u[1] = u[2] = 0.0;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    P += fv[a];
+    u[0] += Lattice<Q>::c(a, 0) * fv[a];
+    u[1] += Lattice<Q>::c(a, 1) * fv[a];
+    u[2] += Lattice<Q>::c(a, 2) * fv[a];
+  }
+  for (int k = 0; k < 3; ++k) u[k] += 0.5 * F[k];
+}
+
+template <int Q>
+__device__ __forceinline__ double pressure_of(double P, const double u[3]) {
+  // Eq. hgl with c_s^2 = 1/3
+  const double cs2 = 1.0 / 3.0, w0 = Lattice<Q>::w0;
+  const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  return cs2 / (1.0 - w0) * (P - w0 * u2 / (2.0 * cs2));
+}
+
+struct FieldArgs {
+  const double* u_in;
+  const double* p_in;
+  void* dst;
+  const double* src;
+  unsigned mask;
+  int dtype;
+  double F[3];
+  double p_ref;
+};
+
+template <int Q, typename S, bool ODD>
+__global__ void k_read(Domain<double> d, FieldArgs a) {
+  const int64_t N = d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    x = (int)(i % d.nx);
+    const int64_t r = i / d.nx;
+    y = (int)(r % d.ny);
+    z = (int)(r / d.ny);
+    double fv[Q];
+    gather<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, i,
+                              ODD ? is_interior(d, x, y, z) : true, fv);
+    for (int b = 0; b < Q; ++b) fv[b] += 3.0 * Lattice<Q>::w(b) * a.p_ref;
+    double P, u[3];
+    macro<Q>(fv, a.F, P, u);
+    int64_t off = 0;
+    auto put = [&](int64_t k, double v) {
+      if (a.dtype == LBM_DTYPE_F64) static_cast<double*>(a.dst)[k] = v;
+      else static_cast<float*>(a.dst)[k] = (float)v;
+    };
+    if (a.mask & LBM_FIELD_U) {
+      for (int k = 0; k < 3; ++k) put(off + k * N + i, u[k]);
+      off += 3 * N;
+    }
+    if (a.mask & LBM_FIELD_P) {
+      put(off + i, pressure_of<Q>(P, u));
+      off += N;
+    }
+    if (a.mask & LBM_FIELD_POPULATIONS) {
+      for (int b = 0; b < Q; ++b) put(off + b * N + i, fv[b]);
+    }
+  }
+}
+
+template <int Q, typename S, bool ODD>
+__global__ void k_write(Domain<double> d, FieldArgs a) {
+  const int64_t N = d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % d.nx);
+    const int64_t r = i / d.nx;
+    const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+    double fv[Q];
+    for (int b = 0; b < Q; ++b)
+      fv[b] = a.src[b * N + i] - 3.0 * Lattice<Q>::w(b) * a.p_ref;
+    put_canonical<Q, S, double, ODD>(d, static_cast<S*>(d.f), x, y, z, i, fv);
+  }
+}
+
+template <int Q, typename S>
+__global__ void k_init(Domain<double> d, FieldArgs a) {
+  const int64_t N = d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % d.nx);
+    const int64_t r = i / d.nx;
+    const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+    double u[3] = {0.0, 0.0, 0.0};
+    if (a.u_in)
+      for (int k = 0; k < 3; ++k) u[k] = a.u_in[k * N + i];
+    const double p = (a.p_in ? a.p_in[i] : 0.0) - a.p_ref;
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double fv[Q];
+    // Eq. edf with lambda_a = w_a p / c_s^2 (Eq. lamda_alpha), c_s^2 = 1/3
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const double cu = Lattice<Q>::c(b, 0) * u[0] + Lattice<Q>::c(b, 1) * u[1] +
+                        Lattice<Q>::c(b, 2) * u[2];
+      fv[b] = Lattice<Q>::w(b) * (3.0 * p + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+    }
+    put_canonical<Q, S, double, false>(d, static_cast<S*>(d.f), x, y, z, i, fv);
+  }
+}
+
+// ---- reductions ---------------------------------------------------------------
+
+struct ReduceArgs {
+  double* u_prev;
+  int have_prev;
+  double* partials;
+  double F[3];
+  double p_ref;
+};
+
+__device__ __forceinline__ void block_reduce(double (&v)[kNumStats], double* shm) {
+  // warp level
+#pragma unroll
+  for (int k = 0; k < kNumStats; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_down_sync(0xffffffffu, v[k], o);
+      v[k] = (k == kNumSums) ? fmax(v[k], t) : v[k] + t;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < kNumStats; ++k) shm[warp * kNumStats + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nwarps; ++w)
+      for (int k = 0; k < kNumStats; ++k) {
+        const double t = shm[w * kNumStats + k];
+        v[k] = (k == kNumSums) ? fmax(v[k], t) : v[k] + t;
+      }
+  }
+}
+
+template <int Q, typename S, bool ODD>
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(Domain<double> d, ReduceArgs a) {
+  __shared__ double shm[(kReduceThreads / 32) * kNumStats];
+  double v[kNumStats];
+  for (int k = 0; k < kNumStats; ++k) v[k] = 0.0;
+  const int64_t N = d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % d.nx);
+    const int64_t r = i / d.nx;
+    const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+    double fv[Q];
+    gather<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, i,
+                              ODD ? is_interior(d, x, y, z) : true, fv);
+    double P, u[3];
+    macro<Q>(fv, a.F, P, u);
+    const bool finite = isfinite(P) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+    if (!finite) {
+      v[kNumSums - 1] += 1.0;
+      continue;
+    }
+    for (int k = 0; k < 3; ++k) {
+      const double up = a.have_prev ? a.u_prev[k * N + i] : 0.0;
+      if (a.have_prev) v[k] += fabs(u[k] - up);
+      v[3 + k] += fabs(u[k]);
+      v[6 + k] += fabs(up);
+      v[10 + k] += u[k];
+      v[kNumSums] = fmax(v[kNumSums], fabs(u[k]));
+      if (a.u_prev) a.u_prev[k * N + i] = u[k];
+    }
+    v[9] += P + 3.0 * (1.0 - Lattice<Q>::w0) * a.p_ref;
+  }
+  block_reduce(v, shm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kNumStats; ++k) a.partials[blockIdx.x * kNumStats + k] = v[k];
+}
+
+// Sums the per-block partials in a fixed order (deterministic result).
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double* partials,
+                                                                 int nblocks, double* out) {
+  __shared__ double shm[(kReduceThreads / 32) * kNumStats];
+  double v[kNumStats];
+  for (int k = 0; k < kNumStats; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < kNumStats; ++k) {
+      const double t = partials[b * kNumStats + k];
+      v[k] = (k == kNumSums) ? fmax(v[k], t) : v[k] + t;
+    }
+  block_reduce(v, shm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kNumStats; ++k) out[k] = v[k];
+}
+
+int grid_for(int64_t N) {
+  int64_t g = (N + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename Fn>
+cudaError_t dispatch(const DomainDesc& d, Fn&& fn) {
+  // fn.template operator()<Q, S>()
+  if (d.Q == 14) {
+    switch (d.storage) {
+      case LBM_STORAGE_F64: return fn.template operator()<14, double>();
+      case LBM_STORAGE_F32: return fn.template operator()<14, float>();
+      case LBM_STORAGE_F16: return fn.template operator()<14, __half>();
+      case LBM_STORAGE_BF16: return fn.template operator()<14, __nv_bfloat16>();
+    }
+  } else if (d.Q == 18) {
+    switch (d.storage) {
+      case LBM_STORAGE_F64: return fn.template operator()<18, double>();
+      case LBM_STORAGE_F32: return fn.template operator()<18, float>();
+      case LBM_STORAGE_F16: return fn.template operator()<18, __half>();
+      case LBM_STORAGE_BF16: return fn.template operator()<18, __nv_bfloat16>();
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_init(const DomainDesc& dd, const double* u, const double* p,
+                        cudaStream_t st) {
+  if (dd.N == 0) return cudaSuccess;
+  const double zero[3] = {0.0, 0.0, 0.0};
+  Domain<double> d = to_domain<double>(dd, zero);
+  FieldArgs a{};
+  a.u_in = u;
+  a.p_in = p;
+  a.p_ref = dd.p_ref;
+  return dispatch(dd, [&]<int Q, typename S>() {
+    k_init<Q, S><<<grid_for(dd.N), 256, 0, st>>>(d, a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_read(const DomainDesc& dd, int64_t n, unsigned mask, void* dst,
+                        int dtype, cudaStream_t st) {
+  if (dd.N == 0) return cudaSuccess;
+  double F[3];
+  force_at(dd, n, F);
+  Domain<double> d = to_domain<double>(dd, F);
+  FieldArgs a{};
+  a.dst = dst;
+  a.mask = mask;
+  a.dtype = dtype;
+  a.p_ref = dd.p_ref;
+  for (int k = 0; k < 3; ++k) a.F[k] = F[k];
+  const bool odd = n & 1;
+  return dispatch(dd, [&]<int Q, typename S>() {
+    if (odd) k_read<Q, S, true><<<grid_for(dd.N), 256, 0, st>>>(d, a);
+    else k_read<Q, S, false><<<grid_for(dd.N), 256, 0, st>>>(d, a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_write(const DomainDesc& dd, int64_t n, const double* src,
+                         cudaStream_t st) {
+  if (dd.N == 0) return cudaSuccess;
+  const double zero[3] = {0.0, 0.0, 0.0};
+  Domain<double> d = to_domain<double>(dd, zero);
+  FieldArgs a{};
+  a.src = src;
+  a.p_ref = dd.p_ref;
+  const bool odd = n & 1;
+  return dispatch(dd, [&]<int Q, typename S>() {
+    if (odd) k_write<Q, S, true><<<grid_for(dd.N), 256, 0, st>>>(d, a);
+    else k_write<Q, S, false><<<grid_for(dd.N), 256, 0, st>>>(d, a);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_reduce(const DomainDesc& dd, int64_t n, double* u_prev, int have_prev,
+                          double* partials, double* out, cudaStream_t st) {
+  double F[3];
+  force_at(dd, n, F);
+  Domain<double> d = to_domain<double>(dd, F);
+  ReduceArgs a{};
+  a.u_prev = u_prev;
+  a.have_prev = have_prev && u_prev != nullptr;
+  a.partials = partials;
+  a.p_ref = dd.p_ref;
+  for (int k = 0; k < 3; ++k) a.F[k] = F[k];
+  int64_t g = (dd.N + kReduceThreads - 1) / kReduceThreads;
+  if (g > kReduceBlocks) g = kReduceBlocks;
+  if (g < 1) g = 1;
+  const bool odd = n & 1;
+  cudaError_t e = dispatch(dd, [&]<int Q, typename S>() {
+    if (odd) k_reduce<Q, S, true><<<(int)g, kReduceThreads, 0, st>>>(d, a);
+    else k_reduce<Q, S, false><<<(int)g, kReduceThreads, 0, st>>>(d, a);
+    return cudaGetLastError();
+  });
+  if (e != cudaSuccess) return e;
+  k_reduce_final<<<1, kReduceThreads, 0, st>>>(partials, (int)g, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

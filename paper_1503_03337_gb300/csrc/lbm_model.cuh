@@ -1,0 +1,416 @@
+// Lattice tables and the per-cell MRT collision of the iD3Q14 (Sec. 3) and
+// iD3Q18 (App. B) incompressible models, written for registers.
+//
+// Everything that depends only on the lattice is a constexpr function, so
+// the moment transform m = T f and its inverse f = T' D^-1 m (Eq. mrteqvT)
+// unroll at compile time into adds and constant multiply-adds; no matrix is
+// stored anywhere.  The rows of T are the orthogonal basis vectors phi_k of
+// Sec. 3 (Eq. m, after orthogonalisation) and App. B (Eq. appendix_m18),
+// evaluated on the velocity set.
+//
+// Every direction a has an opposite abar (Q is even and there is no rest
+// direction), and every row of T is either even (T_k,abar = T_k,a: P, e and
+// the second-order moments) or odd (T_k,abar = -T_k,a: j, q, t).  The
+// transform therefore runs on pair sums s = f_a + f_abar (even rows) and
+// pair differences d = f_a - f_abar (odd rows), which halves its cost.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <utility>
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Velocity sets and weights
+// ---------------------------------------------------------------------------
+template <int Q>
+struct Lattice;
+
+// iD3Q14, Sec. 3: c_1..c_6 on the axes, c_7..c_14 on the cube diagonals.
+template <>
+struct Lattice<14> {
+  static constexpr int Q = 14;
+  __host__ __device__ static constexpr int c(int a, int d) {
+    const int v[14][3] = {{1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+                          {0, 0, 1},   {0, 0, -1},  {1, 1, 1},   {-1, 1, 1},
+                          {1, -1, 1},  {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1},
+                          {1, -1, -1}, {-1, -1, -1}};
+    return v[a][d];
+  }
+  // D3Q15 weights of the discarded rest direction and of the stored ones
+  // (the only weights for which Eq. meq equals T f_eq).
+  static constexpr double w0 = 2.0 / 9.0;
+  __host__ __device__ static constexpr double w(int a) {
+    return a < 6 ? 1.0 / 9.0 : 1.0 / 72.0;
+  }
+};
+
+// iD3Q18, App. B: c_1..c_6 on the axes, c_7..c_18 on the face diagonals.
+template <>
+struct Lattice<18> {
+  static constexpr int Q = 18;
+  __host__ __device__ static constexpr int c(int a, int d) {
+    const int v[18][3] = {{1, 0, 0},  {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
+                          {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, 1, 0},
+                          {1, -1, 0}, {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1},
+                          {1, 0, -1}, {-1, 0, -1}, {0, 1, 1},  {0, -1, 1},
+                          {0, 1, -1}, {0, -1, -1}};
+    return v[a][d];
+  }
+  static constexpr double w0 = 1.0 / 3.0;
+  __host__ __device__ static constexpr double w(int a) {
+    return a < 6 ? 1.0 / 18.0 : 1.0 / 36.0;
+  }
+};
+
+template <int Q>
+__host__ __device__ constexpr int opposite(int a) {
+  for (int b = 0; b < Q; ++b)
+    if (Lattice<Q>::c(b, 0) == -Lattice<Q>::c(a, 0) &&
+        Lattice<Q>::c(b, 1) == -Lattice<Q>::c(a, 1) &&
+        Lattice<Q>::c(b, 2) == -Lattice<Q>::c(a, 2))
+      return b;
+  return -1;
+}
+
+// i-th pair representative: the i-th direction (in index order) whose
+// opposite has a larger index.
+template <int Q>
+__host__ __device__ constexpr int pair_rep(int i) {
+  int seen = 0;
+  for (int a = 0; a < Q; ++a)
+    if (opposite<Q>(a) > a) {
+      if (seen == i) return a;
+      ++seen;
+    }
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Moment basis
+// ---------------------------------------------------------------------------
+enum RowKind { ROW_P, ROW_E, ROW_J, ROW_Q, ROW_NU, ROW_PI, ROW_T };
+
+template <int Q>
+__host__ __device__ constexpr int phi(int k, int a) {
+  const int cx = Lattice<Q>::c(a, 0), cy = Lattice<Q>::c(a, 1),
+            cz = Lattice<Q>::c(a, 2);
+  const int n2 = cx * cx + cy * cy + cz * cz;
+  if (Q == 14) {
+    // P, e, jx, qx, jy, qy, jz, qz, 3pxx, pww, pxy, pyz, pxz, txyz
+    switch (k) {
+      case 0: return 1;
+      case 1: return (7 * n2 - 15) / 2;
+      case 2: return cx;
+      case 3: return (5 * n2 - 13) * cx / 2;
+      case 4: return cy;
+      case 5: return (5 * n2 - 13) * cy / 2;
+      case 6: return cz;
+      case 7: return (5 * n2 - 13) * cz / 2;
+      case 8: return 3 * cx * cx - n2;
+      case 9: return cy * cy - cz * cz;
+      case 10: return cx * cy;
+      case 11: return cy * cz;
+      case 12: return cx * cz;
+      case 13: return cx * cy * cz;
+    }
+  } else {
+    // P, e, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz,
+    // tx, ty, tz
+    switch (k) {
+      case 0: return 1;
+      case 1: return 3 * n2 - 5;
+      case 2: return cx;
+      case 3: return (5 * n2 - 9) * cx;
+      case 4: return cy;
+      case 5: return (5 * n2 - 9) * cy;
+      case 6: return cz;
+      case 7: return (5 * n2 - 9) * cz;
+      case 8: return 3 * cx * cx - n2;
+      case 9: return (3 * n2 - 5) * (3 * cx * cx - n2);
+      case 10: return cy * cy - cz * cz;
+      case 11: return (3 * n2 - 5) * (cy * cy - cz * cz);
+      case 12: return cx * cy;
+      case 13: return cy * cz;
+      case 14: return cx * cz;
+      case 15: return (cy * cy - cz * cz) * cx;
+      case 16: return (cz * cz - cx * cx) * cy;
+      case 17: return (cx * cx - cy * cy) * cz;
+    }
+  }
+  return 0;
+}
+
+template <int Q>
+__host__ __device__ constexpr bool row_even(int k) {
+  return phi<Q>(k, 0) == phi<Q>(k, 1);  // c_1 and c_2 are opposite
+}
+
+template <int Q>
+__host__ __device__ constexpr int row_norm(int k) {
+  int s = 0;
+  for (int a = 0; a < Q; ++a) s += phi<Q>(k, a) * phi<Q>(k, a);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Storage codec: populations live in S, arithmetic runs in R.
+// ---------------------------------------------------------------------------
+template <typename S, typename R>
+struct Codec;
+template <typename R>
+struct Codec<double, R> {
+  __device__ static R load(const double* p) { return R(__ldg(p)); }
+  __device__ static R load_nc(const double* p) { return R(*p); }
+  __device__ static void store(double* p, R v) { *p = double(v); }
+};
+template <typename R>
+struct Codec<float, R> {
+  __device__ static R load(const float* p) { return R(*p); }
+  __device__ static R load_nc(const float* p) { return R(*p); }
+  __device__ static void store(float* p, R v) { *p = float(v); }
+};
+template <typename R>
+struct Codec<__half, R> {
+  __device__ static R load(const __half* p) { return R(__half2float(*p)); }
+  __device__ static R load_nc(const __half* p) { return R(__half2float(*p)); }
+  __device__ static void store(__half* p, R v) { *p = __float2half_rn(float(v)); }
+};
+template <typename R>
+struct Codec<__nv_bfloat16, R> {
+  __device__ static R load(const __nv_bfloat16* p) {
+    return R(__bfloat162float(*p));
+  }
+  __device__ static R load_nc(const __nv_bfloat16* p) {
+    return R(__bfloat162float(*p));
+  }
+  __device__ static void store(__nv_bfloat16* p, R v) {
+    *p = __float2bfloat16_rn(float(v));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Unrolled transforms over pairs
+// ---------------------------------------------------------------------------
+template <int C, typename R>
+__device__ __forceinline__ R term_first(R x) {
+  if constexpr (C == 1) return x;
+  else if constexpr (C == -1) return -x;
+  else return R(C) * x;
+}
+template <int C, typename R>
+__device__ __forceinline__ R term_add(R acc, R x) {
+  if constexpr (C == 1) return acc + x;
+  else if constexpr (C == -1) return acc - x;
+  else return fma(R(C), x, acc);
+}
+
+// m_K = sum_i phi_K(rep_i) v_i, with v = pair sums (even K) or differences.
+template <int Q, int K, int I, bool STARTED, typename R>
+__device__ __forceinline__ R row_sum(R acc, const R* v) {
+  if constexpr (I == Q / 2) {
+    if constexpr (STARTED) return acc;
+    else return R(0);
+  } else {
+    constexpr int C = phi<Q>(K, pair_rep<Q>(I));
+    if constexpr (C == 0) return row_sum<Q, K, I + 1, STARTED>(acc, v);
+    else if constexpr (!STARTED)
+      return row_sum<Q, K, I + 1, true>(term_first<C>(v[I]), v);
+    else return row_sum<Q, K, I + 1, true>(term_add<C>(acc, v[I]), v);
+  }
+}
+
+// Back-transform share of pair I: sum over rows K of the given parity of
+// phi_K(rep_I) * x_K.
+template <int Q, int I, int K, bool EVEN, bool STARTED, typename R>
+__device__ __forceinline__ R col_sum(R acc, const R* x) {
+  if constexpr (K == Q) {
+    if constexpr (STARTED) return acc;
+    else return R(0);
+  } else {
+    constexpr int C = (row_even<Q>(K) == EVEN) ? phi<Q>(K, pair_rep<Q>(I)) : 0;
+    if constexpr (C == 0) return col_sum<Q, I, K + 1, EVEN, STARTED>(acc, x);
+    else if constexpr (!STARTED)
+      return col_sum<Q, I, K + 1, EVEN, true>(term_first<C>(x[K]), x);
+    else return col_sum<Q, I, K + 1, EVEN, true>(term_add<C>(acc, x[K]), x);
+  }
+}
+
+template <int Q, int K = 0, typename R>
+__device__ __forceinline__ void moments(const R* s, const R* d, R* m) {
+  if constexpr (K < Q) {
+    if constexpr (row_even<Q>(K)) m[K] = row_sum<Q, K, 0, false>(R(0), s);
+    else m[K] = row_sum<Q, K, 0, false>(R(0), d);
+    moments<Q, K + 1>(s, d, m);
+  }
+}
+
+// f*_rep = f_rep - (E + O), f*_partner = f_partner - (E - O)
+template <int Q, int I = 0, typename R>
+__device__ __forceinline__ void back_transform(const R* x, R* f) {
+  if constexpr (I < Q / 2) {
+    constexpr int a = pair_rep<Q>(I);
+    constexpr int b = opposite<Q>(a);
+    const R E = col_sum<Q, I, 0, true, false>(R(0), x);
+    const R O = col_sum<Q, I, 0, false, false>(R(0), x);
+    f[a] = f[a] - (E + O);
+    f[b] = f[b] - (E - O);
+    back_transform<Q, I + 1>(x, f);
+  }
+}
+
+template <typename R>
+struct Rates {
+  R sc, se, sq, snu, spi, st;
+};
+
+// ---------------------------------------------------------------------------
+// One-cell collision, Eq. mrteqvT:  f* = f - T^-1 [ S (m - m_eq) - (I - S/2) S_F ]
+//
+// u = j + F/2 and p from Eq. hgl.  The Guo source S_F is the derivative of
+// the equilibrium moments along F at fixed p (the first-order rows give F,
+// the quadratic ones 2 B(u, F) for m_eq = B(u, u)); its P row is zero, so P
+// stays a collision invariant.  Because p is computed from P, P - P_eq = 0
+// exactly and j - u = -F/2, so the conserved rows contribute only -F to the
+// momentum rows whatever s_c is.
+// On return f holds f*, and (ux,uy,uz) the velocity of the pre-collision state.
+// ---------------------------------------------------------------------------
+template <int Q, bool FORCE, typename R>
+__device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, R Fy,
+                                        R Fz, R& ux, R& uy, R& uz) {
+  constexpr int NP = Q / 2;
+  R ps[NP], pd[NP];
+  // pair sums and differences
+  [&]<int... I>(std::integer_sequence<int, I...>) {
+    ((ps[I] = f[pair_rep<Q>(I)] + f[opposite<Q>(pair_rep<Q>(I))],
+      pd[I] = f[pair_rep<Q>(I)] - f[opposite<Q>(pair_rep<Q>(I))]),
+     ...);
+  }(std::make_integer_sequence<int, NP>{});
+
+  R m[Q];
+  moments<Q>(ps, pd, m);
+
+  // velocity (Eq. hgl with the force half step) and pressure (Eq. hgl)
+  const R jx = m[2], jy = m[4], jz = m[6];
+  if constexpr (FORCE) {
+    ux = jx + R(0.5) * Fx;
+    uy = jy + R(0.5) * Fy;
+    uz = jz + R(0.5) * Fz;
+  } else {
+    ux = jx;
+    uy = jy;
+    uz = jz;
+  }
+  const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+  const R u2 = uxx + uyy + uzz;
+  constexpr double cs2 = 1.0 / 3.0;
+  constexpr double w0 = Lattice<Q>::w0;
+  const R p = R(cs2 / (1.0 - w0)) * (m[0] - R(w0 / (2.0 * cs2)) * u2);
+
+  // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K
+  R x[Q];
+  x[0] = R(0);
+  if constexpr (FORCE) {
+    x[2] = -Fx * R(1.0 / row_norm<Q>(2));
+    x[4] = -Fy * R(1.0 / row_norm<Q>(4));
+    x[6] = -Fz * R(1.0 / row_norm<Q>(6));
+  } else {
+    x[2] = R(0);
+    x[4] = R(0);
+    x[6] = R(0);
+  }
+  const R uxy = ux * uy, uyz = uy * uz, uxz = ux * uz;
+  const R pxx_eq = R(3) * uxx - u2;  // 3 p_xx
+  const R pww_eq = uyy - uzz;
+  // force terms: derivative along F of the quadratic equilibria
+  R uF = R(0), sxx = R(0), sww = R(0), sxy = R(0), syz = R(0), sxz = R(0);
+  if constexpr (FORCE) {
+    uF = ux * Fx + uy * Fy + uz * Fz;
+    sxx = R(6) * ux * Fx - R(2) * uF;
+    sww = R(2) * (uy * Fy - uz * Fz);
+    sxy = ux * Fy + uy * Fx;
+    syz = uy * Fz + uz * Fy;
+    sxz = ux * Fz + uz * Fx;
+  }
+  const R hq = R(1) - R(0.5) * s.sq;
+  const R hnu = R(1) - R(0.5) * s.snu;
+  if constexpr (Q == 14) {
+    // e_eq = -7p + u^2 (source 2 u.F); q_eq = -7u/3 (source -7F/3)
+    const R he = R(1) - R(0.5) * s.se;
+    R ne = m[1] - (R(-7) * p + u2);
+    R nqx = m[3] + R(7.0 / 3.0) * ux, nqy = m[5] + R(7.0 / 3.0) * uy,
+      nqz = m[7] + R(7.0 / 3.0) * uz;
+    R n8 = m[8] - pxx_eq, n9 = m[9] - pww_eq, n10 = m[10] - uxy,
+      n11 = m[11] - uyz, n12 = m[12] - uxz;
+    x[1] = s.se * ne;
+    x[3] = s.sq * nqx;
+    x[5] = s.sq * nqy;
+    x[7] = s.sq * nqz;
+    x[8] = s.snu * n8;
+    x[9] = s.snu * n9;
+    x[10] = s.snu * n10;
+    x[11] = s.snu * n11;
+    x[12] = s.snu * n12;
+    if constexpr (FORCE) {
+      x[1] -= he * (R(2) * uF);
+      x[3] += hq * (R(7.0 / 3.0) * Fx);
+      x[5] += hq * (R(7.0 / 3.0) * Fy);
+      x[7] += hq * (R(7.0 / 3.0) * Fz);
+      x[8] -= hnu * sxx;
+      x[9] -= hnu * sww;
+      x[10] -= hnu * sxy;
+      x[11] -= hnu * syz;
+      x[12] -= hnu * sxz;
+    }
+    x[13] = s.st * m[13];
+  } else {
+    // e_eq = -p + u^2/2 (source u.F); q_eq = -2u/3 (source -2F/3);
+    // 3pi_xx and pi_ww equilibria are -1/2 of 3p_xx and p_ww.
+    const R he = R(1) - R(0.5) * s.se;
+    const R hpi = R(1) - R(0.5) * s.spi;
+    R ne = m[1] - (-p + R(0.5) * u2);
+    R nqx = m[3] + R(2.0 / 3.0) * ux, nqy = m[5] + R(2.0 / 3.0) * uy,
+      nqz = m[7] + R(2.0 / 3.0) * uz;
+    x[1] = s.se * ne;
+    x[3] = s.sq * nqx;
+    x[5] = s.sq * nqy;
+    x[7] = s.sq * nqz;
+    x[8] = s.snu * (m[8] - pxx_eq);
+    x[9] = s.spi * (m[9] + R(0.5) * pxx_eq);
+    x[10] = s.snu * (m[10] - pww_eq);
+    x[11] = s.spi * (m[11] + R(0.5) * pww_eq);
+    x[12] = s.snu * (m[12] - uxy);
+    x[13] = s.snu * (m[13] - uyz);
+    x[14] = s.snu * (m[14] - uxz);
+    if constexpr (FORCE) {
+      x[1] -= he * uF;
+      x[3] += hq * (R(2.0 / 3.0) * Fx);
+      x[5] += hq * (R(2.0 / 3.0) * Fy);
+      x[7] += hq * (R(2.0 / 3.0) * Fz);
+      x[8] -= hnu * sxx;
+      x[9] += hpi * (R(0.5) * sxx);
+      x[10] -= hnu * sww;
+      x[11] += hpi * (R(0.5) * sww);
+      x[12] -= hnu * sxy;
+      x[13] -= hnu * syz;
+      x[14] -= hnu * sxz;
+    }
+    x[15] = s.st * m[15];
+    x[16] = s.st * m[16];
+    x[17] = s.st * m[17];
+  }
+  // divide by the row norms D_K (T^-1 = T' D^-1); the momentum rows are done
+  [&]<int... K>(std::integer_sequence<int, K...>) {
+    ((K == 0 || K == 2 || K == 4 || K == 6
+          ? void()
+          : void(x[K] = x[K] * R(1.0 / row_norm<Q>(K)))),
+     ...);
+  }(std::make_integer_sequence<int, Q>{});
+
+  back_transform<Q>(x, f);
+}
+
+}  // namespace lbm

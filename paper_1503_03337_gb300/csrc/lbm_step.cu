@@ -1,0 +1,95 @@
+// Single-domain fused step kernels and their dispatch.
+#include <cmath>
+
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <typename R>
+Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
+  Domain<R> o;
+  o.f = d.f;
+  o.nx = d.nx;
+  o.ny = d.ny;
+  o.nz = d.nz;
+  o.N = d.N;
+  for (int k = 0; k < 3; ++k) o.per[k] = d.per[k];
+  o.moving = d.moving;
+  for (int face = 0; face < 6; ++face)
+    for (int k = 0; k < 3; ++k) o.uw[face][k] = R(d.uw[face][k]);
+  o.s.sc = R(d.s[0]);
+  o.s.se = R(d.s[1]);
+  o.s.sq = R(d.s[2]);
+  o.s.snu = R(d.s[3]);
+  o.s.spi = R(d.s[4]);
+  o.s.st = R(d.s[5]);
+  for (int k = 0; k < 3; ++k) o.F[k] = R(F[k]);
+  return o;
+}
+template Domain<double> to_domain<double>(const DomainDesc&, const double*);
+template Domain<float> to_domain<float>(const DomainDesc&, const double*);
+
+void force_at(const DomainDesc& d, int64_t n, double F[3]) {
+  const double c = d.period > 0.0 ? std::cos(2.0 * M_PI * (double)n / d.period) : 1.0;
+  for (int k = 0; k < 3; ++k) F[k] = d.force[k] * c;
+}
+
+BlockShape default_block(int nx, int ny) {
+  int bx = 32;
+  while (bx < nx && bx < 128) bx *= 2;
+  int by = 256 / bx;
+  while (by > 1 && by / 2 >= ny) by /= 2;
+  return {bx, by};
+}
+
+template <int Q, typename S, typename R, bool ODD, bool FORCE>
+__global__ void __launch_bounds__(256) k_step(Domain<R> d) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  update_cell<Q, S, R, ODD, FORCE>(d, static_cast<S*>(d.f), x, y, z);
+}
+
+template <int Q, typename S, typename R>
+static cudaError_t launch_typed(const DomainDesc& dd, int64_t n, BlockShape b,
+                                cudaStream_t st) {
+  double F[3];
+  force_at(dd, n, F);
+  const bool force = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0 || dd.period > 0.0;
+  Domain<R> d = to_domain<R>(dd, F);
+  dim3 block(b.bx, b.by, 1);
+  dim3 grid((dd.nx + b.bx - 1) / b.bx, (dd.ny + b.by - 1) / b.by, dd.nz);
+  const bool odd = (n & 1) != 0;
+  if (odd) {
+    if (force) k_step<Q, S, R, true, true><<<grid, block, 0, st>>>(d);
+    else k_step<Q, S, R, true, false><<<grid, block, 0, st>>>(d);
+  } else {
+    if (force) k_step<Q, S, R, false, true><<<grid, block, 0, st>>>(d);
+    else k_step<Q, S, R, false, false><<<grid, block, 0, st>>>(d);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(const DomainDesc& d, int64_t n, BlockShape b, cudaStream_t st) {
+  if (d.N == 0) return cudaSuccess;
+  if (d.Q == 14) {
+    switch (d.storage) {
+      case LBM_STORAGE_F64: return launch_typed<14, double, double>(d, n, b, st);
+      case LBM_STORAGE_F32: return launch_typed<14, float, float>(d, n, b, st);
+      case LBM_STORAGE_F16: return launch_typed<14, __half, float>(d, n, b, st);
+      case LBM_STORAGE_BF16: return launch_typed<14, __nv_bfloat16, float>(d, n, b, st);
+    }
+  } else {
+    switch (d.storage) {
+      case LBM_STORAGE_F64: return launch_typed<18, double, double>(d, n, b, st);
+      case LBM_STORAGE_F32: return launch_typed<18, float, float>(d, n, b, st);
+      case LBM_STORAGE_F16: return launch_typed<18, __half, float>(d, n, b, st);
+      case LBM_STORAGE_BF16: return launch_typed<18, __nv_bfloat16, float>(d, n, b, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

@@ -1,0 +1,105 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+Bounds: FP64 build <= 1e-12 relative after 1000 steps; FP32 storage
+<= 1e-5 U; FP16 storage <= 1e-3 U (U the case's velocity scale)."""
+import numpy as np
+import pytest
+
+from paper_1503_03337_gb300 import inputs, lbm
+
+from lbm_cases import gpu_run, oracle_run, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1503_03337_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def both(case, steps):
+    return gpu_run(case, steps), oracle_run(case, steps)
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_fp64_duct_1000_steps(Q):
+    """Duct 16x16x32 (x,y walls, z periodic, body force), FP64, 1000 steps."""
+    case = inputs.duct(Q, 16, 32, nu=0.1, u_max=0.02, storage="f64")
+    g, o = both(case, 1000)
+    assert rel_max(g["u"], o["u"]) <= 1e-12
+    assert rel_max(g["f"], o["f"]) <= 1e-12
+    assert rel_max(g["p"], o["p"]) <= 1e-11
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_fp64_cavity_1000_steps(Q):
+    """Lid-driven cube 24^3 at Re 100, FP64, 1000 steps."""
+    case = inputs.cavity(Q, 24, 100.0, storage="f64")
+    g, o = both(case, 1000)
+    assert rel_max(g["u"], o["u"]) <= 1e-12
+    assert rel_max(g["f"], o["f"]) <= 1e-12
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_fp64_pulsatile_odd_steps(Q):
+    """Oscillating force (period 100), ends on an odd step count."""
+    case = inputs.pulsatile(Q, 16, 4, 100, 4.0, 2e-4, storage="f64")
+    g, o = both(case, 251)
+    assert rel_max(g["u"], o["u"]) <= 1e-12
+    assert rel_max(g["f"], o["f"]) <= 1e-12
+
+
+EDGE = [
+    # ragged sizes, mixed faces, several moving walls, random initial state
+    ("ragged", (13, 7, 5), (1, 2, 0, 0, 2, 1)),
+    ("periodic", (6, 5, 4), (0, 0, 0, 0, 0, 0)),
+    ("thin_x_periodic", (1, 6, 5), (0, 0, 1, 2, 1, 1)),
+    ("thin_x_walls", (1, 4, 3), (1, 1, 2, 1, 0, 0)),
+    ("two_cells", (2, 2, 2), (2, 2, 2, 2, 2, 2)),
+    ("long_x", (67, 3, 3), (1, 1, 0, 0, 1, 2)),
+]
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("name,shape,faces", EDGE)
+@pytest.mark.parametrize("steps", (1, 2, 37))
+def test_fp64_edge_cases(Q, name, shape, faces, steps):
+    rng = np.random.default_rng(hash((name, Q)) & 0xffff)
+    uw = rng.normal(size=(6, 3)) * 0.03
+    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
+                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64",
+                       u_ref=0.03)
+    case.init_u, case.init_p = inputs.random_state(case, seed=3)
+    g, o = both(case, steps)
+    assert rel_max(g["f"], o["f"]) <= 1e-12
+    assert rel_max(g["u"], o["u"]) <= 1e-12
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_fp32_cavity(Q):
+    case = inputs.cavity(Q, 32, 400.0, storage="f32")
+    g, o = both(case, 1000)
+    err = np.max(np.abs(g["u"] - o["u"]))
+    assert err <= 1e-5 * case.u_ref, err
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_fp32_duct(Q):
+    case = inputs.duct(Q, 16, 32, nu=0.1, u_max=0.02, storage="f32")
+    g, o = both(case, 1000)
+    err = np.max(np.abs(g["u"] - o["u"]))
+    assert err <= 1e-5 * case.u_ref, err
+
+
+@pytest.mark.parametrize("storage", ("f16",))
+@pytest.mark.parametrize("Q", (14, 18))
+def test_reduced_precision_cavity(Q, storage):
+    case = inputs.cavity(Q, 32, 400.0, storage=storage)
+    g, o = both(case, 1000)
+    err = np.max(np.abs(g["u"] - o["u"]))
+    assert err <= 1e-3 * case.u_ref, err

@@ -1,0 +1,153 @@
+"""Checkpoint/restore, reductions and whole-size checks through the C-ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_03337_gb300 import inputs, lbm
+
+from lbm_cases import gpu_open, oracle_run, oracle_setup, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1503_03337_gb300 import build
+    build.build()
+    lbm.load()
+
+
+@pytest.mark.parametrize("storage", ("f64", "f32", "f16"))
+@pytest.mark.parametrize("split", (300, 301))
+def test_checkpoint_restore_bit_exact(storage, split):
+    """Run 600 steps straight, or `split` steps, save, restore into a fresh
+    domain at that step, and run the rest: identical populations."""
+    case = inputs.duct(18, 12, 8, nu=0.08, storage=storage)
+    n, Q = case, case.Q
+    a = gpu_open(case)
+    b = gpu_open(case)
+    try:
+        lbm.lbm_init_equilibrium(a)
+        lbm.lbm_step(a, split)
+        ck = lbm.read_populations(a, Q, case.nx, case.ny, case.nz)
+        lbm.lbm_step(a, 600 - split)
+        fa = lbm.read_populations(a, Q, case.nx, case.ny, case.nz)
+        lbm.lbm_set_step(b, split)
+        lbm.lbm_write_populations(b, np.ascontiguousarray(ck), 0)
+        assert lbm.lbm_get_step(b) == split
+        fb0 = lbm.read_populations(b, Q, case.nx, case.ny, case.nz)
+        np.testing.assert_array_equal(fb0, ck)
+        lbm.lbm_step(b, 600 - split)
+        fb = lbm.read_populations(b, Q, case.nx, case.ny, case.nz)
+    finally:
+        lbm.lbm_destroy(a)
+        lbm.lbm_destroy(b)
+    np.testing.assert_array_equal(fa, fb)
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_reductions_match_fields(Q):
+    """FP64 reductions (residual numerators/denominators, mass, flux, max)
+    against sums of the read-back oracle fields."""
+    case = inputs.duct(Q, 10, 6, nu=0.1, storage="f64")
+    case.force = (0.0, 0.0, 3e-5)
+    h = gpu_open(case)
+    try:
+        lbm.lbm_init_equilibrium(h)
+        lbm.lbm_step(h, 40)
+        s0 = lbm.lbm_reductions(h)
+        assert s0.prev_step == -1 and s0.step == 40
+        lbm.lbm_step(h, 7)
+        s1 = lbm.lbm_reductions(h)
+        assert s1.prev_step == 40 and s1.step == 47
+    finally:
+        lbm.lbm_destroy(h)
+    u40 = oracle_run(case, 40)
+    u47 = oracle_run(case, 47)
+    ua, ub = u40["u"], u47["u"]
+    Pb = u47["f"].sum()
+    for k in range(3):
+        assert abs(s1.sum_abs_du[k] - np.abs(ub[k] - ua[k]).sum()) <= 1e-12 * max(1e-300, np.abs(ub[k]).sum())
+        assert abs(s1.sum_abs_u[k] - np.abs(ub[k]).sum()) <= 1e-12 * max(1e-300, np.abs(ub[k]).sum())
+        assert abs(s1.sum_abs_u_prev[k] - np.abs(ua[k]).sum()) <= 1e-12 * max(1e-300, np.abs(ua[k]).sum())
+        assert abs(s1.sum_u[k] - ub[k].sum()) <= 1e-12 * max(1e-300, np.abs(ub[k]).sum())
+    assert abs(s1.sum_P - Pb) <= 1e-12 * max(1.0, abs(Pb))
+    assert abs(s1.max_abs_u - np.abs(ub).max()) <= 1e-15
+    assert s1.nonfinite == 0
+    r = lbm.residual_periodic(s1, 2)
+    assert abs(r - np.abs(ub[2] - ua[2]).sum() / np.abs(ub[2]).sum()) < 1e-12
+
+
+def test_residual_cadence_in_step():
+    case = inputs.cavity(18, 16, 100.0, storage="f32")
+    h = gpu_open(case, residual_interval=50)
+    try:
+        lbm.lbm_init_equilibrium(h)
+        lbm.lbm_step(h, 120)
+        s = lbm.lbm_read_stats(h)
+        assert s.step == 100 and s.prev_step == 50
+        assert 0.0 < lbm.residual_cavity(s) < 1.0
+    finally:
+        lbm.lbm_destroy(h)
+
+
+def test_unstable_run_reported():
+    """A run driven far beyond stability turns non-finite; the reduction
+    notices and lbm_step refuses to continue (failure made on the host side
+    of the physics, no device fault)."""
+    case = inputs.cavity(14, 12, 1e6, U=0.5, storage="f32")
+    h = gpu_open(case)
+    try:
+        lbm.lbm_set_params(h, s_nu=1.999, s_e=1.999, s_q=1.999, s_t=1.999, s_c=1.0,
+                           residual_interval=100)
+        lbm.lbm_init_equilibrium(h)
+        with pytest.raises(lbm.LBMError) as ei:
+            for _ in range(200):
+                lbm.lbm_step(h, 100)
+                lbm.lbm_read_stats(h)
+        assert ei.value.code == lbm.LBM_EUNSTABLE
+        lbm.lbm_init_equilibrium(h)  # clears the condition
+        lbm.lbm_step(h, 1)
+    finally:
+        lbm.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_full_size_single_steps(Q):
+    """128^3 FP32 cavity in the benchmark's launch configuration: from a
+    seeded random state, each of an even and an odd step matches one oracle
+    step taken from the GPU's own read-back populations."""
+    case = inputs.cavity(Q, 128, 1000.0, storage="f32")
+    case.init_u, case.init_p = inputs.random_state(case, seed=7, u_scale=0.03, p_scale=0.01)
+    g, prm = oracle_setup(case)
+    h = gpu_open(case)
+    try:
+        lbm.lbm_init_equilibrium(h, np.ascontiguousarray(case.init_u), np.ascontiguousarray(case.init_p), 0)
+        lbm.lbm_step(h, 2)
+        for n in (2, 3):
+            f0 = lbm.read_populations(h, Q, case.nx, case.ny, case.nz)
+            lbm.lbm_step(h, 1)
+            f1 = lbm.read_populations(h, Q, case.nx, case.ny, case.nz)
+            ref = oracle.step(g, prm, n, f0, nthreads=16)
+            err = np.max(np.abs(f1 - ref))
+            assert err <= 2e-6 * np.max(np.abs(ref)), (n, err)
+    finally:
+        lbm.lbm_destroy(h)
+
+
+def test_full_size_mass_conserved():
+    """sum P is conserved by the step and the lid (property at any size)."""
+    case = inputs.cavity(18, 128, 1000.0, storage="f64")
+    h = gpu_open(case)
+    try:
+        u, p = inputs.random_state(case, seed=9)
+        lbm.lbm_init_equilibrium(h, u, p, 0)
+        s0 = lbm.lbm_reductions(h)
+        lbm.lbm_step(h, 21)
+        s1 = lbm.lbm_reductions(h)
+    finally:
+        lbm.lbm_destroy(h)
+    assert abs(s1.sum_P - s0.sum_P) <= 1e-12 * abs(s0.sum_P) + 1e-9
