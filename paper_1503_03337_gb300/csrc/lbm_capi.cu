@@ -109,12 +109,11 @@ int apply_geometry(lbm_handle* h, const lbm_geom* g) {
   if (!finite_all(&g->u_wall[0][0], 18)) return fail(LBM_EINVAL, "wall velocity not finite");
   h->geom = *g;
   h->d.moving = 0;
-  for (int f = 0; f < 6; ++f)
-    for (int k = 0; k < 3; ++k) {
-      const double v = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
-      h->d.uw[f][k] = v;
-      if (v != 0.0) h->d.moving = 1;
-    }
+  for (int f = 0; f < 6; ++f) {
+    if (g->face[f] == LBM_MOVING_WALL) h->d.moving |= 1 << f;
+    for (int k = 0; k < 3; ++k)
+      h->d.uw[f][k] = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
+  }
   return LBM_OK;
 }
 

@@ -27,7 +27,7 @@ struct Domain {
   int nx, ny, nz;
   int64_t N;         // nx*ny*nz
   int per[3];        // axis is periodic
-  int moving;        // some face is a moving wall
+  int moving;        // bit f set: face f is a moving wall
   R uw[6][3];        // velocity of each face (zero unless MOVING_WALL)
   Rates<R> s;
   R F[3];            // body force at the step's time level t_n
@@ -37,7 +37,7 @@ struct Domain {
 // cell index if it is a fluid node (after periodic wrap); otherwise false
 // and, in `beyond`, the faces (bit f = face f) the ghost node lies beyond.
 template <typename R>
-__device__ __forceinline__ bool resolve(const Domain<R>& d, int x, int y, int z,
+__host__ __device__ __forceinline__ bool resolve(const Domain<R>& d, int x, int y, int z,
                                         int dx, int dy, int dz, int64_t& j,
                                         int& beyond) {
   beyond = 0;
@@ -61,23 +61,20 @@ __device__ __forceinline__ bool resolve(const Domain<R>& d, int x, int y, int z,
 // moving face in x-, x+, y-, y+, z-, z+ order wins (edge and corner ghosts of
 // a lid layer belong to the lid).
 template <typename R>
-__device__ __forceinline__ R ghost_dot(const Domain<R>& d, int beyond, int cx,
+__host__ __device__ __forceinline__ R ghost_dot(const Domain<R>& d, int beyond, int cx,
                                        int cy, int cz) {
-  if (!d.moving) return R(0);
+  const int hit = beyond & d.moving;
+  if (!hit) return R(0);
 #pragma unroll
-  for (int face = 0; face < 6; ++face) {
-    if ((beyond >> face) & 1) {
-      const R ux = d.uw[face][0], uy = d.uw[face][1], uz = d.uw[face][2];
-      if (ux != R(0) || uy != R(0) || uz != R(0))
-        return R(cx) * ux + R(cy) * uy + R(cz) * uz;
-    }
-  }
+  for (int face = 0; face < 6; ++face)
+    if ((hit >> face) & 1)
+      return R(cx) * d.uw[face][0] + R(cy) * d.uw[face][1] + R(cz) * d.uw[face][2];
   return R(0);
 }
 
 // Pre-collision populations f^n of cell (x,y,z) (index i) into fv.
 template <int Q, typename S, typename R, bool ODD>
-__device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
+__host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
                                        int x, int y, int z, int64_t i,
                                        bool interior, R* fv) {
   const int64_t N = d.N;
@@ -116,7 +113,7 @@ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__
 
 // Post-collision populations f* of cell (x,y,z) from fv into storage.
 template <int Q, typename S, typename R, bool ODD>
-__device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
+__host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
                                         int x, int y, int z, int64_t i,
                                         bool interior, const R* fv) {
   const int64_t N = d.N;
@@ -155,13 +152,13 @@ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
 }
 
 template <typename R>
-__device__ __forceinline__ bool is_interior(const Domain<R>& d, int x, int y, int z) {
+__host__ __device__ __forceinline__ bool is_interior(const Domain<R>& d, int x, int y, int z) {
   return x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
 }
 
 // The whole fused update of one cell: gather (stream), collide, scatter.
 template <int Q, typename S, typename R, bool ODD, bool FORCE>
-__device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ f,
+__host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ f,
                                             int x, int y, int z) {
   const int64_t i = (int64_t)x + (int64_t)d.nx * ((int64_t)y + (int64_t)d.ny * z);
   const bool interior = ODD ? is_interior(d, x, y, z) : true;
@@ -175,7 +172,7 @@ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ 
 // Inverse of gather: put canonical pre-collision values fv of cell (x,y,z)
 // where the current parity keeps them (checkpoint restore / init).
 template <int Q, typename S, typename R, bool ODD>
-__device__ __forceinline__ void put_canonical(const Domain<R>& d, S* __restrict__ f,
+__host__ __device__ __forceinline__ void put_canonical(const Domain<R>& d, S* __restrict__ f,
                                               int x, int y, int z, int64_t i,
                                               const R* fv) {
   const int64_t N = d.N;

@@ -144,9 +144,12 @@ __host__ __device__ constexpr int phi(int k, int a) {
   return 0;
 }
 
+// Row k is even if T_k,abar = T_k,a for every direction (else odd).
 template <int Q>
 __host__ __device__ constexpr bool row_even(int k) {
-  return phi<Q>(k, 0) == phi<Q>(k, 1);  // c_1 and c_2 are opposite
+  for (int a = 0; a < Q; ++a)
+    if (phi<Q>(k, a) != phi<Q>(k, opposite<Q>(a))) return false;
+  return true;
 }
 
 template <int Q>
@@ -156,6 +159,35 @@ __host__ __device__ constexpr int row_norm(int k) {
   return s;
 }
 
+// Compile-time checks of the basis: every row has a definite parity under
+// c -> -c, rows are mutually orthogonal (so T^-1 = T' D^-1), and the
+// conserved rows are P = sum f and j = sum c f.
+template <int Q>
+__host__ __device__ constexpr bool basis_ok() {
+  for (int a = 0; a < Q; ++a)
+    if (opposite<Q>(a) < 0 || opposite<Q>(opposite<Q>(a)) != a) return false;
+  for (int k = 0; k < Q; ++k) {
+    const bool even = row_even<Q>(k);
+    for (int a = 0; a < Q; ++a) {
+      const int t = phi<Q>(k, a), tb = phi<Q>(k, opposite<Q>(a));
+      if (even ? (t != tb) : (t != -tb)) return false;
+    }
+    for (int l = 0; l < k; ++l) {
+      int dot = 0;
+      for (int a = 0; a < Q; ++a) dot += phi<Q>(k, a) * phi<Q>(l, a);
+      if (dot != 0) return false;
+    }
+    if (row_norm<Q>(k) <= 0) return false;
+  }
+  for (int a = 0; a < Q; ++a)
+    if (phi<Q>(0, a) != 1 || phi<Q>(2, a) != Lattice<Q>::c(a, 0) ||
+        phi<Q>(4, a) != Lattice<Q>::c(a, 1) || phi<Q>(6, a) != Lattice<Q>::c(a, 2))
+      return false;
+  return true;
+}
+static_assert(basis_ok<14>(), "iD3Q14 moment basis is inconsistent");
+static_assert(basis_ok<18>(), "iD3Q18 moment basis is inconsistent");
+
 // ---------------------------------------------------------------------------
 // Storage codec: populations live in S, arithmetic runs in R.
 // ---------------------------------------------------------------------------
@@ -163,31 +195,31 @@ template <typename S, typename R>
 struct Codec;
 template <typename R>
 struct Codec<double, R> {
-  __device__ static R load(const double* p) { return R(__ldg(p)); }
-  __device__ static R load_nc(const double* p) { return R(*p); }
-  __device__ static void store(double* p, R v) { *p = double(v); }
+  __host__ __device__ static R load(const double* p) {
+#ifdef __CUDA_ARCH__
+    return R(__ldg(p));
+#else
+    return R(*p);
+#endif
+  }
+  __host__ __device__ static void store(double* p, R v) { *p = double(v); }
 };
 template <typename R>
 struct Codec<float, R> {
-  __device__ static R load(const float* p) { return R(*p); }
-  __device__ static R load_nc(const float* p) { return R(*p); }
-  __device__ static void store(float* p, R v) { *p = float(v); }
+  __host__ __device__ static R load(const float* p) { return R(*p); }
+  __host__ __device__ static void store(float* p, R v) { *p = float(v); }
 };
 template <typename R>
 struct Codec<__half, R> {
-  __device__ static R load(const __half* p) { return R(__half2float(*p)); }
-  __device__ static R load_nc(const __half* p) { return R(__half2float(*p)); }
-  __device__ static void store(__half* p, R v) { *p = __float2half_rn(float(v)); }
+  __host__ __device__ static R load(const __half* p) { return R(__half2float(*p)); }
+  __host__ __device__ static void store(__half* p, R v) { *p = __float2half_rn(float(v)); }
 };
 template <typename R>
 struct Codec<__nv_bfloat16, R> {
-  __device__ static R load(const __nv_bfloat16* p) {
+  __host__ __device__ static R load(const __nv_bfloat16* p) {
     return R(__bfloat162float(*p));
   }
-  __device__ static R load_nc(const __nv_bfloat16* p) {
-    return R(__bfloat162float(*p));
-  }
-  __device__ static void store(__nv_bfloat16* p, R v) {
+  __host__ __device__ static void store(__nv_bfloat16* p, R v) {
     *p = __float2bfloat16_rn(float(v));
   }
 };
@@ -196,21 +228,21 @@ struct Codec<__nv_bfloat16, R> {
 // Unrolled transforms over pairs
 // ---------------------------------------------------------------------------
 template <int C, typename R>
-__device__ __forceinline__ R term_first(R x) {
+__host__ __device__ __forceinline__ R term_first(R x) {
   if constexpr (C == 1) return x;
   else if constexpr (C == -1) return -x;
   else return R(C) * x;
 }
 template <int C, typename R>
-__device__ __forceinline__ R term_add(R acc, R x) {
+__host__ __device__ __forceinline__ R term_add(R acc, R x) {
   if constexpr (C == 1) return acc + x;
   else if constexpr (C == -1) return acc - x;
-  else return fma(R(C), x, acc);
+  else return acc + R(C) * x;
 }
 
 // m_K = sum_i phi_K(rep_i) v_i, with v = pair sums (even K) or differences.
 template <int Q, int K, int I, bool STARTED, typename R>
-__device__ __forceinline__ R row_sum(R acc, const R* v) {
+__host__ __device__ __forceinline__ R row_sum(R acc, const R* v) {
   if constexpr (I == Q / 2) {
     if constexpr (STARTED) return acc;
     else return R(0);
@@ -226,7 +258,7 @@ __device__ __forceinline__ R row_sum(R acc, const R* v) {
 // Back-transform share of pair I: sum over rows K of the given parity of
 // phi_K(rep_I) * x_K.
 template <int Q, int I, int K, bool EVEN, bool STARTED, typename R>
-__device__ __forceinline__ R col_sum(R acc, const R* x) {
+__host__ __device__ __forceinline__ R col_sum(R acc, const R* x) {
   if constexpr (K == Q) {
     if constexpr (STARTED) return acc;
     else return R(0);
@@ -240,7 +272,7 @@ __device__ __forceinline__ R col_sum(R acc, const R* x) {
 }
 
 template <int Q, int K = 0, typename R>
-__device__ __forceinline__ void moments(const R* s, const R* d, R* m) {
+__host__ __device__ __forceinline__ void moments(const R* s, const R* d, R* m) {
   if constexpr (K < Q) {
     if constexpr (row_even<Q>(K)) m[K] = row_sum<Q, K, 0, false>(R(0), s);
     else m[K] = row_sum<Q, K, 0, false>(R(0), d);
@@ -250,7 +282,7 @@ __device__ __forceinline__ void moments(const R* s, const R* d, R* m) {
 
 // f*_rep = f_rep - (E + O), f*_partner = f_partner - (E - O)
 template <int Q, int I = 0, typename R>
-__device__ __forceinline__ void back_transform(const R* x, R* f) {
+__host__ __device__ __forceinline__ void back_transform(const R* x, R* f) {
   if constexpr (I < Q / 2) {
     constexpr int a = pair_rep<Q>(I);
     constexpr int b = opposite<Q>(a);
@@ -279,7 +311,7 @@ struct Rates {
 // On return f holds f*, and (ux,uy,uz) the velocity of the pre-collision state.
 // ---------------------------------------------------------------------------
 template <int Q, bool FORCE, typename R>
-__device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, R Fy,
+__host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, R Fy,
                                         R Fz, R& ux, R& uy, R& uz) {
   constexpr int NP = Q / 2;
   R ps[NP], pd[NP];

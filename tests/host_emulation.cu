@@ -1,0 +1,103 @@
+// Host build of the CUDA step's per-cell code (gather, collide, scatter) for
+// CPU tests: cells are updated one after another, which gives the same result
+// as the parallel kernel because every cell reads and writes only its own
+// set of 2Q slots.  Test infrastructure only.
+#include <cstdint>
+#include <cmath>
+
+#include "../paper_1503_03337_gb300/csrc/lbm_kernels.cuh"
+
+using namespace lbm;
+
+template <int Q, typename S, typename R>
+static void step_typed(void* f, int nx, int ny, int nz, const int* per, int moving,
+                       const double* uw, const double* s, const double* F, int64_t n) {
+  Domain<R> d;
+  d.f = f;
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.N = (int64_t)nx * ny * nz;
+  d.moving = moving;
+  for (int k = 0; k < 3; ++k) d.per[k] = per[k];
+  for (int face = 0; face < 6; ++face)
+    for (int k = 0; k < 3; ++k) d.uw[face][k] = R(uw[3 * face + k]);
+  d.s.sc = R(s[0]); d.s.se = R(s[1]); d.s.sq = R(s[2]);
+  d.s.snu = R(s[3]); d.s.spi = R(s[4]); d.s.st = R(s[5]);
+  for (int k = 0; k < 3; ++k) d.F[k] = R(F[k]);
+  const bool force = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        if (n & 1) {
+          if (force) update_cell<Q, S, R, true, true>(d, static_cast<S*>(f), x, y, z);
+          else update_cell<Q, S, R, true, false>(d, static_cast<S*>(f), x, y, z);
+        } else {
+          if (force) update_cell<Q, S, R, false, true>(d, static_cast<S*>(f), x, y, z);
+          else update_cell<Q, S, R, false, false>(d, static_cast<S*>(f), x, y, z);
+        }
+      }
+}
+
+template <int Q, typename S, typename R, bool ODD>
+static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int moving,
+                            const double* uw, double* out, int to_storage) {
+  Domain<R> d{};
+  d.f = f;
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.N = (int64_t)nx * ny * nz;
+  d.moving = moving;
+  for (int k = 0; k < 3; ++k) d.per[k] = per[k];
+  for (int face = 0; face < 6; ++face)
+    for (int k = 0; k < 3; ++k) d.uw[face][k] = R(uw[3 * face + k]);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int64_t i = x + (int64_t)nx * (y + (int64_t)ny * z);
+        R fv[Q];
+        if (to_storage) {
+          for (int a = 0; a < Q; ++a) fv[a] = R(out[a * d.N + i]);
+          put_canonical<Q, S, R, ODD>(d, static_cast<S*>(f), x, y, z, i, fv);
+        } else {
+          gather<Q, S, R, ODD>(d, static_cast<const S*>(f), x, y, z, i,
+                               ODD ? is_interior(d, x, y, z) : true, fv);
+          for (int a = 0; a < Q; ++a) out[a * d.N + i] = double(fv[a]);
+        }
+      }
+}
+
+extern "C" {
+// storage: 0 double, 1 float
+int emu_step(int Q, int storage, void* f, int nx, int ny, int nz, const int* per, int moving,
+             const double* uw, const double* s, const double* F, int64_t n) {
+  if (Q == 14 && storage == 0) step_typed<14, double, double>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else if (Q == 18 && storage == 0) step_typed<18, double, double>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else if (Q == 14 && storage == 1) step_typed<14, float, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else if (Q == 18 && storage == 1) step_typed<18, float, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else return -1;
+  return 0;
+}
+
+// canonical f (FP64) <-> storage layout of parity n (double storage only)
+int emu_canonical(int Q, void* f, int nx, int ny, int nz, const int* per, int moving,
+                  const double* uw, double* canon, int64_t n, int to_storage) {
+  const bool odd = n & 1;
+  if (Q == 14) {
+    if (odd) canonical_typed<14, double, double, true>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+    else canonical_typed<14, double, double, false>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+  } else if (Q == 18) {
+    if (odd) canonical_typed<18, double, double, true>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+    else canonical_typed<18, double, double, false>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+  } else {
+    return -1;
+  }
+  return 0;
+}
+
+int emu_collide(int Q, const double* s, double* f, const double* F) {
+  Rates<double> r{s[0], s[1], s[2], s[3], s[4], s[5]};
+  double ux, uy, uz;
+  if (Q == 14) collide<14, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
+  else if (Q == 18) collide<18, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
+  else return -1;
+  return 0;
+}
+}

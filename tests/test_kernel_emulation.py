@@ -1,0 +1,140 @@
+"""CPU checks of the CUDA step's own per-cell code, compiled for the host
+(tests/host_emulation.cu), against the FP64 oracle.  They catch arithmetic
+and indexing mistakes in the kernel source before it reaches a GPU; the GPU
+parity tests then check the device build itself."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_03337_gb300 import build as pkg_build, inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "host_emulation.cu")
+
+
+@pytest.fixture(scope="module")
+def emu():
+    out_dir = os.path.join(ROOT, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "libhost_emulation.so")
+    deps = [SRC] + [os.path.join(ROOT, "paper_1503_03337_gb300", "csrc", f)
+                    for f in ("lbm_model.cuh", "lbm_kernels.cuh")]
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(map(os.path.getmtime, deps)):
+        tmp = lib + ".tmp%d" % os.getpid()
+        subprocess.run([pkg_build.nvcc(), "-std=c++20", "-O2", "--expt-relaxed-constexpr",
+                        "-Xcompiler", "-fPIC", "-shared", "-x", "cu", SRC, "-o", tmp], check=True)
+        os.replace(tmp, lib)
+    L = ctypes.CDLL(lib)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    L.emu_step.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_int, ip, ctypes.c_int, dp, dp, dp, ctypes.c_int64]
+    L.emu_canonical.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip,
+                                ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int]
+    L.emu_collide.argtypes = [ctypes.c_int, dp, dp, dp]
+    return L
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_collide_matches_oracle(emu, Q):
+    rng = np.random.default_rng(21)
+    for _ in range(50):
+        r = rng.uniform(0.3, 1.9, size=6)
+        f = rng.normal(size=Q) * 0.05 + 0.02
+        F = rng.normal(size=3) * 1e-3
+        got = f.copy()
+        assert emu.emu_collide(Q, _d(r), _d(got), _d(F)) == 0
+        ref = oracle.collide(Q, oracle.Rates(*r), f, F)
+        np.testing.assert_allclose(got, ref, atol=2e-16, rtol=1e-14)
+
+
+class EmuDomain:
+    def __init__(self, emu, case):
+        self.emu, self.case = emu, case
+        self.per = np.array([int(case.faces[2 * k] == inputs.PERIODIC) for k in range(3)],
+                            dtype=np.int32)
+        self.moving = sum(1 << f for f in range(6) if case.faces[f] == inputs.MOVING_WALL)
+        self.uw = np.ascontiguousarray(
+            np.where(np.array(case.faces)[:, None] == inputs.MOVING_WALL, case.u_wall, 0.0))
+        s = oracle.rates(case.Q, case.s_nu)
+        self.s = np.array([s.sc, s.se, s.sq, s.snu, s.spi, s.st])
+        self.A = np.zeros((case.Q, case.nz, case.ny, case.nx))
+        self.n = 0
+
+    def _ip(self):
+        return self.per.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+    def put(self, f, n):
+        self.n = n
+        c = self.case
+        canon = np.ascontiguousarray(f, dtype=np.float64)
+        assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
+                                      self.moving, _d(self.uw), _d(canon), n, 1) == 0
+
+    def get(self):
+        c = self.case
+        out = np.zeros_like(self.A)
+        assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
+                                      self.moving, _d(self.uw), _d(out), self.n, 0) == 0
+        return out
+
+    def step(self, k):
+        c = self.case
+        for _ in range(k):
+            amp = np.cos(2 * np.pi * self.n / c.period) if c.period > 0 else 1.0
+            F = np.array(c.force, dtype=np.float64) * amp
+            assert self.emu.emu_step(c.Q, 0, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
+                                     self.moving, _d(self.uw), _d(self.s), _d(F), self.n) == 0
+            self.n += 1
+
+
+EDGE = [
+    ("ragged", (13, 7, 5), (1, 2, 0, 0, 2, 1)),
+    ("periodic", (6, 5, 4), (0, 0, 0, 0, 0, 0)),
+    ("thin_x_periodic", (1, 6, 5), (0, 0, 1, 2, 1, 1)),
+    ("thin_x_walls", (1, 4, 3), (1, 1, 2, 1, 0, 0)),
+    ("two_cells", (2, 2, 2), (2, 2, 2, 2, 2, 2)),
+    ("lid", (5, 6, 4), (1, 1, 1, 2, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("name,shape,faces", EDGE)
+def test_step_matches_oracle(emu, Q, name, shape, faces):
+    rng = np.random.default_rng(5)
+    uw = rng.normal(size=(6, 3)) * 0.03
+    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
+                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64")
+    g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw)
+    prm = oracle.make_params(oracle.rates(Q, case.s_nu), force=case.force, period=case.period)
+    u0, p0 = inputs.random_state(case, seed=2)
+    f0 = oracle.init_equilibrium(g, u0, p0)
+    d = EmuDomain(emu, case)
+    d.put(f0, 0)
+    np.testing.assert_array_equal(d.get(), f0)
+    f = f0
+    for k in (1, 1, 5, 30):
+        d.step(k)
+        f = oracle.run(g, prm, f, d.n - k, k, nthreads=1)
+        ref = f
+        got = d.get()
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (d.n,)
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_restore_at_odd_parity(emu, Q):
+    """Canonical populations written at an odd step read back unchanged."""
+    faces = (1, 2, 0, 0, 2, 1)
+    case = inputs.Case("r", Q, 5, 4, 3, faces, np.full((6, 3), 0.01), nu=0.1)
+    d = EmuDomain(emu, case)
+    f = inputs.random_populations(Q, (3, 4, 5), seed=1)
+    d.put(f, 7)
+    np.testing.assert_allclose(d.get(), f, atol=1e-17)
