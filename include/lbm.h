@@ -68,6 +68,13 @@ enum lbm_field_bits {
 
 enum lbm_dtype { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 };
 
+/* Rounding of FP16/BF16 stores (ignored for FP32/FP64 storage).  Nearest
+ * loses every per-step change below half a storage ulp in the same
+ * direction; stochastic rounding (a counter-based hash of cell, direction
+ * and step picks up or down with probability equal to the discarded
+ * fraction) makes each store unbiased and is reproducible. */
+enum lbm_rounding { LBM_ROUND_NEAREST = 0, LBM_ROUND_STOCHASTIC = 1 };
+
 /* ---- descriptors -------------------------------------------------------- */
 typedef struct lbm_desc {
   int32_t Q;       /* 14 (Sec. 3) or 18 (App. B)                           */
@@ -99,7 +106,7 @@ typedef struct lbm_params {
   double p_ref;
   int32_t residual_interval; /* > 0: lbm_step runs the FP64 reductions every
                                 that many steps (stats via lbm_read_stats) */
-  int32_t reserved;
+  int32_t rounding;          /* enum lbm_rounding */
 } lbm_params;
 
 /* FP64 reductions over all nodes at step `step`, against the velocity

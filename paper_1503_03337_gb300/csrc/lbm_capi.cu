@@ -88,12 +88,15 @@ int apply_params(lbm_handle* h, const lbm_params* p) {
       !std::isfinite(p->p_ref))
     return fail(LBM_EINVAL, "force, period and p_ref must be finite");
   if (p->residual_interval < 0) return fail(LBM_EINVAL, "residual_interval < 0");
+  if (p->rounding != LBM_ROUND_NEAREST && p->rounding != LBM_ROUND_STOCHASTIC)
+    return fail(LBM_EINVAL, "unknown rounding mode");
   if (h->d.Q == 14) s[4] = s[1];
   h->params = *p;
   for (int k = 0; k < 6; ++k) h->d.s[k] = s[k];
   for (int k = 0; k < 3; ++k) h->d.force[k] = p->force[k];
   h->d.period = p->force_period;
   h->d.p_ref = p->p_ref;
+  h->d.rounding = p->rounding;
   return LBM_OK;
 }
 

@@ -59,8 +59,7 @@ __global__ void k_read(Domain<double> d, FieldArgs a) {
     y = (int)(r % d.ny);
     z = (int)(r / d.ny);
     double fv[Q];
-    gather<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, i,
-                              ODD ? is_interior(d, x, y, z) : true, fv);
+    get_canonical<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, fv);
     for (int b = 0; b < Q; ++b) fv[b] += 3.0 * Lattice<Q>::w(b) * a.p_ref;
     double P, u[3];
     macro<Q>(fv, a.F, P, u);
@@ -94,7 +93,7 @@ __global__ void k_write(Domain<double> d, FieldArgs a) {
     double fv[Q];
     for (int b = 0; b < Q; ++b)
       fv[b] = a.src[b * N + i] - 3.0 * Lattice<Q>::w(b) * a.p_ref;
-    put_canonical<Q, S, double, ODD>(d, static_cast<S*>(d.f), x, y, z, i, fv);
+    put_canonical<Q, S, double, ODD>(d, static_cast<S*>(d.f), x, y, z, fv);
   }
 }
 
@@ -119,7 +118,7 @@ __global__ void k_init(Domain<double> d, FieldArgs a) {
                         Lattice<Q>::c(b, 2) * u[2];
       fv[b] = Lattice<Q>::w(b) * (3.0 * p + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
     }
-    put_canonical<Q, S, double, false>(d, static_cast<S*>(d.f), x, y, z, i, fv);
+    put_canonical<Q, S, double, false>(d, static_cast<S*>(d.f), x, y, z, fv);
   }
 }
 
@@ -169,8 +168,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(Domain<double> d, Red
     const int64_t r = i / d.nx;
     const int y = (int)(r % d.ny), z = (int)(r / d.ny);
     double fv[Q];
-    gather<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, i,
-                              ODD ? is_interior(d, x, y, z) : true, fv);
+    get_canonical<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, fv);
     double P, u[3];
     macro<Q>(fv, a.F, P, u);
     const bool finite = isfinite(P) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);

@@ -30,6 +30,7 @@ struct DomainDesc {
   double force[3];
   double period;
   double p_ref;
+  int rounding;  // enum lbm_rounding
 };
 
 struct BlockShape {

@@ -31,31 +31,8 @@ struct Domain {
   R uw[6][3];        // velocity of each face (zero unless MOVING_WALL)
   Rates<R> s;
   R F[3];            // body force at the step's time level t_n
+  uint32_t key;      // per-step key of the stochastic-rounding hash
 };
-
-// Node (x,y,z)+(dx,dy,dz) with dx,dy,dz in {-1,0,1}.  Returns true and its
-// cell index if it is a fluid node (after periodic wrap); otherwise false
-// and, in `beyond`, the faces (bit f = face f) the ghost node lies beyond.
-template <typename R>
-__host__ __device__ __forceinline__ bool resolve(const Domain<R>& d, int x, int y, int z,
-                                        int dx, int dy, int dz, int64_t& j,
-                                        int& beyond) {
-  beyond = 0;
-  int v[3] = {x + dx, y + dy, z + dz};
-  const int n[3] = {d.nx, d.ny, d.nz};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    if (v[k] < 0) {
-      if (d.per[k]) v[k] += n[k];
-      else beyond |= 1 << (2 * k);
-    } else if (v[k] >= n[k]) {
-      if (d.per[k]) v[k] -= n[k];
-      else beyond |= 1 << (2 * k + 1);
-    }
-  }
-  j = (int64_t)v[0] + (int64_t)d.nx * ((int64_t)v[1] + (int64_t)d.ny * v[2]);
-  return beyond == 0;
-}
 
 // c . u_wall for a ghost node beyond the faces in `beyond`: the first
 // moving face in x-, x+, y-, y+, z-, z+ order wins (edge and corner ghosts of
@@ -72,131 +49,253 @@ __host__ __device__ __forceinline__ R ghost_dot(const Domain<R>& d, int beyond, 
   return R(0);
 }
 
-// Pre-collision populations f^n of cell (x,y,z) (index i) into fv.
+// Neighbour addressing of one cell for the odd (neighbour-touching) step.
+// Along each axis: the index offset to the -1 / +1 neighbour (periodic wrap
+// applied; 0 if that neighbour is a ghost node) and whether it is a ghost
+// node beyond a wall.  Computed once per cell; each link then costs a few
+// integer adds and one select, with no divergent branch.
+struct Links {
+  int om[3], op[3];
+  bool gm[3], gp[3];
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ void axis_links(int v, int n, int stride, int per,
+                                                    int& om, int& op, bool& gm, bool& gp) {
+  const bool lo = v == 0, hi = v == n - 1;
+  om = !lo ? -stride : (per ? (n - 1) * stride : 0);
+  op = !hi ? stride : (per ? -(n - 1) * stride : 0);
+  gm = lo && !per;
+  gp = hi && !per;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ Links make_links(const Domain<R>& d, int x, int y, int z) {
+  Links L;
+  const int sy = d.nx, sz = d.nx * d.ny;
+  axis_links<R>(x, d.nx, 1, d.per[0], L.om[0], L.op[0], L.gm[0], L.gp[0]);
+  axis_links<R>(y, d.ny, sy, d.per[1], L.om[1], L.op[1], L.gm[1], L.gp[1]);
+  axis_links<R>(z, d.nz, sz, d.per[2], L.om[2], L.op[2], L.gm[2], L.gp[2]);
+  return L;
+}
+
+// Links of a cell whose y and z neighbours are all fluid and unwrapped (the
+// bulk of a box): only x needs the select.
+template <typename R>
+__host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x) {
+  Links L;
+  const int sy = d.nx, sz = d.nx * d.ny;
+  axis_links<R>(x, d.nx, 1, d.per[0], L.om[0], L.op[0], L.gm[0], L.gp[0]);
+  L.om[1] = -sy;
+  L.op[1] = sy;
+  L.om[2] = -sz;
+  L.op[2] = sz;
+  L.gm[1] = L.gp[1] = L.gm[2] = L.gp[2] = false;
+  return L;
+}
+
+// Offset and ghost flag of the node x + s*c_A (s = -1: pull source, +1:
+// push target).
+template <int Q, int A, int SIGN>
+__host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool& ghost) {
+  off = 0;
+  ghost = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int c = SIGN * Lattice<Q>::c(A, k);
+    if (c < 0) {
+      off += L.om[k];
+      ghost = ghost || L.gm[k];
+    } else if (c > 0) {
+      off += L.op[k];
+      ghost = ghost || L.gp[k];
+    }
+  }
+}
+
+// The ghost node beyond the faces this link crosses: bit mask of those faces.
+template <int Q, int A, int SIGN>
+__host__ __device__ __forceinline__ int link_faces(const Links& L) {
+  int m = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int c = SIGN * Lattice<Q>::c(A, k);
+    if (c < 0 && L.gm[k]) m |= 1 << (2 * k);
+    if (c > 0 && L.gp[k]) m |= 1 << (2 * k + 1);
+  }
+  return m;
+}
+
+// Does the cell touch a moving face (so some link needs the wall term)?
+template <typename R>
+__host__ __device__ __forceinline__ bool touches_moving(const Domain<R>& d, const Links& L) {
+  const int m = (L.gm[0] ? 1 : 0) | (L.gp[0] ? 2 : 0) | (L.gm[1] ? 4 : 0) |
+                (L.gp[1] ? 8 : 0) | (L.gm[2] ? 16 : 0) | (L.gp[2] ? 32 : 0);
+  return (m & d.moving) != 0;
+}
+
+// Pre-collision populations f^n of cell i into fv.
 template <int Q, typename S, typename R, bool ODD>
 __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
-                                       int x, int y, int z, int64_t i,
-                                       bool interior, R* fv) {
-  const int64_t N = d.N;
+                                                int i, const Links& L, R* fv) {
+  const int N = (int)d.N;
   if constexpr (!ODD) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
       ((fv[A] = Codec<S, R>::load(f + A * N + i)), ...);
     }(std::make_integer_sequence<int, Q>{});
-  } else if (interior) {
-    const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((fv[A] = Codec<S, R>::load(
-            f + opposite<Q>(A) * N + i -
-            (Lattice<Q>::c(A, 0) + Lattice<Q>::c(A, 1) * sy +
-             Lattice<Q>::c(A, 2) * sz))),
-       ...);
-    }(std::make_integer_sequence<int, Q>{});
   } else {
+    // f_a(x) = A[abar][x - c_a], or A[a][x] if x - c_a is a ghost
     [&]<int... A>(std::integer_sequence<int, A...>) {
       (
           [&] {
-            constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
-                          cz = Lattice<Q>::c(A, 2);
-            int64_t j;
-            int beyond;
-            if (resolve(d, x, y, z, -cx, -cy, -cz, j, beyond)) {
-              fv[A] = Codec<S, R>::load(f + opposite<Q>(A) * N + j);
-            } else {
-              fv[A] = Codec<S, R>::load(f + A * N + i) +
-                      R(6.0 * Lattice<Q>::w(A)) * ghost_dot(d, beyond, cx, cy, cz);
-            }
+            int off;
+            bool ghost;
+            link_of<Q, A, -1>(L, off, ghost);
+            const int idx = ghost ? (A * N + i) : (opposite<Q>(A) * N + i + off);
+            fv[A] = Codec<S, R>::load(f + idx);
           }(),
           ...);
     }(std::make_integer_sequence<int, Q>{});
+    if (d.moving && touches_moving(d, L)) {
+      [&]<int... A>(std::integer_sequence<int, A...>) {
+        (
+            [&] {
+              const int faces = link_faces<Q, A, -1>(L);
+              if (faces)
+                fv[A] += R(6.0 * Lattice<Q>::w(A)) *
+                         ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
+                                   Lattice<Q>::c(A, 2));
+            }(),
+            ...);
+      }(std::make_integer_sequence<int, Q>{});
+    }
   }
 }
 
-// Post-collision populations f* of cell (x,y,z) from fv into storage.
-template <int Q, typename S, typename R, bool ODD>
+// Store one post-collision value (stochastically rounded if SR).
+template <typename S, typename R, bool SR, int A>
+__host__ __device__ __forceinline__ void put(S* p, R v, uint32_t h) {
+  if constexpr (SR) {
+    Stochastic<S>::store(p, float(v), mix32_short(h + uint32_t(A + 1) * 0x9e3779b9u));
+  } else {
+    Codec<S, R>::store(p, v);
+  }
+}
+
+// Post-collision populations f* of cell i from fv into storage.
+template <int Q, typename S, typename R, bool ODD, bool SR = false>
 __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
-                                        int x, int y, int z, int64_t i,
-                                        bool interior, const R* fv) {
-  const int64_t N = d.N;
+                                                 int i, const Links& L, R* fv) {
+  const int N = (int)d.N;
+  const uint32_t h = SR ? mix32(uint32_t(i) ^ d.key) : 0u;
   if constexpr (!ODD) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((Codec<S, R>::store(f + opposite<Q>(A) * N + i, fv[A])), ...);
-    }(std::make_integer_sequence<int, Q>{});
-  } else if (interior) {
-    const int64_t sy = d.nx, sz = (int64_t)d.nx * d.ny;
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((Codec<S, R>::store(f + A * N + i +
-                               (Lattice<Q>::c(A, 0) + Lattice<Q>::c(A, 1) * sy +
-                                Lattice<Q>::c(A, 2) * sz),
-                           fv[A])),
-       ...);
+      ((put<S, R, SR, A>(f + opposite<Q>(A) * N + i, fv[A], h)), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
+    if (d.moving && touches_moving(d, L)) {
+      [&]<int... A>(std::integer_sequence<int, A...>) {
+        (
+            [&] {
+              const int faces = link_faces<Q, A, 1>(L);
+              if (faces)
+                fv[A] -= R(6.0 * Lattice<Q>::w(A)) *
+                         ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
+                                   Lattice<Q>::c(A, 2));
+            }(),
+            ...);
+      }(std::make_integer_sequence<int, Q>{});
+    }
+    // f*_a goes to A[a][x + c_a], or back into A[abar][x] if x + c_a is a ghost
     [&]<int... A>(std::integer_sequence<int, A...>) {
       (
           [&] {
-            constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
-                          cz = Lattice<Q>::c(A, 2);
-            int64_t j;
-            int beyond;
-            if (resolve(d, x, y, z, cx, cy, cz, j, beyond)) {
-              Codec<S, R>::store(f + A * N + j, fv[A]);
-            } else {
-              Codec<S, R>::store(
-                  f + opposite<Q>(A) * N + i,
-                  fv[A] - R(6.0 * Lattice<Q>::w(A)) * ghost_dot(d, beyond, cx, cy, cz));
-            }
+            int off;
+            bool ghost;
+            link_of<Q, A, 1>(L, off, ghost);
+            const int idx = ghost ? (opposite<Q>(A) * N + i) : (A * N + i + off);
+            put<S, R, SR, A>(f + idx, fv[A], h);
           }(),
           ...);
     }(std::make_integer_sequence<int, Q>{});
   }
 }
 
-template <typename R>
-__host__ __device__ __forceinline__ bool is_interior(const Domain<R>& d, int x, int y, int z) {
-  return x > 0 && x < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
+__host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
+                                                           S* __restrict__ f, int i,
+                                                           const Links& L) {
+  R fv[Q];
+  gather<Q, S, R, ODD>(d, f, i, L, fv);
+  R ux, uy, uz;
+  collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
+  scatter<Q, S, R, ODD, SR>(d, f, i, L, fv);
 }
 
 // The whole fused update of one cell: gather (stream), collide, scatter.
-template <int Q, typename S, typename R, bool ODD, bool FORCE>
+// On odd steps the y/z-interior test is uniform across a warp whenever a
+// warp lies within one x-row (block width a multiple of 32), so the two
+// addressing variants never diverge inside a warp.
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false>
 __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ f,
-                                            int x, int y, int z) {
-  const int64_t i = (int64_t)x + (int64_t)d.nx * ((int64_t)y + (int64_t)d.ny * z);
-  const bool interior = ODD ? is_interior(d, x, y, z) : true;
-  R fv[Q];
-  gather<Q, S, R, ODD>(d, f, x, y, z, i, interior, fv);
-  R ux, uy, uz;
-  collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
-  scatter<Q, S, R, ODD>(d, f, x, y, z, i, interior, fv);
+                                                     int x, int y, int z) {
+  const int i = x + d.nx * (y + d.ny * z);
+  if constexpr (!ODD) {
+    Links L{};
+    update_with_links<Q, S, R, false, FORCE, SR>(d, f, i, L);
+  } else {
+    if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+      update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links_x(d, x));
+    } else {
+      update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links(d, x, y, z));
+    }
+  }
 }
 
 // Inverse of gather: put canonical pre-collision values fv of cell (x,y,z)
-// where the current parity keeps them (checkpoint restore / init).
+// where the step parity keeps them (checkpoint restore / init).
 template <int Q, typename S, typename R, bool ODD>
 __host__ __device__ __forceinline__ void put_canonical(const Domain<R>& d, S* __restrict__ f,
-                                              int x, int y, int z, int64_t i,
-                                              const R* fv) {
-  const int64_t N = d.N;
-  [&]<int... A>(std::integer_sequence<int, A...>) {
-    (
-        [&] {
-          if constexpr (!ODD) {
-            Codec<S, R>::store(f + A * N + i, fv[A]);
-          } else {
-            constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
-                          cz = Lattice<Q>::c(A, 2);
-            int64_t j;
-            int beyond;
-            if (resolve(d, x, y, z, -cx, -cy, -cz, j, beyond)) {
-              Codec<S, R>::store(f + opposite<Q>(A) * N + j, fv[A]);
-            } else {
-              Codec<S, R>::store(
-                  f + A * N + i,
-                  fv[A] - R(6.0 * Lattice<Q>::w(A)) * ghost_dot(d, beyond, cx, cy, cz));
-            }
-          }
-        }(),
-        ...);
-  }(std::make_integer_sequence<int, Q>{});
+                                                       int x, int y, int z, const R* fv) {
+  const int N = (int)d.N;
+  const int i = x + d.nx * (y + d.ny * z);
+  if constexpr (!ODD) {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      (Codec<S, R>::store(f + A * N + i, fv[A]), ...);
+    }(std::make_integer_sequence<int, Q>{});
+  } else {
+    const Links L = make_links(d, x, y, z);
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      (
+          [&] {
+            int off;
+            bool ghost;
+            link_of<Q, A, -1>(L, off, ghost);
+            R v = fv[A];
+            const int faces = link_faces<Q, A, -1>(L);
+            if (faces)
+              v -= R(6.0 * Lattice<Q>::w(A)) *
+                   ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
+                             Lattice<Q>::c(A, 2));
+            const int idx = ghost ? (A * N + i) : (opposite<Q>(A) * N + i + off);
+            Codec<S, R>::store(f + idx, v);
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, Q>{});
+  }
+}
+
+// Canonical pre-collision populations of cell (x,y,z) at any parity.
+template <int Q, typename S, typename R, bool ODD>
+__host__ __device__ __forceinline__ void get_canonical(const Domain<R>& d, const S* __restrict__ f,
+                                                       int x, int y, int z, R* fv) {
+  const int i = x + d.nx * (y + d.ny * z);
+  if constexpr (!ODD) {
+    Links L{};
+    gather<Q, S, R, false>(d, f, i, L, fv);
+  } else {
+    gather<Q, S, R, true>(d, f, i, make_links(d, x, y, z), fv);
+  }
 }
 
 }  // namespace lbm

@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <cstring>
 #include <utility>
 
 namespace lbm {
@@ -221,6 +222,87 @@ struct Codec<__nv_bfloat16, R> {
   }
   __host__ __device__ static void store(__nv_bfloat16* p, R v) {
     *p = __float2bfloat16_rn(float(v));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Stochastic rounding for 16-bit storage.  Rounding to nearest loses every
+// per-step change smaller than half a storage ulp in the same direction
+// (stagnation), which biases slowly varying populations.  Rounding up with
+// probability equal to the discarded fraction makes every store unbiased.
+// The random bits come from a counter-based hash of (cell, direction, step),
+// so runs are reproducible and independent of launch shape or batching.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  // integer finaliser (xorshift-multiply, constants from public hash designs)
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t mix32_short(uint32_t x) {
+  x ^= x >> 15;
+  x *= 0x2c1b3c6du;
+  x ^= x >> 12;
+  return x;
+}
+
+__host__ __device__ __forceinline__ uint32_t f32_bits(float v) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(v);
+#else
+  uint32_t b;
+  memcpy(&b, &v, 4);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float bits_f32(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float v;
+  memcpy(&v, &b, 4);
+  return v;
+#endif
+}
+
+// Round v to a value with `drop` fewer mantissa bits, stochastically:
+// add uniform random bits below the kept LSB, then truncate the magnitude.
+__host__ __device__ __forceinline__ float dither_truncate(float v, int drop, uint32_t r) {
+  const uint32_t mask = (drop >= 31) ? 0x7fffffffu : ((1u << drop) - 1u);
+  uint32_t b = f32_bits(v);
+  const uint32_t mag = b & 0x7fffffffu;
+  if (mag >= 0x7f800000u) return v;  // inf / nan unchanged
+  b = (b & 0x80000000u) | ((mag + (r & mask)) & ~mask);
+  return bits_f32(b);
+}
+
+template <typename S>
+struct Stochastic {
+  static constexpr bool enabled = false;
+};
+template <>
+struct Stochastic<__half> {
+  static constexpr bool enabled = true;
+  __host__ __device__ static void store(__half* p, float v, uint32_t r) {
+    // half keeps 10 mantissa bits (13 fewer than float) down to 2^-14; below
+    // that its spacing is fixed at 2^-24, so more bits are dropped.
+    const int e = int((f32_bits(v) >> 23) & 0xffu) - 127;
+    if (e < -24) {  // below half's smallest spacing: nearest is within 3e-8
+      *p = __float2half_rn(v);
+      return;
+    }
+    const int drop = e < -14 ? 13 + (-14 - e) : 13;
+    *p = __float2half_rz(dither_truncate(v, drop, r));
+  }
+};
+template <>
+struct Stochastic<__nv_bfloat16> {
+  static constexpr bool enabled = true;
+  __host__ __device__ static void store(__nv_bfloat16* p, float v, uint32_t r) {
+    *p = __float2bfloat16_rz(dither_truncate(v, 16, r));
   }
 };
 

@@ -25,6 +25,7 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
   o.s.spi = R(d.s[4]);
   o.s.st = R(d.s[5]);
   for (int k = 0; k < 3; ++k) o.F[k] = R(F[k]);
+  o.key = 0;
   return o;
 }
 template Domain<double> to_domain<double>(const DomainDesc&, const double*);
@@ -43,13 +44,29 @@ BlockShape default_block(int nx, int ny) {
   return {bx, by};
 }
 
-template <int Q, typename S, typename R, bool ODD, bool FORCE>
+uint32_t step_key(int64_t n) {
+  return mix32(0x5eedu ^ (uint32_t(n) * 0x632be5abu) ^ uint32_t(uint64_t(n) >> 32));
+}
+
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
 __global__ void __launch_bounds__(256) k_step(Domain<R> d) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
-  update_cell<Q, S, R, ODD, FORCE>(d, static_cast<S*>(d.f), x, y, z);
+  update_cell<Q, S, R, ODD, FORCE, SR>(d, static_cast<S*>(d.f), x, y, z);
+}
+
+template <int Q, typename S, typename R, bool SR>
+static void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 block,
+                          cudaStream_t st) {
+  if (odd) {
+    if (force) k_step<Q, S, R, true, true, SR><<<grid, block, 0, st>>>(d);
+    else k_step<Q, S, R, true, false, SR><<<grid, block, 0, st>>>(d);
+  } else {
+    if (force) k_step<Q, S, R, false, true, SR><<<grid, block, 0, st>>>(d);
+    else k_step<Q, S, R, false, false, SR><<<grid, block, 0, st>>>(d);
+  }
 }
 
 template <int Q, typename S, typename R>
@@ -59,16 +76,17 @@ static cudaError_t launch_typed(const DomainDesc& dd, int64_t n, BlockShape b,
   force_at(dd, n, F);
   const bool force = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0 || dd.period > 0.0;
   Domain<R> d = to_domain<R>(dd, F);
+  d.key = step_key(n);
   dim3 block(b.bx, b.by, 1);
   dim3 grid((dd.nx + b.bx - 1) / b.bx, (dd.ny + b.by - 1) / b.by, dd.nz);
   const bool odd = (n & 1) != 0;
-  if (odd) {
-    if (force) k_step<Q, S, R, true, true><<<grid, block, 0, st>>>(d);
-    else k_step<Q, S, R, true, false><<<grid, block, 0, st>>>(d);
-  } else {
-    if (force) k_step<Q, S, R, false, true><<<grid, block, 0, st>>>(d);
-    else k_step<Q, S, R, false, false><<<grid, block, 0, st>>>(d);
+  if constexpr (Stochastic<S>::enabled) {
+    if (dd.rounding == LBM_ROUND_STOCHASTIC) {
+      launch_parity<Q, S, R, true>(d, odd, force, grid, block, st);
+      return cudaGetLastError();
+    }
   }
+  launch_parity<Q, S, R, false>(d, odd, force, grid, block, st);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ class Case:
     u_ref: float = 0.0            # velocity scale for error bounds
     init_u: Optional[np.ndarray] = None   # (3, nz, ny, nx) or None (rest)
     init_p: Optional[np.ndarray] = None   # (nz, ny, nx) or None
+    rounding: int = 0             # 16-bit stores: 0 nearest, 1 stochastic
 
     @property
     def cells(self) -> int:

@@ -23,6 +23,7 @@ LBM_XM, LBM_XP, LBM_YM, LBM_YP, LBM_ZM, LBM_ZP = range(6)
 # fields / dtypes
 LBM_FIELD_U, LBM_FIELD_P, LBM_FIELD_POPULATIONS = 1, 2, 4
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
+LBM_ROUND_NEAREST, LBM_ROUND_STOCHASTIC = 0, 1
 
 STORAGE_NAMES = {"f64": LBM_STORAGE_F64, "f32": LBM_STORAGE_F32,
                  "f16": LBM_STORAGE_F16, "bf16": LBM_STORAGE_BF16}
@@ -48,7 +49,7 @@ class lbm_params(ctypes.Structure):
                 ("s_e", ctypes.c_double), ("s_q", ctypes.c_double), ("s_pi", ctypes.c_double),
                 ("s_t", ctypes.c_double), ("force", ctypes.c_double * 3),
                 ("force_period", ctypes.c_double), ("p_ref", ctypes.c_double),
-                ("residual_interval", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("residual_interval", ctypes.c_int32), ("rounding", ctypes.c_int32)]
 
 
 class lbm_stats(ctypes.Structure):
@@ -156,7 +157,8 @@ def lbm_set_geometry(h, faces, u_wall=None):
 
 
 def make_params(nu=0.0, s_nu=0.0, s_c=1.0, s_e=1.19, s_q=1.2, s_pi=1.19, s_t=0.98,
-                force=(0.0, 0.0, 0.0), force_period=0.0, p_ref=0.0, residual_interval=0):
+                force=(0.0, 0.0, 0.0), force_period=0.0, p_ref=0.0, residual_interval=0,
+                rounding=LBM_ROUND_NEAREST):
     p = lbm_params()
     p.nu, p.s_nu, p.s_c, p.s_e, p.s_q, p.s_pi, p.s_t = nu, s_nu, s_c, s_e, s_q, s_pi, s_t
     for k in range(3):
@@ -164,6 +166,7 @@ def make_params(nu=0.0, s_nu=0.0, s_c=1.0, s_e=1.19, s_q=1.2, s_pi=1.19, s_t=0.9
     p.force_period = float(force_period)
     p.p_ref = float(p_ref)
     p.residual_interval = int(residual_interval)
+    p.rounding = int(rounding)
     return p
 
 

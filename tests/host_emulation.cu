@@ -9,6 +9,8 @@
 
 using namespace lbm;
 
+static int g_sr = 0;
+
 template <int Q, typename S, typename R>
 static void step_typed(void* f, int nx, int ny, int nz, const int* per, int moving,
                        const double* uw, const double* s, const double* F, int64_t n) {
@@ -23,10 +25,18 @@ static void step_typed(void* f, int nx, int ny, int nz, const int* per, int movi
   d.s.sc = R(s[0]); d.s.se = R(s[1]); d.s.sq = R(s[2]);
   d.s.snu = R(s[3]); d.s.spi = R(s[4]); d.s.st = R(s[5]);
   for (int k = 0; k < 3; ++k) d.F[k] = R(F[k]);
+  d.key = mix32(0x5eedu ^ uint32_t(n) * 0x632be5abu);
   const bool force = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0;
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
+        if constexpr (Stochastic<S>::enabled) {
+          if (g_sr) {
+            if (n & 1) update_cell<Q, S, R, true, true, true>(d, static_cast<S*>(f), x, y, z);
+            else update_cell<Q, S, R, false, true, true>(d, static_cast<S*>(f), x, y, z);
+            continue;
+          }
+        }
         if (n & 1) {
           if (force) update_cell<Q, S, R, true, true>(d, static_cast<S*>(f), x, y, z);
           else update_cell<Q, S, R, true, false>(d, static_cast<S*>(f), x, y, z);
@@ -55,28 +65,61 @@ static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int
         R fv[Q];
         if (to_storage) {
           for (int a = 0; a < Q; ++a) fv[a] = R(out[a * d.N + i]);
-          put_canonical<Q, S, R, ODD>(d, static_cast<S*>(f), x, y, z, i, fv);
+          put_canonical<Q, S, R, ODD>(d, static_cast<S*>(f), x, y, z, fv);
         } else {
-          gather<Q, S, R, ODD>(d, static_cast<const S*>(f), x, y, z, i,
-                               ODD ? is_interior(d, x, y, z) : true, fv);
+          get_canonical<Q, S, R, ODD>(d, static_cast<const S*>(f), x, y, z, fv);
           for (int a = 0; a < Q; ++a) out[a * d.N + i] = double(fv[a]);
         }
       }
 }
 
+template <typename S, typename R>
+static int canon_any(int Q, void* f, int nx, int ny, int nz, const int* per, int moving,
+                     const double* uw, double* canon, int64_t n, int to_storage) {
+  const bool odd = n & 1;
+  if (Q == 14) {
+    if (odd) canonical_typed<14, S, R, true>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+    else canonical_typed<14, S, R, false>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+  } else if (Q == 18) {
+    if (odd) canonical_typed<18, S, R, true>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+    else canonical_typed<18, S, R, false>(f, nx, ny, nz, per, moving, uw, canon, to_storage);
+  } else {
+    return -1;
+  }
+  return 0;
+}
+
 extern "C" {
-// storage: 0 double, 1 float
+void emu_set_stochastic(int on) { g_sr = on; }
+
+// storage: 0 double, 1 float, 2 half, 3 bfloat16
 int emu_step(int Q, int storage, void* f, int nx, int ny, int nz, const int* per, int moving,
              const double* uw, const double* s, const double* F, int64_t n) {
   if (Q == 14 && storage == 0) step_typed<14, double, double>(f, nx, ny, nz, per, moving, uw, s, F, n);
   else if (Q == 18 && storage == 0) step_typed<18, double, double>(f, nx, ny, nz, per, moving, uw, s, F, n);
   else if (Q == 14 && storage == 1) step_typed<14, float, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
   else if (Q == 18 && storage == 1) step_typed<18, float, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else if (Q == 14 && storage == 2) step_typed<14, __half, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else if (Q == 18 && storage == 2) step_typed<18, __half, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else if (Q == 14 && storage == 3) step_typed<14, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
+  else if (Q == 18 && storage == 3) step_typed<18, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, uw, s, F, n);
   else return -1;
   return 0;
 }
 
 // canonical f (FP64) <-> storage layout of parity n (double storage only)
+int emu_canonical_storage(int Q, int storage, void* f, int nx, int ny, int nz, const int* per,
+                          int moving, const double* uw, double* canon, int64_t n,
+                          int to_storage) {
+  switch (storage) {
+    case 0: return canon_any<double, double>(Q, f, nx, ny, nz, per, moving, uw, canon, n, to_storage);
+    case 1: return canon_any<float, float>(Q, f, nx, ny, nz, per, moving, uw, canon, n, to_storage);
+    case 2: return canon_any<__half, float>(Q, f, nx, ny, nz, per, moving, uw, canon, n, to_storage);
+    case 3: return canon_any<__nv_bfloat16, float>(Q, f, nx, ny, nz, per, moving, uw, canon, n, to_storage);
+  }
+  return -1;
+}
+
 int emu_canonical(int Q, void* f, int nx, int ny, int nz, const int* per, int moving,
                   const double* uw, double* canon, int64_t n, int to_storage) {
   const bool odd = n & 1;

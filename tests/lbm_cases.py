@@ -29,7 +29,7 @@ def gpu_open(case, stream=None, residual_interval=0):
     h = lbm.lbm_create(case.Q, case.nx, case.ny, case.nz, case.storage, stream)
     lbm.lbm_set_geometry(h, case.faces, case.u_wall)
     lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period,
-                       residual_interval=residual_interval)
+                       residual_interval=residual_interval, rounding=case.rounding)
     return h
 
 
