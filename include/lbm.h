@@ -192,6 +192,11 @@ int lbm_reductions(lbm_handle *h, lbm_stats *out);
  * lbm_reductions).  Synchronises. */
 int lbm_read_stats(lbm_handle *h, lbm_stats *out);
 
+/* Thread-block shape of the step kernel: bx threads along x (a multiple of
+ * 32, so that a warp never spans two x-rows) by by along y, bx*by <= 1024.
+ * Affects speed only, never results.  EINVAL otherwise. */
+int lbm_set_block(lbm_handle *h, int32_t bx, int32_t by);
+
 /* Device memory the handle holds, in bytes. */
 int lbm_memory_bytes(lbm_handle *h, int64_t *bytes);
 

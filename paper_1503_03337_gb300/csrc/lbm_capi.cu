@@ -444,6 +444,14 @@ int lbm_read_stats(lbm_handle* h, lbm_stats* out) {
   return LBM_OK;
 }
 
+int lbm_set_block(lbm_handle* h, int32_t bx, int32_t by) {
+  if (int rc = check(h)) return rc;
+  if (bx < 32 || bx % 32 != 0 || by < 1 || (int64_t)bx * by > 1024)
+    return fail(LBM_EINVAL, "block must be bx (multiple of 32) x by with bx*by <= 1024");
+  h->block = {bx, by};
+  return LBM_OK;
+}
+
 int lbm_memory_bytes(lbm_handle* h, int64_t* bytes) {
   if (int rc = check(h)) return rc;
   if (!bytes) return fail(LBM_EINVAL, "null output");

@@ -79,6 +79,21 @@ __host__ __device__ __forceinline__ Links make_links(const Domain<R>& d, int x, 
   return L;
 }
 
+// Links of a cell whose neighbours are all fluid and unwrapped.
+template <typename R>
+__host__ __device__ __forceinline__ Links make_links_interior(const Domain<R>& d) {
+  Links L;
+  const int sy = d.nx, sz = d.nx * d.ny;
+  L.om[0] = -1;
+  L.op[0] = 1;
+  L.om[1] = -sy;
+  L.op[1] = sy;
+  L.om[2] = -sz;
+  L.op[2] = sz;
+  L.gm[0] = L.gp[0] = L.gm[1] = L.gp[1] = L.gm[2] = L.gp[2] = false;
+  return L;
+}
+
 // Links of a cell whose y and z neighbours are all fluid and unwrapped (the
 // bulk of a box): only x needs the select.
 template <typename R>
@@ -140,8 +155,9 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
                                                 int i, const Links& L, R* fv) {
   const int N = (int)d.N;
   if constexpr (!ODD) {
+    const S* __restrict__ fc = f + i;
     [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((fv[A] = Codec<S, R>::load(f + A * N + i)), ...);
+      ((fv[A] = Codec<S, R>::load(fc + (size_t)A * d.N)), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
     // f_a(x) = A[abar][x - c_a], or A[a][x] if x - c_a is a ghost
@@ -189,8 +205,9 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
   const int N = (int)d.N;
   const uint32_t h = SR ? mix32(uint32_t(i) ^ d.key) : 0u;
   if constexpr (!ODD) {
+    S* __restrict__ fc = f + i;
     [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((put<S, R, SR, A>(f + opposite<Q>(A) * N + i, fv[A], h)), ...);
+      ((put<S, R, SR, A>(fc + (size_t)opposite<Q>(A) * d.N, fv[A], h)), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
     if (d.moving && touches_moving(d, L)) {
@@ -233,19 +250,24 @@ __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
 }
 
 // The whole fused update of one cell: gather (stream), collide, scatter.
-// On odd steps the y/z-interior test is uniform across a warp whenever a
-// warp lies within one x-row (block width a multiple of 32), so the two
-// addressing variants never diverge inside a warp.
+// Odd steps pick one of three addressing variants.  `x_lo`..`x_hi` is the
+// x-range of the calling warp: when a warp lies within one x-row (block
+// width a multiple of 32) every test below is uniform across the warp, so
+// the variants never diverge inside a warp.
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false>
 __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ f,
-                                                     int x, int y, int z) {
+                                                     int x, int y, int z, int x_lo = -1,
+                                                     int x_hi = -1) {
   const int i = x + d.nx * (y + d.ny * z);
   if constexpr (!ODD) {
     Links L{};
     update_with_links<Q, S, R, false, FORCE, SR>(d, f, i, L);
   } else {
     if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
-      update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links_x(d, x));
+      if (x_lo > 0 && x_hi < d.nx - 1)
+        update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links_interior(d));
+      else
+        update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links_x(d, x));
     } else {
       update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links(d, x, y, z));
     }

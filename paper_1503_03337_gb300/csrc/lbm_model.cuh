@@ -382,6 +382,53 @@ struct Rates {
 };
 
 // ---------------------------------------------------------------------------
+// Streaming back-transform: a relaxed row x_K (already divided by D_K) is
+// added into the per-pair accumulators E (even rows) or O (odd rows) as soon
+// as it is known, so no moment array stays live.  Rows are processed in
+// index order; row 0 (P) never contributes and rows 2, 4, 6 (j) contribute
+// only with a force.  `touched` tells at compile time whether an accumulator
+// already holds a value, so its first contribution is a plain product.
+// ---------------------------------------------------------------------------
+template <int Q, bool FORCE>
+__host__ __device__ constexpr bool row_active(int k) {
+  return k != 0 && (FORCE || (k != 2 && k != 4 && k != 6));
+}
+
+template <int Q, bool FORCE>
+__host__ __device__ constexpr bool touched(int I, int K, bool even) {
+  for (int k = 0; k < K; ++k)
+    if (row_active<Q, FORCE>(k) && row_even<Q>(k) == even &&
+        phi<Q>(k, pair_rep<Q>(I)) != 0)
+      return true;
+  return false;
+}
+
+template <int Q, bool FORCE, int K, int I = 0, typename R>
+__host__ __device__ __forceinline__ void add_row(R xk, R* E, R* O) {
+  if constexpr (I < Q / 2) {
+    constexpr int C = phi<Q>(K, pair_rep<Q>(I));
+    constexpr bool EV = row_even<Q>(K);
+    if constexpr (C != 0) {
+      R& acc = EV ? E[I] : O[I];
+      if constexpr (touched<Q, FORCE>(I, K, EV)) acc = term_add<C>(acc, xk);
+      else acc = term_first<C>(xk);
+    }
+    add_row<Q, FORCE, K, I + 1>(xk, E, O);
+  }
+}
+
+// every accumulator receives at least one row (else it would stay unset)
+template <int Q, bool FORCE>
+__host__ __device__ constexpr bool accumulators_covered() {
+  for (int I = 0; I < Q / 2; ++I)
+    if (!touched<Q, FORCE>(I, Q, true) || !touched<Q, FORCE>(I, Q, false)) return false;
+  return true;
+}
+static_assert(accumulators_covered<14, false>() && accumulators_covered<14, true>() &&
+                  accumulators_covered<18, false>() && accumulators_covered<18, true>(),
+              "a pair accumulator receives no row");
+
+// ---------------------------------------------------------------------------
 // One-cell collision, Eq. mrteqvT:  f* = f - T^-1 [ S (m - m_eq) - (I - S/2) S_F ]
 //
 // u = j + F/2 and p from Eq. hgl.  The Guo source S_F is the derivative of
@@ -394,21 +441,21 @@ struct Rates {
 // ---------------------------------------------------------------------------
 template <int Q, bool FORCE, typename R>
 __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, R Fy,
-                                        R Fz, R& ux, R& uy, R& uz) {
+                                                 R Fz, R& ux, R& uy, R& uz) {
   constexpr int NP = Q / 2;
   R ps[NP], pd[NP];
-  // pair sums and differences
+  // pair sums and differences; f itself is not needed again
   [&]<int... I>(std::integer_sequence<int, I...>) {
     ((ps[I] = f[pair_rep<Q>(I)] + f[opposite<Q>(pair_rep<Q>(I))],
       pd[I] = f[pair_rep<Q>(I)] - f[opposite<Q>(pair_rep<Q>(I))]),
      ...);
   }(std::make_integer_sequence<int, NP>{});
 
-  R m[Q];
-  moments<Q>(ps, pd, m);
-
-  // velocity (Eq. hgl with the force half step) and pressure (Eq. hgl)
-  const R jx = m[2], jy = m[4], jz = m[6];
+  // conserved moments, velocity (Eq. hgl with the force half step), pressure
+  const R P = row_sum<Q, 0, 0, false>(R(0), ps);
+  const R jx = row_sum<Q, 2, 0, false>(R(0), pd);
+  const R jy = row_sum<Q, 4, 0, false>(R(0), pd);
+  const R jz = row_sum<Q, 6, 0, false>(R(0), pd);
   if constexpr (FORCE) {
     ux = jx + R(0.5) * Fx;
     uy = jy + R(0.5) * Fy;
@@ -422,20 +469,8 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
   const R u2 = uxx + uyy + uzz;
   constexpr double cs2 = 1.0 / 3.0;
   constexpr double w0 = Lattice<Q>::w0;
-  const R p = R(cs2 / (1.0 - w0)) * (m[0] - R(w0 / (2.0 * cs2)) * u2);
+  const R p = R(cs2 / (1.0 - w0)) * (P - R(w0 / (2.0 * cs2)) * u2);
 
-  // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K
-  R x[Q];
-  x[0] = R(0);
-  if constexpr (FORCE) {
-    x[2] = -Fx * R(1.0 / row_norm<Q>(2));
-    x[4] = -Fy * R(1.0 / row_norm<Q>(4));
-    x[6] = -Fz * R(1.0 / row_norm<Q>(6));
-  } else {
-    x[2] = R(0);
-    x[4] = R(0);
-    x[6] = R(0);
-  }
   const R uxy = ux * uy, uyz = uy * uz, uxz = ux * uz;
   const R pxx_eq = R(3) * uxx - u2;  // 3 p_xx
   const R pww_eq = uyy - uzz;
@@ -451,80 +486,98 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
   }
   const R hq = R(1) - R(0.5) * s.sq;
   const R hnu = R(1) - R(0.5) * s.snu;
-  if constexpr (Q == 14) {
-    // e_eq = -7p + u^2 (source 2 u.F); q_eq = -7u/3 (source -7F/3)
-    const R he = R(1) - R(0.5) * s.se;
-    R ne = m[1] - (R(-7) * p + u2);
-    R nqx = m[3] + R(7.0 / 3.0) * ux, nqy = m[5] + R(7.0 / 3.0) * uy,
-      nqz = m[7] + R(7.0 / 3.0) * uz;
-    R n8 = m[8] - pxx_eq, n9 = m[9] - pww_eq, n10 = m[10] - uxy,
-      n11 = m[11] - uyz, n12 = m[12] - uxz;
-    x[1] = s.se * ne;
-    x[3] = s.sq * nqx;
-    x[5] = s.sq * nqy;
-    x[7] = s.sq * nqz;
-    x[8] = s.snu * n8;
-    x[9] = s.snu * n9;
-    x[10] = s.snu * n10;
-    x[11] = s.snu * n11;
-    x[12] = s.snu * n12;
-    if constexpr (FORCE) {
-      x[1] -= he * (R(2) * uF);
-      x[3] += hq * (R(7.0 / 3.0) * Fx);
-      x[5] += hq * (R(7.0 / 3.0) * Fy);
-      x[7] += hq * (R(7.0 / 3.0) * Fz);
-      x[8] -= hnu * sxx;
-      x[9] -= hnu * sww;
-      x[10] -= hnu * sxy;
-      x[11] -= hnu * syz;
-      x[12] -= hnu * sxz;
-    }
-    x[13] = s.st * m[13];
-  } else {
-    // e_eq = -p + u^2/2 (source u.F); q_eq = -2u/3 (source -2F/3);
-    // 3pi_xx and pi_ww equilibria are -1/2 of 3p_xx and p_ww.
-    const R he = R(1) - R(0.5) * s.se;
-    const R hpi = R(1) - R(0.5) * s.spi;
-    R ne = m[1] - (-p + R(0.5) * u2);
-    R nqx = m[3] + R(2.0 / 3.0) * ux, nqy = m[5] + R(2.0 / 3.0) * uy,
-      nqz = m[7] + R(2.0 / 3.0) * uz;
-    x[1] = s.se * ne;
-    x[3] = s.sq * nqx;
-    x[5] = s.sq * nqy;
-    x[7] = s.sq * nqz;
-    x[8] = s.snu * (m[8] - pxx_eq);
-    x[9] = s.spi * (m[9] + R(0.5) * pxx_eq);
-    x[10] = s.snu * (m[10] - pww_eq);
-    x[11] = s.spi * (m[11] + R(0.5) * pww_eq);
-    x[12] = s.snu * (m[12] - uxy);
-    x[13] = s.snu * (m[13] - uyz);
-    x[14] = s.snu * (m[14] - uxz);
-    if constexpr (FORCE) {
-      x[1] -= he * uF;
-      x[3] += hq * (R(2.0 / 3.0) * Fx);
-      x[5] += hq * (R(2.0 / 3.0) * Fy);
-      x[7] += hq * (R(2.0 / 3.0) * Fz);
-      x[8] -= hnu * sxx;
-      x[9] += hpi * (R(0.5) * sxx);
-      x[10] -= hnu * sww;
-      x[11] += hpi * (R(0.5) * sww);
-      x[12] -= hnu * sxy;
-      x[13] -= hnu * syz;
-      x[14] -= hnu * sxz;
-    }
-    x[15] = s.st * m[15];
-    x[16] = s.st * m[16];
-    x[17] = s.st * m[17];
-  }
-  // divide by the row norms D_K (T^-1 = T' D^-1); the momentum rows are done
-  [&]<int... K>(std::integer_sequence<int, K...>) {
-    ((K == 0 || K == 2 || K == 4 || K == 6
-          ? void()
-          : void(x[K] = x[K] * R(1.0 / row_norm<Q>(K)))),
-     ...);
-  }(std::make_integer_sequence<int, Q>{});
+  const R he = R(1) - R(0.5) * s.se;
 
-  back_transform<Q>(x, f);
+  // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K, streamed into E / O
+  R E[NP], O[NP];
+  auto row = [&]<int K>(R xk) {
+    add_row<Q, FORCE, K>(xk * R(1.0 / row_norm<Q>(K)), E, O);
+  };
+  auto m = [&]<int K>() {
+    if constexpr (row_even<Q>(K)) return row_sum<Q, K, 0, false>(R(0), ps);
+    else return row_sum<Q, K, 0, false>(R(0), pd);
+  };
+  R x1;
+  if constexpr (Q == 14) {
+    // e_eq = -7p + u^2 (source 2 u.F)
+    x1 = s.se * (m.template operator()<1>() - (R(-7) * p + u2));
+    if constexpr (FORCE) x1 -= he * (R(2) * uF);
+  } else {
+    // e_eq = -p + u^2/2 (source u.F)
+    x1 = s.se * (m.template operator()<1>() - (-p + R(0.5) * u2));
+    if constexpr (FORCE) x1 -= he * uF;
+  }
+  row.template operator()<1>(x1);
+  if constexpr (FORCE) {  // momentum rows: s_c (j - u) - (1 - s_c/2) F = -F
+    row.template operator()<2>(-Fx);
+    row.template operator()<4>(-Fy);
+    row.template operator()<6>(-Fz);
+  }
+  // q_eq = -7u/3 (Q14) or -2u/3 (Q18); sources -7F/3 or -2F/3
+  constexpr double cq = Q == 14 ? 7.0 / 3.0 : 2.0 / 3.0;
+  R x3 = s.sq * (m.template operator()<3>() + R(cq) * ux);
+  R x5 = s.sq * (m.template operator()<5>() + R(cq) * uy);
+  R x7 = s.sq * (m.template operator()<7>() + R(cq) * uz);
+  if constexpr (FORCE) {
+    x3 += hq * (R(cq) * Fx);
+    x5 += hq * (R(cq) * Fy);
+    x7 += hq * (R(cq) * Fz);
+  }
+  row.template operator()<3>(x3);
+  row.template operator()<5>(x5);
+  row.template operator()<7>(x7);
+  if constexpr (Q == 14) {
+    R x8 = s.snu * (m.template operator()<8>() - pxx_eq);
+    if constexpr (FORCE) x8 -= hnu * sxx;
+    row.template operator()<8>(x8);
+    R x9 = s.snu * (m.template operator()<9>() - pww_eq);
+    if constexpr (FORCE) x9 -= hnu * sww;
+    row.template operator()<9>(x9);
+    R x10 = s.snu * (m.template operator()<10>() - uxy);
+    if constexpr (FORCE) x10 -= hnu * sxy;
+    row.template operator()<10>(x10);
+    R x11 = s.snu * (m.template operator()<11>() - uyz);
+    if constexpr (FORCE) x11 -= hnu * syz;
+    row.template operator()<11>(x11);
+    R x12 = s.snu * (m.template operator()<12>() - uxz);
+    if constexpr (FORCE) x12 -= hnu * sxz;
+    row.template operator()<12>(x12);
+    row.template operator()<13>(s.st * m.template operator()<13>());
+  } else {
+    // 3pi_xx and pi_ww equilibria (and sources) are -1/2 of 3p_xx and p_ww
+    const R hpi = R(1) - R(0.5) * s.spi;
+    R x8 = s.snu * (m.template operator()<8>() - pxx_eq);
+    if constexpr (FORCE) x8 -= hnu * sxx;
+    row.template operator()<8>(x8);
+    R x9 = s.spi * (m.template operator()<9>() + R(0.5) * pxx_eq);
+    if constexpr (FORCE) x9 += hpi * (R(0.5) * sxx);
+    row.template operator()<9>(x9);
+    R x10 = s.snu * (m.template operator()<10>() - pww_eq);
+    if constexpr (FORCE) x10 -= hnu * sww;
+    row.template operator()<10>(x10);
+    R x11 = s.spi * (m.template operator()<11>() + R(0.5) * pww_eq);
+    if constexpr (FORCE) x11 += hpi * (R(0.5) * sww);
+    row.template operator()<11>(x11);
+    R x12 = s.snu * (m.template operator()<12>() - uxy);
+    if constexpr (FORCE) x12 -= hnu * sxy;
+    row.template operator()<12>(x12);
+    R x13 = s.snu * (m.template operator()<13>() - uyz);
+    if constexpr (FORCE) x13 -= hnu * syz;
+    row.template operator()<13>(x13);
+    R x14 = s.snu * (m.template operator()<14>() - uxz);
+    if constexpr (FORCE) x14 -= hnu * sxz;
+    row.template operator()<14>(x14);
+    row.template operator()<15>(s.st * m.template operator()<15>());
+    row.template operator()<16>(s.st * m.template operator()<16>());
+    row.template operator()<17>(s.st * m.template operator()<17>());
+  }
+  // f*_rep = f_rep - (E + O), f*_partner = f_partner - (E - O), with
+  // f_rep = (s + d)/2 and f_partner = (s - d)/2
+  [&]<int... I>(std::integer_sequence<int, I...>) {
+    ((f[pair_rep<Q>(I)] = R(0.5) * (ps[I] + pd[I]) - (E[I] + O[I]),
+      f[opposite<Q>(pair_rep<Q>(I))] = R(0.5) * (ps[I] - pd[I]) - (E[I] - O[I])),
+     ...);
+  }(std::make_integer_sequence<int, NP>{});
 }
 
 }  // namespace lbm

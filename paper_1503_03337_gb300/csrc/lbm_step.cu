@@ -54,7 +54,11 @@ __global__ void __launch_bounds__(256) k_step(Domain<R> d) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
-  update_cell<Q, S, R, ODD, FORCE, SR>(d, static_cast<S*>(d.f), x, y, z);
+  // a 32-wide x-range containing x; it is the calling warp's range when
+  // blockDim.x is a multiple of 32 (then the path choice is warp-uniform)
+  const int x_lo = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  const int x_hi = x_lo + 31;
+  update_cell<Q, S, R, ODD, FORCE, SR>(d, static_cast<S*>(d.f), x, y, z, x_lo, x_hi);
 }
 
 template <int Q, typename S, typename R, bool SR>

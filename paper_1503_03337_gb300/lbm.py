@@ -82,6 +82,7 @@ SIGNATURES = {
     "lbm_reductions": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_read_stats": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_memory_bytes": (_I, [_VP, ctypes.POINTER(_I64)]),
+    "lbm_set_block": (_I, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -217,6 +218,10 @@ def lbm_read_stats(h):
     s = lbm_stats()
     _check(load().lbm_read_stats(h, ctypes.byref(s)))
     return s
+
+
+def lbm_set_block(h, bx, by):
+    _check(load().lbm_set_block(h, int(bx), int(by)))
 
 
 def lbm_memory_bytes(h):
