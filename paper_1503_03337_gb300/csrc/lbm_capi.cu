@@ -3,8 +3,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 
 #include "lbm_internal.h"
 
@@ -446,9 +449,88 @@ int lbm_read_stats(lbm_handle* h, lbm_stats* out) {
 
 int lbm_set_block(lbm_handle* h, int32_t bx, int32_t by) {
   if (int rc = check(h)) return rc;
-  if (bx < 32 || bx % 32 != 0 || by < 1 || (int64_t)bx * by > 1024)
-    return fail(LBM_EINVAL, "block must be bx (multiple of 32) x by with bx*by <= 1024");
+  if (bx < 32 || bx % 32 != 0 || by < 1 || (int64_t)bx * by > 256)
+    return fail(LBM_EINVAL, "block must be bx (multiple of 32) x by with bx*by <= 256");
   h->block = {bx, by};
+  return LBM_OK;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, std::pair<BlockShape, double>> g_tune_cache;
+
+const BlockShape kCandidates[] = {{32, 1}, {32, 2}, {32, 4}, {32, 8},  {64, 1},
+                                  {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+}  // namespace
+
+int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, double* ms) {
+  if (int rc = check(h)) return rc;
+  DeviceGuard dg(h->device);
+  const auto key = std::make_tuple(h->d.Q, h->d.storage, h->d.nx, h->d.ny, h->d.nz);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end() && trials <= 0) {
+      h->block = it->second.first;
+      if (bx) *bx = h->block.bx;
+      if (by) *by = h->block.by;
+      if (ms) *ms = it->second.second;
+      return LBM_OK;
+    }
+  }
+  if (trials <= 0) trials = 8;
+  trials += trials & 1;  // even: equal numbers of even and odd steps
+  const size_t fbytes = (size_t)h->d.N * h->d.Q * storage_bytes(h->d.storage);
+  void* saved = nullptr;
+  cudaError_t e = cudaMalloc(&saved, fbytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LBM_ENOMEM, "autotune: no memory for the saved state");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = LBM_OK;
+  e = cudaMemcpyAsync(saved, h->d.f, fbytes, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  BlockShape best = h->block;
+  double best_ms = 1e300;
+  const int64_t n0 = h->n;
+  const int xmax = ((h->d.nx + 31) / 32) * 32;
+  for (const BlockShape& b : kCandidates) {
+    if (e != cudaSuccess) break;
+    if (b.bx > xmax && b.bx > 32) continue;
+    int64_t n = n0;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->d, n++, b, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < trials && e == cudaSuccess; ++k) e = launch_step(h->d, n++, b, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess && t / trials < best_ms) {
+      best_ms = t / trials;
+      best = b;
+    }
+    // back to the saved state (and parity) before the next candidate
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->d.f, saved, fbytes, cudaMemcpyDeviceToDevice, h->stream);
+  }
+  if (e != cudaSuccess) rc = cuda_fail(e, "autotune");
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "autotune synchronize");
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(saved);
+  h->n = n0;
+  if (rc) return rc;
+  h->block = best;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {best, best_ms};
+  }
+  if (bx) *bx = best.bx;
+  if (by) *by = best.by;
+  if (ms) *ms = best_ms;
   return LBM_OK;
 }
 

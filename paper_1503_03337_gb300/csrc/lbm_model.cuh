@@ -383,11 +383,9 @@ struct Rates {
 
 // ---------------------------------------------------------------------------
 // Streaming back-transform: a relaxed row x_K (already divided by D_K) is
-// added into the per-pair accumulators E (even rows) or O (odd rows) as soon
-// as it is known, so no moment array stays live.  Rows are processed in
-// index order; row 0 (P) never contributes and rows 2, 4, 6 (j) contribute
-// only with a force.  `touched` tells at compile time whether an accumulator
-// already holds a value, so its first contribution is a plain product.
+// subtracted from the per-pair accumulators E (even rows) or O (odd rows) as
+// soon as it is known, so no moment array stays live.  Row 0 (P) never
+// contributes and rows 2, 4, 6 (j) contribute only with a force.
 // ---------------------------------------------------------------------------
 template <int Q, bool FORCE>
 __host__ __device__ constexpr bool row_active(int k) {
@@ -410,8 +408,7 @@ __host__ __device__ __forceinline__ void add_row(R xk, R* E, R* O) {
     constexpr bool EV = row_even<Q>(K);
     if constexpr (C != 0) {
       R& acc = EV ? E[I] : O[I];
-      if constexpr (touched<Q, FORCE>(I, K, EV)) acc = term_add<C>(acc, xk);
-      else acc = term_first<C>(xk);
+      acc = term_add<-C>(acc, xk);
     }
     add_row<Q, FORCE, K, I + 1>(xk, E, O);
   }
@@ -488,8 +485,13 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
   const R hnu = R(1) - R(0.5) * s.snu;
   const R he = R(1) - R(0.5) * s.se;
 
-  // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K, streamed into E / O
+  // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K, streamed into the pair
+  // accumulators E = s/2 - sum_even phi x and O = d/2 - sum_odd phi x, so
+  // that f*_rep = E + O and f*_partner = E - O at the end
   R E[NP], O[NP];
+  [&]<int... I>(std::integer_sequence<int, I...>) {
+    ((E[I] = R(0.5) * ps[I], O[I] = R(0.5) * pd[I]), ...);
+  }(std::make_integer_sequence<int, NP>{});
   auto row = [&]<int K>(R xk) {
     add_row<Q, FORCE, K>(xk * R(1.0 / row_norm<Q>(K)), E, O);
   };
@@ -571,12 +573,9 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
     row.template operator()<16>(s.st * m.template operator()<16>());
     row.template operator()<17>(s.st * m.template operator()<17>());
   }
-  // f*_rep = f_rep - (E + O), f*_partner = f_partner - (E - O), with
-  // f_rep = (s + d)/2 and f_partner = (s - d)/2
+  // f*_rep = f_rep - (E + O)_rows = E + O, f*_partner = E - O
   [&]<int... I>(std::integer_sequence<int, I...>) {
-    ((f[pair_rep<Q>(I)] = R(0.5) * (ps[I] + pd[I]) - (E[I] + O[I]),
-      f[opposite<Q>(pair_rep<Q>(I))] = R(0.5) * (ps[I] - pd[I]) - (E[I] - O[I])),
-     ...);
+    ((f[pair_rep<Q>(I)] = E[I] + O[I], f[opposite<Q>(pair_rep<Q>(I))] = E[I] - O[I]), ...);
   }(std::make_integer_sequence<int, NP>{});
 }
 

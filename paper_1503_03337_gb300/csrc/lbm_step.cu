@@ -49,7 +49,7 @@ uint32_t step_key(int64_t n) {
 }
 
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
-__global__ void __launch_bounds__(256) k_step(Domain<R> d) {
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> d) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;

@@ -83,6 +83,8 @@ SIGNATURES = {
     "lbm_read_stats": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_memory_bytes": (_I, [_VP, ctypes.POINTER(_I64)]),
     "lbm_set_block": (_I, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_autotune": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -222,6 +224,14 @@ def lbm_read_stats(h):
 
 def lbm_set_block(h, bx, by):
     _check(load().lbm_set_block(h, int(bx), int(by)))
+
+
+def lbm_autotune(h, trials=8):
+    """Returns (bx, by, ms_per_step) of the fastest block shape."""
+    bx, by, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().lbm_autotune(h, int(trials), ctypes.byref(bx), ctypes.byref(by),
+                               ctypes.byref(ms)))
+    return bx.value, by.value, ms.value
 
 
 def lbm_memory_bytes(h):

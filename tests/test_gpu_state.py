@@ -153,3 +153,31 @@ def test_full_size_mass_conserved():
     finally:
         lbm.lbm_destroy(h)
     assert abs(s1.sum_P - s0.sum_P) <= 1e-12 * abs(s0.sum_P) + 1e-9
+
+
+@pytest.mark.parametrize("storage", ("f32", "f16"))
+def test_autotune_keeps_state_and_results(storage):
+    """The autotuner restores populations and step counter, and the block
+    shape it picks changes speed only: results stay bit-identical."""
+    case = inputs.cavity(18, 40, 200.0, storage=storage)
+    a = gpu_open(case)
+    b = gpu_open(case)
+    try:
+        for h in (a, b):
+            lbm.lbm_init_equilibrium(h)
+            lbm.lbm_step(h, 31)
+        f0 = lbm.read_populations(a, 18, 40, 40, 40)
+        bx, by, ms = lbm.lbm_autotune(a, 6)
+        assert bx % 32 == 0 and bx * by <= 256 and ms > 0
+        assert lbm.lbm_get_step(a) == 31
+        np.testing.assert_array_equal(lbm.read_populations(a, 18, 40, 40, 40), f0)
+        lbm.lbm_set_block(b, 32, 8 if (bx, by) != (32, 8) else 1)
+        lbm.lbm_step(a, 25)
+        lbm.lbm_step(b, 25)
+        np.testing.assert_array_equal(lbm.read_populations(a, 18, 40, 40, 40),
+                                      lbm.read_populations(b, 18, 40, 40, 40))
+        # cached choice is reused without timing
+        assert lbm.lbm_autotune(b, 0)[:2] == (bx, by)
+    finally:
+        lbm.lbm_destroy(a)
+        lbm.lbm_destroy(b)
