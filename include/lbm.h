@@ -207,6 +207,47 @@ int lbm_set_block(lbm_handle *h, int32_t bx, int32_t by);
 int lbm_autotune(lbm_handle *h, int32_t trials, int32_t *bx, int32_t *by,
                  double *ms_per_step);
 
+/* ---- allocation-free reductions ------------------------------------------ */
+
+/* The FP64 reductions of lbm_reductions for callers that cannot call
+ * cudaMalloc.  The paper has no counterpart; this is a deployment aid.
+ * Such callers include code whose device memory belongs to another
+ * allocator with a fixed budget, latency-critical loops that must not pay
+ * for cudaMalloc/cudaFree (cudaFree synchronises the whole device), and host
+ * code running where CUDA allocation calls are not allowed.  Nothing is
+ * allocated: the caller passes every input and output, and the only scratch
+ * (one FP64 partial per thread block plus the final statistics, 983,160
+ * bytes) is a static device array that each GPU loading the library keeps
+ * until the process exits.
+ *   desc, geom, params: the domain, as for lbm_create / set_geometry /
+ *       set_params (host structs; rates are not used).
+ *   step: the step counter n the populations belong to (its parity selects
+ *       the storage layout; F(t_n) enters u).
+ *   populations: device buffer of Q*N values of desc->storage in the
+ *       library's storage layout at step n (for even n: canonical
+ *       populations, [a][cell]).
+ *   u_prev: device buffer of 3*N doubles, or NULL.  If non-NULL it receives
+ *       the current velocity (the next call's snapshot), and if also
+ *       prev_step >= 0 the residual sums compare against its old contents,
+ *       which the caller states were taken at prev_step.
+ *   out: host struct, filled as by lbm_reductions.
+ *   cuda_stream: cudaStream_t the work runs on (NULL = legacy stream);
+ *       the call synchronises it.
+ * Limits: N = nx*ny*nz <= 2,097,152 cells (128^3); larger domains are
+ * rejected with LBM_EINVAL and a message naming the limit.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the same static
+ * array: each call overwrites everything it reads, so nothing needs
+ * clearing, but calls whose GPU work overlaps (e.g. on two streams at once)
+ * race on it and must be serialised by the caller.
+ * Errors: EINVAL (null pointer, bad sizes, kinds or storage; N too large),
+ * ECUDA. */
+int lbm_reductions_static(const lbm_desc *desc, const lbm_geom *geom,
+                          const lbm_params *params, int64_t step, const void *populations,
+                          double *u_prev, int64_t prev_step, lbm_stats *out,
+                          void *cuda_stream);
+
 /* Device memory the handle holds, in bytes. */
 int lbm_memory_bytes(lbm_handle *h, int64_t *bytes);
 

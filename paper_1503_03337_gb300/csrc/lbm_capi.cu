@@ -130,6 +130,8 @@ int check(lbm_handle* h) {
 
 }  // namespace
 
+void lbm::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 extern "C" {
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }

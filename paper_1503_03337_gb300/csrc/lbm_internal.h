@@ -39,6 +39,9 @@ struct BlockShape {
 
 BlockShape default_block(int nx, int ny);
 
+// Message returned by lbm_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
+
 // F(t_n) of a domain.
 void force_at(const DomainDesc& d, int64_t n, double F[3]);
 

@@ -85,6 +85,9 @@ SIGNATURES = {
     "lbm_set_block": (_I, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "lbm_autotune": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
+    "lbm_reductions_static": (_I, [ctypes.POINTER(lbm_desc), ctypes.POINTER(lbm_geom),
+                                   ctypes.POINTER(lbm_params), _I64, _VP, _VP, _I64,
+                                   ctypes.POINTER(lbm_stats), _VP]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -232,6 +235,19 @@ def lbm_autotune(h, trials=8):
     _check(load().lbm_autotune(h, int(trials), ctypes.byref(bx), ctypes.byref(by),
                                ctypes.byref(ms)))
     return bx.value, by.value, ms.value
+
+
+def lbm_reductions_static(Q, nx, ny, nz, storage, faces, u_wall, params, step,
+                          populations, u_prev=None, prev_step=-1, stream=None):
+    """Allocation-free FP64 reductions over caller-owned device buffers
+    (populations in the storage layout of `step`, optional 3N snapshot)."""
+    d = lbm_desc(Q, nx, ny, nz, STORAGE_NAMES.get(storage, storage))
+    g = make_geom(faces, u_wall)
+    s = lbm_stats()
+    _check(load().lbm_reductions_static(ctypes.byref(d), ctypes.byref(g), ctypes.byref(params),
+                                        int(step), _ptr(populations), _ptr(u_prev),
+                                        int(prev_step), ctypes.byref(s), stream))
+    return s
 
 
 def lbm_memory_bytes(h):
