@@ -32,7 +32,23 @@ struct Domain {
   Rates<R> s;
   R F[3];            // body force at the step's time level t_n
   uint32_t key;      // per-step key of the stochastic-rounding hash
+  // Element offsets from a cell's slot 0 (index i) used by interior cells
+  // on odd steps:
+  //   pull[a] = abar*N - s(c_a)     (where f_a(x) is read)
+  //   push[a] = a*N + s(c_a)        (where f*_a(x) is written)
+  // with s(c) = cx + cy*nx + cz*nx*ny.  Filled by fill_offsets().
+  int pull[18], push[18];
 };
+
+template <int Q, typename R>
+__host__ __device__ inline void fill_offsets(Domain<R>& d) {
+  const int N = (int)d.N, sy = d.nx, sz = d.nx * d.ny;
+  for (int a = 0; a < Q; ++a) {
+    const int s = Lattice<Q>::c(a, 0) + Lattice<Q>::c(a, 1) * sy + Lattice<Q>::c(a, 2) * sz;
+    d.pull[a] = opposite<Q>(a) * N - s;
+    d.push[a] = a * N + s;
+  }
+}
 
 // c . u_wall for a ghost node beyond the faces in `beyond`: the first
 // moving face in x-, x+, y-, y+, z-, z+ order wins (edge and corner ghosts of
@@ -57,6 +73,7 @@ __host__ __device__ __forceinline__ R ghost_dot(const Domain<R>& d, int beyond, 
 struct Links {
   int om[3], op[3];
   bool gm[3], gp[3];
+  bool interior;  // every neighbour is a fluid, unwrapped node: use pull/push
 };
 
 template <typename R>
@@ -76,6 +93,7 @@ __host__ __device__ __forceinline__ Links make_links(const Domain<R>& d, int x, 
   axis_links<R>(x, d.nx, 1, d.per[0], L.om[0], L.op[0], L.gm[0], L.gp[0]);
   axis_links<R>(y, d.ny, sy, d.per[1], L.om[1], L.op[1], L.gm[1], L.gp[1]);
   axis_links<R>(z, d.nz, sz, d.per[2], L.om[2], L.op[2], L.gm[2], L.gp[2]);
+  L.interior = false;
   return L;
 }
 
@@ -91,6 +109,7 @@ __host__ __device__ __forceinline__ Links make_links_interior(const Domain<R>& d
   L.om[2] = -sz;
   L.op[2] = sz;
   L.gm[0] = L.gp[0] = L.gm[1] = L.gp[1] = L.gm[2] = L.gp[2] = false;
+  L.interior = true;
   return L;
 }
 
@@ -106,6 +125,7 @@ __host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x
   L.om[2] = -sz;
   L.op[2] = sz;
   L.gm[1] = L.gp[1] = L.gm[2] = L.gp[2] = false;
+  L.interior = false;
   return L;
 }
 
@@ -154,10 +174,14 @@ template <int Q, typename S, typename R, bool ODD>
 __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
                                                 int i, const Links& L, R* fv) {
   const int N = (int)d.N;
+  const S* __restrict__ fc = f + i;
   if constexpr (!ODD) {
-    const S* __restrict__ fc = f + i;
     [&]<int... A>(std::integer_sequence<int, A...>) {
       ((fv[A] = Codec<S, R>::load(fc + (size_t)A * d.N)), ...);
+    }(std::make_integer_sequence<int, Q>{});
+  } else if (L.interior) {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      ((fv[A] = Codec<S, R>::load(fc + d.pull[A])), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
     // f_a(x) = A[abar][x - c_a], or A[a][x] if x - c_a is a ghost
@@ -204,10 +228,14 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
                                                  int i, const Links& L, R* fv) {
   const int N = (int)d.N;
   const uint32_t h = SR ? mix32(uint32_t(i) ^ d.key) : 0u;
+  S* __restrict__ fc = f + i;
   if constexpr (!ODD) {
-    S* __restrict__ fc = f + i;
     [&]<int... A>(std::integer_sequence<int, A...>) {
       ((put<S, R, SR, A>(fc + (size_t)opposite<Q>(A) * d.N, fv[A], h)), ...);
+    }(std::make_integer_sequence<int, Q>{});
+  } else if (L.interior) {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      ((put<S, R, SR, A>(fc + d.push[A], fv[A], h)), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
     if (d.moving && touches_moving(d, L)) {

@@ -8,7 +8,7 @@ namespace lbm {
 
 template <typename R>
 Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
-  Domain<R> o;
+  Domain<R> o{};
   o.f = d.f;
   o.nx = d.nx;
   o.ny = d.ny;
@@ -26,6 +26,8 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
   o.s.st = R(d.s[5]);
   for (int k = 0; k < 3; ++k) o.F[k] = R(F[k]);
   o.key = 0;
+  if (d.Q == 14) fill_offsets<14>(o);
+  else fill_offsets<18>(o);
   return o;
 }
 template Domain<double> to_domain<double>(const DomainDesc&, const double*);

@@ -14,7 +14,7 @@ static int g_sr = 0;
 template <int Q, typename S, typename R>
 static void step_typed(void* f, int nx, int ny, int nz, const int* per, int moving,
                        const double* uw, const double* s, const double* F, int64_t n) {
-  Domain<R> d;
+  Domain<R> d{};
   d.f = f;
   d.nx = nx; d.ny = ny; d.nz = nz;
   d.N = (int64_t)nx * ny * nz;
@@ -26,23 +26,26 @@ static void step_typed(void* f, int nx, int ny, int nz, const int* per, int movi
   d.s.snu = R(s[3]); d.s.spi = R(s[4]); d.s.st = R(s[5]);
   for (int k = 0; k < 3; ++k) d.F[k] = R(F[k]);
   d.key = mix32(0x5eedu ^ uint32_t(n) * 0x632be5abu);
+  fill_offsets<Q>(d);
   const bool force = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0;
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
+        // the 32-wide x-range a warp of a 32-multiple-wide block would cover
+        const int xl = x & ~31, xh = xl + 31;
         if constexpr (Stochastic<S>::enabled) {
           if (g_sr) {
-            if (n & 1) update_cell<Q, S, R, true, true, true>(d, static_cast<S*>(f), x, y, z);
-            else update_cell<Q, S, R, false, true, true>(d, static_cast<S*>(f), x, y, z);
+            if (n & 1) update_cell<Q, S, R, true, true, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
+            else update_cell<Q, S, R, false, true, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
             continue;
           }
         }
         if (n & 1) {
-          if (force) update_cell<Q, S, R, true, true>(d, static_cast<S*>(f), x, y, z);
-          else update_cell<Q, S, R, true, false>(d, static_cast<S*>(f), x, y, z);
+          if (force) update_cell<Q, S, R, true, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
+          else update_cell<Q, S, R, true, false>(d, static_cast<S*>(f), x, y, z, xl, xh);
         } else {
-          if (force) update_cell<Q, S, R, false, true>(d, static_cast<S*>(f), x, y, z);
-          else update_cell<Q, S, R, false, false>(d, static_cast<S*>(f), x, y, z);
+          if (force) update_cell<Q, S, R, false, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
+          else update_cell<Q, S, R, false, false>(d, static_cast<S*>(f), x, y, z, xl, xh);
         }
       }
 }
@@ -54,6 +57,7 @@ static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int
   d.f = f;
   d.nx = nx; d.ny = ny; d.nz = nz;
   d.N = (int64_t)nx * ny * nz;
+  fill_offsets<Q>(d);
   d.moving = moving;
   for (int k = 0; k < 3; ++k) d.per[k] = per[k];
   for (int face = 0; face < 6; ++face)

@@ -103,6 +103,9 @@ EDGE = [
     ("thin_x_walls", (1, 4, 3), (1, 1, 2, 1, 0, 0)),
     ("two_cells", (2, 2, 2), (2, 2, 2, 2, 2, 2)),
     ("lid", (5, 6, 4), (1, 1, 1, 2, 1, 1)),
+    # wide enough for whole 32-cell x-ranges away from the x faces, which
+    # take the interior offset tables
+    ("wide_x", (70, 4, 3), (1, 2, 1, 2, 0, 0)),
 ]
 
 
