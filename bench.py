@@ -285,7 +285,7 @@ def run_gpu(a, rank, world, dist):
                 lbm.lbm_destroy(hv)
                 bpu = 2 * Q * STORAGE_BYTES[st]
                 variants["D3Q%d_%s" % (Q, st)] = {
-                    "block": [bv[0], bv[1]],
+                    "block": [bv[0], bv[1], bv[2]],
                     "glups": round(cv.cells / (tv * 1e-3) / 1e9, 3),
                     "hbm_gbs": round(bpu * cv.cells / (tv * 1e-3) / 1e9, 1),
                     "frac_of_measured_hbm": round(bpu * cv.cells / (tv * 1e-3) / 1e9 / peak, 4)}
@@ -310,7 +310,7 @@ def run_gpu(a, rank, world, dist):
                    "l2": "flushed between steps (256 MiB write), outside the event-timed region; "
                          "the flush also absorbs the write-back of the previous step's dirty lines, "
                          "see steady_state for back-to-back steps",
-                   "block": [block[0], block[1]],
+                   "block": [block[0], block[1]], "cells_per_thread": block[2],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": round(wall, 4)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

@@ -20,7 +20,7 @@ struct lbm_handle {
   lbm_geom geom{};
   lbm_params params{};
   int64_t n = 0;
-  BlockShape block{32, 8};
+  BlockShape block{32, 8, 1};
   // reductions
   double* u_prev = nullptr;     // 3*N snapshot, allocated on first use
   int have_prev = 0;
@@ -449,11 +449,15 @@ int lbm_read_stats(lbm_handle* h, lbm_stats* out) {
   return LBM_OK;
 }
 
-int lbm_set_block(lbm_handle* h, int32_t bx, int32_t by) {
+int lbm_set_block(lbm_handle* h, int32_t bx, int32_t by, int32_t cells_per_thread) {
   if (int rc = check(h)) return rc;
   if (bx < 32 || bx % 32 != 0 || by < 1 || (int64_t)bx * by > 256)
     return fail(LBM_EINVAL, "block must be bx (multiple of 32) x by with bx*by <= 256");
-  h->block = {bx, by};
+  if (cells_per_thread != 1 && cells_per_thread != 2)
+    return fail(LBM_EINVAL, "cells_per_thread must be 1 or 2");
+  if (cells_per_thread == 2 && h->d.storage == LBM_STORAGE_F64)
+    return fail(LBM_EINVAL, "two cells per thread needs FP32 arithmetic (not FP64 storage)");
+  h->block = {bx, by, cells_per_thread};
   return LBM_OK;
 }
 
@@ -461,11 +465,14 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, std::pair<BlockShape, double>> g_tune_cache;
 
-const BlockShape kCandidates[] = {{32, 1}, {32, 2}, {32, 4}, {32, 8},  {64, 1},
-                                  {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+const BlockShape kCandidates[] = {
+    {32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1}, {64, 1, 1}, {64, 2, 1}, {64, 4, 1},
+    {128, 1, 1}, {128, 2, 1}, {256, 1, 1}, {32, 1, 2}, {32, 2, 2}, {32, 4, 2}, {64, 1, 2},
+    {64, 2, 2}, {128, 1, 2}};
 }  // namespace
 
-int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, double* ms) {
+int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, int32_t* cpt,
+                 double* ms) {
   if (int rc = check(h)) return rc;
   DeviceGuard dg(h->device);
   const auto key = std::make_tuple(h->d.Q, h->d.storage, h->d.nx, h->d.ny, h->d.nz);
@@ -476,6 +483,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, double
       h->block = it->second.first;
       if (bx) *bx = h->block.bx;
       if (by) *by = h->block.by;
+      if (cpt) *cpt = h->block.cpt;
       if (ms) *ms = it->second.second;
       return LBM_OK;
     }
@@ -500,7 +508,8 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, double
   const int xmax = ((h->d.nx + 31) / 32) * 32;
   for (const BlockShape& b : kCandidates) {
     if (e != cudaSuccess) break;
-    if (b.bx > xmax && b.bx > 32) continue;
+    if (b.bx * b.cpt > xmax && b.bx > 32) continue;
+    if (b.cpt == 2 && h->d.storage == LBM_STORAGE_F64) continue;
     int64_t n = n0;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->d, n++, b, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
@@ -532,6 +541,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, double
   }
   if (bx) *bx = best.bx;
   if (by) *by = best.by;
+  if (cpt) *cpt = best.cpt;
   if (ms) *ms = best_ms;
   return LBM_OK;
 }

@@ -35,6 +35,7 @@ struct DomainDesc {
 
 struct BlockShape {
   int bx, by;
+  int cpt;  // cells per thread: 1, or 2 (pairs along x, FP32 arithmetic only)
 };
 
 BlockShape default_block(int nx, int ny);

@@ -302,6 +302,84 @@ __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __re
   }
 }
 
+// Two cells per thread (FP32 arithmetic, 4- or 2-byte storage): the cells
+// xa and xa + 32 of one x-row.  With a warp's lanes on xa = x_lo..x_lo+31 the
+// warp updates the 64 cells x_lo..x_lo+63, every load and store instruction
+// still touches 32 consecutive values, and the pair is collided together in
+// packed FP32 (one instruction for both cells).  Even steps and odd-step
+// warps whose 64 cells and all their neighbours are interior use the offset
+// tables; other odd-step warps resolve each cell's links separately.
+template <int Q, typename S, bool ODD, bool FORCE, bool SR>
+__device__ __forceinline__ void update_pair(const Domain<float>& d, S* __restrict__ f, int xa,
+                                            int y, int z, int x_lo) {
+  const int xb = xa + 32;
+  const bool vb = xb < d.nx;
+  const int ia = xa + d.nx * (y + d.ny * z);
+  const int ib = ia + 32;
+  const int N = (int)d.N;
+  bool simple = true;
+  bool yz = true;
+  if constexpr (ODD) {
+    yz = y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+    simple = yz && x_lo > 0 && x_lo + 63 < d.nx - 1;
+  }
+  pf2 fv[Q];
+  if (simple) {
+    const S* __restrict__ fa = f + ia;
+    const S* __restrict__ fb = f + ib;
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      (
+          [&] {
+            const int off = ODD ? d.pull[A] : A * N;
+            const float a = Codec<S, float>::load(fa + off);
+            const float b = vb ? Codec<S, float>::load(fb + off) : 0.0f;
+            fv[A] = pf2(a, b);
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, Q>{});
+  } else {
+    float ta[Q], tb[Q];
+    const Links La = yz ? make_links_x(d, xa) : make_links(d, xa, y, z);
+    gather<Q, S, float, true>(d, f, ia, La, ta);
+    if (vb) {
+      const Links Lb = yz ? make_links_x(d, xb) : make_links(d, xb, y, z);
+      gather<Q, S, float, true>(d, f, ib, Lb, tb);
+    } else {
+      for (int a = 0; a < Q; ++a) tb[a] = 0.0f;
+    }
+    for (int a = 0; a < Q; ++a) fv[a] = pf2(ta[a], tb[a]);
+  }
+  pf2 ux, uy, uz;
+  collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
+  if (simple) {
+    S* __restrict__ fa = f + ia;
+    S* __restrict__ fb = f + ib;
+    const uint32_t ha = SR ? mix32(uint32_t(ia) ^ d.key) : 0u;
+    const uint32_t hb = SR ? mix32(uint32_t(ib) ^ d.key) : 0u;
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      (
+          [&] {
+            const int off = ODD ? d.push[A] : opposite<Q>(A) * N;
+            put<S, float, SR, A>(fa + off, fv[A].v.x, ha);
+            if (vb) put<S, float, SR, A>(fb + off, fv[A].v.y, hb);
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, Q>{});
+  } else {
+    float ta[Q], tb[Q];
+    for (int a = 0; a < Q; ++a) {
+      ta[a] = fv[a].v.x;
+      tb[a] = fv[a].v.y;
+    }
+    const Links La = yz ? make_links_x(d, xa) : make_links(d, xa, y, z);
+    scatter<Q, S, float, true, SR>(d, f, ia, La, ta);
+    if (vb) {
+      const Links Lb = yz ? make_links_x(d, xb) : make_links(d, xb, y, z);
+      scatter<Q, S, float, true, SR>(d, f, ib, Lb, tb);
+    }
+  }
+}
+
 // Inverse of gather: put canonical pre-collision values fv of cell (x,y,z)
 // where the step parity keeps them (checkpoint restore / init).
 template <int Q, typename S, typename R, bool ODD>

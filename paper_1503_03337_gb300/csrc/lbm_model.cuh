@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <utility>
@@ -307,19 +308,84 @@ struct Stochastic<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------------------
+// Two cells per thread: a packed pair of FP32 values.  On the device every
+// add, multiply and multiply-add is one packed FP32x2 instruction
+// (__fadd2_rn / __fmul2_rn / __ffma2_rn of sm_100 and later), so the
+// collision of two cells costs the instructions of one.  Arithmetic stays
+// IEEE FP32, rounded to nearest, per component.
+// ---------------------------------------------------------------------------
+// (The scalar branches serve host builds of this header; device code is
+// only ever built for sm_103a.)
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define LBM_PACKED_F32X2 1
+#else
+#define LBM_PACKED_F32X2 0
+#endif
+
+struct pf2 {
+  float2 v;
+  pf2() = default;
+  __host__ __device__ pf2(float s) : v(make_float2(s, s)) {}  // broadcast
+  __host__ __device__ pf2(float a, float b) : v(make_float2(a, b)) {}
+};
+
+__host__ __device__ __forceinline__ pf2 pf2_from(float2 v) {
+  pf2 r;
+  r.v = v;
+  return r;
+}
+__host__ __device__ __forceinline__ pf2 operator+(pf2 a, pf2 b) {
+#if LBM_PACKED_F32X2
+  return pf2_from(__fadd2_rn(a.v, b.v));
+#else
+  return pf2(a.v.x + b.v.x, a.v.y + b.v.y);
+#endif
+}
+__host__ __device__ __forceinline__ pf2 operator*(pf2 a, pf2 b) {
+#if LBM_PACKED_F32X2
+  return pf2_from(__fmul2_rn(a.v, b.v));
+#else
+  return pf2(a.v.x * b.v.x, a.v.y * b.v.y);
+#endif
+}
+// a * b + c
+__host__ __device__ __forceinline__ pf2 fmadd(pf2 a, pf2 b, pf2 c) {
+#if LBM_PACKED_F32X2
+  return pf2_from(__ffma2_rn(a.v, b.v, c.v));
+#else
+  return pf2(std::fma(a.v.x, b.v.x, c.v.x), std::fma(a.v.y, b.v.y, c.v.y));
+#endif
+}
+__host__ __device__ __forceinline__ pf2 operator-(pf2 a, pf2 b) {
+  return fmadd(b, pf2(-1.0f), a);
+}
+__host__ __device__ __forceinline__ pf2 operator-(pf2 a) { return a * pf2(-1.0f); }
+__host__ __device__ __forceinline__ pf2 operator*(float s, pf2 a) { return pf2(s) * a; }
+__host__ __device__ __forceinline__ pf2 operator*(pf2 a, float s) { return a * pf2(s); }
+__host__ __device__ __forceinline__ pf2 operator+(pf2 a, float s) { return a + pf2(s); }
+__host__ __device__ __forceinline__ pf2 operator-(pf2 a, float s) { return a - pf2(s); }
+__host__ __device__ __forceinline__ pf2& operator+=(pf2& a, pf2 b) { return a = a + b; }
+__host__ __device__ __forceinline__ pf2& operator-=(pf2& a, pf2 b) { return a = a - b; }
+
+__host__ __device__ __forceinline__ float fmadd(float a, float b, float c) { return a * b + c; }
+__host__ __device__ __forceinline__ double fmadd(double a, double b, double c) {
+  return a * b + c;
+}
+
+// ---------------------------------------------------------------------------
 // Unrolled transforms over pairs
 // ---------------------------------------------------------------------------
-template <int C, typename R>
-__host__ __device__ __forceinline__ R term_first(R x) {
+template <int C, typename V>
+__host__ __device__ __forceinline__ V term_first(V x) {
   if constexpr (C == 1) return x;
   else if constexpr (C == -1) return -x;
-  else return R(C) * x;
+  else return V(C) * x;
 }
-template <int C, typename R>
-__host__ __device__ __forceinline__ R term_add(R acc, R x) {
+template <int C, typename V>
+__host__ __device__ __forceinline__ V term_add(V acc, V x) {
   if constexpr (C == 1) return acc + x;
   else if constexpr (C == -1) return acc - x;
-  else return acc + R(C) * x;
+  else return fmadd(V(C), x, acc);
 }
 
 // m_K = sum_i phi_K(rep_i) v_i, with v = pair sums (even K) or differences.
@@ -436,11 +502,13 @@ static_assert(accumulators_covered<14, false>() && accumulators_covered<14, true
 // momentum rows whatever s_c is.
 // On return f holds f*, and (ux,uy,uz) the velocity of the pre-collision state.
 // ---------------------------------------------------------------------------
-template <int Q, bool FORCE, typename R>
-__host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, R Fy,
-                                                 R Fz, R& ux, R& uy, R& uz) {
+// V is the value type (float, double, or pf2 for two cells at once) and R
+// the scalar type of rates, force and constants.
+template <int Q, bool FORCE, typename V, typename R>
+__host__ __device__ __forceinline__ void collide(V* f, const Rates<R>& s, R Fx, R Fy,
+                                                 R Fz, V& ux, V& uy, V& uz) {
   constexpr int NP = Q / 2;
-  R ps[NP], pd[NP];
+  V ps[NP], pd[NP];
   // pair sums and differences; f itself is not needed again
   [&]<int... I>(std::integer_sequence<int, I...>) {
     ((ps[I] = f[pair_rep<Q>(I)] + f[opposite<Q>(pair_rep<Q>(I))],
@@ -449,10 +517,10 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
   }(std::make_integer_sequence<int, NP>{});
 
   // conserved moments, velocity (Eq. hgl with the force half step), pressure
-  const R P = row_sum<Q, 0, 0, false>(R(0), ps);
-  const R jx = row_sum<Q, 2, 0, false>(R(0), pd);
-  const R jy = row_sum<Q, 4, 0, false>(R(0), pd);
-  const R jz = row_sum<Q, 6, 0, false>(R(0), pd);
+  const V P = row_sum<Q, 0, 0, false>(V(R(0)), ps);
+  const V jx = row_sum<Q, 2, 0, false>(V(R(0)), pd);
+  const V jy = row_sum<Q, 4, 0, false>(V(R(0)), pd);
+  const V jz = row_sum<Q, 6, 0, false>(V(R(0)), pd);
   if constexpr (FORCE) {
     ux = jx + R(0.5) * Fx;
     uy = jy + R(0.5) * Fy;
@@ -462,17 +530,17 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
     uy = jy;
     uz = jz;
   }
-  const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
-  const R u2 = uxx + uyy + uzz;
+  const V uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+  const V u2 = uxx + uyy + uzz;
   constexpr double cs2 = 1.0 / 3.0;
   constexpr double w0 = Lattice<Q>::w0;
-  const R p = R(cs2 / (1.0 - w0)) * (P - R(w0 / (2.0 * cs2)) * u2);
+  const V p = R(cs2 / (1.0 - w0)) * (P - R(w0 / (2.0 * cs2)) * u2);
 
-  const R uxy = ux * uy, uyz = uy * uz, uxz = ux * uz;
-  const R pxx_eq = R(3) * uxx - u2;  // 3 p_xx
-  const R pww_eq = uyy - uzz;
+  const V uxy = ux * uy, uyz = uy * uz, uxz = ux * uz;
+  const V pxx_eq = R(3) * uxx - u2;  // 3 p_xx
+  const V pww_eq = uyy - uzz;
   // force terms: derivative along F of the quadratic equilibria
-  R uF = R(0), sxx = R(0), sww = R(0), sxy = R(0), syz = R(0), sxz = R(0);
+  V uF = V(R(0)), sxx = V(R(0)), sww = V(R(0)), sxy = V(R(0)), syz = V(R(0)), sxz = V(R(0));
   if constexpr (FORCE) {
     uF = ux * Fx + uy * Fy + uz * Fz;
     sxx = R(6) * ux * Fx - R(2) * uF;
@@ -488,18 +556,18 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
   // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K, streamed into the pair
   // accumulators E = s/2 - sum_even phi x and O = d/2 - sum_odd phi x, so
   // that f*_rep = E + O and f*_partner = E - O at the end
-  R E[NP], O[NP];
+  V E[NP], O[NP];
   [&]<int... I>(std::integer_sequence<int, I...>) {
     ((E[I] = R(0.5) * ps[I], O[I] = R(0.5) * pd[I]), ...);
   }(std::make_integer_sequence<int, NP>{});
-  auto row = [&]<int K>(R xk) {
+  auto row = [&]<int K>(V xk) {
     add_row<Q, FORCE, K>(xk * R(1.0 / row_norm<Q>(K)), E, O);
   };
   auto m = [&]<int K>() {
-    if constexpr (row_even<Q>(K)) return row_sum<Q, K, 0, false>(R(0), ps);
-    else return row_sum<Q, K, 0, false>(R(0), pd);
+    if constexpr (row_even<Q>(K)) return row_sum<Q, K, 0, false>(V(R(0)), ps);
+    else return row_sum<Q, K, 0, false>(V(R(0)), pd);
   };
-  R x1;
+  V x1;
   if constexpr (Q == 14) {
     // e_eq = -7p + u^2 (source 2 u.F)
     x1 = s.se * (m.template operator()<1>() - (R(-7) * p + u2));
@@ -511,15 +579,15 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
   }
   row.template operator()<1>(x1);
   if constexpr (FORCE) {  // momentum rows: s_c (j - u) - (1 - s_c/2) F = -F
-    row.template operator()<2>(-Fx);
-    row.template operator()<4>(-Fy);
-    row.template operator()<6>(-Fz);
+    row.template operator()<2>(V(-Fx));
+    row.template operator()<4>(V(-Fy));
+    row.template operator()<6>(V(-Fz));
   }
   // q_eq = -7u/3 (Q14) or -2u/3 (Q18); sources -7F/3 or -2F/3
   constexpr double cq = Q == 14 ? 7.0 / 3.0 : 2.0 / 3.0;
-  R x3 = s.sq * (m.template operator()<3>() + R(cq) * ux);
-  R x5 = s.sq * (m.template operator()<5>() + R(cq) * uy);
-  R x7 = s.sq * (m.template operator()<7>() + R(cq) * uz);
+  V x3 = s.sq * (m.template operator()<3>() + R(cq) * ux);
+  V x5 = s.sq * (m.template operator()<5>() + R(cq) * uy);
+  V x7 = s.sq * (m.template operator()<7>() + R(cq) * uz);
   if constexpr (FORCE) {
     x3 += hq * (R(cq) * Fx);
     x5 += hq * (R(cq) * Fy);
@@ -529,44 +597,44 @@ __host__ __device__ __forceinline__ void collide(R* f, const Rates<R>& s, R Fx, 
   row.template operator()<5>(x5);
   row.template operator()<7>(x7);
   if constexpr (Q == 14) {
-    R x8 = s.snu * (m.template operator()<8>() - pxx_eq);
+    V x8 = s.snu * (m.template operator()<8>() - pxx_eq);
     if constexpr (FORCE) x8 -= hnu * sxx;
     row.template operator()<8>(x8);
-    R x9 = s.snu * (m.template operator()<9>() - pww_eq);
+    V x9 = s.snu * (m.template operator()<9>() - pww_eq);
     if constexpr (FORCE) x9 -= hnu * sww;
     row.template operator()<9>(x9);
-    R x10 = s.snu * (m.template operator()<10>() - uxy);
+    V x10 = s.snu * (m.template operator()<10>() - uxy);
     if constexpr (FORCE) x10 -= hnu * sxy;
     row.template operator()<10>(x10);
-    R x11 = s.snu * (m.template operator()<11>() - uyz);
+    V x11 = s.snu * (m.template operator()<11>() - uyz);
     if constexpr (FORCE) x11 -= hnu * syz;
     row.template operator()<11>(x11);
-    R x12 = s.snu * (m.template operator()<12>() - uxz);
+    V x12 = s.snu * (m.template operator()<12>() - uxz);
     if constexpr (FORCE) x12 -= hnu * sxz;
     row.template operator()<12>(x12);
     row.template operator()<13>(s.st * m.template operator()<13>());
   } else {
     // 3pi_xx and pi_ww equilibria (and sources) are -1/2 of 3p_xx and p_ww
     const R hpi = R(1) - R(0.5) * s.spi;
-    R x8 = s.snu * (m.template operator()<8>() - pxx_eq);
+    V x8 = s.snu * (m.template operator()<8>() - pxx_eq);
     if constexpr (FORCE) x8 -= hnu * sxx;
     row.template operator()<8>(x8);
-    R x9 = s.spi * (m.template operator()<9>() + R(0.5) * pxx_eq);
+    V x9 = s.spi * (m.template operator()<9>() + R(0.5) * pxx_eq);
     if constexpr (FORCE) x9 += hpi * (R(0.5) * sxx);
     row.template operator()<9>(x9);
-    R x10 = s.snu * (m.template operator()<10>() - pww_eq);
+    V x10 = s.snu * (m.template operator()<10>() - pww_eq);
     if constexpr (FORCE) x10 -= hnu * sww;
     row.template operator()<10>(x10);
-    R x11 = s.spi * (m.template operator()<11>() + R(0.5) * pww_eq);
+    V x11 = s.spi * (m.template operator()<11>() + R(0.5) * pww_eq);
     if constexpr (FORCE) x11 += hpi * (R(0.5) * sww);
     row.template operator()<11>(x11);
-    R x12 = s.snu * (m.template operator()<12>() - uxy);
+    V x12 = s.snu * (m.template operator()<12>() - uxy);
     if constexpr (FORCE) x12 -= hnu * sxy;
     row.template operator()<12>(x12);
-    R x13 = s.snu * (m.template operator()<13>() - uyz);
+    V x13 = s.snu * (m.template operator()<13>() - uyz);
     if constexpr (FORCE) x13 -= hnu * syz;
     row.template operator()<13>(x13);
-    R x14 = s.snu * (m.template operator()<14>() - uxz);
+    V x14 = s.snu * (m.template operator()<14>() - uxz);
     if constexpr (FORCE) x14 -= hnu * sxz;
     row.template operator()<14>(x14);
     row.template operator()<15>(s.st * m.template operator()<15>());

@@ -43,7 +43,7 @@ BlockShape default_block(int nx, int ny) {
   while (bx < nx && bx < 128) bx *= 2;
   int by = 256 / bx;
   while (by > 1 && by / 2 >= ny) by /= 2;
-  return {bx, by};
+  return {bx, by, 1};
 }
 
 uint32_t step_key(int64_t n) {
@@ -63,9 +63,35 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> 
   update_cell<Q, S, R, ODD, FORCE, SR>(d, static_cast<S*>(d.f), x, y, z, x_lo, x_hi);
 }
 
+// Two cells per thread (see update_pair); blockDim.x threads cover
+// 2*blockDim.x cells of a row, each warp 64 consecutive cells.
+template <int Q, typename S, bool ODD, bool FORCE, bool SR>
+__global__ void __launch_bounds__(256, 2) k_step2(Domain<float> d) {
+  const int lane = threadIdx.x & 31;
+  const int x_lo = blockIdx.x * (2 * blockDim.x) + (threadIdx.x >> 5) * 64;
+  const int xa = x_lo + lane;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (xa >= d.nx || y >= d.ny) return;
+  update_pair<Q, S, ODD, FORCE, SR>(d, static_cast<S*>(d.f), xa, y, z, x_lo);
+}
+
 template <int Q, typename S, typename R, bool SR>
 static void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 block,
-                          cudaStream_t st) {
+                          int cpt, cudaStream_t st) {
+  if constexpr (sizeof(S) <= 4) {
+    if (cpt == 2) {
+      grid.x = (d.nx + 2 * block.x - 1) / (2 * block.x);
+      if (odd) {
+        if (force) k_step2<Q, S, true, true, SR><<<grid, block, 0, st>>>(d);
+        else k_step2<Q, S, true, false, SR><<<grid, block, 0, st>>>(d);
+      } else {
+        if (force) k_step2<Q, S, false, true, SR><<<grid, block, 0, st>>>(d);
+        else k_step2<Q, S, false, false, SR><<<grid, block, 0, st>>>(d);
+      }
+      return;
+    }
+  }
   if (odd) {
     if (force) k_step<Q, S, R, true, true, SR><<<grid, block, 0, st>>>(d);
     else k_step<Q, S, R, true, false, SR><<<grid, block, 0, st>>>(d);
@@ -88,11 +114,11 @@ static cudaError_t launch_typed(const DomainDesc& dd, int64_t n, BlockShape b,
   const bool odd = (n & 1) != 0;
   if constexpr (Stochastic<S>::enabled) {
     if (dd.rounding == LBM_ROUND_STOCHASTIC) {
-      launch_parity<Q, S, R, true>(d, odd, force, grid, block, st);
+      launch_parity<Q, S, R, true>(d, odd, force, grid, block, b.cpt, st);
       return cudaGetLastError();
     }
   }
-  launch_parity<Q, S, R, false>(d, odd, force, grid, block, st);
+  launch_parity<Q, S, R, false>(d, odd, force, grid, block, b.cpt, st);
   return cudaGetLastError();
 }
 

@@ -82,9 +82,10 @@ SIGNATURES = {
     "lbm_reductions": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_read_stats": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_memory_bytes": (_I, [_VP, ctypes.POINTER(_I64)]),
-    "lbm_set_block": (_I, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_set_block": (_I, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "lbm_autotune": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
-                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
+                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_double)]),
     "lbm_reductions_static": (_I, [ctypes.POINTER(lbm_desc), ctypes.POINTER(lbm_geom),
                                    ctypes.POINTER(lbm_params), _I64, _VP, _VP, _I64,
                                    ctypes.POINTER(lbm_stats), _VP]),
@@ -225,16 +226,16 @@ def lbm_read_stats(h):
     return s
 
 
-def lbm_set_block(h, bx, by):
-    _check(load().lbm_set_block(h, int(bx), int(by)))
+def lbm_set_block(h, bx, by, cells_per_thread=1):
+    _check(load().lbm_set_block(h, int(bx), int(by), int(cells_per_thread)))
 
 
 def lbm_autotune(h, trials=8):
-    """Returns (bx, by, ms_per_step) of the fastest block shape."""
-    bx, by, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    """Returns (bx, by, cells_per_thread, ms_per_step) of the fastest launch."""
+    bx, by, cpt, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(load().lbm_autotune(h, int(trials), ctypes.byref(bx), ctypes.byref(by),
-                               ctypes.byref(ms)))
-    return bx.value, by.value, ms.value
+                               ctypes.byref(cpt), ctypes.byref(ms)))
+    return bx.value, by.value, cpt.value, ms.value
 
 
 def lbm_reductions_static(Q, nx, ny, nz, storage, faces, u_wall, params, step,

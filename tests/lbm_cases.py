@@ -22,7 +22,7 @@ def oracle_run(case, steps, f0=None, n0=0):
     return {"f": f, "u": u, "p": p}
 
 
-def gpu_open(case, stream=None, residual_interval=0):
+def gpu_open(case, stream=None, residual_interval=0, launch=None):
     import torch
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
@@ -30,11 +30,13 @@ def gpu_open(case, stream=None, residual_interval=0):
     lbm.lbm_set_geometry(h, case.faces, case.u_wall)
     lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period,
                        residual_interval=residual_interval, rounding=case.rounding)
+    if launch is not None:
+        lbm.lbm_set_block(h, *launch)
     return h
 
 
-def gpu_run(case, steps, keep=False):
-    h = gpu_open(case)
+def gpu_run(case, steps, keep=False, launch=None):
+    h = gpu_open(case, launch=launch)
     try:
         u0 = None if case.init_u is None else np.ascontiguousarray(case.init_u, dtype=np.float64)
         p0 = None if case.init_p is None else np.ascontiguousarray(case.init_p, dtype=np.float64)

@@ -80,6 +80,29 @@ def test_fp64_edge_cases(Q, name, shape, faces, steps):
     assert rel_max(g["u"], o["u"]) <= 1e-12
 
 
+PAIR_CASES = EDGE + [
+    ("wide_rows", (200, 6, 5), (1, 2, 1, 2, 0, 0)),
+    ("wide_periodic", (131, 4, 4), (0, 0, 1, 1, 2, 1)),
+]
+
+
+@pytest.mark.parametrize("launch", ((32, 2, 2), (64, 1, 2), (32, 1, 1)))
+@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("name,shape,faces", PAIR_CASES)
+def test_fp32_launch_shapes(Q, name, shape, faces, launch):
+    """Every launch shape, including two cells per thread in packed FP32,
+    against the oracle from a seeded random state (odd step count)."""
+    rng = np.random.default_rng(hash((name, Q)) & 0xffff)
+    uw = rng.normal(size=(6, 3)) * 0.03
+    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
+                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f32",
+                       u_ref=0.03)
+    case.init_u, case.init_p = inputs.random_state(case, seed=3)
+    g, o = gpu_run(case, 37, launch=launch), oracle_run(case, 37)
+    assert rel_max(g["f"], o["f"]) <= 2e-6
+    assert np.max(np.abs(g["u"] - o["u"])) <= 1e-5 * case.u_ref
+
+
 @pytest.mark.parametrize("Q", (14, 18))
 def test_fp32_cavity(Q):
     case = inputs.cavity(Q, 32, 400.0, storage="f32")

@@ -167,17 +167,17 @@ def test_autotune_keeps_state_and_results(storage):
             lbm.lbm_init_equilibrium(h)
             lbm.lbm_step(h, 31)
         f0 = lbm.read_populations(a, 18, 40, 40, 40)
-        bx, by, ms = lbm.lbm_autotune(a, 6)
-        assert bx % 32 == 0 and bx * by <= 256 and ms > 0
+        bx, by, cpt, ms = lbm.lbm_autotune(a, 6)
+        assert bx % 32 == 0 and bx * by <= 256 and cpt in (1, 2) and ms > 0
         assert lbm.lbm_get_step(a) == 31
         np.testing.assert_array_equal(lbm.read_populations(a, 18, 40, 40, 40), f0)
-        lbm.lbm_set_block(b, 32, 8 if (bx, by) != (32, 8) else 1)
+        lbm.lbm_set_block(b, 32, 8 if (bx, by) != (32, 8) else 1, 3 - cpt)
         lbm.lbm_step(a, 25)
         lbm.lbm_step(b, 25)
         np.testing.assert_array_equal(lbm.read_populations(a, 18, 40, 40, 40),
                                       lbm.read_populations(b, 18, 40, 40, 40))
         # cached choice is reused without timing
-        assert lbm.lbm_autotune(b, 0)[:2] == (bx, by)
+        assert lbm.lbm_autotune(b, 0)[:3] == (bx, by, cpt)
     finally:
         lbm.lbm_destroy(a)
         lbm.lbm_destroy(b)
