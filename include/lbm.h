@@ -195,14 +195,17 @@ int lbm_read_stats(lbm_handle *h, lbm_stats *out);
 /* Launch shape of the step kernel: bx threads along x (a multiple of 32, so
  * that a warp never spans two x-rows) by by along y, bx*by <= 256, each
  * thread updating cells_per_thread cells: 1, or 2 (cells x and x+32 collided
- * together in packed FP32; not for FP64 storage).  Affects speed only, never
- * results.  EINVAL otherwise. */
+ * together in packed FP32; not for FP64 storage).  bx and by never change
+ * results; cells_per_thread changes where the compiler fuses multiply-adds,
+ * so results with 1 and 2 agree to FP32 rounding, not bit for bit.
+ * EINVAL otherwise. */
 int lbm_set_block(lbm_handle *h, int32_t bx, int32_t by, int32_t cells_per_thread);
 
 /* Autotuner: time the step kernel on this domain for each candidate launch
  * shape (block shape and cells per thread) (`trials` steps each, CUDA events on the handle's stream) and keep
  * the fastest.  The populations and step counter are saved before and
- * restored after, so results are unaffected; the choice is cached per
+ * restored after, so the state is unaffected (the chosen cells per thread
+ * sets the FP32 rounding pattern, see lbm_set_block); the choice is cached per
  * (Q, storage, nx, ny, nz) for later handles of the same shape.  trials <= 0
  * uses the cache only (or 8 trials on a miss).  Outputs may be NULL.
  * Synchronises; needs Q*N storage values of temporary device memory. */

@@ -157,13 +157,14 @@ def test_full_size_mass_conserved():
 
 @pytest.mark.parametrize("storage", ("f32", "f16"))
 def test_autotune_keeps_state_and_results(storage):
-    """The autotuner restores populations and step counter, and the block
-    shape it picks changes speed only: results stay bit-identical."""
+    """The autotuner restores populations and step counter.  The block shape
+    changes speed only (bit-identical results at equal cells per thread);
+    one versus two cells per thread agree to FP32 rounding."""
     case = inputs.cavity(18, 40, 200.0, storage=storage)
-    a = gpu_open(case)
-    b = gpu_open(case)
+    hs = [gpu_open(case) for _ in range(3)]
+    a, b, c = hs
     try:
-        for h in (a, b):
+        for h in hs:
             lbm.lbm_init_equilibrium(h)
             lbm.lbm_step(h, 31)
         f0 = lbm.read_populations(a, 18, 40, 40, 40)
@@ -171,13 +172,16 @@ def test_autotune_keeps_state_and_results(storage):
         assert bx % 32 == 0 and bx * by <= 256 and cpt in (1, 2) and ms > 0
         assert lbm.lbm_get_step(a) == 31
         np.testing.assert_array_equal(lbm.read_populations(a, 18, 40, 40, 40), f0)
-        lbm.lbm_set_block(b, 32, 8 if (bx, by) != (32, 8) else 1, 3 - cpt)
-        lbm.lbm_step(a, 25)
-        lbm.lbm_step(b, 25)
-        np.testing.assert_array_equal(lbm.read_populations(a, 18, 40, 40, 40),
-                                      lbm.read_populations(b, 18, 40, 40, 40))
+        lbm.lbm_set_block(b, 32, 8 if (bx, by) != (32, 8) else 1, cpt)
+        lbm.lbm_set_block(c, 64, 1, 3 - cpt)
+        for h in hs:
+            lbm.lbm_step(h, 25)
+        fa, fb, fc = (lbm.read_populations(h, 18, 40, 40, 40) for h in hs)
+        np.testing.assert_array_equal(fa, fb)
+        tol = 2e-6 if storage == "f32" else 2e-3
+        assert np.max(np.abs(fa - fc)) <= tol * np.max(np.abs(fa))
         # cached choice is reused without timing
         assert lbm.lbm_autotune(b, 0)[:3] == (bx, by, cpt)
     finally:
-        lbm.lbm_destroy(a)
-        lbm.lbm_destroy(b)
+        for h in hs:
+            lbm.lbm_destroy(h)
