@@ -169,7 +169,7 @@ def run_gpu(a, rank, world, dist):
         lbm.lbm_set_geometry(h, case.faces, case.u_wall)
         lbm.lbm_set_params(h, nu=case.nu, residual_interval=residual_interval)
         lbm.lbm_init_equilibrium(h)
-        block = lbm.lbm_autotune(h, a.tune_trials)  # restores the state it used
+        block, _ = lbm.lbm_autotune(h, a.tune_trials)  # restores the state it used
         return case, h, block
 
     def timed_steps(h, K, interval):
@@ -285,7 +285,7 @@ def run_gpu(a, rank, world, dist):
                 lbm.lbm_destroy(hv)
                 bpu = 2 * Q * STORAGE_BYTES[st]
                 variants["D3Q%d_%s" % (Q, st)] = {
-                    "block": [bv[0], bv[1], bv[2]],
+                    "launch": list(bv),
                     "glups": round(cv.cells / (tv * 1e-3) / 1e9, 3),
                     "hbm_gbs": round(bpu * cv.cells / (tv * 1e-3) / 1e9, 1),
                     "frac_of_measured_hbm": round(bpu * cv.cells / (tv * 1e-3) / 1e9 / peak, 4)}
@@ -310,7 +310,8 @@ def run_gpu(a, rank, world, dist):
                    "l2": "flushed between steps (256 MiB write), outside the event-timed region; "
                          "the flush also absorbs the write-back of the previous step's dirty lines, "
                          "see steady_state for back-to-back steps",
-                   "block": [block[0], block[1]], "cells_per_thread": block[2],
+                   "launch": {"block": [block[0], block[1]], "cells_per_thread": block[2],
+                              "prefetch_waves": block[3]},
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": round(wall, 4)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

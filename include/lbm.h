@@ -192,25 +192,33 @@ int lbm_reductions(lbm_handle *h, lbm_stats *out);
  * lbm_reductions).  Synchronises. */
 int lbm_read_stats(lbm_handle *h, lbm_stats *out);
 
-/* Launch shape of the step kernel: bx threads along x (a multiple of 32, so
- * that a warp never spans two x-rows) by by along y, bx*by <= 256, each
- * thread updating cells_per_thread cells: 1, or 2 (cells x and x+32 collided
- * together in packed FP32; not for FP64 storage).  bx and by never change
+/* Launch shape of the step kernel.  Affects speed, and (cells_per_thread
+ * only) the FP32 rounding pattern: bx, by and prefetch_waves never change
  * results; cells_per_thread changes where the compiler fuses multiply-adds,
- * so results with 1 and 2 agree to FP32 rounding, not bit for bit.
- * EINVAL otherwise. */
-int lbm_set_block(lbm_handle *h, int32_t bx, int32_t by, int32_t cells_per_thread);
+ * so results with 1 and 2 agree to FP32 rounding, not bit for bit. */
+typedef struct lbm_launch {
+  int32_t bx, by;           /* threads along x (multiple of 32, so a warp never
+                               spans two x-rows) and y; bx*by <= 256          */
+  int32_t cells_per_thread; /* 1, or 2 (cells x and x+32 collided together in
+                               packed FP32; not for FP64 storage)             */
+  int32_t prefetch_waves;   /* 0..4: each CTA bulk-prefetches into L2 the rows
+                               the CTA this many waves of resident CTAs ahead
+                               will read (0 = off)                           */
+} lbm_launch;
+
+/* Set / read the launch shape.  EINVAL if out of range. */
+int lbm_set_launch(lbm_handle *h, const lbm_launch *launch);
+int lbm_get_launch(lbm_handle *h, lbm_launch *launch);
 
 /* Autotuner: time the step kernel on this domain for each candidate launch
- * shape (block shape and cells per thread) (`trials` steps each, CUDA events on the handle's stream) and keep
+ * shape (block shape, cells per thread, L2 prefetch) (`trials` steps each, CUDA events on the handle's stream) and keep
  * the fastest.  The populations and step counter are saved before and
  * restored after, so the state is unaffected (the chosen cells per thread
  * sets the FP32 rounding pattern, see lbm_set_block); the choice is cached per
  * (Q, storage, nx, ny, nz) for later handles of the same shape.  trials <= 0
  * uses the cache only (or 8 trials on a miss).  Outputs may be NULL.
  * Synchronises; needs Q*N storage values of temporary device memory. */
-int lbm_autotune(lbm_handle *h, int32_t trials, int32_t *bx, int32_t *by,
-                 int32_t *cells_per_thread, double *ms_per_step);
+int lbm_autotune(lbm_handle *h, int32_t trials, lbm_launch *chosen, double *ms_per_step);
 
 /* ---- allocation-free reductions ------------------------------------------ */
 

@@ -20,7 +20,7 @@ struct lbm_handle {
   lbm_geom geom{};
   lbm_params params{};
   int64_t n = 0;
-  BlockShape block{32, 8, 1};
+  BlockShape block{32, 8, 1, 0};
   // reductions
   double* u_prev = nullptr;     // 3*N snapshot, allocated on first use
   int have_prev = 0;
@@ -449,15 +449,18 @@ int lbm_read_stats(lbm_handle* h, lbm_stats* out) {
   return LBM_OK;
 }
 
-int lbm_set_block(lbm_handle* h, int32_t bx, int32_t by, int32_t cells_per_thread) {
+int lbm_set_launch(lbm_handle* h, const lbm_launch* l) {
   if (int rc = check(h)) return rc;
-  if (bx < 32 || bx % 32 != 0 || by < 1 || (int64_t)bx * by > 256)
+  if (!l) return fail(LBM_EINVAL, "null launch");
+  if (l->bx < 32 || l->bx % 32 != 0 || l->by < 1 || (int64_t)l->bx * l->by > 256)
     return fail(LBM_EINVAL, "block must be bx (multiple of 32) x by with bx*by <= 256");
-  if (cells_per_thread != 1 && cells_per_thread != 2)
+  if (l->cells_per_thread != 1 && l->cells_per_thread != 2)
     return fail(LBM_EINVAL, "cells_per_thread must be 1 or 2");
-  if (cells_per_thread == 2 && h->d.storage == LBM_STORAGE_F64)
+  if (l->cells_per_thread == 2 && h->d.storage == LBM_STORAGE_F64)
     return fail(LBM_EINVAL, "two cells per thread needs FP32 arithmetic (not FP64 storage)");
-  h->block = {bx, by, cells_per_thread};
+  if (l->prefetch_waves < 0 || l->prefetch_waves > 4)
+    return fail(LBM_EINVAL, "prefetch_waves must be in 0..4");
+  h->block = {l->bx, l->by, l->cells_per_thread, l->prefetch_waves};
   return LBM_OK;
 }
 
@@ -466,13 +469,12 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, std::pair<BlockShape, double>> g_tune_cache;
 
 const BlockShape kCandidates[] = {
-    {32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1}, {64, 1, 1}, {64, 2, 1}, {64, 4, 1},
-    {128, 1, 1}, {128, 2, 1}, {256, 1, 1}, {32, 1, 2}, {32, 2, 2}, {32, 4, 2}, {64, 1, 2},
-    {64, 2, 2}, {128, 1, 2}};
+    {32, 2, 1, 0}, {32, 4, 1, 0}, {64, 1, 1, 0}, {64, 2, 1, 0}, {128, 1, 1, 0}, {128, 2, 1, 0},
+    {32, 2, 1, 1}, {32, 4, 1, 1}, {64, 1, 1, 1}, {64, 2, 1, 1}, {128, 1, 1, 1}, {128, 2, 1, 1},
+    {32, 2, 2, 0}, {64, 1, 2, 0}, {32, 2, 2, 1}, {64, 1, 2, 1}, {64, 2, 1, 2}, {32, 4, 1, 2}};
 }  // namespace
 
-int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, int32_t* cpt,
-                 double* ms) {
+int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) {
   if (int rc = check(h)) return rc;
   DeviceGuard dg(h->device);
   const auto key = std::make_tuple(h->d.Q, h->d.storage, h->d.nx, h->d.ny, h->d.nz);
@@ -481,9 +483,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, int32_
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end() && trials <= 0) {
       h->block = it->second.first;
-      if (bx) *bx = h->block.bx;
-      if (by) *by = h->block.by;
-      if (cpt) *cpt = h->block.cpt;
+      if (chosen) *chosen = {h->block.bx, h->block.by, h->block.cpt, h->block.pf};
       if (ms) *ms = it->second.second;
       return LBM_OK;
     }
@@ -539,10 +539,15 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* bx, int32_t* by, int32_
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = {best, best_ms};
   }
-  if (bx) *bx = best.bx;
-  if (by) *by = best.by;
-  if (cpt) *cpt = best.cpt;
+  if (chosen) *chosen = {best.bx, best.by, best.cpt, best.pf};
   if (ms) *ms = best_ms;
+  return LBM_OK;
+}
+
+int lbm_get_launch(lbm_handle* h, lbm_launch* out) {
+  if (int rc = check(h)) return rc;
+  if (!out) return fail(LBM_EINVAL, "null output");
+  *out = {h->block.bx, h->block.by, h->block.cpt, h->block.pf};
   return LBM_OK;
 }
 

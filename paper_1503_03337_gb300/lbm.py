@@ -52,6 +52,14 @@ class lbm_params(ctypes.Structure):
                 ("residual_interval", ctypes.c_int32), ("rounding", ctypes.c_int32)]
 
 
+class lbm_launch(ctypes.Structure):
+    _fields_ = [("bx", ctypes.c_int32), ("by", ctypes.c_int32),
+                ("cells_per_thread", ctypes.c_int32), ("prefetch_waves", ctypes.c_int32)]
+
+    def astuple(self):
+        return (self.bx, self.by, self.cells_per_thread, self.prefetch_waves)
+
+
 class lbm_stats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("prev_step", ctypes.c_int64),
                 ("sum_abs_du", ctypes.c_double * 3), ("sum_abs_u", ctypes.c_double * 3),
@@ -82,9 +90,9 @@ SIGNATURES = {
     "lbm_reductions": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_read_stats": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_memory_bytes": (_I, [_VP, ctypes.POINTER(_I64)]),
-    "lbm_set_block": (_I, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
-    "lbm_autotune": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
-                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+    "lbm_set_launch": (_I, [_VP, ctypes.POINTER(lbm_launch)]),
+    "lbm_get_launch": (_I, [_VP, ctypes.POINTER(lbm_launch)]),
+    "lbm_autotune": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(lbm_launch),
                           ctypes.POINTER(ctypes.c_double)]),
     "lbm_reductions_static": (_I, [ctypes.POINTER(lbm_desc), ctypes.POINTER(lbm_geom),
                                    ctypes.POINTER(lbm_params), _I64, _VP, _VP, _I64,
@@ -226,16 +234,23 @@ def lbm_read_stats(h):
     return s
 
 
-def lbm_set_block(h, bx, by, cells_per_thread=1):
-    _check(load().lbm_set_block(h, int(bx), int(by), int(cells_per_thread)))
+def lbm_set_launch(h, bx, by, cells_per_thread=1, prefetch_waves=0):
+    l = lbm_launch(int(bx), int(by), int(cells_per_thread), int(prefetch_waves))
+    _check(load().lbm_set_launch(h, ctypes.byref(l)))
+
+
+def lbm_get_launch(h):
+    l = lbm_launch()
+    _check(load().lbm_get_launch(h, ctypes.byref(l)))
+    return l.astuple()
 
 
 def lbm_autotune(h, trials=8):
-    """Returns (bx, by, cells_per_thread, ms_per_step) of the fastest launch."""
-    bx, by, cpt, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(load().lbm_autotune(h, int(trials), ctypes.byref(bx), ctypes.byref(by),
-                               ctypes.byref(cpt), ctypes.byref(ms)))
-    return bx.value, by.value, cpt.value, ms.value
+    """Returns ((bx, by, cells_per_thread, prefetch_waves), ms_per_step) of
+    the fastest launch."""
+    l, ms = lbm_launch(), ctypes.c_double()
+    _check(load().lbm_autotune(h, int(trials), ctypes.byref(l), ctypes.byref(ms)))
+    return l.astuple(), ms.value
 
 
 def lbm_reductions_static(Q, nx, ny, nz, storage, faces, u_wall, params, step,

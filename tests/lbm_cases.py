@@ -31,7 +31,7 @@ def gpu_open(case, stream=None, residual_interval=0, launch=None):
     lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period,
                        residual_interval=residual_interval, rounding=case.rounding)
     if launch is not None:
-        lbm.lbm_set_block(h, *launch)
+        lbm.lbm_set_launch(h, *launch)
     return h
 
 
