@@ -310,8 +310,7 @@ def run_gpu(a, rank, world, dist):
                    "l2": "flushed between steps (256 MiB write), outside the event-timed region; "
                          "the flush also absorbs the write-back of the previous step's dirty lines, "
                          "see steady_state for back-to-back steps",
-                   "launch": {"block": [block[0], block[1]], "cells_per_thread": block[2],
-                              "prefetch_waves": block[3]},
+                   "launch": {"block": [block[0], block[1]], "cells_per_thread": block[2]},
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": round(wall, 4)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

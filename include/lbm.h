@@ -193,17 +193,14 @@ int lbm_reductions(lbm_handle *h, lbm_stats *out);
 int lbm_read_stats(lbm_handle *h, lbm_stats *out);
 
 /* Launch shape of the step kernel.  Affects speed, and (cells_per_thread
- * only) the FP32 rounding pattern: bx, by and prefetch_waves never change
- * results; cells_per_thread changes where the compiler fuses multiply-adds,
- * so results with 1 and 2 agree to FP32 rounding, not bit for bit. */
+ * only) the FP32 rounding pattern: bx and by never change results;
+ * cells_per_thread changes where the compiler fuses multiply-adds, so
+ * results with 1 and 2 agree to FP32 rounding, not bit for bit. */
 typedef struct lbm_launch {
   int32_t bx, by;           /* threads along x (multiple of 32, so a warp never
                                spans two x-rows) and y; bx*by <= 256          */
   int32_t cells_per_thread; /* 1, or 2 (cells x and x+32 collided together in
                                packed FP32; not for FP64 storage)             */
-  int32_t prefetch_waves;   /* 0..4: each CTA bulk-prefetches into L2 the rows
-                               the CTA this many waves of resident CTAs ahead
-                               will read (0 = off)                           */
 } lbm_launch;
 
 /* Set / read the launch shape.  EINVAL if out of range. */
@@ -211,7 +208,7 @@ int lbm_set_launch(lbm_handle *h, const lbm_launch *launch);
 int lbm_get_launch(lbm_handle *h, lbm_launch *launch);
 
 /* Autotuner: time the step kernel on this domain for each candidate launch
- * shape (block shape, cells per thread, L2 prefetch) (`trials` steps each, CUDA events on the handle's stream) and keep
+ * shape (block shape, cells per thread) (`trials` steps each, CUDA events on the handle's stream) and keep
  * the fastest.  The populations and step counter are saved before and
  * restored after, so the state is unaffected (the chosen cells per thread
  * sets the FP32 rounding pattern, see lbm_set_block); the choice is cached per

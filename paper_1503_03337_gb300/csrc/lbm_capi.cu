@@ -20,7 +20,7 @@ struct lbm_handle {
   lbm_geom geom{};
   lbm_params params{};
   int64_t n = 0;
-  BlockShape block{32, 8, 1, 0};
+  BlockShape block{32, 8, 1};
   // reductions
   double* u_prev = nullptr;     // 3*N snapshot, allocated on first use
   int have_prev = 0;
@@ -458,9 +458,7 @@ int lbm_set_launch(lbm_handle* h, const lbm_launch* l) {
     return fail(LBM_EINVAL, "cells_per_thread must be 1 or 2");
   if (l->cells_per_thread == 2 && h->d.storage == LBM_STORAGE_F64)
     return fail(LBM_EINVAL, "two cells per thread needs FP32 arithmetic (not FP64 storage)");
-  if (l->prefetch_waves < 0 || l->prefetch_waves > 4)
-    return fail(LBM_EINVAL, "prefetch_waves must be in 0..4");
-  h->block = {l->bx, l->by, l->cells_per_thread, l->prefetch_waves};
+  h->block = {l->bx, l->by, l->cells_per_thread};
   return LBM_OK;
 }
 
@@ -468,10 +466,9 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, std::pair<BlockShape, double>> g_tune_cache;
 
-const BlockShape kCandidates[] = {
-    {32, 2, 1, 0}, {32, 4, 1, 0}, {64, 1, 1, 0}, {64, 2, 1, 0}, {128, 1, 1, 0}, {128, 2, 1, 0},
-    {32, 2, 1, 1}, {32, 4, 1, 1}, {64, 1, 1, 1}, {64, 2, 1, 1}, {128, 1, 1, 1}, {128, 2, 1, 1},
-    {32, 2, 2, 0}, {64, 1, 2, 0}, {32, 2, 2, 1}, {64, 1, 2, 1}, {64, 2, 1, 2}, {32, 4, 1, 2}};
+const BlockShape kCandidates[] = {{32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1},
+                                  {64, 1, 1},  {64, 2, 1}, {64, 4, 1}, {128, 1, 1},
+                                  {128, 2, 1}, {256, 1, 1}, {32, 2, 2}, {64, 1, 2}};
 }  // namespace
 
 int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) {
@@ -483,7 +480,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end() && trials <= 0) {
       h->block = it->second.first;
-      if (chosen) *chosen = {h->block.bx, h->block.by, h->block.cpt, h->block.pf};
+      if (chosen) *chosen = {h->block.bx, h->block.by, h->block.cpt};
       if (ms) *ms = it->second.second;
       return LBM_OK;
     }
@@ -539,7 +536,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = {best, best_ms};
   }
-  if (chosen) *chosen = {best.bx, best.by, best.cpt, best.pf};
+  if (chosen) *chosen = {best.bx, best.by, best.cpt};
   if (ms) *ms = best_ms;
   return LBM_OK;
 }
@@ -547,7 +544,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
 int lbm_get_launch(lbm_handle* h, lbm_launch* out) {
   if (int rc = check(h)) return rc;
   if (!out) return fail(LBM_EINVAL, "null output");
-  *out = {h->block.bx, h->block.by, h->block.cpt, h->block.pf};
+  *out = {h->block.bx, h->block.by, h->block.cpt};
   return LBM_OK;
 }
 

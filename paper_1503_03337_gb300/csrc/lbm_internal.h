@@ -36,7 +36,6 @@ struct DomainDesc {
 struct BlockShape {
   int bx, by;
   int cpt;  // cells per thread: 1, or 2 (pairs along x, FP32 arithmetic only)
-  int pf;   // L2 prefetch distance in waves of resident CTAs (0 = off)
 };
 
 BlockShape default_block(int nx, int ny);

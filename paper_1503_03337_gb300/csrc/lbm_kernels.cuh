@@ -38,7 +38,6 @@ struct Domain {
   //   push[a] = a*N + s(c_a)        (where f*_a(x) is written)
   // with s(c) = cx + cy*nx + cz*nx*ny.  Filled by fill_offsets().
   int pull[18], push[18];
-  int prefetch;      // step kernels: L2 prefetch distance in CTAs (0 = off)
 };
 
 template <int Q, typename R>

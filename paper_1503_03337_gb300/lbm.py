@@ -54,10 +54,10 @@ class lbm_params(ctypes.Structure):
 
 class lbm_launch(ctypes.Structure):
     _fields_ = [("bx", ctypes.c_int32), ("by", ctypes.c_int32),
-                ("cells_per_thread", ctypes.c_int32), ("prefetch_waves", ctypes.c_int32)]
+                ("cells_per_thread", ctypes.c_int32)]
 
     def astuple(self):
-        return (self.bx, self.by, self.cells_per_thread, self.prefetch_waves)
+        return (self.bx, self.by, self.cells_per_thread)
 
 
 class lbm_stats(ctypes.Structure):
@@ -234,8 +234,8 @@ def lbm_read_stats(h):
     return s
 
 
-def lbm_set_launch(h, bx, by, cells_per_thread=1, prefetch_waves=0):
-    l = lbm_launch(int(bx), int(by), int(cells_per_thread), int(prefetch_waves))
+def lbm_set_launch(h, bx, by, cells_per_thread=1):
+    l = lbm_launch(int(bx), int(by), int(cells_per_thread))
     _check(load().lbm_set_launch(h, ctypes.byref(l)))
 
 
@@ -246,8 +246,7 @@ def lbm_get_launch(h):
 
 
 def lbm_autotune(h, trials=8):
-    """Returns ((bx, by, cells_per_thread, prefetch_waves), ms_per_step) of
-    the fastest launch."""
+    """Returns ((bx, by, cells_per_thread), ms_per_step) of the fastest launch."""
     l, ms = lbm_launch(), ctypes.c_double()
     _check(load().lbm_autotune(h, int(trials), ctypes.byref(l), ctypes.byref(ms)))
     return l.astuple(), ms.value

@@ -86,7 +86,7 @@ PAIR_CASES = EDGE + [
 ]
 
 
-@pytest.mark.parametrize("launch", ((32, 2, 2, 0), (64, 1, 2, 1), (32, 1, 1, 0), (64, 2, 1, 2)))
+@pytest.mark.parametrize("launch", ((32, 2, 2), (64, 1, 2), (32, 1, 1), (64, 2, 1)))
 @pytest.mark.parametrize("Q", (14, 18))
 @pytest.mark.parametrize("name,shape,faces", PAIR_CASES)
 def test_fp32_launch_shapes(Q, name, shape, faces, launch):

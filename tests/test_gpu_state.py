@@ -168,13 +168,13 @@ def test_autotune_keeps_state_and_results(storage):
             lbm.lbm_init_equilibrium(h)
             lbm.lbm_step(h, 31)
         f0 = lbm.read_populations(a, 18, 40, 40, 40)
-        (bx, by, cpt, pf), ms = lbm.lbm_autotune(a, 6)
+        (bx, by, cpt), ms = lbm.lbm_autotune(a, 6)
         assert bx % 32 == 0 and bx * by <= 256 and cpt in (1, 2) and ms > 0
-        assert lbm.lbm_get_launch(a) == (bx, by, cpt, pf)
+        assert lbm.lbm_get_launch(a) == (bx, by, cpt)
         assert lbm.lbm_get_step(a) == 31
         np.testing.assert_array_equal(lbm.read_populations(a, 18, 40, 40, 40), f0)
-        lbm.lbm_set_launch(b, 32, 8 if (bx, by) != (32, 8) else 1, cpt, 1 - min(pf, 1))
-        lbm.lbm_set_launch(c, 64, 1, 3 - cpt, 0)
+        lbm.lbm_set_launch(b, 32, 8 if (bx, by) != (32, 8) else 1, cpt)
+        lbm.lbm_set_launch(c, 64, 1, 3 - cpt)
         for h in hs:
             lbm.lbm_step(h, 25)
         fa, fb, fc = (lbm.read_populations(h, 18, 40, 40, 40) for h in hs)
@@ -182,7 +182,7 @@ def test_autotune_keeps_state_and_results(storage):
         tol = 2e-6 if storage == "f32" else 2e-3
         assert np.max(np.abs(fa - fc)) <= tol * np.max(np.abs(fa))
         # cached choice is reused without timing
-        assert lbm.lbm_autotune(b, 0)[0] == (bx, by, cpt, pf)
+        assert lbm.lbm_autotune(b, 0)[0] == (bx, by, cpt)
     finally:
         for h in hs:
             lbm.lbm_destroy(h)
