@@ -261,6 +261,66 @@ int lbm_reductions_static(const lbm_desc *desc, const lbm_geom *geom,
 /* Device memory the handle holds, in bytes. */
 int lbm_memory_bytes(lbm_handle *h, int64_t *bytes);
 
+/* ---- batches of independent domains -------------------------------------- */
+
+/* A batch advances many independent domains (different sizes, Q, storage,
+ * step counters) together: one kernel launch covers every active domain, in
+ * persistent mode one cooperative launch runs a whole chunk of steps with a
+ * bounded grid barrier between steps, and the launches of a chunk are
+ * captured once in a CUDA graph and replayed.  Each domain computes exactly
+ * what a single-domain handle with one cell per thread computes, so a
+ * domain's result is the same alone and in any mix.  Batched domains store
+ * FP32, FP16 or BF16. */
+typedef struct lbm_batch lbm_batch;
+
+/* Up to `capacity` domains whose population buffers together stay within
+ * `budget_bytes` (<= 0: no limit).  Work is queued on `cuda_stream`. */
+int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void *cuda_stream,
+                     lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+
+/* Add a domain (stream-ordered allocation of Q*N storage values, f = 0,
+ * step 0); returns its slot.  EBUSY if no slot is free or the budget would
+ * be exceeded; EINVAL for bad descriptors (as lbm_create/set_geometry/
+ * set_params). */
+int lbm_batch_add(lbm_batch *b, const lbm_desc *desc, const lbm_geom *geom,
+                  const lbm_params *params, int32_t *slot);
+
+/* Remove a domain; its slot and memory are reused (stream-ordered free). */
+int lbm_batch_remove(lbm_batch *b, int32_t slot);
+
+/* As lbm_init_equilibrium for one domain (device arrays or NULL only). */
+int lbm_batch_init_equilibrium(lbm_batch *b, int32_t slot, const double *u, const double *p,
+                               int on_device);
+
+/* Advance every active domain by nsteps, `chunk` steps per launch (or per
+ * graph replay).  Asynchronous.  Returns LBM_ETIMEOUT if a grid barrier of
+ * an earlier launch timed out. */
+int lbm_batch_step(lbm_batch *b, int64_t nsteps, int32_t chunk);
+
+int lbm_batch_get_step(lbm_batch *b, int32_t slot, int64_t *n);
+
+/* As lbm_read_fields for one domain, into a device buffer.  Synchronises. */
+int lbm_batch_read_fields(lbm_batch *b, int32_t slot, unsigned mask, void *dst,
+                          int dst_on_device, int dtype);
+
+/* As lbm_reductions for one domain (snapshot kept per domain). */
+int lbm_batch_reductions(lbm_batch *b, int32_t slot, lbm_stats *out);
+
+/* Launch shape of the batch kernel (bx multiple of 32, bx*by <= 256) and
+ * mode: persistent (1: cooperative launch per chunk, grid barrier between
+ * steps) or per step (0: one launch per step).  Speed only. */
+int lbm_batch_set_launch(lbm_batch *b, int32_t bx, int32_t by, int32_t persistent);
+
+/* Active domains, bytes of population storage, total cells. */
+int lbm_batch_info(lbm_batch *b, int32_t *active, int64_t *used_bytes, int64_t *total_cells);
+
+/* Test hook for the time-out path of the persistent grid barrier: the
+ * barrier waits for `extra_arrivals` CTAs beyond the grid (that never come)
+ * and gives up after `spin_limit` polls, so the next lbm_batch_step reports
+ * LBM_ETIMEOUT.  (0, 1 << 26) restores normal operation. */
+int lbm_batch_set_barrier_test(lbm_batch *b, int32_t extra_arrivals, int64_t spin_limit);
+
 /* Message for the calling thread's most recent failure ("" if none). */
 const char *lbm_last_error(void);
 const char *lbm_strerror(int code);

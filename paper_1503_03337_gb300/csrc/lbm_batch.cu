@@ -1,0 +1,641 @@
+// Batched stepping of many independent domains (C-ABI lbm_batch_*).
+//
+// Domains of different sizes, Q, storage types and step counters live in one
+// batch.  A device table holds one descriptor per active domain and the
+// prefix sums of its tiles (a tile is one CTA's block of cells), so a single
+// kernel launch advances every domain: CTAs take tiles round-robin across
+// all domains, and each tile runs the same per-cell update as the
+// single-domain kernel, at its own domain's parity and force time level.
+//
+// Persistent mode: one cooperative launch runs `chunk` steps, with a grid
+// barrier between steps (the in-place AA update needs every cell of step s
+// done before step s+1 reads its neighbours).  The barrier spins a bounded
+// number of times; on time-out it raises a flag, every CTA returns, and the
+// host reports LBM_ETIMEOUT.  Population loads go through L2 only (ld.cg),
+// because L1 is not coherent between SMs across the steps of one launch.
+// Per-step mode: one ordinary launch per step, no barrier.  Either way the
+// launches of a chunk are captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <typename R>
+Domain<R> to_domain(const DomainDesc& d, const double F[3]);
+
+namespace {
+
+struct BatchEntry {
+  Domain<float> d;  // F and key are set per step on the device
+  int Q, storage, rounding;
+  int tiles_x, tiles_y;
+  int64_t tile_begin;  // first tile of this domain in the launch
+  int64_t n;           // step counter of this domain before the launch
+  double force[3];
+  double period;
+};
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int timed_out;
+  int extra;  // test hook: arrivals the barrier waits for beyond the grid
+};
+
+// Bounded grid-wide barrier for a cooperative launch.  Returns false (in
+// every thread of the CTA) if the wait timed out anywhere.
+__device__ bool grid_sync(GridBarrier* g, long long spin_limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    volatile unsigned int* vgen = &g->gen;
+    volatile int* vflag = &g->timed_out;
+    const unsigned int gen = *vgen;
+    __threadfence();
+    const unsigned int expected = gridDim.x + (unsigned int)g->extra;
+    if (atomicAdd(&g->count, 1u) == expected - 1) {
+      atomicExch(&g->count, 0u);
+      __threadfence();
+      atomicAdd(&g->gen, 1u);
+    } else {
+      long long k = 0;
+      while (*vgen == gen) {
+        if (*vflag || ++k > spin_limit) {
+          atomicExch(&g->timed_out, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    ok = !*vflag;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int Q, typename S, bool ODD, bool SR>
+__device__ __forceinline__ void batch_tile(const Domain<float>& d, int64_t t, int tiles_x,
+                                           int tiles_y) {
+  const int tx = (int)(t % tiles_x);
+  const int64_t r = t / tiles_x;
+  const int ty = (int)(r % tiles_y);
+  const int z = (int)(r / tiles_y);
+  const int x = tx * blockDim.x + threadIdx.x;
+  const int y = ty * blockDim.y + threadIdx.y;
+  if (x >= d.nx || y >= d.ny) return;
+  const int x_lo = tx * blockDim.x + (threadIdx.x & ~31);
+  update_cell<Q, S, float, ODD, true, SR, true>(d, static_cast<S*>(d.f), x, y, z, x_lo,
+                                                x_lo + 31);
+}
+
+template <int Q, typename S>
+__device__ __forceinline__ void batch_tile_dispatch(const Domain<float>& d, int64_t t, int tx,
+                                                    int ty, bool odd, bool sr) {
+  if constexpr (Stochastic<S>::enabled) {
+    if (sr) {
+      if (odd) batch_tile<Q, S, true, true>(d, t, tx, ty);
+      else batch_tile<Q, S, false, true>(d, t, tx, ty);
+      return;
+    }
+  }
+  if (odd) batch_tile<Q, S, true, false>(d, t, tx, ty);
+  else batch_tile<Q, S, false, false>(d, t, tx, ty);
+}
+
+// Steps `nsteps` (persistent mode, cooperative launch) or 1 (per-step mode)
+// of every domain in `ents`; `s0` is the step offset of this launch within
+// the chunk (per-step mode).
+__global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__ ents, int nent,
+                                                  int64_t total_tiles, int nsteps, int s0,
+                                                  GridBarrier* bar, long long spin_limit) {
+  __shared__ Domain<float> sd;
+  __shared__ int s_meta[5];  // Q, storage, odd, sr, tiles_x ; tiles_y below
+  __shared__ int s_tiles_y;
+  __shared__ int64_t s_begin;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int s = 0; s < nsteps; ++s) {
+    for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+      int lo = 0, hi = nent - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ents[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      const BatchEntry& e = ents[lo];
+      __syncthreads();  // the previous tile is done with sd
+      const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
+      for (int w = tid; w < nw; w += nthr)
+        reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
+      if (tid == 0) {
+        const int64_t n = e.n + s0 + s;
+        s_meta[0] = e.Q;
+        s_meta[1] = e.storage;
+        s_meta[2] = (int)(n & 1);
+        s_meta[3] = e.rounding == LBM_ROUND_STOCHASTIC;
+        s_meta[4] = e.tiles_x;
+        s_tiles_y = e.tiles_y;
+        s_begin = e.tile_begin;
+      }
+      __syncthreads();
+      // the force and hash key of this step overwrite words of the copy, so
+      // they are written after the copy has completed
+      if (tid == 0) {
+        const int64_t n = e.n + s0 + s;
+        const double c = e.period > 0.0 ? cos(2.0 * M_PI * (double)n / e.period) : 1.0;
+        for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
+        sd.key = step_key(n);
+      }
+      __syncthreads();
+      const int64_t lt = t - s_begin;
+      const bool odd = s_meta[2] != 0, sr = s_meta[3] != 0;
+      const int tx = s_meta[4], ty = s_tiles_y;
+      if (s_meta[0] == 14) {
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<14, float>(sd, lt, tx, ty, odd, sr);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<14, __half>(sd, lt, tx, ty, odd, sr);
+        else batch_tile_dispatch<14, __nv_bfloat16>(sd, lt, tx, ty, odd, sr);
+      } else {
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<18, float>(sd, lt, tx, ty, odd, sr);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<18, __half>(sd, lt, tx, ty, odd, sr);
+        else batch_tile_dispatch<18, __nv_bfloat16>(sd, lt, tx, ty, odd, sr);
+      }
+    }
+    if (s + 1 < nsteps && !grid_sync(bar, spin_limit)) return;
+  }
+}
+
+// After a chunk: advance every domain's step counter and publish the
+// barrier's time-out flag to the host.
+__global__ void k_batch_advance(BatchEntry* ents, int nent, int nsteps, const GridBarrier* bar,
+                                int* host_flag) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nent; k += gridDim.x * blockDim.x)
+    ents[k].n += nsteps;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && bar->timed_out) *host_flag = 1;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct BatchSlot {
+  bool used = false;
+  DomainDesc dd{};
+  lbm_geom geom{};
+  lbm_params params{};
+  int64_t n = 0;
+  size_t fbytes = 0;
+  double* u_prev = nullptr;
+  int have_prev = 0;
+  int64_t prev_step = -1;
+};
+
+struct lbm_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int capacity = 0;
+  int64_t budget = 0, used_bytes = 0;
+  std::vector<BatchSlot> slots;
+  // device state
+  BatchEntry* ents = nullptr;
+  GridBarrier* bar = nullptr;
+  int* flag_host = nullptr;  // mapped pinned: barrier timed out
+  int* flag_dev = nullptr;
+  double* partials = nullptr;
+  double* stats_host = nullptr;  // mapped pinned, kNumStats
+  double* stats_dev = nullptr;
+  // launch
+  int bx = 64, by = 2;
+  int persistent = 1;
+  int grid = 0;
+  long long spin_limit = 1ll << 26;
+  int extra_arrivals = 0;
+  // table
+  bool dirty = true;
+  int nent = 0;
+  int64_t total_tiles = 0;
+  std::vector<int> order;  // slot of each entry
+  // graph of one chunk
+  cudaGraphExec_t graph = nullptr;
+  int graph_chunk = 0;
+  bool graph_ok = true;
+};
+
+namespace {
+
+int bfail(int code, const std::string& m) {
+  set_last_error(m);
+  return code;
+}
+int bcuda(cudaError_t e, const char* where) {
+  set_last_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return LBM_ECUDA;
+}
+
+size_t storage_size(int s) {
+  return s == LBM_STORAGE_F64 ? 8 : s == LBM_STORAGE_F32 ? 4 : 2;
+}
+
+void drop_graph(lbm_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_chunk = 0;
+}
+
+int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, DomainDesc& dd) {
+  if (desc->Q != 14 && desc->Q != 18) return bfail(LBM_EINVAL, "Q must be 14 or 18");
+  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
+    return bfail(LBM_EINVAL, "grid sizes must be >= 1");
+  if (desc->storage != LBM_STORAGE_F32 && desc->storage != LBM_STORAGE_F16 &&
+      desc->storage != LBM_STORAGE_BF16)
+    return bfail(LBM_EINVAL, "batched domains store FP32, FP16 or BF16");
+  const int64_t N = (int64_t)desc->nx * desc->ny * desc->nz;
+  if (N * desc->Q >= (int64_t(1) << 31) || desc->nz > 65535)
+    return bfail(LBM_EINVAL, "domain too large (Q*N must be < 2^31)");
+  for (int f = 0; f < 6; ++f)
+    if (g->face[f] < LBM_PERIODIC || g->face[f] > LBM_MOVING_WALL)
+      return bfail(LBM_EINVAL, "unknown face kind");
+  dd = DomainDesc{};
+  dd.Q = desc->Q;
+  dd.nx = desc->nx;
+  dd.ny = desc->ny;
+  dd.nz = desc->nz;
+  dd.storage = desc->storage;
+  dd.N = N;
+  for (int k = 0; k < 3; ++k) {
+    const bool lo = g->face[2 * k] == LBM_PERIODIC, hi = g->face[2 * k + 1] == LBM_PERIODIC;
+    if (lo != hi) return bfail(LBM_EINVAL, "opposite faces must both be periodic or neither");
+    dd.per[k] = lo;
+  }
+  for (int f = 0; f < 6; ++f) {
+    if (g->face[f] == LBM_MOVING_WALL) dd.moving |= 1 << f;
+    for (int k = 0; k < 3; ++k)
+      dd.uw[f][k] = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
+  }
+  double s[6] = {p->s_c, p->s_e, p->s_q, p->s_nu, p->s_pi, p->s_t};
+  if (p->nu > 0.0) s[3] = 1.0 / (3.0 * p->nu + 0.5);
+  if (desc->Q == 14) s[4] = s[1];
+  for (int k = 0; k < 6; ++k)
+    if (!(s[k] > 0.0 && s[k] < 2.0)) return bfail(LBM_EINVAL, "relaxation rates must lie in (0, 2)");
+  for (int k = 0; k < 6; ++k) dd.s[k] = s[k];
+  for (int k = 0; k < 3; ++k) dd.force[k] = p->force[k];
+  if (!std::isfinite(p->force_period) || !std::isfinite(p->p_ref))
+    return bfail(LBM_EINVAL, "force period and p_ref must be finite");
+  dd.period = p->force_period;
+  dd.p_ref = p->p_ref;
+  if (p->rounding != LBM_ROUND_NEAREST && p->rounding != LBM_ROUND_STOCHASTIC)
+    return bfail(LBM_EINVAL, "unknown rounding mode");
+  dd.rounding = p->rounding;
+  return LBM_OK;
+}
+
+// Rebuild and upload the descriptor table of the active domains.
+int upload_table(lbm_batch* b) {
+  std::vector<BatchEntry> ents;
+  b->order.clear();
+  int64_t tiles = 0;
+  for (int i = 0; i < (int)b->slots.size(); ++i) {
+    const BatchSlot& s = b->slots[i];
+    if (!s.used) continue;
+    BatchEntry e{};
+    const double zero[3] = {0.0, 0.0, 0.0};
+    e.d = to_domain<float>(s.dd, zero);
+    e.Q = s.dd.Q;
+    e.storage = s.dd.storage;
+    e.rounding = s.dd.rounding;
+    e.tiles_x = (s.dd.nx + b->bx - 1) / b->bx;
+    e.tiles_y = (s.dd.ny + b->by - 1) / b->by;
+    e.tile_begin = tiles;
+    e.n = s.n;
+    for (int k = 0; k < 3; ++k) e.force[k] = s.dd.force[k];
+    e.period = s.dd.period;
+    tiles += (int64_t)e.tiles_x * e.tiles_y * s.dd.nz;
+    ents.push_back(e);
+    b->order.push_back(i);
+  }
+  b->nent = (int)ents.size();
+  b->total_tiles = tiles;
+  if (!ents.empty()) {
+    cudaError_t e = cudaMemcpyAsync(b->ents, ents.data(), sizeof(BatchEntry) * ents.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bcuda(e, "batch table upload");
+    // the copy reads `ents` (pageable) before returning
+  }
+  b->dirty = false;
+  drop_graph(b);
+  return LBM_OK;
+}
+
+int grid_for_batch(lbm_batch* b) {
+  int per_sm = 0, sms = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch,
+                                                                b->bx * b->by, 0);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess || per_sm < 1) return 0;
+  return per_sm * sms;
+}
+
+// Queue one chunk of `chunk` steps (no graph).
+cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
+  dim3 block(b->bx, b->by, 1);
+  if (b->persistent) {
+    cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier) - sizeof(int), b->stream);
+    if (e != cudaSuccess) return e;
+    const BatchEntry* ents = b->ents;
+    int nent = b->nent;
+    int64_t total = b->total_tiles;
+    int nsteps = chunk, s0 = 0;
+    GridBarrier* bar = b->bar;
+    long long spin = b->spin_limit;
+    void* args[] = {&ents, &nent, &total, &nsteps, &s0, &bar, &spin};
+    e = cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->grid), block, args, 0,
+                                    b->stream);
+    if (e != cudaSuccess) return e;
+  } else {
+    const int64_t g64 = std::min<int64_t>(b->total_tiles, int64_t(1) << 30);
+    for (int s = 0; s < chunk; ++s) {
+      k_batch<<<(unsigned)g64, block, 0, b->stream>>>(b->ents, b->nent, b->total_tiles, 1, s,
+                                                      b->bar, b->spin_limit);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  k_batch_advance<<<1, 256, 0, b->stream>>>(b->ents, b->nent, chunk, b->bar, b->flag_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, lbm_batch** out) {
+  if (!out) return bfail(LBM_EINVAL, "null output");
+  *out = nullptr;
+  if (capacity < 1 || capacity > 65536) return bfail(LBM_EINVAL, "capacity must be 1..65536");
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return bfail(LBM_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaGetDevice(&b->device);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->capacity = capacity;
+  b->budget = budget_bytes > 0 ? budget_bytes : INT64_MAX;
+  b->slots.resize(capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ents, sizeof(BatchEntry) * capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->bar, sizeof(GridBarrier));
+  if (e == cudaSuccess) e = cudaMalloc(&b->partials, sizeof(double) * kReduceBlocks * kNumStats);
+  if (e == cudaSuccess) e = cudaHostAlloc(&b->flag_host, sizeof(int), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->flag_dev, b->flag_host, 0);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(&b->stats_host, sizeof(double) * kNumStats, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->stats_dev, b->stats_host, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), b->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    lbm_batch_destroy(b);
+    return bfail(LBM_ENOMEM, "batch allocation failed");
+  }
+  *b->flag_host = 0;
+  b->grid = grid_for_batch(b);
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  for (BatchSlot& s : b->slots) {
+    if (s.dd.f) cudaFree(s.dd.f);
+    if (s.u_prev) cudaFree(s.u_prev);
+  }
+  if (b->ents) cudaFree(b->ents);
+  if (b->bar) cudaFree(b->bar);
+  if (b->partials) cudaFree(b->partials);
+  if (b->flag_host) cudaFreeHost(b->flag_host);
+  if (b->stats_host) cudaFreeHost(b->stats_host);
+  delete b;
+}
+
+int lbm_batch_add(lbm_batch* b, const lbm_desc* desc, const lbm_geom* geom,
+                  const lbm_params* params, int32_t* slot_out) {
+  if (!b || !desc || !geom || !params || !slot_out) return bfail(LBM_EINVAL, "null argument");
+  DomainDesc dd;
+  if (int rc = fill_desc(desc, geom, params, dd)) return rc;
+  int slot = -1;
+  for (int i = 0; i < b->capacity; ++i)
+    if (!b->slots[i].used) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return bfail(LBM_EBUSY, "no free slot");
+  const size_t fbytes = (size_t)dd.N * dd.Q * storage_size(dd.storage);
+  if (b->used_bytes + (int64_t)fbytes > b->budget) return bfail(LBM_EBUSY, "memory budget exhausted");
+  void* f = nullptr;
+  cudaError_t e = cudaMallocAsync(&f, fbytes, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, fbytes, b->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (f) cudaFreeAsync(f, b->stream);
+    return bfail(LBM_ENOMEM, "population allocation failed");
+  }
+  dd.f = f;
+  BatchSlot& s = b->slots[slot];
+  s = BatchSlot{};
+  s.used = true;
+  s.dd = dd;
+  s.geom = *geom;
+  s.params = *params;
+  s.fbytes = fbytes;
+  b->used_bytes += (int64_t)fbytes;
+  b->dirty = true;
+  *slot_out = slot;
+  return LBM_OK;
+}
+
+static int check_slot(lbm_batch* b, int32_t slot) {
+  if (!b) return bfail(LBM_EINVAL, "null batch");
+  if (slot < 0 || slot >= b->capacity || !b->slots[slot].used)
+    return bfail(LBM_EINVAL, "no domain in that slot");
+  return LBM_OK;
+}
+
+int lbm_batch_remove(lbm_batch* b, int32_t slot) {
+  if (int rc = check_slot(b, slot)) return rc;
+  BatchSlot& s = b->slots[slot];
+  cudaFreeAsync(s.dd.f, b->stream);
+  if (s.u_prev) cudaFreeAsync(s.u_prev, b->stream);
+  b->used_bytes -= (int64_t)s.fbytes;
+  s = BatchSlot{};
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_init_equilibrium(lbm_batch* b, int32_t slot, const double* u, const double* p,
+                               int on_device) {
+  if (int rc = check_slot(b, slot)) return rc;
+  if (!on_device && (u || p)) return bfail(LBM_EINVAL, "batch init takes device arrays");
+  BatchSlot& s = b->slots[slot];
+  cudaError_t e = launch_init(s.dd, u, p, b->stream);
+  if (e != cudaSuccess) return bcuda(e, "init kernel");
+  s.n = 0;
+  s.have_prev = 0;
+  s.prev_step = -1;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps, int32_t chunk) {
+  if (!b) return bfail(LBM_EINVAL, "null batch");
+  if (nsteps < 0) return bfail(LBM_EINVAL, "nsteps < 0");
+  if (*static_cast<volatile int*>(b->flag_host))
+    return bfail(LBM_ETIMEOUT, "a grid barrier of an earlier batch launch timed out");
+  if (b->dirty)
+    if (int rc = upload_table(b)) return rc;
+  if (b->nent == 0 || nsteps == 0) return LBM_OK;
+  if (chunk < 1) chunk = 1;
+  if (b->persistent && b->grid < 1) b->persistent = 0;
+  int64_t left = nsteps;
+  while (left > 0) {
+    const int c = (int)std::min<int64_t>(left, chunk);
+    cudaError_t e = cudaSuccess;
+    if (c == chunk && b->graph_ok) {
+      if (!b->graph || b->graph_chunk != c) {
+        drop_graph(b);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          cudaError_t e1 = enqueue_chunk(b, c);
+          e = cudaStreamEndCapture(b->stream, &g);
+          if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {  // capture not possible here: launch directly
+          cudaGetLastError();
+          b->graph_ok = false;
+          b->graph = nullptr;
+        } else {
+          b->graph_chunk = c;
+        }
+      }
+      if (b->graph) e = cudaGraphLaunch(b->graph, b->stream);
+      else e = enqueue_chunk(b, c);
+    } else {
+      e = enqueue_chunk(b, c);
+    }
+    if (e != cudaSuccess) return bcuda(e, "batch step");
+    for (int k : b->order) b->slots[k].n += c;
+    left -= c;
+  }
+  return LBM_OK;
+}
+
+int lbm_batch_get_step(lbm_batch* b, int32_t slot, int64_t* n) {
+  if (int rc = check_slot(b, slot)) return rc;
+  if (!n) return bfail(LBM_EINVAL, "null output");
+  *n = b->slots[slot].n;
+  return LBM_OK;
+}
+
+int lbm_batch_read_fields(lbm_batch* b, int32_t slot, unsigned mask, void* dst,
+                          int dst_on_device, int dtype) {
+  if (int rc = check_slot(b, slot)) return rc;
+  if (!dst || !dst_on_device) return bfail(LBM_EINVAL, "batch read-back takes a device buffer");
+  if (mask == 0 || (mask & ~7u)) return bfail(LBM_EINVAL, "bad field mask");
+  if (dtype != LBM_DTYPE_F64 && dtype != LBM_DTYPE_F32) return bfail(LBM_EINVAL, "bad dtype");
+  BatchSlot& s = b->slots[slot];
+  cudaError_t e = launch_read(s.dd, s.n, mask, dst, dtype, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch read");
+  return LBM_OK;
+}
+
+int lbm_batch_reductions(lbm_batch* b, int32_t slot, lbm_stats* out) {
+  if (int rc = check_slot(b, slot)) return rc;
+  if (!out) return bfail(LBM_EINVAL, "null output");
+  BatchSlot& s = b->slots[slot];
+  if (!s.u_prev) {
+    cudaError_t e = cudaMallocAsync(&s.u_prev, sizeof(double) * 3 * s.dd.N, b->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s.u_prev = nullptr;
+      return bfail(LBM_ENOMEM, "snapshot allocation failed");
+    }
+    s.have_prev = 0;
+  }
+  cudaError_t e = launch_reduce(s.dd, s.n, s.u_prev, s.have_prev, b->partials, b->stats_dev,
+                                b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch reduction");
+  const double* v = b->stats_host;
+  out->step = s.n;
+  out->prev_step = s.have_prev ? s.prev_step : -1;
+  for (int k = 0; k < 3; ++k) {
+    out->sum_abs_du[k] = v[k];
+    out->sum_abs_u[k] = v[3 + k];
+    out->sum_abs_u_prev[k] = v[6 + k];
+    out->sum_u[k] = v[10 + k];
+  }
+  out->sum_P = v[9];
+  out->nonfinite = (int64_t)v[kNumSums - 1];
+  out->max_abs_u = v[kNumSums];
+  s.have_prev = 1;
+  s.prev_step = s.n;
+  return LBM_OK;
+}
+
+int lbm_batch_set_launch(lbm_batch* b, int32_t bx, int32_t by, int32_t persistent) {
+  if (!b) return bfail(LBM_EINVAL, "null batch");
+  if (bx < 32 || bx % 32 != 0 || by < 1 || (int64_t)bx * by > 256)
+    return bfail(LBM_EINVAL, "block must be bx (multiple of 32) x by with bx*by <= 256");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch set_launch");
+  b->bx = bx;
+  b->by = by;
+  b->persistent = persistent ? 1 : 0;
+  b->grid = grid_for_batch(b);
+  b->graph_ok = true;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_info(lbm_batch* b, int32_t* active, int64_t* used_bytes, int64_t* total_cells) {
+  if (!b) return bfail(LBM_EINVAL, "null batch");
+  int n = 0;
+  int64_t cells = 0;
+  for (const BatchSlot& s : b->slots)
+    if (s.used) {
+      ++n;
+      cells += s.dd.N;
+    }
+  if (active) *active = n;
+  if (used_bytes) *used_bytes = b->used_bytes;
+  if (total_cells) *total_cells = cells;
+  return LBM_OK;
+}
+
+int lbm_batch_set_barrier_test(lbm_batch* b, int32_t extra_arrivals, int64_t spin_limit) {
+  if (!b) return bfail(LBM_EINVAL, "null batch");
+  if (extra_arrivals < 0 || spin_limit < 1) return bfail(LBM_EINVAL, "bad barrier test values");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "barrier test");
+  b->extra_arrivals = extra_arrivals;
+  b->spin_limit = spin_limit;
+  GridBarrier g{0u, 0u, 0, extra_arrivals};
+  e = cudaMemcpy(b->bar, &g, sizeof g, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bcuda(e, "barrier test");
+  *b->flag_host = 0;
+  drop_graph(b);
+  return LBM_OK;
+}
+
+}  // extern "C"

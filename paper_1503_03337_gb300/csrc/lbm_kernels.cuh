@@ -40,6 +40,11 @@ struct Domain {
   int pull[18], push[18];
 };
 
+// Per-step key of the stochastic-rounding hash.
+__host__ __device__ inline uint32_t step_key(int64_t n) {
+  return mix32(0x5eedu ^ (uint32_t(n) * 0x632be5abu) ^ uint32_t(uint64_t(n) >> 32));
+}
+
 template <int Q, typename R>
 __host__ __device__ inline void fill_offsets(Domain<R>& d) {
   const int N = (int)d.N, sy = d.nx, sz = d.nx * d.ny;
@@ -169,19 +174,19 @@ __host__ __device__ __forceinline__ bool touches_moving(const Domain<R>& d, cons
   return (m & d.moving) != 0;
 }
 
-// Pre-collision populations f^n of cell i into fv.
-template <int Q, typename S, typename R, bool ODD>
+// Pre-collision populations f^n of cell i into fv (CG: L2-only loads).
+template <int Q, typename S, typename R, bool ODD, bool CG = false>
 __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
                                                 int i, const Links& L, R* fv) {
   const int N = (int)d.N;
   const S* __restrict__ fc = f + i;
   if constexpr (!ODD) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((fv[A] = Codec<S, R>::load(fc + (size_t)A * d.N)), ...);
+      ((fv[A] = load_pop<S, R, CG>(fc + (size_t)A * d.N)), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else if (L.interior) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((fv[A] = Codec<S, R>::load(fc + d.pull[A])), ...);
+      ((fv[A] = load_pop<S, R, CG>(fc + d.pull[A])), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
     // f_a(x) = A[abar][x - c_a], or A[a][x] if x - c_a is a ghost
@@ -192,7 +197,7 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
             bool ghost;
             link_of<Q, A, -1>(L, off, ghost);
             const int idx = ghost ? (A * N + i) : (opposite<Q>(A) * N + i + off);
-            fv[A] = Codec<S, R>::load(f + idx);
+            fv[A] = load_pop<S, R, CG>(f + idx);
           }(),
           ...);
     }(std::make_integer_sequence<int, Q>{});
@@ -266,12 +271,12 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
   }
 }
 
-template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR, bool CG = false>
 __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
                                                            S* __restrict__ f, int i,
                                                            const Links& L) {
   R fv[Q];
-  gather<Q, S, R, ODD>(d, f, i, L, fv);
+  gather<Q, S, R, ODD, CG>(d, f, i, L, fv);
   R ux, uy, uz;
   collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
   scatter<Q, S, R, ODD, SR>(d, f, i, L, fv);
@@ -282,22 +287,23 @@ __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
 // x-range of the calling warp: when a warp lies within one x-row (block
 // width a multiple of 32) every test below is uniform across the warp, so
 // the variants never diverge inside a warp.
-template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false>
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false,
+          bool CG = false>
 __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ f,
                                                      int x, int y, int z, int x_lo = -1,
                                                      int x_hi = -1) {
   const int i = x + d.nx * (y + d.ny * z);
   if constexpr (!ODD) {
     Links L{};
-    update_with_links<Q, S, R, false, FORCE, SR>(d, f, i, L);
+    update_with_links<Q, S, R, false, FORCE, SR, CG>(d, f, i, L);
   } else {
     if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
       if (x_lo > 0 && x_hi < d.nx - 1)
-        update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links_interior(d));
+        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_interior(d));
       else
-        update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links_x(d, x));
+        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_x(d, x));
     } else {
-      update_with_links<Q, S, R, true, FORCE, SR>(d, f, i, make_links(d, x, y, z));
+      update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links(d, x, y, z));
     }
   }
 }

@@ -195,6 +195,9 @@ static_assert(basis_ok<18>(), "iD3Q18 moment basis is inconsistent");
 // ---------------------------------------------------------------------------
 template <typename S, typename R>
 struct Codec;
+// load_cg reads through L2 only (ld.global.cg).  A kernel that runs several
+// steps in one launch must read populations this way: L1 is not coherent
+// between SMs, and a line cached in one step could be stale in the next.
 template <typename R>
 struct Codec<double, R> {
   __host__ __device__ static R load(const double* p) {
@@ -204,16 +207,37 @@ struct Codec<double, R> {
     return R(*p);
 #endif
   }
+  __host__ __device__ static R load_cg(const double* p) {
+#ifdef __CUDA_ARCH__
+    return R(__ldcg(p));
+#else
+    return R(*p);
+#endif
+  }
   __host__ __device__ static void store(double* p, R v) { *p = double(v); }
 };
 template <typename R>
 struct Codec<float, R> {
   __host__ __device__ static R load(const float* p) { return R(*p); }
+  __host__ __device__ static R load_cg(const float* p) {
+#ifdef __CUDA_ARCH__
+    return R(__ldcg(p));
+#else
+    return R(*p);
+#endif
+  }
   __host__ __device__ static void store(float* p, R v) { *p = float(v); }
 };
 template <typename R>
 struct Codec<__half, R> {
   __host__ __device__ static R load(const __half* p) { return R(__half2float(*p)); }
+  __host__ __device__ static R load_cg(const __half* p) {
+#ifdef __CUDA_ARCH__
+    return R(__half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p)))));
+#else
+    return R(__half2float(*p));
+#endif
+  }
   __host__ __device__ static void store(__half* p, R v) { *p = __float2half_rn(float(v)); }
 };
 template <typename R>
@@ -221,10 +245,24 @@ struct Codec<__nv_bfloat16, R> {
   __host__ __device__ static R load(const __nv_bfloat16* p) {
     return R(__bfloat162float(*p));
   }
+  __host__ __device__ static R load_cg(const __nv_bfloat16* p) {
+#ifdef __CUDA_ARCH__
+    return R(__bfloat162float(
+        __ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p)))));
+#else
+    return R(__bfloat162float(*p));
+#endif
+  }
   __host__ __device__ static void store(__nv_bfloat16* p, R v) {
     *p = __float2bfloat16_rn(float(v));
   }
 };
+
+template <typename S, typename R, bool CG>
+__host__ __device__ __forceinline__ R load_pop(const S* p) {
+  if constexpr (CG) return Codec<S, R>::load_cg(p);
+  else return Codec<S, R>::load(p);
+}
 
 // ---------------------------------------------------------------------------
 // Stochastic rounding for 16-bit storage.  Rounding to nearest loses every

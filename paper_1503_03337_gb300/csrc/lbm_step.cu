@@ -46,10 +46,6 @@ BlockShape default_block(int nx, int ny) {
   return {bx, by, 1};
 }
 
-uint32_t step_key(int64_t n) {
-  return mix32(0x5eedu ^ (uint32_t(n) * 0x632be5abu) ^ uint32_t(uint64_t(n) >> 32));
-}
-
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> d) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;

@@ -97,6 +97,20 @@ SIGNATURES = {
     "lbm_reductions_static": (_I, [ctypes.POINTER(lbm_desc), ctypes.POINTER(lbm_geom),
                                    ctypes.POINTER(lbm_params), _I64, _VP, _VP, _I64,
                                    ctypes.POINTER(lbm_stats), _VP]),
+    "lbm_batch_create": (_I, [ctypes.c_int32, _I64, _VP, ctypes.POINTER(_VP)]),
+    "lbm_batch_destroy": (None, [_VP]),
+    "lbm_batch_add": (_I, [_VP, ctypes.POINTER(lbm_desc), ctypes.POINTER(lbm_geom),
+                           ctypes.POINTER(lbm_params), ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_remove": (_I, [_VP, ctypes.c_int32]),
+    "lbm_batch_init_equilibrium": (_I, [_VP, ctypes.c_int32, _VP, _VP, _I]),
+    "lbm_batch_step": (_I, [_VP, _I64, ctypes.c_int32]),
+    "lbm_batch_get_step": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(_I64)]),
+    "lbm_batch_read_fields": (_I, [_VP, ctypes.c_int32, ctypes.c_uint, _VP, _I, _I]),
+    "lbm_batch_reductions": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(lbm_stats)]),
+    "lbm_batch_set_launch": (_I, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "lbm_batch_info": (_I, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_I64),
+                            ctypes.POINTER(_I64)]),
+    "lbm_batch_set_barrier_test": (_I, [_VP, ctypes.c_int32, _I64]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -269,6 +283,71 @@ def lbm_memory_bytes(h):
     n = _I64()
     _check(load().lbm_memory_bytes(h, ctypes.byref(n)))
     return n.value
+
+
+# ---- batches -------------------------------------------------------------------
+
+def lbm_batch_create(capacity, budget_bytes=0, stream=None):
+    b = _VP()
+    _check(load().lbm_batch_create(int(capacity), int(budget_bytes), stream, ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_destroy(b):
+    load().lbm_batch_destroy(b)
+
+
+def lbm_batch_add(b, Q, nx, ny, nz, storage, faces, u_wall=None, **params):
+    d = lbm_desc(Q, nx, ny, nz, STORAGE_NAMES.get(storage, storage))
+    g = make_geom(faces, u_wall)
+    p = make_params(**params)
+    slot = ctypes.c_int32()
+    _check(load().lbm_batch_add(b, ctypes.byref(d), ctypes.byref(g), ctypes.byref(p),
+                                ctypes.byref(slot)))
+    return slot.value
+
+
+def lbm_batch_remove(b, slot):
+    _check(load().lbm_batch_remove(b, int(slot)))
+
+
+def lbm_batch_init_equilibrium(b, slot, u=None, p=None):
+    _check(load().lbm_batch_init_equilibrium(b, int(slot), _ptr(u), _ptr(p), 1))
+
+
+def lbm_batch_step(b, nsteps, chunk=1):
+    _check(load().lbm_batch_step(b, int(nsteps), int(chunk)))
+
+
+def lbm_batch_get_step(b, slot):
+    n = _I64()
+    _check(load().lbm_batch_get_step(b, int(slot), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_batch_read_fields(b, slot, mask, dst, dtype=LBM_DTYPE_F64):
+    _check(load().lbm_batch_read_fields(b, int(slot), int(mask), _ptr(dst), 1, int(dtype)))
+    return dst
+
+
+def lbm_batch_reductions(b, slot):
+    s = lbm_stats()
+    _check(load().lbm_batch_reductions(b, int(slot), ctypes.byref(s)))
+    return s
+
+
+def lbm_batch_set_launch(b, bx, by, persistent):
+    _check(load().lbm_batch_set_launch(b, int(bx), int(by), int(persistent)))
+
+
+def lbm_batch_info(b):
+    a, u, c = ctypes.c_int32(), _I64(), _I64()
+    _check(load().lbm_batch_info(b, ctypes.byref(a), ctypes.byref(u), ctypes.byref(c)))
+    return a.value, u.value, c.value
+
+
+def lbm_batch_set_barrier_test(b, extra_arrivals, spin_limit):
+    _check(load().lbm_batch_set_barrier_test(b, int(extra_arrivals), int(spin_limit)))
 
 
 # ---- residual forms over lbm_stats (Eq. sc, Eq. cr, Eq. cavity_creterion) ---
