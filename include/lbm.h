@@ -307,6 +307,11 @@ int lbm_batch_read_fields(lbm_batch *b, int32_t slot, unsigned mask, void *dst,
 /* As lbm_reductions for one domain (snapshot kept per domain). */
 int lbm_batch_reductions(lbm_batch *b, int32_t slot, lbm_stats *out);
 
+/* Reductions of every active domain, queued together with one
+ * synchronisation: out[k] belongs to slots[k], k < *count.  Both arrays
+ * must hold `capacity` entries. */
+int lbm_batch_reductions_all(lbm_batch *b, lbm_stats *out, int32_t *slots, int32_t *count);
+
 /* Launch shape of the batch kernel (bx multiple of 32, bx*by <= 256) and
  * mode: persistent (1: cooperative launch per chunk, grid barrier between
  * steps) or per step (0: one launch per step).  Speed only. */

@@ -212,7 +212,7 @@ struct lbm_batch {
   int* flag_host = nullptr;  // mapped pinned: barrier timed out
   int* flag_dev = nullptr;
   double* partials = nullptr;
-  double* stats_host = nullptr;  // mapped pinned, kNumStats
+  double* stats_host = nullptr;  // mapped pinned, kNumStats per slot
   double* stats_dev = nullptr;
   // launch
   int bx = 64, by = 2;
@@ -395,7 +395,7 @@ int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, 
   if (e == cudaSuccess) e = cudaHostAlloc(&b->flag_host, sizeof(int), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->flag_dev, b->flag_host, 0);
   if (e == cudaSuccess)
-    e = cudaHostAlloc(&b->stats_host, sizeof(double) * kNumStats, cudaHostAllocMapped);
+    e = cudaHostAlloc(&b->stats_host, sizeof(double) * kNumStats * capacity, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->stats_dev, b->stats_host, 0);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), b->stream);
   if (e != cudaSuccess) {
@@ -559,9 +559,8 @@ int lbm_batch_read_fields(lbm_batch* b, int32_t slot, unsigned mask, void* dst,
   return LBM_OK;
 }
 
-int lbm_batch_reductions(lbm_batch* b, int32_t slot, lbm_stats* out) {
-  if (int rc = check_slot(b, slot)) return rc;
-  if (!out) return bfail(LBM_EINVAL, "null output");
+// Queue the FP64 reductions of one slot into its stats area.
+static int queue_reduction(lbm_batch* b, int32_t slot) {
   BatchSlot& s = b->slots[slot];
   if (!s.u_prev) {
     cudaError_t e = cudaMallocAsync(&s.u_prev, sizeof(double) * 3 * s.dd.N, b->stream);
@@ -572,11 +571,17 @@ int lbm_batch_reductions(lbm_batch* b, int32_t slot, lbm_stats* out) {
     }
     s.have_prev = 0;
   }
-  cudaError_t e = launch_reduce(s.dd, s.n, s.u_prev, s.have_prev, b->partials, b->stats_dev,
-                                b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaError_t e = launch_reduce(s.dd, s.n, s.u_prev, s.have_prev, b->partials,
+                                b->stats_dev + (size_t)slot * kNumStats, b->stream);
   if (e != cudaSuccess) return bcuda(e, "batch reduction");
-  const double* v = b->stats_host;
+  return LBM_OK;
+}
+
+// Statistics of a slot whose reduction has completed; the snapshot is now
+// the current velocity.
+static void take_stats(lbm_batch* b, int32_t slot, lbm_stats* out) {
+  BatchSlot& s = b->slots[slot];
+  const double* v = b->stats_host + (size_t)slot * kNumStats;
   out->step = s.n;
   out->prev_step = s.have_prev ? s.prev_step : -1;
   for (int k = 0; k < 3; ++k) {
@@ -590,6 +595,30 @@ int lbm_batch_reductions(lbm_batch* b, int32_t slot, lbm_stats* out) {
   out->max_abs_u = v[kNumSums];
   s.have_prev = 1;
   s.prev_step = s.n;
+}
+
+int lbm_batch_reductions(lbm_batch* b, int32_t slot, lbm_stats* out) {
+  if (int rc = check_slot(b, slot)) return rc;
+  if (!out) return bfail(LBM_EINVAL, "null output");
+  if (int rc = queue_reduction(b, slot)) return rc;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch reduction");
+  take_stats(b, slot, out);
+  return LBM_OK;
+}
+
+int lbm_batch_reductions_all(lbm_batch* b, lbm_stats* out, int32_t* slots, int32_t* count) {
+  if (!b || !out || !slots || !count) return bfail(LBM_EINVAL, "null argument");
+  int n = 0;
+  for (int i = 0; i < b->capacity; ++i)
+    if (b->slots[i].used) {
+      if (int rc = queue_reduction(b, i)) return rc;
+      slots[n++] = i;
+    }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch reductions");
+  for (int k = 0; k < n; ++k) take_stats(b, slots[k], &out[k]);
+  *count = n;
   return LBM_OK;
 }
 

@@ -107,6 +107,9 @@ SIGNATURES = {
     "lbm_batch_get_step": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(_I64)]),
     "lbm_batch_read_fields": (_I, [_VP, ctypes.c_int32, ctypes.c_uint, _VP, _I, _I]),
     "lbm_batch_reductions": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(lbm_stats)]),
+    "lbm_batch_reductions_all": (_I, [_VP, ctypes.POINTER(lbm_stats),
+                                      ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
     "lbm_batch_set_launch": (_I, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "lbm_batch_info": (_I, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_I64),
                             ctypes.POINTER(_I64)]),
@@ -334,6 +337,15 @@ def lbm_batch_reductions(b, slot):
     s = lbm_stats()
     _check(load().lbm_batch_reductions(b, int(slot), ctypes.byref(s)))
     return s
+
+
+def lbm_batch_reductions_all(b, capacity):
+    """{slot: lbm_stats} for every active domain (one synchronisation)."""
+    out = (lbm_stats * capacity)()
+    slots = (ctypes.c_int32 * capacity)()
+    n = ctypes.c_int32()
+    _check(load().lbm_batch_reductions_all(b, out, slots, ctypes.byref(n)))
+    return {slots[k]: out[k] for k in range(n.value)}
 
 
 def lbm_batch_set_launch(b, bx, by, persistent):
