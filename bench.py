@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-trials", type=int, default=16)
+    ap.add_argument("--workload", default="cavity128",
+                    choices=("cavity128", "batch256", "serving"),
+                    help="cavity128: the fused-step throughput line (default); batch256: "
+                         "256 uneven domains, batched vs one launch per domain; serving: "
+                         "request trace, batched server vs one domain at a time")
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--max-steps", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -383,6 +390,110 @@ def oracle_reference_arm(a, budget_s=90.0):
                       % (a.n, a.n, nz_s, a.n, a.Q)}
 
 
+def run_batch256(a):
+    """256 independent cavities/ducts (seed 0, sides 24-160, Q14/Q18, FP32/FP16),
+    a.steps steps each: batched (persistent and per-step modes) against one
+    launch per domain per step."""
+    import torch
+
+    from paper_1503_03337_gb300 import lbm
+    lbm.load()
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    cases = [inputs.batch_case(d) for d in inputs.batch_draw(256, seed=0)]
+    cells = sum(c.cells for c in cases)
+    steps = max(2, a.steps + (a.steps & 1))
+    res = {}
+    with torch.cuda.stream(stream):
+        b = lbm.lbm_batch_create(256, 0, sp)
+        slots = []
+        for c in cases:
+            s = lbm.lbm_batch_add(b, c.Q, c.nx, c.ny, c.nz, c.storage, c.faces, c.u_wall,
+                                  nu=c.nu, force=c.force)
+            lbm.lbm_batch_init_equilibrium(b, s)
+            slots.append(s)
+        for mode, launch in (("persistent", (64, 2, 1)), ("per_step", (64, 2, 0))):
+            lbm.lbm_batch_set_launch(b, *launch)
+            lbm.lbm_batch_step(b, 4, 2)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lbm.lbm_batch_step(b, steps, 10)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            res[mode] = {"glups": cells * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps}
+        lbm.lbm_batch_destroy(b)
+        # one launch per domain per step, domains one after another
+        hs = []
+        for c in cases:
+            h = lbm.lbm_create(c.Q, c.nx, c.ny, c.nz, c.storage, sp)
+            lbm.lbm_set_geometry(h, c.faces, c.u_wall)
+            lbm.lbm_set_params(h, nu=c.nu, force=c.force)
+            lbm.lbm_set_launch(h, 64, 2, 1)
+            lbm.lbm_init_equilibrium(h)
+            hs.append(h)
+        for h in hs:
+            lbm.lbm_step(h, 2)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            for h in hs:
+                lbm.lbm_step(h, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res["one_launch_per_domain"] = {"glups": cells * steps / (ms * 1e-3) / 1e9,
+                                        "ms_per_step": ms / steps}
+        for h in hs:
+            lbm.lbm_destroy(h)
+    best = max(res["persistent"]["glups"], res["per_step"]["glups"])
+    return {"metric": "batched GLUPS, 256 uneven domains", "value": round(best, 3),
+            "unit": "GLUPS", "n_gpus": 1, "steps": steps, "higher_is_better": True,
+            "data": "synthetic (seed-0 draw of cavities and ducts)",
+            "config": {"workload": "256 domains, sides 24-160, Q14/Q18, FP32/FP16",
+                       "cells": cells, "chunk": 10},
+            "modes": res,
+            "speedup_vs_one_launch_per_domain":
+                round(best / res["one_launch_per_domain"]["glups"], 3)}
+
+
+def run_serving(a):
+    """Poisson request trace served by the continuous-batching loop and by
+    one domain at a time (FIFO), both from the same arrival times."""
+    import torch
+
+    from paper_1503_03337_gb300 import lbm
+    from paper_1503_03337_gb300.serving import (BatchBackend, SequentialBackend, Server,
+                                                summarize)
+    lbm.load()
+    stream = torch.cuda.Stream()
+    trace = inputs.request_trace(a.requests, rate=200.0, seed=0, lmin=32, lmax=256,
+                                 max_steps=a.max_steps)
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, be in (("batched", BatchBackend(256, 150 << 30, stream.cuda_stream)),
+                         ("one_at_a_time", SequentialBackend(stream.cuda_stream))):
+            t0 = time.perf_counter()
+            res = Server(be, check_every=100, tol=1e-8, chunk=50).run(trace)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            be.close()
+            out[name] = summarize(res, wall)
+    return {"metric": "serving p50/p99 time-to-converged and aggregate GLUPS",
+            "value": round(out["batched"]["glups"], 3), "unit": "GLUPS",
+            "higher_is_better": True, "n_gpus": 1,
+            "data": "synthetic Poisson trace (seed 0, 200/s)",
+            "config": {"workload": "serving", "requests": a.requests,
+                       "sizes": "32^3-256^3 (Q14/Q18, cavity/duct/pulsatile)",
+                       "max_steps": a.max_steps, "residual_tol": 1e-8,
+                       "hbm_budget_bytes": 150 << 30},
+            "batched": out["batched"], "one_at_a_time": out["one_at_a_time"]}
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -403,6 +514,11 @@ def main():
                "e2e": {"value": cb["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
+        return
+    if a.workload != "cavity128":
+        fn = run_batch256 if a.workload == "batch256" else run_serving
+        if rank == 0:
+            print(json.dumps(fn(a)))
         return
     if world > 1:
         import torch
