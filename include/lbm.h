@@ -264,9 +264,10 @@ int lbm_memory_bytes(lbm_handle *h, int64_t *bytes);
 /* ---- batches of independent domains -------------------------------------- */
 
 /* A batch advances many independent domains (different sizes, Q, storage,
- * step counters) together: one kernel launch covers every active domain, in
- * persistent mode one cooperative launch runs a whole chunk of steps with a
- * bounded grid barrier between steps, and the launches of a chunk are
+ * step counters) together.  Grouped mode (default): each step is one launch
+ * per group of domains sharing Q, storage, rounding and parity.  Persistent
+ * mode: one cooperative launch runs a whole chunk of steps of all domains,
+ * with a bounded grid barrier between steps.  The launches of a chunk are
  * captured once in a CUDA graph and replayed.  Each domain computes exactly
  * what a single-domain handle with one cell per thread computes, so a
  * domain's result is the same alone and in any mix.  Batched domains store
@@ -312,9 +313,10 @@ int lbm_batch_reductions(lbm_batch *b, int32_t slot, lbm_stats *out);
  * must hold `capacity` entries. */
 int lbm_batch_reductions_all(lbm_batch *b, lbm_stats *out, int32_t *slots, int32_t *count);
 
-/* Launch shape of the batch kernel (bx multiple of 32, bx*by <= 256) and
- * mode: persistent (1: cooperative launch per chunk, grid barrier between
- * steps) or per step (0: one launch per step).  Speed only. */
+/* Launch shape of the batch kernels (bx multiple of 32, bx*by <= 256) and
+ * mode: grouped (0: one launch per domain group per step) or persistent (1:
+ * one cooperative launch per chunk, grid barrier between steps).  Speed
+ * only. */
 int lbm_batch_set_launch(lbm_batch *b, int32_t bx, int32_t by, int32_t persistent);
 
 /* Active domains, bytes of population storage, total cells. */

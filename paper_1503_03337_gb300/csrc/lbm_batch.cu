@@ -7,14 +7,17 @@
 // all domains, and each tile runs the same per-cell update as the
 // single-domain kernel, at its own domain's parity and force time level.
 //
-// Persistent mode: one cooperative launch runs `chunk` steps, with a grid
-// barrier between steps (the in-place AA update needs every cell of step s
-// done before step s+1 reads its neighbours).  The barrier spins a bounded
-// number of times; on time-out it raises a flag, every CTA returns, and the
-// host reports LBM_ETIMEOUT.  Population loads go through L2 only (ld.cg),
-// because L1 is not coherent between SMs across the steps of one launch.
-// Per-step mode: one ordinary launch per step, no barrier.  Either way the
-// launches of a chunk are captured once in a CUDA graph and replayed.
+// Grouped mode (default): every step launches one kernel per group of
+// domains sharing Q, storage, rounding and parity; each is the single-domain
+// update specialised at compile time plus a per-CTA domain lookup.
+// Persistent mode: one cooperative launch runs `chunk` steps of all domains,
+// with a grid barrier between steps (the in-place AA update needs every cell
+// of step s done before step s+1 reads its neighbours).  The barrier spins a
+// bounded number of times; on time-out it raises a flag, every CTA returns,
+// and the host reports LBM_ETIMEOUT.  Population loads go through L2 only
+// (ld.cg), because L1 is not coherent between SMs across the steps of one
+// launch.  Either way the launches of a chunk are captured once in a CUDA
+// graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +25,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lbm_internal.h"
@@ -83,7 +87,7 @@ __device__ bool grid_sync(GridBarrier* g, long long spin_limit) {
   return ok != 0;
 }
 
-template <int Q, typename S, bool ODD, bool SR>
+template <int Q, typename S, bool ODD, bool SR, bool CG>
 __device__ __forceinline__ void batch_tile(const Domain<float>& d, int64_t t, int tiles_x,
                                            int tiles_y) {
   const int tx = (int)(t % tiles_x);
@@ -94,37 +98,41 @@ __device__ __forceinline__ void batch_tile(const Domain<float>& d, int64_t t, in
   const int y = ty * blockDim.y + threadIdx.y;
   if (x >= d.nx || y >= d.ny) return;
   const int x_lo = tx * blockDim.x + (threadIdx.x & ~31);
-  update_cell<Q, S, float, ODD, true, SR, true>(d, static_cast<S*>(d.f), x, y, z, x_lo,
-                                                x_lo + 31);
+  update_cell<Q, S, float, ODD, true, SR, CG>(d, static_cast<S*>(d.f), x, y, z, x_lo,
+                                              x_lo + 31);
 }
 
-template <int Q, typename S>
+template <int Q, typename S, bool CG>
 __device__ __forceinline__ void batch_tile_dispatch(const Domain<float>& d, int64_t t, int tx,
                                                     int ty, bool odd, bool sr) {
   if constexpr (Stochastic<S>::enabled) {
     if (sr) {
-      if (odd) batch_tile<Q, S, true, true>(d, t, tx, ty);
-      else batch_tile<Q, S, false, true>(d, t, tx, ty);
+      if (odd) batch_tile<Q, S, true, true, CG>(d, t, tx, ty);
+      else batch_tile<Q, S, false, true, CG>(d, t, tx, ty);
       return;
     }
   }
-  if (odd) batch_tile<Q, S, true, false>(d, t, tx, ty);
-  else batch_tile<Q, S, false, false>(d, t, tx, ty);
+  if (odd) batch_tile<Q, S, true, false, CG>(d, t, tx, ty);
+  else batch_tile<Q, S, false, false, CG>(d, t, tx, ty);
 }
 
-// Steps `nsteps` (persistent mode, cooperative launch) or 1 (per-step mode)
-// of every domain in `ents`; `s0` is the step offset of this launch within
-// the chunk (per-step mode).
+// Steps `nsteps` (persistent mode, cooperative launch, CG = true: loads
+// through L2 only) or 1 (per-step mode, CG = false) of every domain in
+// `ents`; `s0` is the step offset of this launch within the chunk.  A CTA
+// copies a domain's descriptor to shared memory only when its next tile
+// belongs to another domain or step.
+template <bool CG>
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__ ents, int nent,
                                                   int64_t total_tiles, int nsteps, int s0,
                                                   GridBarrier* bar, long long spin_limit) {
   __shared__ Domain<float> sd;
-  __shared__ int s_meta[5];  // Q, storage, odd, sr, tiles_x ; tiles_y below
-  __shared__ int s_tiles_y;
+  __shared__ int s_meta[6];  // Q, storage, odd, sr, tiles_x, tiles_y
   __shared__ int64_t s_begin;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
+  int cur = -1;  // entry held in sd (uniform across the CTA)
   for (int s = 0; s < nsteps; ++s) {
+    cur = -1;
     for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
       int lo = 0, hi = nent - 1;
       while (lo < hi) {
@@ -132,46 +140,80 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
         if (ents[mid].tile_begin <= t) lo = mid;
         else hi = mid - 1;
       }
-      const BatchEntry& e = ents[lo];
-      __syncthreads();  // the previous tile is done with sd
-      const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
-      for (int w = tid; w < nw; w += nthr)
-        reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
-      if (tid == 0) {
-        const int64_t n = e.n + s0 + s;
-        s_meta[0] = e.Q;
-        s_meta[1] = e.storage;
-        s_meta[2] = (int)(n & 1);
-        s_meta[3] = e.rounding == LBM_ROUND_STOCHASTIC;
-        s_meta[4] = e.tiles_x;
-        s_tiles_y = e.tiles_y;
-        s_begin = e.tile_begin;
+      if (lo != cur) {
+        const BatchEntry& e = ents[lo];
+        __syncthreads();  // every thread is done with the previous sd
+        const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
+        for (int w = tid; w < nw; w += nthr)
+          reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
+        __syncthreads();
+        // the force and hash key of this step overwrite words of the copy
+        if (tid == 0) {
+          const int64_t n = e.n + s0 + s;
+          const double c = e.period > 0.0 ? cos(2.0 * M_PI * (double)n / e.period) : 1.0;
+          for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
+          sd.key = step_key(n);
+          s_meta[0] = e.Q;
+          s_meta[1] = e.storage;
+          s_meta[2] = (int)(n & 1);
+          s_meta[3] = e.rounding == LBM_ROUND_STOCHASTIC;
+          s_meta[4] = e.tiles_x;
+          s_meta[5] = e.tiles_y;
+          s_begin = e.tile_begin;
+        }
+        __syncthreads();
+        cur = lo;
       }
-      __syncthreads();
-      // the force and hash key of this step overwrite words of the copy, so
-      // they are written after the copy has completed
-      if (tid == 0) {
-        const int64_t n = e.n + s0 + s;
-        const double c = e.period > 0.0 ? cos(2.0 * M_PI * (double)n / e.period) : 1.0;
-        for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
-        sd.key = step_key(n);
-      }
-      __syncthreads();
       const int64_t lt = t - s_begin;
       const bool odd = s_meta[2] != 0, sr = s_meta[3] != 0;
-      const int tx = s_meta[4], ty = s_tiles_y;
+      const int tx = s_meta[4], ty = s_meta[5];
       if (s_meta[0] == 14) {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<14, float>(sd, lt, tx, ty, odd, sr);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<14, __half>(sd, lt, tx, ty, odd, sr);
-        else batch_tile_dispatch<14, __nv_bfloat16>(sd, lt, tx, ty, odd, sr);
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<14, float, CG>(sd, lt, tx, ty, odd, sr);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<14, __half, CG>(sd, lt, tx, ty, odd, sr);
+        else batch_tile_dispatch<14, __nv_bfloat16, CG>(sd, lt, tx, ty, odd, sr);
       } else {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<18, float>(sd, lt, tx, ty, odd, sr);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<18, __half>(sd, lt, tx, ty, odd, sr);
-        else batch_tile_dispatch<18, __nv_bfloat16>(sd, lt, tx, ty, odd, sr);
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<18, float, CG>(sd, lt, tx, ty, odd, sr);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<18, __half, CG>(sd, lt, tx, ty, odd, sr);
+        else batch_tile_dispatch<18, __nv_bfloat16, CG>(sd, lt, tx, ty, odd, sr);
       }
     }
     if (s + 1 < nsteps && !grid_sync(bar, spin_limit)) return;
   }
+}
+
+// Grouped mode: the domains of one launch share Q, storage, rounding and
+// parity, so the kernel is the single-domain update specialised at compile
+// time; a CTA only looks up which domain its tile belongs to.
+template <int Q, typename S, bool ODD, bool SR>
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
+    k_group(const BatchEntry* __restrict__ ents, int nent, int s) {
+  __shared__ Domain<float> sd;
+  __shared__ int s_tx, s_ty;
+  __shared__ int64_t s_begin;
+  const int64_t t = blockIdx.x;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  int lo = 0, hi = nent - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ents[mid].tile_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchEntry& e = ents[lo];
+  const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
+  for (int w = tid; w < nw; w += blockDim.x * blockDim.y)
+    reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
+  __syncthreads();
+  if (tid == 0) {
+    const int64_t n = e.n + s;
+    const double c = e.period > 0.0 ? cos(2.0 * M_PI * (double)n / e.period) : 1.0;
+    for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
+    sd.key = step_key(n);
+    s_tx = e.tiles_x;
+    s_ty = e.tiles_y;
+    s_begin = e.tile_begin;
+  }
+  __syncthreads();
+  batch_tile<Q, S, ODD, SR, false>(sd, t - s_begin, s_tx, s_ty);
 }
 
 // After a chunk: advance every domain's step counter and publish the
@@ -216,15 +258,21 @@ struct lbm_batch {
   double* stats_dev = nullptr;
   // launch
   int bx = 64, by = 2;
-  int persistent = 1;
+  int persistent = 0;
   int grid = 0;
   long long spin_limit = 1ll << 26;
   int extra_arrivals = 0;
-  // table
+  // table: entries sorted by group; in persistent mode one run over all
   bool dirty = true;
   int nent = 0;
   int64_t total_tiles = 0;
   std::vector<int> order;  // slot of each entry
+  struct Group {
+    int Q, storage, sr, parity;  // parity of the domains' step counters
+    int first, count;            // entries
+    int64_t tiles;
+  };
+  std::vector<Group> groups;
   // graph of one chunk
   cudaGraphExec_t graph = nullptr;
   int graph_chunk = 0;
@@ -299,14 +347,26 @@ int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, Doma
   return LBM_OK;
 }
 
-// Rebuild and upload the descriptor table of the active domains.
+// Rebuild and upload the descriptor table of the active domains, sorted into
+// groups of equal (Q, storage, rounding, parity).  Tile prefix sums restart
+// at zero in every group (grouped launches) and the persistent kernel, which
+// walks all entries, gets its own running prefix in a second table half.
 int upload_table(lbm_batch* b) {
+  std::vector<int> idx;
+  for (int i = 0; i < (int)b->slots.size(); ++i)
+    if (b->slots[i].used) idx.push_back(i);
+  auto key = [&](int i) {
+    const BatchSlot& s = b->slots[i];
+    const int sr = s.dd.rounding == LBM_ROUND_STOCHASTIC && s.dd.storage != LBM_STORAGE_F32;
+    return std::make_tuple(s.dd.Q, s.dd.storage, sr, (int)(s.n & 1));
+  };
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return key(a) < key(c); });
   std::vector<BatchEntry> ents;
   b->order.clear();
+  b->groups.clear();
   int64_t tiles = 0;
-  for (int i = 0; i < (int)b->slots.size(); ++i) {
+  for (int i : idx) {
     const BatchSlot& s = b->slots[i];
-    if (!s.used) continue;
     BatchEntry e{};
     const double zero[3] = {0.0, 0.0, 0.0};
     e.d = to_domain<float>(s.dd, zero);
@@ -319,17 +379,39 @@ int upload_table(lbm_batch* b) {
     e.n = s.n;
     for (int k = 0; k < 3; ++k) e.force[k] = s.dd.force[k];
     e.period = s.dd.period;
-    tiles += (int64_t)e.tiles_x * e.tiles_y * s.dd.nz;
+    const int64_t nt = (int64_t)e.tiles_x * e.tiles_y * s.dd.nz;
+    tiles += nt;
+    const auto k = key(i);
+    if (b->groups.empty() ||
+        std::make_tuple(b->groups.back().Q, b->groups.back().storage, b->groups.back().sr,
+                        b->groups.back().parity) != k) {
+      b->groups.push_back({std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+                           (int)ents.size(), 0, 0});
+    }
     ents.push_back(e);
+    b->groups.back().count += 1;
+    b->groups.back().tiles += nt;
     b->order.push_back(i);
   }
   b->nent = (int)ents.size();
   b->total_tiles = tiles;
+  // second half: the same entries with tile_begin local to their group
+  std::vector<BatchEntry> local = ents;
+  for (const auto& g : b->groups) {
+    int64_t t = 0;
+    for (int k = g.first; k < g.first + g.count; ++k) {
+      local[k].tile_begin = t;
+      t += (int64_t)local[k].tiles_x * local[k].tiles_y * local[k].d.nz;
+    }
+  }
   if (!ents.empty()) {
     cudaError_t e = cudaMemcpyAsync(b->ents, ents.data(), sizeof(BatchEntry) * ents.size(),
                                     cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->ents + b->capacity, local.data(), sizeof(BatchEntry) * local.size(),
+                          cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) return bcuda(e, "batch table upload");
-    // the copy reads `ents` (pageable) before returning
+    // the copies read the (pageable) host vectors before returning
   }
   b->dirty = false;
   drop_graph(b);
@@ -338,7 +420,7 @@ int upload_table(lbm_batch* b) {
 
 int grid_for_batch(lbm_batch* b) {
   int per_sm = 0, sms = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch,
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true>,
                                                                 b->bx * b->by, 0);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e != cudaSuccess || per_sm < 1) return 0;
@@ -358,19 +440,42 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
     GridBarrier* bar = b->bar;
     long long spin = b->spin_limit;
     void* args[] = {&ents, &nent, &total, &nsteps, &s0, &bar, &spin};
-    e = cudaLaunchCooperativeKernel((const void*)k_batch, dim3(b->grid), block, args, 0,
+    e = cudaLaunchCooperativeKernel((const void*)k_batch<true>, dim3(b->grid), block, args, 0,
                                     b->stream);
     if (e != cudaSuccess) return e;
   } else {
-    const int64_t g64 = std::min<int64_t>(b->total_tiles, int64_t(1) << 30);
-    for (int s = 0; s < chunk; ++s) {
-      k_batch<<<(unsigned)g64, block, 0, b->stream>>>(b->ents, b->nent, b->total_tiles, 1, s,
-                                                      b->bar, b->spin_limit);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
+    for (int s = 0; s < chunk; ++s)
+      for (const auto& g : b->groups) {
+        const BatchEntry* ge = b->ents + b->capacity + g.first;
+        const bool odd = ((g.parity + s) & 1) != 0;
+        const unsigned grid = (unsigned)g.tiles;
+        auto go = [&]<int Q, typename S>() {
+          if constexpr (Stochastic<S>::enabled) {
+            if (g.sr) {
+              if (odd) k_group<Q, S, true, true><<<grid, block, 0, b->stream>>>(ge, g.count, s);
+              else k_group<Q, S, false, true><<<grid, block, 0, b->stream>>>(ge, g.count, s);
+              return;
+            }
+          }
+          if (odd) k_group<Q, S, true, false><<<grid, block, 0, b->stream>>>(ge, g.count, s);
+          else k_group<Q, S, false, false><<<grid, block, 0, b->stream>>>(ge, g.count, s);
+        };
+        if (g.Q == 14) {
+          if (g.storage == LBM_STORAGE_F32) go.template operator()<14, float>();
+          else if (g.storage == LBM_STORAGE_F16) go.template operator()<14, __half>();
+          else go.template operator()<14, __nv_bfloat16>();
+        } else {
+          if (g.storage == LBM_STORAGE_F32) go.template operator()<18, float>();
+          else if (g.storage == LBM_STORAGE_F16) go.template operator()<18, __half>();
+          else go.template operator()<18, __nv_bfloat16>();
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
   }
   k_batch_advance<<<1, 256, 0, b->stream>>>(b->ents, b->nent, chunk, b->bar, b->flag_dev);
+  k_batch_advance<<<1, 256, 0, b->stream>>>(b->ents + b->capacity, b->nent, chunk, b->bar,
+                                            b->flag_dev);
   return cudaGetLastError();
 }
 
@@ -389,7 +494,7 @@ int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, 
   b->capacity = capacity;
   b->budget = budget_bytes > 0 ? budget_bytes : INT64_MAX;
   b->slots.resize(capacity);
-  if (e == cudaSuccess) e = cudaMalloc(&b->ents, sizeof(BatchEntry) * capacity);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ents, 2 * sizeof(BatchEntry) * capacity);
   if (e == cudaSuccess) e = cudaMalloc(&b->bar, sizeof(GridBarrier));
   if (e == cudaSuccess) e = cudaMalloc(&b->partials, sizeof(double) * kReduceBlocks * kNumStats);
   if (e == cudaSuccess) e = cudaHostAlloc(&b->flag_host, sizeof(int), cudaHostAllocMapped);
@@ -535,6 +640,11 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps, int32_t chunk) {
     if (e != cudaSuccess) return bcuda(e, "batch step");
     for (int k : b->order) b->slots[k].n += c;
     left -= c;
+    // grouped launches key on parity: an odd chunk flips every group's parity
+    if (c & 1) {
+      for (auto& g : b->groups) g.parity ^= 1;
+      drop_graph(b);
+    }
   }
   return LBM_OK;
 }
