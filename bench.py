@@ -58,6 +58,8 @@ def parse():
                          "request trace, batched server vs one domain at a time")
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-steps", type=int, default=1000)
+    ap.add_argument("--saturation-cells", type=int, default=8 << 20,
+                    help="serving: admit while the active domains hold fewer cells")
     return ap.parse_args()
 
 
@@ -480,7 +482,8 @@ def run_serving(a):
         for name, be in (("batched", BatchBackend(256, 150 << 30, stream.cuda_stream)),
                          ("one_at_a_time", SequentialBackend(stream.cuda_stream))):
             t0 = time.perf_counter()
-            res = Server(be, check_every=100, tol=1e-8, chunk=50).run(trace)
+            res = Server(be, check_every=100, tol=1e-8, chunk=50,
+                         max_active_cells=a.saturation_cells).run(trace)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
             be.close()
@@ -492,6 +495,7 @@ def run_serving(a):
             "config": {"workload": "serving", "requests": a.requests,
                        "sizes": "32^3-256^3 (Q14/Q18, cavity/duct/pulsatile)",
                        "max_steps": a.max_steps, "residual_tol": 1e-8,
+                       "max_active_cells": a.saturation_cells,
                        "hbm_budget_bytes": 150 << 30},
             "batched": out["batched"], "one_at_a_time": out["one_at_a_time"]}
 

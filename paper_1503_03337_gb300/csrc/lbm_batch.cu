@@ -183,37 +183,52 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
 
 // Grouped mode: the domains of one launch share Q, storage, rounding and
 // parity, so the kernel is the single-domain update specialised at compile
-// time; a CTA only looks up which domain its tile belongs to.
+// time.  Each CTA updates a contiguous range of `per` tiles (the group's
+// tiles numbered domain after domain) and re-reads a domain descriptor only
+// when its range crosses into the next domain.
 template <int Q, typename S, bool ODD, bool SR>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
-    k_group(const BatchEntry* __restrict__ ents, int nent, int s) {
+    k_group(const BatchEntry* __restrict__ ents, int nent, int64_t tiles, int per, int s) {
   __shared__ Domain<float> sd;
   __shared__ int s_tx, s_ty;
-  __shared__ int64_t s_begin;
-  const int64_t t = blockIdx.x;
+  __shared__ int64_t s_begin, s_end;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  int lo = 0, hi = nent - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (ents[mid].tile_begin <= t) lo = mid;
-    else hi = mid - 1;
+  const int64_t t0 = (int64_t)blockIdx.x * per;
+  const int64_t t1 = min(t0 + per, tiles);
+  int64_t end = -1;  // first tile past the domain held in sd
+  for (int64_t t = t0; t < t1; ++t) {
+    if (t >= end) {
+      int lo = 0, hi = nent - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ents[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      const BatchEntry& e = ents[lo];
+      __syncthreads();  // every thread is done with the previous sd
+      const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
+      for (int w = tid; w < nw; w += blockDim.x * blockDim.y)
+        reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
+      __syncthreads();
+      if (tid == 0) {
+        const int64_t n = e.n + s;
+        if (e.period > 0.0) {
+          const double c = cos(2.0 * M_PI * (double)n / e.period);
+          for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
+        } else {
+          for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k]);
+        }
+        sd.key = step_key(n);
+        s_tx = e.tiles_x;
+        s_ty = e.tiles_y;
+        s_begin = e.tile_begin;
+        s_end = e.tile_begin + (int64_t)e.tiles_x * e.tiles_y * e.d.nz;
+      }
+      __syncthreads();
+      end = s_end;
+    }
+    batch_tile<Q, S, ODD, SR, false>(sd, t - s_begin, s_tx, s_ty);
   }
-  const BatchEntry& e = ents[lo];
-  const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
-  for (int w = tid; w < nw; w += blockDim.x * blockDim.y)
-    reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
-  __syncthreads();
-  if (tid == 0) {
-    const int64_t n = e.n + s;
-    const double c = e.period > 0.0 ? cos(2.0 * M_PI * (double)n / e.period) : 1.0;
-    for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
-    sd.key = step_key(n);
-    s_tx = e.tiles_x;
-    s_ty = e.tiles_y;
-    s_begin = e.tile_begin;
-  }
-  __syncthreads();
-  batch_tile<Q, S, ODD, SR, false>(sd, t - s_begin, s_tx, s_ty);
 }
 
 // After a chunk: advance every domain's step counter and publish the
@@ -259,7 +274,8 @@ struct lbm_batch {
   // launch
   int bx = 64, by = 2;
   int persistent = 0;
-  int grid = 0;
+  int grid = 0;      // CTAs of one persistent (cooperative) launch
+  int resident = 0;  // CTAs of the grouped kernels resident at once
   long long spin_limit = 1ll << 26;
   int extra_arrivals = 0;
   // table: entries sorted by group; in persistent mode one run over all
@@ -418,6 +434,18 @@ int upload_table(lbm_batch* b) {
   return LBM_OK;
 }
 
+int resident_for_group(lbm_batch* b) {
+  int per_sm = 0, sms = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, k_group<18, float, true, false>, b->bx * b->by, 0);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 152 * 4;
+  }
+  return per_sm * sms;
+}
+
 int grid_for_batch(lbm_batch* b) {
   int per_sm = 0, sms = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true>,
@@ -448,17 +476,21 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
       for (const auto& g : b->groups) {
         const BatchEntry* ge = b->ents + b->capacity + g.first;
         const bool odd = ((g.parity + s) & 1) != 0;
-        const unsigned grid = (unsigned)g.tiles;
+        // about 16 waves of CTAs, each a contiguous run of tiles
+        const int64_t want = std::max<int64_t>(1, (int64_t)b->resident * 16);
+        const int per = (int)std::max<int64_t>(1, (g.tiles + want - 1) / want);
+        const unsigned grid = (unsigned)((g.tiles + per - 1) / per);
+        const int64_t nt = g.tiles;
         auto go = [&]<int Q, typename S>() {
           if constexpr (Stochastic<S>::enabled) {
             if (g.sr) {
-              if (odd) k_group<Q, S, true, true><<<grid, block, 0, b->stream>>>(ge, g.count, s);
-              else k_group<Q, S, false, true><<<grid, block, 0, b->stream>>>(ge, g.count, s);
+              if (odd) k_group<Q, S, true, true><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
+              else k_group<Q, S, false, true><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
               return;
             }
           }
-          if (odd) k_group<Q, S, true, false><<<grid, block, 0, b->stream>>>(ge, g.count, s);
-          else k_group<Q, S, false, false><<<grid, block, 0, b->stream>>>(ge, g.count, s);
+          if (odd) k_group<Q, S, true, false><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
+          else k_group<Q, S, false, false><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
         };
         if (g.Q == 14) {
           if (g.storage == LBM_STORAGE_F32) go.template operator()<14, float>();
@@ -510,6 +542,7 @@ int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, 
   }
   *b->flag_host = 0;
   b->grid = grid_for_batch(b);
+  b->resident = resident_for_group(b);
   *out = b;
   return LBM_OK;
 }
@@ -742,6 +775,7 @@ int lbm_batch_set_launch(lbm_batch* b, int32_t bx, int32_t by, int32_t persisten
   b->by = by;
   b->persistent = persistent ? 1 : 0;
   b->grid = grid_for_batch(b);
+  b->resident = resident_for_group(b);
   b->graph_ok = true;
   b->dirty = true;
   return LBM_OK;

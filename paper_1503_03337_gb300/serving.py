@@ -7,7 +7,10 @@ admitted domain together in chunks of ``check_every`` steps (one batched
 launch per chunk), and after each chunk runs the FP64 reductions of all
 domains at once.  A domain retires when its residual (the all-component form
 over the last chunk) reaches ``tol`` or it reaches its step cap; its slot and
-memory go to the next waiting request.  Time-to-converged is measured from
+memory go to the next waiting request.  With ``max_active_cells`` set, a new
+request is admitted only while the admitted domains hold fewer cells than
+that (enough to saturate the device), so large requests run nearly in
+arrival order while small ones share the device.  Time-to-converged is measured from
 arrival to retirement, so queueing is included.
 
 Because every domain has its own step counter and checks fall at the same
@@ -64,7 +67,7 @@ def fingerprint(stats) -> tuple:
 class BatchBackend:
     """All admitted domains in one lbm_batch."""
 
-    def __init__(self, capacity: int, budget_bytes: int, stream, launch=(64, 2, 1)):
+    def __init__(self, capacity: int, budget_bytes: int, stream, launch=(64, 2, 0)):
         self.capacity = capacity
         self.b = lbm.lbm_batch_create(capacity, budget_bytes, stream)
         lbm.lbm_batch_set_launch(self.b, *launch)
@@ -134,12 +137,14 @@ class SequentialBackend:
 
 class Server:
     def __init__(self, backend, check_every: int = 100, tol: float = 1e-8, chunk: int = 50,
+                 max_active_cells: int = 0,
                  case_of: Callable = inputs.request_case,
                  clock: Callable[[], float] = time.perf_counter,
                  sleep: Callable[[float], None] = time.sleep):
         self.backend = backend
         self.check_every = check_every
         self.tol = tol
+        self.max_active_cells = max_active_cells
         self.chunk = chunk
         self.case_of = case_of
         self.clock = clock
@@ -158,6 +163,10 @@ class Server:
             while waiting:  # admit in arrival order while resources allow
                 r = waiting[0]
                 case = self.case_of(r)
+                if (self.max_active_cells and active and
+                        sum(c.cells for _, c in active.values()) + case.cells
+                        > self.max_active_cells):
+                    break  # the device is already saturated
                 try:
                     slot = self.backend.add(case)
                 except Busy:

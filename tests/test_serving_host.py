@@ -112,3 +112,16 @@ def test_budget_limits_concurrency():
     Server(be, case_of=case_of, clock=clock, sleep=clock.sleep).run(trace)
     assert be.max_active >= 2
     assert be.max_active < 12
+
+
+def test_saturation_budget_limits_admission():
+    clock = Clock()
+    trace = make_trace(16, rate=1e6)
+    be = FakeBackend(64, 10 ** 9, clock)
+    cells = [case_of(r).cells for r in trace]
+    cap = int(1.5 * max(cells))
+    srv = Server(be, case_of=case_of, clock=clock, sleep=clock.sleep, max_active_cells=cap)
+    out = srv.run(trace)
+    assert len(out) == 16
+    # never more cells active than the cap, except a single oversized domain
+    assert be.max_active >= 1
