@@ -87,13 +87,9 @@ __device__ bool grid_sync(GridBarrier* g, long long spin_limit) {
   return ok != 0;
 }
 
+// Tile (tx, ty, z) of a domain: blockDim.x cells along x by blockDim.y rows.
 template <int Q, typename S, bool ODD, bool SR, bool CG>
-__device__ __forceinline__ void batch_tile(const Domain<float>& d, int64_t t, int tiles_x,
-                                           int tiles_y) {
-  const int tx = (int)(t % tiles_x);
-  const int64_t r = t / tiles_x;
-  const int ty = (int)(r % tiles_y);
-  const int z = (int)(r / tiles_y);
+__device__ __forceinline__ void batch_tile(const Domain<float>& d, int tx, int ty, int z) {
   const int x = tx * blockDim.x + threadIdx.x;
   const int y = ty * blockDim.y + threadIdx.y;
   if (x >= d.nx || y >= d.ny) return;
@@ -103,44 +99,67 @@ __device__ __forceinline__ void batch_tile(const Domain<float>& d, int64_t t, in
 }
 
 template <int Q, typename S, bool CG>
-__device__ __forceinline__ void batch_tile_dispatch(const Domain<float>& d, int64_t t, int tx,
-                                                    int ty, bool odd, bool sr) {
+__device__ __forceinline__ void batch_tile_dispatch(const Domain<float>& d, int tx, int ty,
+                                                    int tz, bool odd, bool sr) {
   if constexpr (Stochastic<S>::enabled) {
     if (sr) {
-      if (odd) batch_tile<Q, S, true, true, CG>(d, t, tx, ty);
-      else batch_tile<Q, S, false, true, CG>(d, t, tx, ty);
+      if (odd) batch_tile<Q, S, true, true, CG>(d, tx, ty, tz);
+      else batch_tile<Q, S, false, true, CG>(d, tx, ty, tz);
       return;
     }
   }
-  if (odd) batch_tile<Q, S, true, false, CG>(d, t, tx, ty);
-  else batch_tile<Q, S, false, false, CG>(d, t, tx, ty);
+  if (odd) batch_tile<Q, S, true, false, CG>(d, tx, ty, tz);
+  else batch_tile<Q, S, false, false, CG>(d, tx, ty, tz);
 }
 
+// Walks the tiles of one domain in order (x fastest) without divisions.
+struct TileCursor {
+  int tx, ty, tz, nx, ny;
+  __device__ void start(int local, int tiles_x, int tiles_y) {
+    nx = tiles_x;
+    ny = tiles_y;
+    tx = local % nx;
+    const int r = local / nx;
+    ty = r % ny;
+    tz = r / ny;
+  }
+  __device__ void next() {
+    if (++tx == nx) {
+      tx = 0;
+      if (++ty == ny) {
+        ty = 0;
+        ++tz;
+      }
+    }
+  }
+};
+
 // Steps `nsteps` (persistent mode, cooperative launch, CG = true: loads
-// through L2 only) or 1 (per-step mode, CG = false) of every domain in
-// `ents`; `s0` is the step offset of this launch within the chunk.  A CTA
-// copies a domain's descriptor to shared memory only when its next tile
-// belongs to another domain or step.
+// through L2 only) of every domain in `ents`.  Each CTA updates a contiguous
+// range of `per` tiles of the launch's tile list every step and re-reads a
+// domain descriptor only when its range crosses into the next domain.
 template <bool CG>
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__ ents, int nent,
-                                                  int64_t total_tiles, int nsteps, int s0,
+                                                  int64_t total_tiles, int nsteps, int per,
                                                   GridBarrier* bar, long long spin_limit) {
   __shared__ Domain<float> sd;
   __shared__ int s_meta[6];  // Q, storage, odd, sr, tiles_x, tiles_y
-  __shared__ int64_t s_begin;
+  __shared__ int64_t s_begin, s_end;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
-  int cur = -1;  // entry held in sd (uniform across the CTA)
+  const int64_t t0 = (int64_t)blockIdx.x * per;
+  const int64_t t1 = min(t0 + per, total_tiles);
   for (int s = 0; s < nsteps; ++s) {
-    cur = -1;
-    for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-      int lo = 0, hi = nent - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ents[mid].tile_begin <= t) lo = mid;
-        else hi = mid - 1;
-      }
-      if (lo != cur) {
+    int64_t end = -1;
+    TileCursor cur{};
+    for (int64_t t = t0; t < t1; ++t) {
+      if (t >= end) {
+        int lo = 0, hi = nent - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ents[mid].tile_begin <= t) lo = mid;
+          else hi = mid - 1;
+        }
         const BatchEntry& e = ents[lo];
         __syncthreads();  // every thread is done with the previous sd
         const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
@@ -149,9 +168,13 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
         __syncthreads();
         // the force and hash key of this step overwrite words of the copy
         if (tid == 0) {
-          const int64_t n = e.n + s0 + s;
-          const double c = e.period > 0.0 ? cos(2.0 * M_PI * (double)n / e.period) : 1.0;
-          for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
+          const int64_t n = e.n + s;
+          if (e.period > 0.0) {
+            const double c = cos(2.0 * M_PI * (double)n / e.period);
+            for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
+          } else {
+            for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k]);
+          }
           sd.key = step_key(n);
           s_meta[0] = e.Q;
           s_meta[1] = e.storage;
@@ -160,22 +183,23 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
           s_meta[4] = e.tiles_x;
           s_meta[5] = e.tiles_y;
           s_begin = e.tile_begin;
+          s_end = e.tile_begin + (int64_t)e.tiles_x * e.tiles_y * e.d.nz;
         }
         __syncthreads();
-        cur = lo;
+        end = s_end;
+        cur.start((int)(t - s_begin), s_meta[4], s_meta[5]);
       }
-      const int64_t lt = t - s_begin;
       const bool odd = s_meta[2] != 0, sr = s_meta[3] != 0;
-      const int tx = s_meta[4], ty = s_meta[5];
       if (s_meta[0] == 14) {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<14, float, CG>(sd, lt, tx, ty, odd, sr);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<14, __half, CG>(sd, lt, tx, ty, odd, sr);
-        else batch_tile_dispatch<14, __nv_bfloat16, CG>(sd, lt, tx, ty, odd, sr);
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<14, float, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<14, __half, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
+        else batch_tile_dispatch<14, __nv_bfloat16, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
       } else {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<18, float, CG>(sd, lt, tx, ty, odd, sr);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<18, __half, CG>(sd, lt, tx, ty, odd, sr);
-        else batch_tile_dispatch<18, __nv_bfloat16, CG>(sd, lt, tx, ty, odd, sr);
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<18, float, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<18, __half, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
+        else batch_tile_dispatch<18, __nv_bfloat16, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
       }
+      cur.next();
     }
     if (s + 1 < nsteps && !grid_sync(bar, spin_limit)) return;
   }
@@ -196,6 +220,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
   const int64_t t0 = (int64_t)blockIdx.x * per;
   const int64_t t1 = min(t0 + per, tiles);
   int64_t end = -1;  // first tile past the domain held in sd
+  TileCursor cur{};
   for (int64_t t = t0; t < t1; ++t) {
     if (t >= end) {
       int lo = 0, hi = nent - 1;
@@ -226,8 +251,10 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
       }
       __syncthreads();
       end = s_end;
+      cur.start((int)(t - s_begin), s_tx, s_ty);
     }
-    batch_tile<Q, S, ODD, SR, false>(sd, t - s_begin, s_tx, s_ty);
+    batch_tile<Q, S, ODD, SR, false>(sd, cur.tx, cur.ty, cur.tz);
+    cur.next();
   }
 }
 
@@ -271,6 +298,8 @@ struct lbm_batch {
   double* partials = nullptr;
   double* stats_host = nullptr;  // mapped pinned, kNumStats per slot
   double* stats_dev = nullptr;
+  BatchEntry* table_host = nullptr;  // pinned staging of the descriptor table
+  cudaEvent_t table_done = nullptr;  // its last upload has been read
   // launch
   int bx = 64, by = 2;
   int persistent = 0;
@@ -421,13 +450,19 @@ int upload_table(lbm_batch* b) {
     }
   }
   if (!ents.empty()) {
-    cudaError_t e = cudaMemcpyAsync(b->ents, ents.data(), sizeof(BatchEntry) * ents.size(),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(b->ents + b->capacity, local.data(), sizeof(BatchEntry) * local.size(),
+    // the pinned staging area may still be read by the previous upload
+    cudaError_t e = cudaEventSynchronize(b->table_done);
+    if (e == cudaSuccess) {
+      std::memcpy(b->table_host, ents.data(), sizeof(BatchEntry) * ents.size());
+      std::memcpy(b->table_host + b->capacity, local.data(), sizeof(BatchEntry) * local.size());
+      e = cudaMemcpyAsync(b->ents, b->table_host, sizeof(BatchEntry) * ents.size(),
                           cudaMemcpyHostToDevice, b->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->ents + b->capacity, b->table_host + b->capacity,
+                          sizeof(BatchEntry) * local.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->table_done, b->stream);
     if (e != cudaSuccess) return bcuda(e, "batch table upload");
-    // the copies read the (pageable) host vectors before returning
   }
   b->dirty = false;
   drop_graph(b);
@@ -464,10 +499,11 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
     const BatchEntry* ents = b->ents;
     int nent = b->nent;
     int64_t total = b->total_tiles;
-    int nsteps = chunk, s0 = 0;
+    int nsteps = chunk;
+    int per = (int)std::max<int64_t>(1, (total + b->grid - 1) / b->grid);
     GridBarrier* bar = b->bar;
     long long spin = b->spin_limit;
-    void* args[] = {&ents, &nent, &total, &nsteps, &s0, &bar, &spin};
+    void* args[] = {&ents, &nent, &total, &nsteps, &per, &bar, &spin};
     e = cudaLaunchCooperativeKernel((const void*)k_batch<true>, dim3(b->grid), block, args, 0,
                                     b->stream);
     if (e != cudaSuccess) return e;
@@ -534,6 +570,9 @@ int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, 
   if (e == cudaSuccess)
     e = cudaHostAlloc(&b->stats_host, sizeof(double) * kNumStats * capacity, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->stats_dev, b->stats_host, 0);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(&b->table_host, 2 * sizeof(BatchEntry) * capacity, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->table_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), b->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -560,6 +599,8 @@ void lbm_batch_destroy(lbm_batch* b) {
   if (b->partials) cudaFree(b->partials);
   if (b->flag_host) cudaFreeHost(b->flag_host);
   if (b->stats_host) cudaFreeHost(b->stats_host);
+  if (b->table_host) cudaFreeHost(b->table_host);
+  if (b->table_done) cudaEventDestroy(b->table_done);
   delete b;
 }
 
