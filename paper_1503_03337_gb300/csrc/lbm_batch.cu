@@ -318,10 +318,13 @@ struct lbm_batch {
     int64_t tiles;
   };
   std::vector<Group> groups;
-  // graph of one chunk
+  // graph of one chunk; captured when a table version runs a second chunk
+  // (membership changes invalidate it, and a capture that is used once
+  // costs more than it saves)
   cudaGraphExec_t graph = nullptr;
   int graph_chunk = 0;
   bool graph_ok = true;
+  int chunks_this_version = 0;
 };
 
 namespace {
@@ -465,6 +468,7 @@ int upload_table(lbm_batch* b) {
     if (e != cudaSuccess) return bcuda(e, "batch table upload");
   }
   b->dirty = false;
+  b->chunks_this_version = 0;
   drop_graph(b);
   return LBM_OK;
 }
@@ -686,7 +690,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps, int32_t chunk) {
   while (left > 0) {
     const int c = (int)std::min<int64_t>(left, chunk);
     cudaError_t e = cudaSuccess;
-    if (c == chunk && b->graph_ok) {
+    if (c == chunk && b->graph_ok && (b->graph || b->chunks_this_version >= 1)) {
       if (!b->graph || b->graph_chunk != c) {
         drop_graph(b);
         cudaGraph_t g = nullptr;
@@ -714,6 +718,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps, int32_t chunk) {
     if (e != cudaSuccess) return bcuda(e, "batch step");
     for (int k : b->order) b->slots[k].n += c;
     left -= c;
+    b->chunks_this_version += 1;
     // grouped launches key on parity: an odd chunk flips every group's parity
     if (c & 1) {
       for (auto& g : b->groups) g.parity ^= 1;
