@@ -516,9 +516,9 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
       for (const auto& g : b->groups) {
         const BatchEntry* ge = b->ents + b->capacity + g.first;
         const bool odd = ((g.parity + s) & 1) != 0;
-        // about 16 waves of CTAs, each a contiguous run of tiles
-        const int64_t want = std::max<int64_t>(1, (int64_t)b->resident * 16);
-        const int per = (int)std::max<int64_t>(1, (g.tiles + want - 1) / want);
+        // about two waves of CTAs, each a contiguous run of at most 32 tiles
+        const int64_t waves2 = std::max<int64_t>(1, (int64_t)b->resident * 2);
+        const int per = (int)std::min<int64_t>(32, std::max<int64_t>(1, g.tiles / waves2));
         const unsigned grid = (unsigned)((g.tiles + per - 1) / per);
         const int64_t nt = g.tiles;
         auto go = [&]<int Q, typename S>() {
