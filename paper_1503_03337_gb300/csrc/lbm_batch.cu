@@ -88,14 +88,14 @@ __device__ bool grid_sync(GridBarrier* g, long long spin_limit) {
 }
 
 // Tile (tx, ty, z) of a domain: blockDim.x cells along x by blockDim.y rows.
-template <int Q, typename S, bool ODD, bool SR, bool CG>
+template <int Q, typename S, bool ODD, bool SR, bool CG, bool FORCE = true>
 __device__ __forceinline__ void batch_tile(const Domain<float>& d, int tx, int ty, int z) {
   const int x = tx * blockDim.x + threadIdx.x;
   const int y = ty * blockDim.y + threadIdx.y;
   if (x >= d.nx || y >= d.ny) return;
   const int x_lo = tx * blockDim.x + (threadIdx.x & ~31);
-  update_cell<Q, S, float, ODD, true, SR, CG>(d, static_cast<S*>(d.f), x, y, z, x_lo,
-                                              x_lo + 31);
+  update_cell<Q, S, float, ODD, FORCE, SR, CG>(d, static_cast<S*>(d.f), x, y, z, x_lo,
+                                               x_lo + 31);
 }
 
 template <int Q, typename S, bool CG>
@@ -209,8 +209,9 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
 // parity, so the kernel is the single-domain update specialised at compile
 // time.  Each CTA updates a contiguous range of `per` tiles (the group's
 // tiles numbered domain after domain) and re-reads a domain descriptor only
-// when its range crosses into the next domain.
-template <int Q, typename S, bool ODD, bool SR>
+// when its range crosses into the next domain.  FORCE = false groups hold
+// only domains without a body force.
+template <int Q, typename S, bool ODD, bool SR, bool FORCE>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
     k_group(const BatchEntry* __restrict__ ents, int nent, int64_t tiles, int per, int s) {
   __shared__ Domain<float> sd;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
       end = s_end;
       cur.start((int)(t - s_begin), s_tx, s_ty);
     }
-    batch_tile<Q, S, ODD, SR, false>(sd, cur.tx, cur.ty, cur.tz);
+    batch_tile<Q, S, ODD, SR, false, FORCE>(sd, cur.tx, cur.ty, cur.tz);
     cur.next();
   }
 }
@@ -313,8 +314,8 @@ struct lbm_batch {
   int64_t total_tiles = 0;
   std::vector<int> order;  // slot of each entry
   struct Group {
-    int Q, storage, sr, parity;  // parity of the domains' step counters
-    int first, count;            // entries
+    int Q, storage, sr, force, parity;  // parity of the domains' step counters
+    int first, count;                   // entries
     int64_t tiles;
   };
   std::vector<Group> groups;
@@ -406,7 +407,8 @@ int upload_table(lbm_batch* b) {
   auto key = [&](int i) {
     const BatchSlot& s = b->slots[i];
     const int sr = s.dd.rounding == LBM_ROUND_STOCHASTIC && s.dd.storage != LBM_STORAGE_F32;
-    return std::make_tuple(s.dd.Q, s.dd.storage, sr, (int)(s.n & 1));
+    const int force = s.dd.force[0] != 0.0 || s.dd.force[1] != 0.0 || s.dd.force[2] != 0.0;
+    return std::make_tuple(s.dd.Q, s.dd.storage, sr, force, (int)(s.n & 1));
   };
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return key(a) < key(c); });
   std::vector<BatchEntry> ents;
@@ -432,9 +434,9 @@ int upload_table(lbm_batch* b) {
     const auto k = key(i);
     if (b->groups.empty() ||
         std::make_tuple(b->groups.back().Q, b->groups.back().storage, b->groups.back().sr,
-                        b->groups.back().parity) != k) {
+                        b->groups.back().force, b->groups.back().parity) != k) {
       b->groups.push_back({std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-                           (int)ents.size(), 0, 0});
+                           std::get<4>(k), (int)ents.size(), 0, 0});
     }
     ents.push_back(e);
     b->groups.back().count += 1;
@@ -476,7 +478,7 @@ int upload_table(lbm_batch* b) {
 int resident_for_group(lbm_batch* b) {
   int per_sm = 0, sms = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, k_group<18, float, true, false>, b->bx * b->by, 0);
+      &per_sm, k_group<18, float, true, false, true>, b->bx * b->by, 0);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
@@ -521,16 +523,20 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
         const int per = (int)std::min<int64_t>(32, std::max<int64_t>(1, g.tiles / waves2));
         const unsigned grid = (unsigned)((g.tiles + per - 1) / per);
         const int64_t nt = g.tiles;
-        auto go = [&]<int Q, typename S>() {
+        auto go2 = [&]<int Q, typename S, bool FORCE>() {
           if constexpr (Stochastic<S>::enabled) {
             if (g.sr) {
-              if (odd) k_group<Q, S, true, true><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
-              else k_group<Q, S, false, true><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
+              if (odd) k_group<Q, S, true, true, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
+              else k_group<Q, S, false, true, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
               return;
             }
           }
-          if (odd) k_group<Q, S, true, false><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
-          else k_group<Q, S, false, false><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
+          if (odd) k_group<Q, S, true, false, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
+          else k_group<Q, S, false, false, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
+        };
+        auto go = [&]<int Q, typename S>() {
+          if (g.force) go2.template operator()<Q, S, true>();
+          else go2.template operator()<Q, S, false>();
         };
         if (g.Q == 14) {
           if (g.storage == LBM_STORAGE_F32) go.template operator()<14, float>();
