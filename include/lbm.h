@@ -264,11 +264,8 @@ int lbm_memory_bytes(lbm_handle *h, int64_t *bytes);
 /* ---- batches of independent domains -------------------------------------- */
 
 /* A batch advances many independent domains (different sizes, Q, storage,
- * step counters) together.  Grouped mode (default): domains are packed into
- * clusters that fit in the L2 cache, a chunk runs all its steps on one
- * cluster before the next (so small domains stay L2-resident), and each
- * step of a cluster is one launch per group of domains sharing Q, storage,
- * rounding, force and parity.  Persistent
+ * step counters) together.  Grouped mode (default): each step is one launch
+ * per group of domains sharing Q, storage, rounding and parity.  Persistent
  * mode: one cooperative launch runs a whole chunk of steps of all domains,
  * with a bounded grid barrier between steps.  The launches of a chunk are
  * captured once in a CUDA graph and replayed.  Each domain computes exactly

@@ -314,13 +314,11 @@ struct lbm_batch {
   int64_t total_tiles = 0;
   std::vector<int> order;  // slot of each entry
   struct Group {
-    int cluster;                        // L2 cluster the group belongs to
     int Q, storage, sr, force, parity;  // parity of the domains' step counters
     int first, count;                   // entries
     int64_t tiles;
   };
-  std::vector<Group> groups;  // ordered by cluster
-  int64_t l2_budget = 0;      // bytes of populations one cluster may hold
+  std::vector<Group> groups;
   // graph of one chunk; captured when a table version runs a second chunk
   // (membership changes invalidate it, and a capture that is used once
   // costs more than it saves)
@@ -398,47 +396,19 @@ int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, Doma
   return LBM_OK;
 }
 
-// Rebuild and upload the descriptor table of the active domains.
-//
-// Domains are first packed into L2 clusters: sets whose population buffers
-// together fit in about three quarters of the L2 cache (a domain larger than
-// that is a cluster of its own).  A chunk runs all its steps on one cluster
-// before the next, so small and medium domains stay L2-resident from step to
-// step, as they would if served one at a time; domains are independent, so
-// the order changes no result.  Within a cluster, domains are sorted into
-// groups of equal (Q, storage, rounding, force, parity) for the grouped
-// launches.  Tile prefix sums restart at zero in every group, and the
-// persistent kernel, which walks all entries, gets its own running prefix in
-// a second table half.
+// Rebuild and upload the descriptor table of the active domains, sorted into
+// groups of equal (Q, storage, rounding, parity).  Tile prefix sums restart
+// at zero in every group (grouped launches) and the persistent kernel, which
+// walks all entries, gets its own running prefix in a second table half.
 int upload_table(lbm_batch* b) {
   std::vector<int> idx;
   for (int i = 0; i < (int)b->slots.size(); ++i)
     if (b->slots[i].used) idx.push_back(i);
-  // first-fit packing in slot order
-  std::vector<int> cluster_of(b->slots.size(), 0);
-  {
-    std::vector<int64_t> fill;
-    for (int i : idx) {
-      const int64_t sz = (int64_t)b->slots[i].fbytes;
-      int c = -1;
-      for (int k = 0; k < (int)fill.size(); ++k)
-        if (fill[k] + sz <= b->l2_budget) {
-          c = k;
-          break;
-        }
-      if (c < 0) {
-        c = (int)fill.size();
-        fill.push_back(0);
-      }
-      fill[c] += sz;
-      cluster_of[i] = c;
-    }
-  }
   auto key = [&](int i) {
     const BatchSlot& s = b->slots[i];
     const int sr = s.dd.rounding == LBM_ROUND_STOCHASTIC && s.dd.storage != LBM_STORAGE_F32;
     const int force = s.dd.force[0] != 0.0 || s.dd.force[1] != 0.0 || s.dd.force[2] != 0.0;
-    return std::make_tuple(cluster_of[i], s.dd.Q, s.dd.storage, sr, force, (int)(s.n & 1));
+    return std::make_tuple(s.dd.Q, s.dd.storage, sr, force, (int)(s.n & 1));
   };
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return key(a) < key(c); });
   std::vector<BatchEntry> ents;
@@ -463,11 +433,10 @@ int upload_table(lbm_batch* b) {
     tiles += nt;
     const auto k = key(i);
     if (b->groups.empty() ||
-        std::make_tuple(b->groups.back().cluster, b->groups.back().Q, b->groups.back().storage,
-                        b->groups.back().sr, b->groups.back().force,
-                        b->groups.back().parity) != k) {
+        std::make_tuple(b->groups.back().Q, b->groups.back().storage, b->groups.back().sr,
+                        b->groups.back().force, b->groups.back().parity) != k) {
       b->groups.push_back({std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-                           std::get<4>(k), std::get<5>(k), (int)ents.size(), 0, 0});
+                           std::get<4>(k), (int)ents.size(), 0, 0});
     }
     ents.push_back(e);
     b->groups.back().count += 1;
@@ -545,13 +514,8 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
                                     b->stream);
     if (e != cudaSuccess) return e;
   } else {
-    size_t gb = 0;
-    while (gb < b->groups.size()) {  // one cluster: groups [gb, ge)
-      size_t gend = gb;
-      while (gend < b->groups.size() && b->groups[gend].cluster == b->groups[gb].cluster) ++gend;
-      for (int s = 0; s < chunk; ++s)
-        for (size_t gi = gb; gi < gend; ++gi) {
-        const auto& g = b->groups[gi];
+    for (int s = 0; s < chunk; ++s)
+      for (const auto& g : b->groups) {
         const BatchEntry* ge = b->ents + b->capacity + g.first;
         const bool odd = ((g.parity + s) & 1) != 0;
         // about two waves of CTAs, each a contiguous run of at most 32 tiles
@@ -585,9 +549,7 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        }
-      gb = gend;
-    }
+      }
   }
   k_batch_advance<<<1, 256, 0, b->stream>>>(b->ents, b->nent, chunk, b->bar, b->flag_dev);
   k_batch_advance<<<1, 256, 0, b->stream>>>(b->ents + b->capacity, b->nent, chunk, b->bar,
@@ -630,14 +592,6 @@ int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, 
   *b->flag_host = 0;
   b->grid = grid_for_batch(b);
   b->resident = resident_for_group(b);
-  {
-    int l2 = 0;
-    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device) != cudaSuccess || l2 <= 0) {
-      cudaGetLastError();
-      l2 = 96 << 20;
-    }
-    b->l2_budget = (int64_t)l2 * 3 / 4;
-  }
   *out = b;
   return LBM_OK;
 }
