@@ -315,8 +315,8 @@ int lbm_batch_reductions_all(lbm_batch *b, lbm_stats *out, int32_t *slots, int32
 
 /* Launch shape of the batch kernels (bx multiple of 32, bx*by <= 256) and
  * mode: grouped (0: one launch per domain group per step) or persistent (1:
- * one cooperative launch per chunk, grid barrier between steps).  Speed
- * only. */
+ * one cooperative launch per chunk, grid barrier between steps; a batch
+ * holding a stochastically rounded domain runs grouped).  Speed only. */
 int lbm_batch_set_launch(lbm_batch *b, int32_t bx, int32_t by, int32_t persistent);
 
 /* Active domains, bytes of population storage, total cells. */

@@ -28,236 +28,12 @@
 #include <tuple>
 #include <vector>
 
-#include "lbm_internal.h"
-#include "lbm_kernels.cuh"
+
+#include "lbm_batch.cuh"
 
 namespace lbm {
-
-template <typename R>
-Domain<R> to_domain(const DomainDesc& d, const double F[3]);
-
+namespace batchk {
 namespace {
-
-struct BatchEntry {
-  Domain<float> d;  // F and key are set per step on the device
-  int Q, storage, rounding;
-  int tiles_x, tiles_y;
-  int64_t tile_begin;  // first tile of this domain in the launch
-  int64_t n;           // step counter of this domain before the launch
-  double force[3];
-  double period;
-};
-
-struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
-  int timed_out;
-  int extra;  // test hook: arrivals the barrier waits for beyond the grid
-};
-
-// Bounded grid-wide barrier for a cooperative launch.  Returns false (in
-// every thread of the CTA) if the wait timed out anywhere.
-__device__ bool grid_sync(GridBarrier* g, long long spin_limit) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    volatile unsigned int* vgen = &g->gen;
-    volatile int* vflag = &g->timed_out;
-    const unsigned int gen = *vgen;
-    __threadfence();
-    const unsigned int expected = gridDim.x + (unsigned int)g->extra;
-    if (atomicAdd(&g->count, 1u) == expected - 1) {
-      atomicExch(&g->count, 0u);
-      __threadfence();
-      atomicAdd(&g->gen, 1u);
-    } else {
-      long long k = 0;
-      while (*vgen == gen) {
-        if (*vflag || ++k > spin_limit) {
-          atomicExch(&g->timed_out, 1);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __threadfence();
-    ok = !*vflag;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-// Tile (tx, ty, z) of a domain: blockDim.x cells along x by blockDim.y rows.
-template <int Q, typename S, bool ODD, bool SR, bool CG, bool FORCE = true>
-__device__ __forceinline__ void batch_tile(const Domain<float>& d, int tx, int ty, int z) {
-  const int x = tx * blockDim.x + threadIdx.x;
-  const int y = ty * blockDim.y + threadIdx.y;
-  if (x >= d.nx || y >= d.ny) return;
-  const int x_lo = tx * blockDim.x + (threadIdx.x & ~31);
-  update_cell<Q, S, float, ODD, FORCE, SR, CG>(d, static_cast<S*>(d.f), x, y, z, x_lo,
-                                               x_lo + 31);
-}
-
-template <int Q, typename S, bool CG>
-__device__ __forceinline__ void batch_tile_dispatch(const Domain<float>& d, int tx, int ty,
-                                                    int tz, bool odd, bool sr) {
-  if constexpr (Stochastic<S>::enabled) {
-    if (sr) {
-      if (odd) batch_tile<Q, S, true, true, CG>(d, tx, ty, tz);
-      else batch_tile<Q, S, false, true, CG>(d, tx, ty, tz);
-      return;
-    }
-  }
-  if (odd) batch_tile<Q, S, true, false, CG>(d, tx, ty, tz);
-  else batch_tile<Q, S, false, false, CG>(d, tx, ty, tz);
-}
-
-// Walks the tiles of one domain in order (x fastest) without divisions.
-struct TileCursor {
-  int tx, ty, tz, nx, ny;
-  __device__ void start(int local, int tiles_x, int tiles_y) {
-    nx = tiles_x;
-    ny = tiles_y;
-    tx = local % nx;
-    const int r = local / nx;
-    ty = r % ny;
-    tz = r / ny;
-  }
-  __device__ void next() {
-    if (++tx == nx) {
-      tx = 0;
-      if (++ty == ny) {
-        ty = 0;
-        ++tz;
-      }
-    }
-  }
-};
-
-// Steps `nsteps` (persistent mode, cooperative launch, CG = true: loads
-// through L2 only) of every domain in `ents`.  Each CTA updates a contiguous
-// range of `per` tiles of the launch's tile list every step and re-reads a
-// domain descriptor only when its range crosses into the next domain.
-template <bool CG>
-__global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__ ents, int nent,
-                                                  int64_t total_tiles, int nsteps, int per,
-                                                  GridBarrier* bar, long long spin_limit) {
-  __shared__ Domain<float> sd;
-  __shared__ int s_meta[6];  // Q, storage, odd, sr, tiles_x, tiles_y
-  __shared__ int64_t s_begin, s_end;
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int nthr = blockDim.x * blockDim.y;
-  const int64_t t0 = (int64_t)blockIdx.x * per;
-  const int64_t t1 = min(t0 + per, total_tiles);
-  for (int s = 0; s < nsteps; ++s) {
-    int64_t end = -1;
-    TileCursor cur{};
-    for (int64_t t = t0; t < t1; ++t) {
-      if (t >= end) {
-        int lo = 0, hi = nent - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (ents[mid].tile_begin <= t) lo = mid;
-          else hi = mid - 1;
-        }
-        const BatchEntry& e = ents[lo];
-        __syncthreads();  // every thread is done with the previous sd
-        const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
-        for (int w = tid; w < nw; w += nthr)
-          reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
-        __syncthreads();
-        // the force and hash key of this step overwrite words of the copy
-        if (tid == 0) {
-          const int64_t n = e.n + s;
-          if (e.period > 0.0) {
-            const double c = cos(2.0 * M_PI * (double)n / e.period);
-            for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
-          } else {
-            for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k]);
-          }
-          sd.key = step_key(n);
-          s_meta[0] = e.Q;
-          s_meta[1] = e.storage;
-          s_meta[2] = (int)(n & 1);
-          s_meta[3] = e.rounding == LBM_ROUND_STOCHASTIC;
-          s_meta[4] = e.tiles_x;
-          s_meta[5] = e.tiles_y;
-          s_begin = e.tile_begin;
-          s_end = e.tile_begin + (int64_t)e.tiles_x * e.tiles_y * e.d.nz;
-        }
-        __syncthreads();
-        end = s_end;
-        cur.start((int)(t - s_begin), s_meta[4], s_meta[5]);
-      }
-      const bool odd = s_meta[2] != 0, sr = s_meta[3] != 0;
-      if (s_meta[0] == 14) {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<14, float, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<14, __half, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
-        else batch_tile_dispatch<14, __nv_bfloat16, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
-      } else {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_dispatch<18, float, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_dispatch<18, __half, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
-        else batch_tile_dispatch<18, __nv_bfloat16, CG>(sd, cur.tx, cur.ty, cur.tz, odd, sr);
-      }
-      cur.next();
-    }
-    if (s + 1 < nsteps && !grid_sync(bar, spin_limit)) return;
-  }
-}
-
-// Grouped mode: the domains of one launch share Q, storage, rounding and
-// parity, so the kernel is the single-domain update specialised at compile
-// time.  Each CTA updates a contiguous range of `per` tiles (the group's
-// tiles numbered domain after domain) and re-reads a domain descriptor only
-// when its range crosses into the next domain.  FORCE = false groups hold
-// only domains without a body force.
-template <int Q, typename S, bool ODD, bool SR, bool FORCE>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
-    k_group(const BatchEntry* __restrict__ ents, int nent, int64_t tiles, int per, int s) {
-  __shared__ Domain<float> sd;
-  __shared__ int s_tx, s_ty;
-  __shared__ int64_t s_begin, s_end;
-  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-  const int64_t t0 = (int64_t)blockIdx.x * per;
-  const int64_t t1 = min(t0 + per, tiles);
-  int64_t end = -1;  // first tile past the domain held in sd
-  TileCursor cur{};
-  for (int64_t t = t0; t < t1; ++t) {
-    if (t >= end) {
-      int lo = 0, hi = nent - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ents[mid].tile_begin <= t) lo = mid;
-        else hi = mid - 1;
-      }
-      const BatchEntry& e = ents[lo];
-      __syncthreads();  // every thread is done with the previous sd
-      const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
-      for (int w = tid; w < nw; w += blockDim.x * blockDim.y)
-        reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(&e.d)[w];
-      __syncthreads();
-      if (tid == 0) {
-        const int64_t n = e.n + s;
-        if (e.period > 0.0) {
-          const double c = cos(2.0 * M_PI * (double)n / e.period);
-          for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k] * c);
-        } else {
-          for (int k = 0; k < 3; ++k) sd.F[k] = float(e.force[k]);
-        }
-        sd.key = step_key(n);
-        s_tx = e.tiles_x;
-        s_ty = e.tiles_y;
-        s_begin = e.tile_begin;
-        s_end = e.tile_begin + (int64_t)e.tiles_x * e.tiles_y * e.d.nz;
-      }
-      __syncthreads();
-      end = s_end;
-      cur.start((int)(t - s_begin), s_tx, s_ty);
-    }
-    batch_tile<Q, S, ODD, SR, false, FORCE>(sd, cur.tx, cur.ty, cur.tz);
-    cur.next();
-  }
-}
 
 // After a chunk: advance every domain's step counter and publish the
 // barrier's time-out flag to the host.
@@ -269,7 +45,10 @@ __global__ void k_batch_advance(BatchEntry* ents, int nent, int nsteps, const Gr
 }
 
 }  // namespace
+}  // namespace batchk
 }  // namespace lbm
+
+using namespace lbm::batchk;
 
 using namespace lbm;
 
@@ -304,6 +83,7 @@ struct lbm_batch {
   // launch
   int bx = 64, by = 2;
   int persistent = 0;
+  bool has_sr = false;  // some domain rounds stochastically (grouped mode only)
   int grid = 0;      // CTAs of one persistent (cooperative) launch
   int resident = 0;  // CTAs of the grouped kernels resident at once
   long long spin_limit = 1ll << 26;
@@ -445,6 +225,8 @@ int upload_table(lbm_batch* b) {
   }
   b->nent = (int)ents.size();
   b->total_tiles = tiles;
+  b->has_sr = false;
+  for (const auto& g : b->groups) b->has_sr = b->has_sr || g.sr;
   // second half: the same entries with tile_begin local to their group
   std::vector<BatchEntry> local = ents;
   for (const auto& g : b->groups) {
@@ -476,11 +258,9 @@ int upload_table(lbm_batch* b) {
 }
 
 int resident_for_group(lbm_batch* b) {
-  int per_sm = 0, sms = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, k_group<18, float, true, false, true>, b->bx * b->by, 0);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  if (e != cudaSuccess || per_sm < 1) {
+  int per_sm = group_blocks_per_sm(b->bx * b->by), sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     return 152 * 4;
   }
@@ -488,66 +268,40 @@ int resident_for_group(lbm_batch* b) {
 }
 
 int grid_for_batch(lbm_batch* b) {
-  int per_sm = 0, sms = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true>,
-                                                                b->bx * b->by, 0);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  if (e != cudaSuccess || per_sm < 1) return 0;
+  int per_sm = persistent_blocks_per_sm(b->bx * b->by), sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
   return per_sm * sms;
 }
 
 // Queue one chunk of `chunk` steps (no graph).
 cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
   dim3 block(b->bx, b->by, 1);
-  if (b->persistent) {
+  if (b->persistent && !b->has_sr) {
     cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier) - sizeof(int), b->stream);
     if (e != cudaSuccess) return e;
-    const BatchEntry* ents = b->ents;
-    int nent = b->nent;
-    int64_t total = b->total_tiles;
-    int nsteps = chunk;
-    int per = (int)std::max<int64_t>(1, (total + b->grid - 1) / b->grid);
-    GridBarrier* bar = b->bar;
-    long long spin = b->spin_limit;
-    void* args[] = {&ents, &nent, &total, &nsteps, &per, &bar, &spin};
-    e = cudaLaunchCooperativeKernel((const void*)k_batch<true>, dim3(b->grid), block, args, 0,
-                                    b->stream);
+    PersistentLaunch p{b->ents, b->nent, b->total_tiles, chunk,
+                       (int)std::max<int64_t>(1, (b->total_tiles + b->grid - 1) / b->grid),
+                       b->bar, b->spin_limit, dim3(b->grid), block, b->stream};
+    e = launch_persistent(p);
     if (e != cudaSuccess) return e;
   } else {
     for (int s = 0; s < chunk; ++s)
       for (const auto& g : b->groups) {
         const BatchEntry* ge = b->ents + b->capacity + g.first;
         const bool odd = ((g.parity + s) & 1) != 0;
-        // about two waves of CTAs, each a contiguous run of at most 32 tiles
-        const int64_t waves2 = std::max<int64_t>(1, (int64_t)b->resident * 2);
-        const int per = (int)std::min<int64_t>(32, std::max<int64_t>(1, g.tiles / waves2));
+        // contiguous runs of tiles per CTA, short enough to leave about 16
+        // waves of CTAs (a partly filled last wave then costs little)
+        const int64_t waves16 = std::max<int64_t>(1, (int64_t)b->resident * 16);
+        const int per = (int)std::min<int64_t>(32, std::max<int64_t>(1, g.tiles / waves16));
         const unsigned grid = (unsigned)((g.tiles + per - 1) / per);
         const int64_t nt = g.tiles;
-        auto go2 = [&]<int Q, typename S, bool FORCE>() {
-          if constexpr (Stochastic<S>::enabled) {
-            if (g.sr) {
-              if (odd) k_group<Q, S, true, true, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
-              else k_group<Q, S, false, true, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
-              return;
-            }
-          }
-          if (odd) k_group<Q, S, true, false, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
-          else k_group<Q, S, false, false, FORCE><<<grid, block, 0, b->stream>>>(ge, g.count, nt, per, s);
-        };
-        auto go = [&]<int Q, typename S>() {
-          if (g.force) go2.template operator()<Q, S, true>();
-          else go2.template operator()<Q, S, false>();
-        };
-        if (g.Q == 14) {
-          if (g.storage == LBM_STORAGE_F32) go.template operator()<14, float>();
-          else if (g.storage == LBM_STORAGE_F16) go.template operator()<14, __half>();
-          else go.template operator()<14, __nv_bfloat16>();
-        } else {
-          if (g.storage == LBM_STORAGE_F32) go.template operator()<18, float>();
-          else if (g.storage == LBM_STORAGE_F16) go.template operator()<18, __half>();
-          else go.template operator()<18, __nv_bfloat16>();
-        }
-        cudaError_t e = cudaGetLastError();
+        GroupLaunch gl{g.storage, g.sr, g.force, odd ? 1 : 0, dim3(grid), block, b->stream,
+                       ge, g.count, nt, per, s};
+        cudaError_t e = g.Q == 14 ? launch_group_q14(gl) : launch_group_q18(gl);
         if (e != cudaSuccess) return e;
       }
   }
