@@ -37,7 +37,7 @@ struct GridBarrier {
 
 // Bounded grid-wide barrier for a cooperative launch.  Returns false (in
 // every thread of the CTA) if the wait timed out anywhere.
-__device__ bool grid_sync(GridBarrier* g, long long spin_limit) {
+__device__ inline bool grid_sync(GridBarrier* g, long long spin_limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
