@@ -319,6 +319,16 @@ int lbm_batch_reductions_all(lbm_batch *b, lbm_stats *out, int32_t *slots, int32
  * holding a stochastically rounded domain runs grouped).  Speed only. */
 int lbm_batch_set_launch(lbm_batch *b, int32_t bx, int32_t by, int32_t persistent);
 
+/* Work split of grouped mode (no counterpart in the paper; speed only,
+ * results are unchanged).  tiles_per_cta: consecutive tiles (one tile =
+ * bx x by cells of one z-plane) each CTA of a group launch updates; 0 picks
+ * it from the group size.  solo_min_cells: a domain with at least this many
+ * cells runs as its own launch of the single-domain update every step
+ * instead of sharing a group launch; 0 = two waves of resident CTAs, < 0 =
+ * never.  Synchronises the batch's stream; the next step regroups.
+ * Returns LBM_EINVAL for tiles_per_cta outside 0..4096. */
+int lbm_batch_set_schedule(lbm_batch *b, int32_t tiles_per_cta, int64_t solo_min_cells);
+
 /* Active domains, bytes of population storage, total cells. */
 int lbm_batch_info(lbm_batch *b, int32_t *active, int64_t *used_bytes, int64_t *total_cells);
 

@@ -9,7 +9,11 @@
 //
 // Grouped mode (default): every step launches one kernel per group of
 // domains sharing Q, storage, rounding and parity; each is the single-domain
-// update specialised at compile time plus a per-CTA domain lookup.
+// update specialised at compile time plus a per-CTA domain lookup.  A domain
+// big enough to fill the device by itself (solo) gets its own launch of the
+// single-domain update instead, so batching costs it nothing.  Every domain's
+// force and rounding key for the steps ahead are computed once per domain
+// and step by a small prepare kernel.
 // Persistent mode: one cooperative launch runs `chunk` steps of all domains,
 // with a grid barrier between steps (the in-place AA update needs every cell
 // of step s done before step s+1 reads its neighbours).  The barrier spins a
@@ -34,6 +38,24 @@
 namespace lbm {
 namespace batchk {
 namespace {
+
+// Force F(t_n) and rounding key of entry k at steps n .. n + ns - 1, where n
+// is its counter plus s0 (Eq. wa's cosine, evaluated in FP64 and rounded
+// once, as the single-domain path does on the host).
+__global__ void k_batch_prepare(const BatchEntry* __restrict__ ents, int nent, int s0, int ns,
+                                StepDyn* dyn, int stride) {
+  const int total = nent * ns;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int k = q % nent, s = q / nent;
+    const BatchEntry& e = ents[k];
+    const int64_t n = e.n + s0 + s;
+    const double c = e.period > 0.0 ? cos(2.0 * M_PI * (double)n / e.period) : 1.0;
+    StepDyn v;
+    for (int a = 0; a < 3; ++a) v.F[a] = float(e.force[a] * c);
+    v.key = step_key(n);
+    dyn[(size_t)s * stride + k] = v;
+  }
+}
 
 // After a chunk: advance every domain's step counter and publish the
 // barrier's time-out flag to the host.
@@ -79,6 +101,7 @@ struct lbm_batch {
   double* stats_host = nullptr;  // mapped pinned, kNumStats per slot
   double* stats_dev = nullptr;
   BatchEntry* table_host = nullptr;  // pinned staging of the descriptor table
+  StepDyn* dyn = nullptr;  // kDynSteps x capacity: force and key per step and entry
   cudaEvent_t table_done = nullptr;  // its last upload has been read
   // launch
   int bx = 64, by = 2;
@@ -86,6 +109,8 @@ struct lbm_batch {
   bool has_sr = false;  // some domain rounds stochastically (grouped mode only)
   int grid = 0;      // CTAs of one persistent (cooperative) launch
   int resident = 0;  // CTAs of the grouped kernels resident at once
+  int tiles_per_cta = 0;        // grouped launches; 0: automatic
+  int64_t solo_min_cells = 0;   // 0: automatic; < 0: no solo domains
   long long spin_limit = 1ll << 26;
   int extra_arrivals = 0;
   // table: entries sorted by group; in persistent mode one run over all
@@ -95,10 +120,12 @@ struct lbm_batch {
   std::vector<int> order;  // slot of each entry
   struct Group {
     int Q, storage, sr, force, parity;  // parity of the domains' step counters
+    int solo;                           // one launch per entry
     int first, count;                   // entries
     int64_t tiles;
   };
   std::vector<Group> groups;
+  std::vector<BatchEntry> host_ents;  // the uploaded table (group-local half)
   // graph of one chunk; captured when a table version runs a second chunk
   // (membership changes invalidate it, and a capture that is used once
   // costs more than it saves)
@@ -109,6 +136,8 @@ struct lbm_batch {
 };
 
 namespace {
+
+constexpr int kDynSteps = 32;  // steps of force/key computed per prepare launch
 
 int bfail(int code, const std::string& m) {
   set_last_error(m);
@@ -180,15 +209,24 @@ int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, Doma
 // groups of equal (Q, storage, rounding, parity).  Tile prefix sums restart
 // at zero in every group (grouped launches) and the persistent kernel, which
 // walks all entries, gets its own running prefix in a second table half.
+int64_t solo_threshold(const lbm_batch* b) {
+  if (b->solo_min_cells < 0) return INT64_MAX;
+  if (b->solo_min_cells > 0) return b->solo_min_cells;
+  // two full waves of resident CTAs
+  return 2 * (int64_t)std::max(1, b->resident) * b->bx * b->by;
+}
+
 int upload_table(lbm_batch* b) {
   std::vector<int> idx;
   for (int i = 0; i < (int)b->slots.size(); ++i)
     if (b->slots[i].used) idx.push_back(i);
+  const int64_t solo_min = solo_threshold(b);
   auto key = [&](int i) {
     const BatchSlot& s = b->slots[i];
     const int sr = s.dd.rounding == LBM_ROUND_STOCHASTIC && s.dd.storage != LBM_STORAGE_F32;
     const int force = s.dd.force[0] != 0.0 || s.dd.force[1] != 0.0 || s.dd.force[2] != 0.0;
-    return std::make_tuple(s.dd.Q, s.dd.storage, sr, force, (int)(s.n & 1));
+    const int solo = s.dd.N >= solo_min;
+    return std::make_tuple(s.dd.Q, s.dd.storage, sr, force, (int)(s.n & 1), solo);
   };
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return key(a) < key(c); });
   std::vector<BatchEntry> ents;
@@ -214,9 +252,10 @@ int upload_table(lbm_batch* b) {
     const auto k = key(i);
     if (b->groups.empty() ||
         std::make_tuple(b->groups.back().Q, b->groups.back().storage, b->groups.back().sr,
-                        b->groups.back().force, b->groups.back().parity) != k) {
+                        b->groups.back().force, b->groups.back().parity,
+                        b->groups.back().solo) != k) {
       b->groups.push_back({std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-                           std::get<4>(k), (int)ents.size(), 0, 0});
+                           std::get<4>(k), std::get<5>(k), (int)ents.size(), 0, 0});
     }
     ents.push_back(e);
     b->groups.back().count += 1;
@@ -251,6 +290,7 @@ int upload_table(lbm_batch* b) {
     if (e == cudaSuccess) e = cudaEventRecord(b->table_done, b->stream);
     if (e != cudaSuccess) return bcuda(e, "batch table upload");
   }
+  b->host_ents = local;
   b->dirty = false;
   b->chunks_this_version = 0;
   drop_graph(b);
@@ -289,21 +329,47 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
     e = launch_persistent(p);
     if (e != cudaSuccess) return e;
   } else {
-    for (int s = 0; s < chunk; ++s)
+    const BatchEntry* local = b->ents + b->capacity;
+    for (int s = 0; s < chunk; ++s) {
+      if (s % kDynSteps == 0) {
+        const int ns = std::min(kDynSteps, chunk - s);
+        const int total = b->nent * ns;
+        const int blocks = std::min(1024, (total + 255) / 256);
+        k_batch_prepare<<<blocks, 256, 0, b->stream>>>(local, b->nent, s, ns, b->dyn,
+                                                       b->capacity);
+      }
+      const StepDyn* dyn = b->dyn + (size_t)(s % kDynSteps) * b->capacity;
       for (const auto& g : b->groups) {
-        const BatchEntry* ge = b->ents + b->capacity + g.first;
         const bool odd = ((g.parity + s) & 1) != 0;
-        // contiguous runs of tiles per CTA, short enough to leave about 16
-        // waves of CTAs (a partly filled last wave then costs little)
-        const int64_t waves16 = std::max<int64_t>(1, (int64_t)b->resident * 16);
-        const int per = (int)std::min<int64_t>(32, std::max<int64_t>(1, g.tiles / waves16));
+        if (g.solo) {
+          for (int k = g.first; k < g.first + g.count; ++k) {
+            const BatchEntry& he = b->host_ents[k];
+            const int periodic = he.period > 0.0;
+            SoloLaunch sl{g.storage, g.sr, g.force, odd ? 1 : 0, periodic,
+                          dim3(he.tiles_x, he.tiles_y, he.d.nz), block, b->stream, he.d, dyn + k};
+            if (!periodic)  // constant force in the descriptor
+              for (int a = 0; a < 3; ++a) sl.d.F[a] = float(he.force[a]);
+            cudaError_t e = g.Q == 14 ? launch_solo_q14(sl) : launch_solo_q18(sl);
+            if (e != cudaSuccess) return e;
+          }
+          continue;
+        }
+        // contiguous runs of tiles per CTA, short enough to leave about
+        // eight waves of CTAs (a partly filled last wave then costs little)
+        // and, in big groups, long enough to spread each descriptor load
+        // over several tiles
+        int per = b->tiles_per_cta;
+        if (per < 1) {
+          const int64_t waves = std::max<int64_t>(1, (int64_t)b->resident * 8);
+          per = (int)std::min<int64_t>(16, std::max<int64_t>(1, g.tiles / waves));
+        }
         const unsigned grid = (unsigned)((g.tiles + per - 1) / per);
-        const int64_t nt = g.tiles;
-        GroupLaunch gl{g.storage, g.sr, g.force, odd ? 1 : 0, dim3(grid), block, b->stream,
-                       ge, g.count, nt, per, s};
+        GroupLaunch gl{g.storage,       g.sr,          g.force, odd ? 1 : 0, dim3(grid), block,
+                       b->stream,       local + g.first, dyn + g.first, g.count, (int)g.tiles, per};
         cudaError_t e = g.Q == 14 ? launch_group_q14(gl) : launch_group_q18(gl);
         if (e != cudaSuccess) return e;
       }
+    }
   }
   k_batch_advance<<<1, 256, 0, b->stream>>>(b->ents, b->nent, chunk, b->bar, b->flag_dev);
   k_batch_advance<<<1, 256, 0, b->stream>>>(b->ents + b->capacity, b->nent, chunk, b->bar,
@@ -337,6 +403,7 @@ int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, 
   if (e == cudaSuccess)
     e = cudaHostAlloc(&b->table_host, 2 * sizeof(BatchEntry) * capacity, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->table_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dyn, sizeof(StepDyn) * kDynSteps * capacity);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(GridBarrier), b->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -365,6 +432,7 @@ void lbm_batch_destroy(lbm_batch* b) {
   if (b->stats_host) cudaFreeHost(b->stats_host);
   if (b->table_host) cudaFreeHost(b->table_host);
   if (b->table_done) cudaEventDestroy(b->table_done);
+  if (b->dyn) cudaFree(b->dyn);
   delete b;
 }
 
@@ -583,6 +651,17 @@ int lbm_batch_set_launch(lbm_batch* b, int32_t bx, int32_t by, int32_t persisten
   b->grid = grid_for_batch(b);
   b->resident = resident_for_group(b);
   b->graph_ok = true;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_set_schedule(lbm_batch* b, int32_t tiles_per_cta, int64_t solo_min_cells) {
+  if (!b) return bfail(LBM_EINVAL, "null batch");
+  if (tiles_per_cta < 0 || tiles_per_cta > 4096) return bfail(LBM_EINVAL, "tiles_per_cta must be 0..4096");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch set_schedule");
+  b->tiles_per_cta = tiles_per_cta;
+  b->solo_min_cells = solo_min_cells;
   b->dirty = true;
   return LBM_OK;
 }

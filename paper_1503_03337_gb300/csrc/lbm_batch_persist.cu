@@ -34,13 +34,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
     TileCursor cur{};
     for (int64_t t = t0; t < t1; ++t) {
       if (t >= end) {
-        int lo = 0, hi = nent - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (ents[mid].tile_begin <= t) lo = mid;
-          else hi = mid - 1;
-        }
-        const BatchEntry& e = ents[lo];
+        const BatchEntry& e = ents[find_entry(ents, nent, t)];
         __syncthreads();  // every thread is done with the previous sd
         const int nw = (int)(sizeof(Domain<float>) / sizeof(int));
         for (int w = tid; w < nw; w += nthr)

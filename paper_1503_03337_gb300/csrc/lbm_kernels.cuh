@@ -227,12 +227,13 @@ __host__ __device__ __forceinline__ void put(S* p, R v, uint32_t h) {
   }
 }
 
-// Post-collision populations f* of cell i from fv into storage.
+// Post-collision populations f* of cell i from fv into storage (`key`: the
+// step's stochastic-rounding key).
 template <int Q, typename S, typename R, bool ODD, bool SR = false>
 __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
-                                                 int i, const Links& L, R* fv) {
+                                                 int i, const Links& L, R* fv, uint32_t key) {
   const int N = (int)d.N;
-  const uint32_t h = SR ? mix32(uint32_t(i) ^ d.key) : 0u;
+  const uint32_t h = SR ? mix32(uint32_t(i) ^ key) : 0u;
   S* __restrict__ fc = f + i;
   if constexpr (!ODD) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
@@ -274,12 +275,13 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR, bool CG = false>
 __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
                                                            S* __restrict__ f, int i,
-                                                           const Links& L) {
+                                                           const Links& L, const R* F,
+                                                           const uint32_t* key) {
   R fv[Q];
   gather<Q, S, R, ODD, CG>(d, f, i, L, fv);
   R ux, uy, uz;
-  collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
-  scatter<Q, S, R, ODD, SR>(d, f, i, L, fv);
+  collide<Q, FORCE>(fv, d.s, F[0], F[1], F[2], ux, uy, uz);
+  scatter<Q, S, R, ODD, SR>(d, f, i, L, fv, SR ? *key : 0u);
 }
 
 // The whole fused update of one cell: gather (stream), collide, scatter.
@@ -287,25 +289,37 @@ __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
 // x-range of the calling warp: when a warp lies within one x-row (block
 // width a multiple of 32) every test below is uniform across the warp, so
 // the variants never diverge inside a warp.
+// update_cell_at reads the step's body force F[0..2] and rounding key *key
+// where they are used (F and key may live outside the descriptor);
+// update_cell takes them from the descriptor.
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false,
+          bool CG = false>
+__host__ __device__ __forceinline__ void update_cell_at(const Domain<R>& d, S* __restrict__ f,
+                                                        const R* F, const uint32_t* key, int x,
+                                                        int y, int z, int x_lo, int x_hi) {
+  const int i = x + d.nx * (y + d.ny * z);
+  if constexpr (!ODD) {
+    Links L{};
+    update_with_links<Q, S, R, false, FORCE, SR, CG>(d, f, i, L, F, key);
+  } else {
+    if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+      if (x_lo > 0 && x_hi < d.nx - 1)
+        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_interior(d), F,
+                                                        key);
+      else
+        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_x(d, x), F, key);
+    } else {
+      update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links(d, x, y, z), F, key);
+    }
+  }
+}
+
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false,
           bool CG = false>
 __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ f,
                                                      int x, int y, int z, int x_lo = -1,
                                                      int x_hi = -1) {
-  const int i = x + d.nx * (y + d.ny * z);
-  if constexpr (!ODD) {
-    Links L{};
-    update_with_links<Q, S, R, false, FORCE, SR, CG>(d, f, i, L);
-  } else {
-    if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
-      if (x_lo > 0 && x_hi < d.nx - 1)
-        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_interior(d));
-      else
-        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_x(d, x));
-    } else {
-      update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links(d, x, y, z));
-    }
-  }
+  update_cell_at<Q, S, R, ODD, FORCE, SR, CG>(d, f, d.F, &d.key, x, y, z, x_lo, x_hi);
 }
 
 // Two cells per thread (FP32 arithmetic, 4- or 2-byte storage): the cells
@@ -378,10 +392,10 @@ __device__ __forceinline__ void update_pair(const Domain<float>& d, S* __restric
       tb[a] = fv[a].v.y;
     }
     const Links La = yz ? make_links_x(d, xa) : make_links(d, xa, y, z);
-    scatter<Q, S, float, true, SR>(d, f, ia, La, ta);
+    scatter<Q, S, float, true, SR>(d, f, ia, La, ta, d.key);
     if (vb) {
       const Links Lb = yz ? make_links_x(d, xb) : make_links(d, xb, y, z);
-      scatter<Q, S, float, true, SR>(d, f, ib, Lb, tb);
+      scatter<Q, S, float, true, SR>(d, f, ib, Lb, tb, d.key);
     }
   }
 }

@@ -1,6 +1,7 @@
 """Batched stepping (lbm_batch_*): every domain of a batch computes exactly
 what a single-domain handle computes, alone or in any mix, in both launch
-modes; the persistent grid barrier's time-out path reports LBM_ETIMEOUT."""
+modes and under every work split (grouped, solo, tiles per CTA); the
+persistent grid barrier's time-out path reports LBM_ETIMEOUT."""
 import numpy as np
 import pytest
 
@@ -56,13 +57,19 @@ def single_pops(c, steps):
         lbm.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("persistent", (1, 0))
-def test_batch_same_alone_and_in_mix(torch, persistent):
+# (persistent, tiles_per_cta, solo_min_cells): the default schedule, every
+# domain solo, every domain grouped one tile per CTA, mixed with long runs
+SCHEDULES = [(1, 0, 0), (0, 0, 0), (0, 3, 1), (0, 1, -1), (0, 7, 2000)]
+
+
+@pytest.mark.parametrize("persistent,per,solo", SCHEDULES)
+def test_batch_same_alone_and_in_mix(torch, persistent, per, solo):
     stream = torch.cuda.current_stream().cuda_stream
     cases = mix()
     b = lbm.lbm_batch_create(8, 0, stream)
     try:
         lbm.lbm_batch_set_launch(b, 64, 2, persistent)
+        lbm.lbm_batch_set_schedule(b, per, solo)
         slots = {}
         steps = {}
         for k in range(4):
@@ -93,13 +100,15 @@ def test_batch_same_alone_and_in_mix(torch, persistent):
         lbm.lbm_batch_destroy(b)
 
 
-def test_batch_pulsatile_matches_oracle(torch):
+@pytest.mark.parametrize("solo", (-1, 1))
+def test_batch_pulsatile_matches_oracle(torch, solo):
     """Oscillating force evaluated on the device at each domain's own time
-    level, against the oracle."""
+    level, against the oracle, grouped and solo."""
     stream = torch.cuda.current_stream().cuda_stream
     c = inputs.pulsatile(18, 16, 4, 40, 3.0, 2e-4, storage="f32")
     b = lbm.lbm_batch_create(2, 0, stream)
     try:
+        lbm.lbm_batch_set_schedule(b, 0, solo)
         s = add(b, c)
         lbm.lbm_batch_init_equilibrium(b, s)
         lbm.lbm_batch_step(b, 61, 8)
@@ -110,6 +119,19 @@ def test_batch_pulsatile_matches_oracle(torch):
     o = oracle_run(c, 61)
     err = np.max(np.abs(u.cpu().numpy().reshape(o["u"].shape) - o["u"]))
     assert err <= 1e-5 * np.max(np.abs(o["u"]))
+
+
+def test_batch_schedule_rejects_bad_values(torch):
+    stream = torch.cuda.current_stream().cuda_stream
+    b = lbm.lbm_batch_create(2, 0, stream)
+    try:
+        with pytest.raises(lbm.LBMError) as ei:
+            lbm.lbm_batch_set_schedule(b, -1, 0)
+        assert ei.value.code == lbm.LBM_EINVAL
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_batch_set_schedule(b, 5000, 0)
+    finally:
+        lbm.lbm_batch_destroy(b)
 
 
 def test_batch_budget_and_slots(torch):
