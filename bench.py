@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--Re", type=float, default=1000.0)
     ap.add_argument("--residual-interval", type=int, default=1000)
+    ap.add_argument("--precision-n", type=int, default=256,
+                    help="cube side of the storage-precision comparison (0: skip); its "
+                         "buffers are several times larger than L2, so steps run back to back")
+    ap.add_argument("--precision-steps", type=int, default=200)
     ap.add_argument("--variant-steps", type=int, default=400,
                     help="steps per extra (Q, storage) variant; 0 to skip")
     ap.add_argument("--e2e-chunk", type=int, default=100)
@@ -302,6 +306,41 @@ def run_gpu(a, rank, world, dist):
                     "hbm_gbs": round(bpu * cv.cells / (tv * 1e-3) / 1e9, 1),
                     "frac_of_measured_hbm": round(bpu * cv.cells / (tv * 1e-3) / 1e9 / peak, 4)}
 
+    # --- storage precision at a size far above L2: back-to-back steps ------------------
+    precision = {}
+    if a.precision_n > 0 and a.precision_steps > 0 and rank == 0:
+        for Q in (14, 18):
+            for st in ("f32", "f16", "bf16"):
+                cp = inputs.cavity(Q, a.precision_n, a.Re, U=0.05, storage=st)
+                hp = lbm.lbm_create(Q, cp.nx, cp.ny, cp.nz, st, sp)
+                lbm.lbm_set_geometry(hp, cp.faces, cp.u_wall)
+                lbm.lbm_set_params(hp, nu=cp.nu, residual_interval=0)
+                lbm.lbm_init_equilibrium(hp)
+                bp, _ = lbm.lbm_autotune(hp, 4)
+                lbm.lbm_step(hp, 10)
+                k = a.precision_steps + (a.precision_steps & 1)
+                e0.record(stream)
+                lbm.lbm_step(hp, k)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tp = e0.elapsed_time(e1) / k
+                lbm.lbm_destroy(hp)
+                bpu = 2 * Q * STORAGE_BYTES[st]
+                precision["D3Q%d_%s" % (Q, st)] = {
+                    "launch": list(bp),
+                    "glups": round(cp.cells / (tp * 1e-3) / 1e9, 3),
+                    "hbm_gbs": round(bpu * cp.cells / (tp * 1e-3) / 1e9, 1),
+                    "frac_of_measured_hbm": round(bpu * cp.cells / (tp * 1e-3) / 1e9 / peak, 4)}
+            f32 = precision["D3Q%d_f32" % Q]["glups"]
+            for st in ("f16", "bf16"):
+                precision["D3Q%d_%s" % (Q, st)]["vs_f32"] = round(
+                    precision["D3Q%d_%s" % (Q, st)]["glups"] / f32, 3)
+        precision["note"] = ("lid-driven cavity %d^3, %d back-to-back steps after 10, one event "
+                             "pair; population buffers %d-%d MB, all far above the 129 MB L2"
+                             % (a.precision_n, a.precision_steps,
+                                2 * 14 * a.precision_n ** 3 >> 20,
+                                4 * 18 * a.precision_n ** 3 >> 20))
+
     launches = a.steps + 2 * len(red)
     res = {
         "metric": "D3Q18 MRT fused-step GLUPS (lattice updates/s) and HBM-roofline fraction",
@@ -336,6 +375,7 @@ def run_gpu(a, rank, world, dist):
         "residual_last": {"step": stats.step, "cavity": (lbm.residual_cavity(stats)
                                                          if stats.prev_step >= 0 else None)},
         "variants": variants,
+        "precision": precision,
         "steady_state": steady,
     }
     return res
