@@ -3,9 +3,10 @@
 Workload (one bench step = one lattice update of the whole domain):
 lid-driven cube 128^3, D3Q18, FP32 populations, lid 0.05 along x on y+,
 Re = 1000 (nu = U L / Re), FP64 residual every 1000 steps, synthetic state
-from rest.  Between bench steps a 256 MiB buffer is written to flush L2;
-each step is timed with CUDA events on the stream the kernels run on, and
-the flush lies outside those events.
+from rest.  The timed steps run back to back (the 151 MB population buffer
+is larger than the 129 MB L2, and each step sweeps all of it), bracketed by
+CUDA events on the stream the kernels run on.  The same step is also timed
+one by one after an L2 flush, as a secondary figure.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -49,12 +50,14 @@ def parse():
                     help="cube side of the storage-precision comparison (0: skip); its "
                          "buffers are several times larger than L2, so steps run back to back")
     ap.add_argument("--precision-steps", type=int, default=200)
-    ap.add_argument("--variant-steps", type=int, default=400,
-                    help="steps per extra (Q, storage) variant; 0 to skip")
+    ap.add_argument("--flushed-steps", type=int, default=400,
+                    help="steps timed one by one after an L2 flush (secondary figure)")
     ap.add_argument("--e2e-chunk", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-trials", type=int, default=16)
+    ap.add_argument("--launch", default="",
+                    help="fixed launch shape bx,by,cells_per_thread instead of the autotuner")
     ap.add_argument("--workload", default="cavity128",
                     choices=("cavity128", "batch256", "serving"),
                     help="cavity128: the fused-step throughput line (default); batch256: "
@@ -74,38 +77,61 @@ def workload_name(a):
 # ---- clocks ------------------------------------------------------------------
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons:
+    one nvidia-smi process runs around the region, and only samples whose
+    own timestamps fall between __enter__ and __exit__ are kept."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
+        self.lines = []
         self.samples = []
-        self._stop = threading.Event()
+        self._p = None
         self._t = None
+        self.t0 = self.t1 = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(
-                    ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                     "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
-                parts = [p.strip() for p in out.stdout.strip().split(",")]
-                if len(parts) >= 7:
-                    self.samples.append(parts)
-            except Exception:
-                pass
-            self._stop.wait(0.1)
+    def _read(self):
+        for line in self._p.stdout:
+            self.lines.append(line)
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)  # nvidia-smi is up before the region starts
+        except Exception:
+            self._p = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *exc):
-        self._stop.set()
-        self._t.join(timeout=10)
+        self.t1 = time.time()
+        if self._p is None:
+            return
+        time.sleep(0.2)
+        self._p.terminate()
+        try:
+            self._p.wait(timeout=5)
+        except Exception:
+            self._p.kill()
+        self._t.join(timeout=5)
+        import datetime
+        for line in self.lines:
+            parts = [p.strip() for p in line.strip().split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            if self.t0 <= ts <= self.t1:
+                self.samples.append(parts[1:])
 
     def summary(self):
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -115,7 +141,8 @@ class ClockSampler:
                           if s[3 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(self.samples),
+                "sampling": "nvidia-smi -lms 50 during the timed region"}
 
 
 # ---- ncu-derived traffic --------------------------------------------------------
@@ -178,6 +205,7 @@ def run_gpu(a, rank, world, dist):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush_sink = torch.empty(1, dtype=torch.float32, device="cuda")
 
     def open_case(Q, storage, residual_interval):
         case = inputs.cavity(Q, a.n, a.Re, U=0.05, storage=storage)
@@ -185,7 +213,11 @@ def run_gpu(a, rank, world, dist):
         lbm.lbm_set_geometry(h, case.faces, case.u_wall)
         lbm.lbm_set_params(h, nu=case.nu, residual_interval=residual_interval)
         lbm.lbm_init_equilibrium(h)
-        block, _ = lbm.lbm_autotune(h, a.tune_trials)  # restores the state it used
+        if a.launch:
+            block = tuple(int(v) for v in a.launch.split(","))
+            lbm.lbm_set_launch(h, *block)
+        else:
+            block, _ = lbm.lbm_autotune(h, a.tune_trials)  # restores the state it used
         return case, h, block
 
     def timed_steps(h, K, interval):
@@ -196,6 +228,7 @@ def run_gpu(a, rank, world, dist):
         n0 = lbm.lbm_get_step(h)
         for k in range(K):
             flush.fill_(float(k))
+            flush_sink.copy_(flush.sum().reshape(1))
             ev[k][0].record(stream)
             lbm.lbm_step(h, 1)
             ev[k][1].record(stream)
@@ -203,45 +236,50 @@ def run_gpu(a, rank, world, dist):
                 red.append(k)
         return ev, red
 
-    # --- main workload -------------------------------------------------------
+    # --- main workload: back-to-back steps ----------------------------------------
+    # The population buffer (151 MB for D3Q18 FP32 at 128^3) is larger than
+    # the 129 MB L2 and every step sweeps all of it, so consecutive steps find
+    # nothing useful in L2 (an ncu capture of steady-state steps reads 149 MB
+    # and writes 147-153 MB from/to DRAM per step).  The residual reductions
+    # run inside lbm_step at their cadence and are part of the timed work.
     case, h, block = open_case(a.Q, a.storage, a.residual_interval)
     cells = case.cells
     bytes_per_update = 2 * a.Q * STORAGE_BYTES[a.storage]
-    for _ in range(max(0, a.warmup)):
-        flush.fill_(0.0)
-        lbm.lbm_step(h, 1)
+    lbm.lbm_step(h, max(3, a.warmup))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n_before = lbm.lbm_get_step(h)
     with ClockSampler(dev) as clk:
         t0 = time.perf_counter()
-        ev, red = timed_steps(h, a.steps, a.residual_interval)
+        e0.record(stream)
+        lbm.lbm_step(h, a.steps)
+        e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    times = [s.elapsed_time(e) for s, e in ev]
-    red_set = set(red)
-    step_only = [t for k, t in enumerate(times) if k not in red_set] or times
-    total_ms = sum(times)
-    kernel_ms = statistics.mean(step_only)
+    total_ms = e0.elapsed_time(e1)
+    kernel_ms = total_ms / a.steps
+    n_red = (sum(1 for n in range(n_before + 1, n_before + a.steps + 1)
+                 if a.residual_interval and n % a.residual_interval == 0))
     stats = lbm.lbm_read_stats(h)
-    # steady state: back-to-back steps without flushes (the population
-    # buffer of this workload is larger than L2)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    ss_steps = max(2, min(a.steps, 2000))
-    ss_steps += ss_steps & 1
-    e0.record(stream)
-    lbm.lbm_step(h, ss_steps)
-    e1.record(stream)
+    # the same steps timed one by one with the L2 flushed in between (a
+    # 256 MiB write, then a read of it, so that the flush leaves only clean
+    # lines and the timed step pays no write-back of the flush)
+    lbm.lbm_set_params(h, nu=case.nu, residual_interval=0)
+    fl_steps = max(2, min(a.steps, a.flushed_steps))
+    ev, _ = timed_steps(h, fl_steps, 0)
     torch.cuda.synchronize()
-    steady = {"glups": round(cells * ss_steps / (e0.elapsed_time(e1) * 1e-3) / 1e9, 3),
-              "steps": ss_steps,
-              "note": "back-to-back steps, one event pair, no L2 flush (buffer %d MB vs 129 MB L2)"
-                      % (bytes_per_update * cells // 2 // (1 << 20))}
+    fl_ms = statistics.mean(s0.elapsed_time(s1) for s0, s1 in ev)
+    flushed = {"glups": round(cells / (fl_ms * 1e-3) / 1e9, 3), "steps": fl_steps,
+               "ms_per_step": round(fl_ms, 6),
+               "note": "per-step CUDA events, 256 MiB L2 flush (write then read) before each step, "
+                       "outside the events"}
     lbm.lbm_destroy(h)
 
     if dist:
@@ -257,7 +295,7 @@ def run_gpu(a, rank, world, dist):
 
     # --- e2e through the C-ABI with host buffers ---------------------------------
     e2e = None
-    if True:
+    if a.e2e_steps > 0:
         case_e, he, _ = open_case(a.Q, a.storage, 0)
         N = case_e.cells
         u0 = torch.zeros(3 * N, dtype=torch.float64).pin_memory()
@@ -285,26 +323,6 @@ def run_gpu(a, rank, world, dist):
                "lattice_updates_per_step": a.e2e_chunk,
                "calls": "lbm_init_equilibrium(host u,p) + lbm_step(%d) + lbm_read_fields(U -> host)"
                         % a.e2e_chunk}
-
-    # --- other (Q, storage) variants, same workload shape ------------------------------
-    variants = {}
-    if a.variant_steps > 0 and rank == 0:
-        for Q in (14, 18):
-            for st in ("f32", "f16", "bf16"):
-                cv, hv, bv = open_case(Q, st, 0)
-                for _ in range(10):
-                    flush.fill_(0.0)
-                    lbm.lbm_step(hv, 1)
-                evv, _ = timed_steps(hv, a.variant_steps, 0)
-                torch.cuda.synchronize()
-                tv = statistics.mean(s.elapsed_time(e) for s, e in evv)
-                lbm.lbm_destroy(hv)
-                bpu = 2 * Q * STORAGE_BYTES[st]
-                variants["D3Q%d_%s" % (Q, st)] = {
-                    "launch": list(bv),
-                    "glups": round(cv.cells / (tv * 1e-3) / 1e9, 3),
-                    "hbm_gbs": round(bpu * cv.cells / (tv * 1e-3) / 1e9, 1),
-                    "frac_of_measured_hbm": round(bpu * cv.cells / (tv * 1e-3) / 1e9 / peak, 4)}
 
     # --- storage precision at a size far above L2: back-to-back steps ------------------
     precision = {}
@@ -341,7 +359,9 @@ def run_gpu(a, rank, world, dist):
                                 2 * 14 * a.precision_n ** 3 >> 20,
                                 4 * 18 * a.precision_n ** 3 >> 20))
 
-    launches = a.steps + 2 * len(red)
+    # the step kernels plus, per residual check, the reduction kernel and its
+    # final pass
+    launches = a.steps + 2 * n_red
     res = {
         "metric": "D3Q18 MRT fused-step GLUPS (lattice updates/s) and HBM-roofline fraction",
         "value": round(glups, 4),
@@ -358,9 +378,9 @@ def run_gpu(a, rank, world, dist):
         "config": {"workload": workload_name(a), "grid": [a.n, a.n, a.n], "Q": a.Q,
                    "storage": a.storage, "Re": a.Re, "lid_velocity": 0.05,
                    "residual_interval": a.residual_interval,
-                   "l2": "flushed between steps (256 MiB write), outside the event-timed region; "
-                         "the flush also absorbs the write-back of the previous step's dirty lines, "
-                         "see steady_state for back-to-back steps",
+                   "l2": "inputs larger than L2: back-to-back steps over a %d MB population "
+                         "buffer (L2 129 MB); see flushed_per_step for the same step timed one "
+                         "by one after an L2 flush" % (bytes_per_update * cells // 2 // 10**6),
                    "launch": {"block": [block[0], block[1]], "cells_per_thread": block[2]},
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "wall_s_timed_region": round(wall, 4)},
@@ -374,9 +394,8 @@ def run_gpu(a, rank, world, dist):
         "clocks": clk.summary(),
         "residual_last": {"step": stats.step, "cavity": (lbm.residual_cavity(stats)
                                                          if stats.prev_step >= 0 else None)},
-        "variants": variants,
         "precision": precision,
-        "steady_state": steady,
+        "flushed_per_step": flushed,
     }
     return res
 

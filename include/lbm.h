@@ -207,6 +207,13 @@ typedef struct lbm_launch {
 int lbm_set_launch(lbm_handle *h, const lbm_launch *launch);
 int lbm_get_launch(lbm_handle *h, lbm_launch *launch);
 
+/* Overlap of consecutive step launches (no counterpart in the paper; speed
+ * only, results unchanged).  enable != 0 (the default): each step kernel is
+ * launched as a programmatic dependent of the previous one, so its CTAs are
+ * scheduled while the previous step drains and wait on the device for that
+ * step's completion before reading any population.  0: plain stream order. */
+int lbm_set_overlap(lbm_handle *h, int32_t enable);
+
 /* Autotuner: time the step kernel on this domain for each candidate launch
  * shape (block shape, cells per thread) (`trials` steps each, CUDA events on the handle's stream) and keep
  * the fastest.  The populations and step counter are saved before and

@@ -458,7 +458,13 @@ int lbm_set_launch(lbm_handle* h, const lbm_launch* l) {
     return fail(LBM_EINVAL, "cells_per_thread must be 1 or 2");
   if (l->cells_per_thread == 2 && h->d.storage == LBM_STORAGE_F64)
     return fail(LBM_EINVAL, "two cells per thread needs FP32 arithmetic (not FP64 storage)");
-  h->block = {l->bx, l->by, l->cells_per_thread};
+  h->block = {l->bx, l->by, l->cells_per_thread, h->block.pdl};
+  return LBM_OK;
+}
+
+int lbm_set_overlap(lbm_handle* h, int32_t enable) {
+  if (int rc = check(h)) return rc;
+  h->block.pdl = enable ? 1 : 0;
   return LBM_OK;
 }
 
@@ -479,7 +485,8 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end() && trials <= 0) {
-      h->block = it->second.first;
+      const BlockShape& c = it->second.first;
+      h->block = {c.bx, c.by, c.cpt, h->block.pdl};
       if (chosen) *chosen = {h->block.bx, h->block.by, h->block.cpt};
       if (ms) *ms = it->second.second;
       return LBM_OK;
@@ -503,8 +510,9 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
   double best_ms = 1e300;
   const int64_t n0 = h->n;
   const int xmax = ((h->d.nx + 31) / 32) * 32;
-  for (const BlockShape& b : kCandidates) {
+  for (BlockShape b : kCandidates) {
     if (e != cudaSuccess) break;
+    b.pdl = h->block.pdl;
     if (b.bx * b.cpt > xmax && b.bx > 32) continue;
     if (b.cpt == 2 && h->d.storage == LBM_STORAGE_F64) continue;
     int64_t n = n0;

@@ -35,7 +35,8 @@ struct DomainDesc {
 
 struct BlockShape {
   int bx, by;
-  int cpt;  // cells per thread: 1, or 2 (pairs along x, FP32 arithmetic only)
+  int cpt;      // cells per thread: 1, or 2 (pairs along x, FP32 arithmetic only)
+  int pdl = 1;  // programmatic dependent launch of consecutive steps
 };
 
 BlockShape default_block(int nx, int ny);

@@ -13,8 +13,19 @@ namespace lbm {
 template <typename R>
 Domain<R> to_domain(const DomainDesc& d, const double F[3]);
 
+// Programmatic dependent launch: a step kernel lets the next launch in the
+// stream start (its CTAs become resident as this grid drains) and waits for
+// the previous grid's completion and memory before touching any population.
+// Without the launch attribute both instructions have no effect.
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_acquire() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> d) {
+  pdl_release();
+  pdl_acquire();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -30,6 +41,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> 
 // 2*blockDim.x cells of a row, each warp 64 consecutive cells.
 template <int Q, typename S, bool ODD, bool FORCE, bool SR>
 __global__ void __launch_bounds__(256, 2) k_step2(Domain<float> d) {
+  pdl_release();
+  pdl_acquire();
   const int lane = threadIdx.x & 31;
   const int x_lo = blockIdx.x * (2 * blockDim.x) + (threadIdx.x >> 5) * 64;
   const int xa = x_lo + lane;
@@ -39,9 +52,20 @@ __global__ void __launch_bounds__(256, 2) k_step2(Domain<float> d) {
   update_pair<Q, S, ODD, FORCE, SR>(d, static_cast<S*>(d.f), xa, y, z, x_lo);
 }
 
-template <typename K, typename R>
-void launch_one(K kernel, const Domain<R>& d, dim3 grid, dim3 block, cudaStream_t st) {
-  kernel<<<grid, block, 0, st>>>(d);
+template <typename R>
+void launch_one(void (*kernel)(Domain<R>), const Domain<R>& d, dim3 grid, dim3 block, bool pdl,
+                cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, d);
 }
 
 template <int Q, typename S, typename R, bool SR>
@@ -51,21 +75,21 @@ void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 blo
     if (b.cpt == 2) {
       grid.x = (d.nx + 2 * block.x - 1) / (2 * block.x);
       if (odd) {
-        if (force) launch_one(k_step2<Q, S, true, true, SR>, d, grid, block, st);
-        else launch_one(k_step2<Q, S, true, false, SR>, d, grid, block, st);
+        if (force) launch_one(k_step2<Q, S, true, true, SR>, d, grid, block, b.pdl != 0, st);
+        else launch_one(k_step2<Q, S, true, false, SR>, d, grid, block, b.pdl != 0, st);
       } else {
-        if (force) launch_one(k_step2<Q, S, false, true, SR>, d, grid, block, st);
-        else launch_one(k_step2<Q, S, false, false, SR>, d, grid, block, st);
+        if (force) launch_one(k_step2<Q, S, false, true, SR>, d, grid, block, b.pdl != 0, st);
+        else launch_one(k_step2<Q, S, false, false, SR>, d, grid, block, b.pdl != 0, st);
       }
       return;
     }
   }
   if (odd) {
-    if (force) launch_one(k_step<Q, S, R, true, true, SR>, d, grid, block, st);
-    else launch_one(k_step<Q, S, R, true, false, SR>, d, grid, block, st);
+    if (force) launch_one(k_step<Q, S, R, true, true, SR>, d, grid, block, b.pdl != 0, st);
+    else launch_one(k_step<Q, S, R, true, false, SR>, d, grid, block, b.pdl != 0, st);
   } else {
-    if (force) launch_one(k_step<Q, S, R, false, true, SR>, d, grid, block, st);
-    else launch_one(k_step<Q, S, R, false, false, SR>, d, grid, block, st);
+    if (force) launch_one(k_step<Q, S, R, false, true, SR>, d, grid, block, b.pdl != 0, st);
+    else launch_one(k_step<Q, S, R, false, false, SR>, d, grid, block, b.pdl != 0, st);
   }
 }
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "lbm_read_stats": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_memory_bytes": (_I, [_VP, ctypes.POINTER(_I64)]),
     "lbm_set_launch": (_I, [_VP, ctypes.POINTER(lbm_launch)]),
+    "lbm_set_overlap": (_I, [_VP, ctypes.c_int32]),
     "lbm_get_launch": (_I, [_VP, ctypes.POINTER(lbm_launch)]),
     "lbm_autotune": (_I, [_VP, ctypes.c_int32, ctypes.POINTER(lbm_launch),
                           ctypes.POINTER(ctypes.c_double)]),
@@ -250,6 +251,10 @@ def lbm_read_stats(h):
     s = lbm_stats()
     _check(load().lbm_read_stats(h, ctypes.byref(s)))
     return s
+
+
+def lbm_set_overlap(h, enable):
+    _check(load().lbm_set_overlap(h, int(enable)))
 
 
 def lbm_set_launch(h, bx, by, cells_per_thread=1):
