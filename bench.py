@@ -192,6 +192,25 @@ def measured_hbm_peak():
     return 6800.0, "fallback"
 
 
+# ---- multi-GPU aggregation (replicas) ------------------------------------------
+
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (a time): the whole job is as slow as
+    its slowest replica.  dist is torch.distributed or None (one process)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, cells, steps, seconds):
+    """GLUPS of the whole job: `world` independent replicas, each updating
+    `cells` cells `steps` times, in `seconds` (the max over ranks)."""
+    return world * cells * steps / seconds / 1e9
+
+
 # ---- GPU leg -----------------------------------------------------------------------
 
 def run_gpu(a, rank, world, dist):
@@ -282,13 +301,8 @@ def run_gpu(a, rank, world, dist):
                        "outside the events"}
     lbm.lbm_destroy(h)
 
-    if dist:
-        import torch.distributed as td
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        total_ms = float(t.item())
-
-    glups = world * cells * a.steps / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
+    glups = replica_throughput(world, cells, a.steps, total_ms * 1e-3)
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_update * cells / (kernel_ms * 1e-3) / 1e9
     traffic = recorded_traffic(a.Q, a.storage, a.n)
@@ -313,12 +327,9 @@ def run_gpu(a, rank, world, dist):
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         lbm.lbm_destroy(he)
-        if dist:
-            import torch.distributed as td
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * N * a.e2e_chunk * a.e2e_steps / el / 1e9, "unit": "GLUPS",
+        el = max_over_ranks(el, dist, "cuda")
+        e2e = {"value": replica_throughput(world, N, a.e2e_chunk * a.e2e_steps, el),
+               "unit": "GLUPS",
                "h2d_bytes_per_step": 4 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
                "lattice_updates_per_step": a.e2e_chunk,
                "calls": "lbm_init_equilibrium(host u,p) + lbm_step(%d) + lbm_read_fields(U -> host)"

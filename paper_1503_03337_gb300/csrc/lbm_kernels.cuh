@@ -174,6 +174,27 @@ __host__ __device__ __forceinline__ bool touches_moving(const Domain<R>& d, cons
   return (m & d.moving) != 0;
 }
 
+// Moving-wall terms of the links of a pull whose source node is a ghost
+// beyond a moving face: +6 w_a (c_a . u_w) (halfway bounce-back off a moving
+// wall).
+template <int Q, typename R>
+__host__ __device__ __forceinline__ void add_pull_wall_terms(const Domain<R>& d, const Links& L,
+                                                             R* fv) {
+  if (d.moving && touches_moving(d, L)) {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      (
+          [&] {
+            const int faces = link_faces<Q, A, -1>(L);
+            if (faces)
+              fv[A] += R(6.0 * Lattice<Q>::w(A)) *
+                       ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
+                                 Lattice<Q>::c(A, 2));
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, Q>{});
+  }
+}
+
 // Pre-collision populations f^n of cell i into fv (CG: L2-only loads).
 template <int Q, typename S, typename R, bool ODD, bool CG = false>
 __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
@@ -201,19 +222,7 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
           }(),
           ...);
     }(std::make_integer_sequence<int, Q>{});
-    if (d.moving && touches_moving(d, L)) {
-      [&]<int... A>(std::integer_sequence<int, A...>) {
-        (
-            [&] {
-              const int faces = link_faces<Q, A, -1>(L);
-              if (faces)
-                fv[A] += R(6.0 * Lattice<Q>::w(A)) *
-                         ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
-                                   Lattice<Q>::c(A, 2));
-            }(),
-            ...);
-      }(std::make_integer_sequence<int, Q>{});
-    }
+    add_pull_wall_terms<Q>(d, L, fv);
   }
 }
 
@@ -322,82 +331,94 @@ __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __re
   update_cell_at<Q, S, R, ODD, FORCE, SR, CG>(d, f, d.F, &d.key, x, y, z, x_lo, x_hi);
 }
 
-// Two cells per thread (FP32 arithmetic, 4- or 2-byte storage): the cells
-// xa and xa + 32 of one x-row.  With a warp's lanes on xa = x_lo..x_lo+31 the
-// warp updates the 64 cells x_lo..x_lo+63, every load and store instruction
-// still touches 32 consecutive values, and the pair is collided together in
-// packed FP32 (one instruction for both cells).  Even steps and odd-step
-// warps whose 64 cells and all their neighbours are interior use the offset
-// tables; other odd-step warps resolve each cell's links separately.
+// Links of cell x of a warp spanning x_lo..x_hi on an odd step: the offset
+// tables for warps whose cells and neighbours are all interior, the x-only
+// selects in the bulk of y and z, else the full per-axis selects (the same
+// choice as update_cell, warp-uniform).
+template <typename R>
+__host__ __device__ __forceinline__ Links links_in_warp(const Domain<R>& d, int x, int y, int z,
+                                                        int x_lo, int x_hi) {
+  if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+    if (x_lo > 0 && x_hi < d.nx - 1) return make_links_interior(d);
+    return make_links_x(d, x);
+  }
+  return make_links(d, x, y, z);
+}
+
+// Storage values of cell i's pre-collision populations: the gather's
+// addressing without the conversion and the wall terms.
+template <int Q, typename S, typename R, bool ODD>
+__host__ __device__ __forceinline__ void gather_raw(const Domain<R>& d, const S* __restrict__ f,
+                                                    int i, const Links& L, S* raw) {
+  const int N = (int)d.N;
+  const S* __restrict__ fc = f + i;
+  if constexpr (!ODD) {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      ((raw[A] = fc[(size_t)A * d.N]), ...);
+    }(std::make_integer_sequence<int, Q>{});
+  } else if (L.interior) {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      ((raw[A] = fc[d.pull[A]]), ...);
+    }(std::make_integer_sequence<int, Q>{});
+  } else {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      (
+          [&] {
+            int off;
+            bool ghost;
+            link_of<Q, A, -1>(L, off, ghost);
+            raw[A] = f[ghost ? (A * N + i) : (opposite<Q>(A) * N + i + off)];
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, Q>{});
+  }
+}
+
+// The rest of the update of cell i from its gathered storage values: the
+// conversion and wall terms of gather, then collide and scatter.  Together
+// with gather_raw these are update_cell's operations in update_cell's order.
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
+__host__ __device__ __forceinline__ void finish_cell(const Domain<R>& d, S* __restrict__ f, int i,
+                                                     const Links& L, const S* raw) {
+  R fv[Q];
+  [&]<int... A>(std::integer_sequence<int, A...>) {
+    ((fv[A] = Codec<S, R>::value(raw[A])), ...);
+  }(std::make_integer_sequence<int, Q>{});
+  if constexpr (ODD)
+    if (!L.interior) add_pull_wall_terms<Q>(d, L, fv);
+  R ux, uy, uz;
+  collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
+  scatter<Q, S, R, ODD, SR>(d, f, i, L, fv, d.key);
+}
+
+// Two cells per thread: the cells xa and xa + 32 of one x-row, so that a
+// warp on xa = x_lo..x_lo+31 covers the 64 cells x_lo..x_lo+63 and every
+// load and store still touches 32 consecutive values.  The thread issues the
+// loads of both cells before updating either, which doubles the loads a
+// warp keeps in flight (what bounds the step with 2-byte storage, where one
+// cell's loads are only 36 bytes).  Each cell's operations are update_cell's
+// in the same order (the compiler may still fuse multiply-adds differently
+// in this kernel, so results agree with one cell per thread to FP32
+// rounding).  In-place
+// safety: on either parity the locations a cell reads are the ones it
+// writes, so the loads of xa + 32 never see a store of xa.
 template <int Q, typename S, bool ODD, bool FORCE, bool SR>
-__device__ __forceinline__ void update_pair(const Domain<float>& d, S* __restrict__ f, int xa,
-                                            int y, int z, int x_lo) {
+__device__ __forceinline__ void update_two(const Domain<float>& d, S* __restrict__ f, int xa, int y,
+                                           int z, int x_lo) {
   const int xb = xa + 32;
   const bool vb = xb < d.nx;
   const int ia = xa + d.nx * (y + d.ny * z);
   const int ib = ia + 32;
-  const int N = (int)d.N;
-  bool simple = true;
-  bool yz = true;
+  Links La{}, Lb{};
   if constexpr (ODD) {
-    yz = y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
-    simple = yz && x_lo > 0 && x_lo + 63 < d.nx - 1;
+    La = links_in_warp(d, xa, y, z, x_lo, x_lo + 31);
+    Lb = links_in_warp(d, xb, y, z, x_lo + 32, x_lo + 63);
   }
-  pf2 fv[Q];
-  if (simple) {
-    const S* __restrict__ fa = f + ia;
-    const S* __restrict__ fb = f + ib;
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      (
-          [&] {
-            const int off = ODD ? d.pull[A] : A * N;
-            const float a = Codec<S, float>::load(fa + off);
-            const float b = vb ? Codec<S, float>::load(fb + off) : 0.0f;
-            fv[A] = pf2(a, b);
-          }(),
-          ...);
-    }(std::make_integer_sequence<int, Q>{});
-  } else {
-    float ta[Q], tb[Q];
-    const Links La = yz ? make_links_x(d, xa) : make_links(d, xa, y, z);
-    gather<Q, S, float, true>(d, f, ia, La, ta);
-    if (vb) {
-      const Links Lb = yz ? make_links_x(d, xb) : make_links(d, xb, y, z);
-      gather<Q, S, float, true>(d, f, ib, Lb, tb);
-    } else {
-      for (int a = 0; a < Q; ++a) tb[a] = 0.0f;
-    }
-    for (int a = 0; a < Q; ++a) fv[a] = pf2(ta[a], tb[a]);
-  }
-  pf2 ux, uy, uz;
-  collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
-  if (simple) {
-    S* __restrict__ fa = f + ia;
-    S* __restrict__ fb = f + ib;
-    const uint32_t ha = SR ? mix32(uint32_t(ia) ^ d.key) : 0u;
-    const uint32_t hb = SR ? mix32(uint32_t(ib) ^ d.key) : 0u;
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      (
-          [&] {
-            const int off = ODD ? d.push[A] : opposite<Q>(A) * N;
-            put<S, float, SR, A>(fa + off, fv[A].v.x, ha);
-            if (vb) put<S, float, SR, A>(fb + off, fv[A].v.y, hb);
-          }(),
-          ...);
-    }(std::make_integer_sequence<int, Q>{});
-  } else {
-    float ta[Q], tb[Q];
-    for (int a = 0; a < Q; ++a) {
-      ta[a] = fv[a].v.x;
-      tb[a] = fv[a].v.y;
-    }
-    const Links La = yz ? make_links_x(d, xa) : make_links(d, xa, y, z);
-    scatter<Q, S, float, true, SR>(d, f, ia, La, ta, d.key);
-    if (vb) {
-      const Links Lb = yz ? make_links_x(d, xb) : make_links(d, xb, y, z);
-      scatter<Q, S, float, true, SR>(d, f, ib, Lb, tb, d.key);
-    }
-  }
+  S ra[Q], rb[Q];
+  gather_raw<Q, S, float, ODD>(d, f, ia, La, ra);
+  if (vb) gather_raw<Q, S, float, ODD>(d, f, ib, Lb, rb);
+  finish_cell<Q, S, float, ODD, FORCE, SR>(d, f, ia, La, ra);
+  if (vb) finish_cell<Q, S, float, ODD, FORCE, SR>(d, f, ib, Lb, rb);
 }
 
 // Inverse of gather: put canonical pre-collision values fv of cell (x,y,z)

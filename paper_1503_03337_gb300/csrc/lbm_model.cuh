@@ -200,6 +200,7 @@ struct Codec;
 // between SMs, and a line cached in one step could be stale in the next.
 template <typename R>
 struct Codec<double, R> {
+  __host__ __device__ static R value(double v) { return R(v); }
   __host__ __device__ static R load(const double* p) {
 #ifdef __CUDA_ARCH__
     return R(__ldg(p));
@@ -218,6 +219,7 @@ struct Codec<double, R> {
 };
 template <typename R>
 struct Codec<float, R> {
+  __host__ __device__ static R value(float v) { return R(v); }
   __host__ __device__ static R load(const float* p) { return R(*p); }
   __host__ __device__ static R load_cg(const float* p) {
 #ifdef __CUDA_ARCH__
@@ -230,6 +232,7 @@ struct Codec<float, R> {
 };
 template <typename R>
 struct Codec<__half, R> {
+  __host__ __device__ static R value(__half v) { return R(__half2float(v)); }
   __host__ __device__ static R load(const __half* p) { return R(__half2float(*p)); }
   __host__ __device__ static R load_cg(const __half* p) {
 #ifdef __CUDA_ARCH__
@@ -242,6 +245,7 @@ struct Codec<__half, R> {
 };
 template <typename R>
 struct Codec<__nv_bfloat16, R> {
+  __host__ __device__ static R value(__nv_bfloat16 v) { return R(__bfloat162float(v)); }
   __host__ __device__ static R load(const __nv_bfloat16* p) {
     return R(__bfloat162float(*p));
   }
@@ -344,66 +348,6 @@ struct Stochastic<__nv_bfloat16> {
     *p = __float2bfloat16_rz(dither_truncate(v, 16, r));
   }
 };
-
-// ---------------------------------------------------------------------------
-// Two cells per thread: a packed pair of FP32 values.  On the device every
-// add, multiply and multiply-add is one packed FP32x2 instruction
-// (__fadd2_rn / __fmul2_rn / __ffma2_rn of sm_100 and later), so the
-// collision of two cells costs the instructions of one.  Arithmetic stays
-// IEEE FP32, rounded to nearest, per component.
-// ---------------------------------------------------------------------------
-// (The scalar branches serve host builds of this header; device code is
-// only ever built for sm_103a.)
-#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
-#define LBM_PACKED_F32X2 1
-#else
-#define LBM_PACKED_F32X2 0
-#endif
-
-struct pf2 {
-  float2 v;
-  pf2() = default;
-  __host__ __device__ pf2(float s) : v(make_float2(s, s)) {}  // broadcast
-  __host__ __device__ pf2(float a, float b) : v(make_float2(a, b)) {}
-};
-
-__host__ __device__ __forceinline__ pf2 pf2_from(float2 v) {
-  pf2 r;
-  r.v = v;
-  return r;
-}
-__host__ __device__ __forceinline__ pf2 operator+(pf2 a, pf2 b) {
-#if LBM_PACKED_F32X2
-  return pf2_from(__fadd2_rn(a.v, b.v));
-#else
-  return pf2(a.v.x + b.v.x, a.v.y + b.v.y);
-#endif
-}
-__host__ __device__ __forceinline__ pf2 operator*(pf2 a, pf2 b) {
-#if LBM_PACKED_F32X2
-  return pf2_from(__fmul2_rn(a.v, b.v));
-#else
-  return pf2(a.v.x * b.v.x, a.v.y * b.v.y);
-#endif
-}
-// a * b + c
-__host__ __device__ __forceinline__ pf2 fmadd(pf2 a, pf2 b, pf2 c) {
-#if LBM_PACKED_F32X2
-  return pf2_from(__ffma2_rn(a.v, b.v, c.v));
-#else
-  return pf2(std::fma(a.v.x, b.v.x, c.v.x), std::fma(a.v.y, b.v.y, c.v.y));
-#endif
-}
-__host__ __device__ __forceinline__ pf2 operator-(pf2 a, pf2 b) {
-  return fmadd(b, pf2(-1.0f), a);
-}
-__host__ __device__ __forceinline__ pf2 operator-(pf2 a) { return a * pf2(-1.0f); }
-__host__ __device__ __forceinline__ pf2 operator*(float s, pf2 a) { return pf2(s) * a; }
-__host__ __device__ __forceinline__ pf2 operator*(pf2 a, float s) { return a * pf2(s); }
-__host__ __device__ __forceinline__ pf2 operator+(pf2 a, float s) { return a + pf2(s); }
-__host__ __device__ __forceinline__ pf2 operator-(pf2 a, float s) { return a - pf2(s); }
-__host__ __device__ __forceinline__ pf2& operator+=(pf2& a, pf2 b) { return a = a + b; }
-__host__ __device__ __forceinline__ pf2& operator-=(pf2& a, pf2 b) { return a = a - b; }
 
 __host__ __device__ __forceinline__ float fmadd(float a, float b, float c) { return a * b + c; }
 __host__ __device__ __forceinline__ double fmadd(double a, double b, double c) {

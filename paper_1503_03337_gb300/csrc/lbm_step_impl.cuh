@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> 
   update_cell<Q, S, R, ODD, FORCE, SR>(d, static_cast<S*>(d.f), x, y, z, x_lo, x_hi);
 }
 
-// Two cells per thread (see update_pair); blockDim.x threads cover
+// Two cells per thread (see update_two); blockDim.x threads cover
 // 2*blockDim.x cells of a row, each warp 64 consecutive cells.
 template <int Q, typename S, bool ODD, bool FORCE, bool SR>
-__global__ void __launch_bounds__(256, 2) k_step2(Domain<float> d) {
+__global__ void __launch_bounds__(256, 3) k_step2(Domain<float> d) {
   pdl_release();
   pdl_acquire();
   const int lane = threadIdx.x & 31;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256, 2) k_step2(Domain<float> d) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (xa >= d.nx || y >= d.ny) return;
-  update_pair<Q, S, ODD, FORCE, SR>(d, static_cast<S*>(d.f), xa, y, z, x_lo);
+  update_two<Q, S, ODD, FORCE, SR>(d, static_cast<S*>(d.f), xa, y, z, x_lo);
 }
 
 template <typename R>
