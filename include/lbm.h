@@ -328,15 +328,26 @@ int lbm_batch_reductions_all(lbm_batch *b, lbm_stats *out, int32_t *slots, int32
  * holding a stochastically rounded domain runs grouped).  Speed only. */
 int lbm_batch_set_launch(lbm_batch *b, int32_t bx, int32_t by, int32_t persistent);
 
-/* Work split of grouped mode (no counterpart in the paper; speed only,
- * results are unchanged).  tiles_per_cta: consecutive tiles (one tile =
- * bx x by cells of one z-plane) each CTA of a group launch updates; 0 picks
- * it from the group size.  solo_min_cells: a domain with at least this many
- * cells runs as its own launch of the single-domain update every step
- * instead of sharing a group launch; 0 = two waves of resident CTAs, < 0 =
- * never.  Synchronises the batch's stream; the next step regroups.
- * Returns LBM_EINVAL for tiles_per_cta outside 0..4096. */
-int lbm_batch_set_schedule(lbm_batch *b, int32_t tiles_per_cta, int64_t solo_min_cells);
+/* Work split and order of grouped mode (no counterpart in the paper; speed
+ * only, results are unchanged).
+ *   tiles_per_cta: consecutive tiles (one tile = bx x by cells of one
+ *     z-plane) each CTA of a group launch updates; 0 picks it from the
+ *     group size.
+ *   solo_min_cells: a domain with at least this many cells runs as its own
+ *     launch of the single-domain update every step instead of sharing a
+ *     group launch; 0 = two waves of resident CTAs, < 0 = never.  A domain
+ *     with no partner in its group also runs solo.
+ *   cluster_bytes: the active domains are packed into L2 clusters of at most
+ *     this many population bytes (a larger domain forms its own); the steps
+ *     of a chunk run in blocks of up to 32, and within a block each cluster
+ *     runs all the block's steps before the next cluster starts, so its
+ *     populations stay in L2 between steps.  0 = half of the device's
+ *     L2, < 0 = one cluster (every domain advances step by step
+ *     together).
+ * Synchronises the batch's stream; the next step regroups.  Returns
+ * LBM_EINVAL for tiles_per_cta outside 0..4096. */
+int lbm_batch_set_schedule(lbm_batch *b, int32_t tiles_per_cta, int64_t solo_min_cells,
+                           int64_t cluster_bytes);
 
 /* Active domains, bytes of population storage, total cells. */
 int lbm_batch_info(lbm_batch *b, int32_t *active, int64_t *used_bytes, int64_t *total_cells);

@@ -10,10 +10,12 @@
 // Grouped mode (default): every step launches one kernel per group of
 // domains sharing Q, storage, rounding and parity; each is the single-domain
 // update specialised at compile time plus a per-CTA domain lookup.  A domain
-// big enough to fill the device by itself (solo) gets its own launch of the
-// single-domain update instead, so batching costs it nothing.  Every domain's
-// force and rounding key for the steps ahead are computed once per domain
-// and step by a small prepare kernel.
+// big enough to fill the device by itself, or alone in its group, (solo)
+// gets its own launch of the single-domain update instead, so batching costs
+// it nothing.  Domains are packed into L2-sized clusters that run a block of
+// steps each in turn, keeping a cluster's populations in L2 from step to
+// step.  Every domain's force and rounding key for the steps ahead are
+// computed once per domain and step by a small prepare kernel.
 // Persistent mode: one cooperative launch runs `chunk` steps of all domains,
 // with a grid barrier between steps (the in-place AA update needs every cell
 // of step s done before step s+1 reads its neighbours).  The barrier spins a
@@ -27,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <tuple>
@@ -111,6 +114,8 @@ struct lbm_batch {
   int resident = 0;  // CTAs of the grouped kernels resident at once
   int tiles_per_cta = 0;        // grouped launches; 0: automatic
   int64_t solo_min_cells = 0;   // 0: automatic; < 0: no solo domains
+  int64_t cluster_bytes = 0;    // L2 cluster budget; 0: automatic; < 0: one cluster
+  int64_t l2_bytes = 0;         // the device's L2 size
   long long spin_limit = 1ll << 26;
   int extra_arrivals = 0;
   // table: entries sorted by group; in persistent mode one run over all
@@ -119,16 +124,19 @@ struct lbm_batch {
   int64_t total_tiles = 0;
   std::vector<int> order;  // slot of each entry
   struct Group {
+    int cluster;                        // L2 cluster (groups are sorted by it)
     int Q, storage, sr, force, parity;  // parity of the domains' step counters
     int solo;                           // one launch per entry
     int first, count;                   // entries
     int64_t tiles;
   };
   std::vector<Group> groups;
+  int nclusters = 0;
   std::vector<BatchEntry> host_ents;  // the uploaded table (group-local half)
-  // graph of one chunk; captured when a table version runs a second chunk
-  // (membership changes invalidate it, and a capture that is used once
-  // costs more than it saves)
+  // graph of one chunk; captured when a table version runs its third chunk
+  // (membership changes invalidate it; a serving loop changes membership
+  // every check or two, and a capture replayed once or twice costs more
+  // host time than the direct launches it replaces)
   cudaGraphExec_t graph = nullptr;
   int graph_chunk = 0;
   bool graph_ok = true;
@@ -205,10 +213,6 @@ int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, Doma
   return LBM_OK;
 }
 
-// Rebuild and upload the descriptor table of the active domains, sorted into
-// groups of equal (Q, storage, rounding, parity).  Tile prefix sums restart
-// at zero in every group (grouped launches) and the persistent kernel, which
-// walks all entries, gets its own running prefix in a second table half.
 int64_t solo_threshold(const lbm_batch* b) {
   if (b->solo_min_cells < 0) return INT64_MAX;
   if (b->solo_min_cells > 0) return b->solo_min_cells;
@@ -216,17 +220,75 @@ int64_t solo_threshold(const lbm_batch* b) {
   return 2 * (int64_t)std::max(1, b->resident) * b->bx * b->by;
 }
 
+int64_t cluster_budget(const lbm_batch* b) {
+  if (b->cluster_bytes < 0) return INT64_MAX;
+  if (b->cluster_bytes > 0) return b->cluster_bytes;
+  // half of L2: a cluster's populations stay resident across the steps it
+  // runs back to back (measured on a mix of 15-75 MB domains: budgets of a
+  // quarter to a half of L2 run 16 % faster than three quarters)
+  return b->l2_bytes > 0 ? b->l2_bytes / 2 : (int64_t)64 << 20;
+}
+
+// L2 clusters: the active domains packed first-fit, largest first, into sets
+// whose population bytes fit the cluster budget (a larger domain is a
+// cluster of its own).  A chunk runs its steps in blocks of up to kDynSteps;
+// within a block the clusters run one after another, each for all the
+// block's steps, so a cluster's populations stay in L2 from step to step.
+// Domains are independent, so the order changes no result.
+std::vector<int> assign_clusters(lbm_batch* b, const std::vector<int>& idx) {
+  const int64_t budget = cluster_budget(b);
+  std::vector<int> by_size = idx;
+  std::stable_sort(by_size.begin(), by_size.end(), [&](int a, int c) {
+    return b->slots[a].fbytes > b->slots[c].fbytes;
+  });
+  std::vector<int64_t> used;
+  std::vector<int> cluster(b->slots.size(), 0);
+  for (int i : by_size) {
+    const int64_t f = (int64_t)b->slots[i].fbytes;
+    int c = -1;
+    for (int k = 0; k < (int)used.size(); ++k)
+      if (used[k] + f <= budget) {
+        c = k;
+        break;
+      }
+    if (c < 0) {
+      c = (int)used.size();
+      used.push_back(0);
+    }
+    used[c] += f;
+    cluster[i] = c;
+  }
+  b->nclusters = (int)used.size();
+  return cluster;
+}
+
+// Rebuild and upload the descriptor table of the active domains, sorted into
+// groups of equal (cluster, Q, storage, rounding, force, parity, solo).  A
+// domain runs solo (its own launch of the single-domain update) when it is
+// big enough to fill the device or has no partner in its group.  Tile prefix
+// sums restart at zero in every group (grouped launches) and the persistent
+// kernel, which walks all entries, gets its own running prefix in a second
+// table half.
 int upload_table(lbm_batch* b) {
   std::vector<int> idx;
   for (int i = 0; i < (int)b->slots.size(); ++i)
     if (b->slots[i].used) idx.push_back(i);
   const int64_t solo_min = solo_threshold(b);
-  auto key = [&](int i) {
+  const std::vector<int> cluster = assign_clusters(b, idx);
+  auto base_key = [&](int i) {
     const BatchSlot& s = b->slots[i];
     const int sr = s.dd.rounding == LBM_ROUND_STOCHASTIC && s.dd.storage != LBM_STORAGE_F32;
     const int force = s.dd.force[0] != 0.0 || s.dd.force[1] != 0.0 || s.dd.force[2] != 0.0;
-    const int solo = s.dd.N >= solo_min;
-    return std::make_tuple(s.dd.Q, s.dd.storage, sr, force, (int)(s.n & 1), solo);
+    return std::make_tuple(cluster[i], s.dd.Q, s.dd.storage, sr, force, (int)(s.n & 1));
+  };
+  std::map<decltype(base_key(0)), int> partners;
+  for (int i : idx)
+    if (b->slots[i].dd.N < solo_min) partners[base_key(i)] += 1;
+  auto key = [&](int i) {
+    const auto k = base_key(i);
+    const auto it = partners.find(k);
+    const int solo = b->slots[i].dd.N >= solo_min || it == partners.end() || it->second < 2;
+    return std::tuple_cat(k, std::make_tuple(solo));
   };
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return key(a) < key(c); });
   std::vector<BatchEntry> ents;
@@ -251,11 +313,12 @@ int upload_table(lbm_batch* b) {
     tiles += nt;
     const auto k = key(i);
     if (b->groups.empty() ||
-        std::make_tuple(b->groups.back().Q, b->groups.back().storage, b->groups.back().sr,
-                        b->groups.back().force, b->groups.back().parity,
+        std::make_tuple(b->groups.back().cluster, b->groups.back().Q, b->groups.back().storage,
+                        b->groups.back().sr, b->groups.back().force, b->groups.back().parity,
                         b->groups.back().solo) != k) {
       b->groups.push_back({std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-                           std::get<4>(k), std::get<5>(k), (int)ents.size(), 0, 0});
+                           std::get<4>(k), std::get<5>(k), std::get<6>(k), (int)ents.size(), 0,
+                           0});
     }
     ents.push_back(e);
     b->groups.back().count += 1;
@@ -317,6 +380,39 @@ int grid_for_batch(lbm_batch* b) {
   return per_sm * sms;
 }
 
+// Step s (of the chunk) of one group: one launch per solo entry, or one
+// grouped launch.
+cudaError_t launch_group_step(lbm_batch* b, const lbm_batch::Group& g, int s,
+                              const BatchEntry* local, dim3 block) {
+  const StepDyn* dyn = b->dyn + (size_t)(s % kDynSteps) * b->capacity;
+  const bool odd = ((g.parity + s) & 1) != 0;
+  if (g.solo) {
+    for (int k = g.first; k < g.first + g.count; ++k) {
+      const BatchEntry& he = b->host_ents[k];
+      const int periodic = he.period > 0.0;
+      SoloLaunch sl{g.storage, g.sr, g.force, odd ? 1 : 0, periodic,
+                    dim3(he.tiles_x, he.tiles_y, he.d.nz), block, b->stream, he.d, dyn + k};
+      if (!periodic)  // constant force in the descriptor
+        for (int a = 0; a < 3; ++a) sl.d.F[a] = float(he.force[a]);
+      cudaError_t e = g.Q == 14 ? launch_solo_q14(sl) : launch_solo_q18(sl);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  // contiguous runs of tiles per CTA, short enough to leave about eight
+  // waves of CTAs (a partly filled last wave then costs little) and, in big
+  // groups, long enough to spread each descriptor load over several tiles
+  int per = b->tiles_per_cta;
+  if (per < 1) {
+    const int64_t waves = std::max<int64_t>(1, (int64_t)b->resident * 8);
+    per = (int)std::min<int64_t>(16, std::max<int64_t>(1, g.tiles / waves));
+  }
+  const unsigned grid = (unsigned)((g.tiles + per - 1) / per);
+  GroupLaunch gl{g.storage,       g.sr,          g.force, odd ? 1 : 0, dim3(grid), block,
+                 b->stream,       local + g.first, dyn + g.first, g.count, (int)g.tiles, per};
+  return g.Q == 14 ? launch_group_q14(gl) : launch_group_q18(gl);
+}
+
 // Queue one chunk of `chunk` steps (no graph).
 cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
   dim3 block(b->bx, b->by, 1);
@@ -330,44 +426,21 @@ cudaError_t enqueue_chunk(lbm_batch* b, int chunk) {
     if (e != cudaSuccess) return e;
   } else {
     const BatchEntry* local = b->ents + b->capacity;
-    for (int s = 0; s < chunk; ++s) {
-      if (s % kDynSteps == 0) {
-        const int ns = std::min(kDynSteps, chunk - s);
-        const int total = b->nent * ns;
-        const int blocks = std::min(1024, (total + 255) / 256);
-        k_batch_prepare<<<blocks, 256, 0, b->stream>>>(local, b->nent, s, ns, b->dyn,
-                                                       b->capacity);
-      }
-      const StepDyn* dyn = b->dyn + (size_t)(s % kDynSteps) * b->capacity;
-      for (const auto& g : b->groups) {
-        const bool odd = ((g.parity + s) & 1) != 0;
-        if (g.solo) {
-          for (int k = g.first; k < g.first + g.count; ++k) {
-            const BatchEntry& he = b->host_ents[k];
-            const int periodic = he.period > 0.0;
-            SoloLaunch sl{g.storage, g.sr, g.force, odd ? 1 : 0, periodic,
-                          dim3(he.tiles_x, he.tiles_y, he.d.nz), block, b->stream, he.d, dyn + k};
-            if (!periodic)  // constant force in the descriptor
-              for (int a = 0; a < 3; ++a) sl.d.F[a] = float(he.force[a]);
-            cudaError_t e = g.Q == 14 ? launch_solo_q14(sl) : launch_solo_q18(sl);
-            if (e != cudaSuccess) return e;
-          }
-          continue;
-        }
-        // contiguous runs of tiles per CTA, short enough to leave about
-        // eight waves of CTAs (a partly filled last wave then costs little)
-        // and, in big groups, long enough to spread each descriptor load
-        // over several tiles
-        int per = b->tiles_per_cta;
-        if (per < 1) {
-          const int64_t waves = std::max<int64_t>(1, (int64_t)b->resident * 8);
-          per = (int)std::min<int64_t>(16, std::max<int64_t>(1, g.tiles / waves));
-        }
-        const unsigned grid = (unsigned)((g.tiles + per - 1) / per);
-        GroupLaunch gl{g.storage,       g.sr,          g.force, odd ? 1 : 0, dim3(grid), block,
-                       b->stream,       local + g.first, dyn + g.first, g.count, (int)g.tiles, per};
-        cudaError_t e = g.Q == 14 ? launch_group_q14(gl) : launch_group_q18(gl);
-        if (e != cudaSuccess) return e;
+    for (int s0 = 0; s0 < chunk; s0 += kDynSteps) {
+      const int ns = std::min(kDynSteps, chunk - s0);
+      const int total = b->nent * ns;
+      const int blocks = std::min(1024, (total + 255) / 256);
+      k_batch_prepare<<<blocks, 256, 0, b->stream>>>(local, b->nent, s0, ns, b->dyn,
+                                                     b->capacity);
+      size_t g0 = 0;
+      while (g0 < b->groups.size()) {  // one cluster: groups g0 .. g1-1
+        size_t g1 = g0;
+        while (g1 < b->groups.size() && b->groups[g1].cluster == b->groups[g0].cluster) ++g1;
+        for (int s = s0; s < s0 + ns; ++s)
+          for (size_t gi = g0; gi < g1; ++gi)
+            if (cudaError_t e = launch_group_step(b, b->groups[gi], s, local, block))
+              return e;
+        g0 = g1;
       }
     }
   }
@@ -413,6 +486,10 @@ int lbm_batch_create(int32_t capacity, int64_t budget_bytes, void* cuda_stream, 
   *b->flag_host = 0;
   b->grid = grid_for_batch(b);
   b->resident = resident_for_group(b);
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device) == cudaSuccess)
+    b->l2_bytes = l2;
+  cudaGetLastError();
   *out = b;
   return LBM_OK;
 }
@@ -518,7 +595,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps, int32_t chunk) {
   while (left > 0) {
     const int c = (int)std::min<int64_t>(left, chunk);
     cudaError_t e = cudaSuccess;
-    if (c == chunk && b->graph_ok && (b->graph || b->chunks_this_version >= 1)) {
+    if (c == chunk && b->graph_ok && (b->graph || b->chunks_this_version >= 2)) {
       if (!b->graph || b->graph_chunk != c) {
         drop_graph(b);
         cudaGraph_t g = nullptr;
@@ -655,13 +732,15 @@ int lbm_batch_set_launch(lbm_batch* b, int32_t bx, int32_t by, int32_t persisten
   return LBM_OK;
 }
 
-int lbm_batch_set_schedule(lbm_batch* b, int32_t tiles_per_cta, int64_t solo_min_cells) {
+int lbm_batch_set_schedule(lbm_batch* b, int32_t tiles_per_cta, int64_t solo_min_cells,
+                           int64_t cluster_bytes) {
   if (!b) return bfail(LBM_EINVAL, "null batch");
   if (tiles_per_cta < 0 || tiles_per_cta > 4096) return bfail(LBM_EINVAL, "tiles_per_cta must be 0..4096");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(e, "batch set_schedule");
   b->tiles_per_cta = tiles_per_cta;
   b->solo_min_cells = solo_min_cells;
+  b->cluster_bytes = cluster_bytes;
   b->dirty = true;
   return LBM_OK;
 }

@@ -11,6 +11,7 @@
 
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
+#include "lbm_launch.cuh"
 
 namespace lbm {
 
@@ -174,6 +175,8 @@ template <int Q, typename S, bool ODD, bool SR, bool FORCE>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
     k_group(const BatchEntry* __restrict__ ents, const StepDyn* __restrict__ dyn, int nent,
             int tiles, int per) {
+  pdl_release();
+  pdl_acquire();
   __shared__ Domain<float> sd;
   __shared__ int s_tx, s_ty, s_begin, s_end;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -213,6 +216,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
 template <int Q, typename S, bool ODD, bool SR, bool FORCE, bool DYN>
 __global__ void __launch_bounds__(256, DYN ? 3 : 4)
     k_solo(Domain<float> d, const StepDyn* __restrict__ dyn) {
+  pdl_release();
+  pdl_acquire();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -271,36 +276,36 @@ void launch_group_typed(const GroupLaunch& g) {
   if constexpr (Stochastic<S>::enabled) {
     if (g.sr) {
       if (g.odd)
-        k_group<Q, S, true, true, FORCE><<<g.grid, g.block, 0, g.stream>>>(g.ents, g.dyn, g.count, g.tiles, g.per);
+        launch_pdl(k_group<Q, S, true, true, FORCE>, g.grid, g.block, true, g.stream, g.ents, g.dyn, g.count, g.tiles, g.per);
       else
-        k_group<Q, S, false, true, FORCE><<<g.grid, g.block, 0, g.stream>>>(g.ents, g.dyn, g.count, g.tiles, g.per);
+        launch_pdl(k_group<Q, S, false, true, FORCE>, g.grid, g.block, true, g.stream, g.ents, g.dyn, g.count, g.tiles, g.per);
       return;
     }
   }
   if (g.odd)
-    k_group<Q, S, true, false, FORCE><<<g.grid, g.block, 0, g.stream>>>(g.ents, g.dyn, g.count, g.tiles, g.per);
+    launch_pdl(k_group<Q, S, true, false, FORCE>, g.grid, g.block, true, g.stream, g.ents, g.dyn, g.count, g.tiles, g.per);
   else
-    k_group<Q, S, false, false, FORCE><<<g.grid, g.block, 0, g.stream>>>(g.ents, g.dyn, g.count, g.tiles, g.per);
+    launch_pdl(k_group<Q, S, false, false, FORCE>, g.grid, g.block, true, g.stream, g.ents, g.dyn, g.count, g.tiles, g.per);
 }
 
 template <int Q, typename S, bool FORCE>
 void launch_solo_typed(const SoloLaunch& g) {
   if constexpr (Stochastic<S>::enabled) {
     if (g.sr) {
-      if (g.odd) k_solo<Q, S, true, true, FORCE, true><<<g.grid, g.block, 0, g.stream>>>(g.d, g.dyn);
-      else k_solo<Q, S, false, true, FORCE, true><<<g.grid, g.block, 0, g.stream>>>(g.d, g.dyn);
+      if (g.odd) launch_pdl(k_solo<Q, S, true, true, FORCE, true>, g.grid, g.block, true, g.stream, g.d, g.dyn);
+      else launch_pdl(k_solo<Q, S, false, true, FORCE, true>, g.grid, g.block, true, g.stream, g.d, g.dyn);
       return;
     }
   }
   if constexpr (FORCE) {
     if (g.dyn_force) {
-      if (g.odd) k_solo<Q, S, true, false, true, true><<<g.grid, g.block, 0, g.stream>>>(g.d, g.dyn);
-      else k_solo<Q, S, false, false, true, true><<<g.grid, g.block, 0, g.stream>>>(g.d, g.dyn);
+      if (g.odd) launch_pdl(k_solo<Q, S, true, false, true, true>, g.grid, g.block, true, g.stream, g.d, g.dyn);
+      else launch_pdl(k_solo<Q, S, false, false, true, true>, g.grid, g.block, true, g.stream, g.d, g.dyn);
       return;
     }
   }
-  if (g.odd) k_solo<Q, S, true, false, FORCE, false><<<g.grid, g.block, 0, g.stream>>>(g.d, g.dyn);
-  else k_solo<Q, S, false, false, FORCE, false><<<g.grid, g.block, 0, g.stream>>>(g.d, g.dyn);
+  if (g.odd) launch_pdl(k_solo<Q, S, true, false, FORCE, false>, g.grid, g.block, true, g.stream, g.d, g.dyn);
+  else launch_pdl(k_solo<Q, S, false, false, FORCE, false>, g.grid, g.block, true, g.stream, g.d, g.dyn);
 }
 
 template <int Q, typename L, template <int, typename, bool> class Op>

@@ -7,20 +7,12 @@
 
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
+#include "lbm_launch.cuh"
 
 namespace lbm {
 
 template <typename R>
 Domain<R> to_domain(const DomainDesc& d, const double F[3]);
-
-// Programmatic dependent launch: a step kernel lets the next launch in the
-// stream start (its CTAs become resident as this grid drains) and waits for
-// the previous grid's completion and memory before touching any population.
-// Without the launch attribute both instructions have no effect.
-__device__ __forceinline__ void pdl_release() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_acquire() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
 __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> d) {
@@ -55,17 +47,7 @@ __global__ void __launch_bounds__(256, 3) k_step2(Domain<float> d) {
 template <typename R>
 void launch_one(void (*kernel)(Domain<R>), const Domain<R>& d, dim3 grid, dim3 block, bool pdl,
                 cudaStream_t st) {
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, kernel, d);
+  launch_pdl(kernel, grid, block, pdl, st, d);
 }
 
 template <int Q, typename S, typename R, bool SR>

@@ -112,7 +112,7 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
     "lbm_batch_set_launch": (_I, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
-    "lbm_batch_set_schedule": (_I, [_VP, ctypes.c_int32, ctypes.c_int64]),
+    "lbm_batch_set_schedule": (_I, [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]),
     "lbm_batch_info": (_I, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_I64),
                             ctypes.POINTER(_I64)]),
     "lbm_batch_set_barrier_test": (_I, [_VP, ctypes.c_int32, _I64]),
@@ -358,8 +358,9 @@ def lbm_batch_set_launch(b, bx, by, persistent):
     _check(load().lbm_batch_set_launch(b, int(bx), int(by), int(persistent)))
 
 
-def lbm_batch_set_schedule(b, tiles_per_cta=0, solo_min_cells=0):
-    _check(load().lbm_batch_set_schedule(b, int(tiles_per_cta), int(solo_min_cells)))
+def lbm_batch_set_schedule(b, tiles_per_cta=0, solo_min_cells=0, cluster_bytes=0):
+    _check(load().lbm_batch_set_schedule(b, int(tiles_per_cta), int(solo_min_cells),
+                                         int(cluster_bytes)))
 
 
 def lbm_batch_info(b):

@@ -57,19 +57,21 @@ def single_pops(c, steps):
         lbm.lbm_destroy(h)
 
 
-# (persistent, tiles_per_cta, solo_min_cells): the default schedule, every
-# domain solo, every domain grouped one tile per CTA, mixed with long runs
-SCHEDULES = [(1, 0, 0), (0, 0, 0), (0, 3, 1), (0, 1, -1), (0, 7, 2000)]
+# (persistent, tiles_per_cta, solo_min_cells, cluster_bytes): the default
+# schedule, every domain solo, every domain grouped one tile per CTA in one
+# cluster, long runs, and clusters so small that every domain is its own
+SCHEDULES = [(1, 0, 0, 0), (0, 0, 0, 0), (0, 3, 1, 0), (0, 1, -1, -1), (0, 7, 2000, 0),
+             (0, 0, 0, 1 << 16), (0, 2, -1, 3 << 20)]
 
 
-@pytest.mark.parametrize("persistent,per,solo", SCHEDULES)
-def test_batch_same_alone_and_in_mix(torch, persistent, per, solo):
+@pytest.mark.parametrize("persistent,per,solo,cluster", SCHEDULES)
+def test_batch_same_alone_and_in_mix(torch, persistent, per, solo, cluster):
     stream = torch.cuda.current_stream().cuda_stream
     cases = mix()
     b = lbm.lbm_batch_create(8, 0, stream)
     try:
         lbm.lbm_batch_set_launch(b, 64, 2, persistent)
-        lbm.lbm_batch_set_schedule(b, per, solo)
+        lbm.lbm_batch_set_schedule(b, per, solo, cluster)
         slots = {}
         steps = {}
         for k in range(4):
