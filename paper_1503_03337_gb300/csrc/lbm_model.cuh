@@ -427,7 +427,39 @@ __host__ __device__ __forceinline__ void back_transform(const R* x, R* f) {
 template <typename R>
 struct Rates {
   R sc, se, sq, snu, spi, st;
+  // Per row K of T, with D_K its norm: k[K] = s_K / D_K and
+  // h[K] = (1 - s_K/2) / D_K (for the momentum rows, which carry only the
+  // force, h[K] = 1 / D_K).  Filled once per launch by scale_rows, so the
+  // collision multiplies each relaxed row once.
+  R k[18], h[18];
 };
+
+// Relaxation rate of row K (Eq. sD3Q15meaning / Eq. sD3Q19): conserved rows
+// s_c, energy s_e, heat flux s_q, the stress rows s_nu (the pi rows of Q18
+// s_pi), the third-order rows s_t.
+template <int Q, typename R>
+__host__ __device__ constexpr R rate_of(const Rates<R>& r, int K) {
+  if (K == 0 || K == 2 || K == 4 || K == 6) return r.sc;
+  if (K == 1) return r.se;
+  if (K == 3 || K == 5 || K == 7) return r.sq;
+  if (Q == 14) return K == 13 ? r.st : r.snu;
+  if (K == 9 || K == 11) return r.spi;
+  return K >= 15 ? r.st : r.snu;
+}
+
+template <int Q, typename R>
+__host__ __device__ inline void scale_rows(Rates<R>& r) {
+  for (int K = 0; K < 18; ++K) {
+    r.k[K] = R(0);
+    r.h[K] = R(0);
+  }
+  for (int K = 0; K < Q; ++K) {
+    const R inv = R(1.0 / row_norm<Q>(K));
+    const R sk = rate_of<Q>(r, K);
+    r.k[K] = sk * inv;
+    r.h[K] = (K == 2 || K == 4 || K == 6) ? inv : (R(1) - R(0.5) * sk) * inv;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Streaming back-transform: a relaxed row x_K (already divided by D_K) is
@@ -531,9 +563,6 @@ __host__ __device__ __forceinline__ void collide(V* f, const Rates<R>& s, R Fx, 
     syz = uy * Fz + uz * Fy;
     sxz = ux * Fz + uz * Fx;
   }
-  const R hq = R(1) - R(0.5) * s.sq;
-  const R hnu = R(1) - R(0.5) * s.snu;
-  const R he = R(1) - R(0.5) * s.se;
 
   // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K, streamed into the pair
   // accumulators E = s/2 - sum_even phi x and O = d/2 - sum_odd phi x, so
@@ -542,9 +571,8 @@ __host__ __device__ __forceinline__ void collide(V* f, const Rates<R>& s, R Fx, 
   [&]<int... I>(std::integer_sequence<int, I...>) {
     ((E[I] = R(0.5) * ps[I], O[I] = R(0.5) * pd[I]), ...);
   }(std::make_integer_sequence<int, NP>{});
-  auto row = [&]<int K>(V xk) {
-    add_row<Q, FORCE, K>(xk * R(1.0 / row_norm<Q>(K)), E, O);
-  };
+  // xk arrives divided by D_K (the factors of s.k and s.h)
+  auto row = [&]<int K>(V xk) { add_row<Q, FORCE, K>(xk, E, O); };
   auto m = [&]<int K>() {
     if constexpr (row_even<Q>(K)) return row_sum<Q, K, 0, false>(V(R(0)), ps);
     else return row_sum<Q, K, 0, false>(V(R(0)), pd);
@@ -552,76 +580,75 @@ __host__ __device__ __forceinline__ void collide(V* f, const Rates<R>& s, R Fx, 
   V x1;
   if constexpr (Q == 14) {
     // e_eq = -7p + u^2 (source 2 u.F)
-    x1 = s.se * (m.template operator()<1>() - (R(-7) * p + u2));
-    if constexpr (FORCE) x1 -= he * (R(2) * uF);
+    x1 = s.k[1] * (m.template operator()<1>() - (R(-7) * p + u2));
+    if constexpr (FORCE) x1 -= s.h[1] * (R(2) * uF);
   } else {
     // e_eq = -p + u^2/2 (source u.F)
-    x1 = s.se * (m.template operator()<1>() - (-p + R(0.5) * u2));
-    if constexpr (FORCE) x1 -= he * uF;
+    x1 = s.k[1] * (m.template operator()<1>() - (-p + R(0.5) * u2));
+    if constexpr (FORCE) x1 -= s.h[1] * uF;
   }
   row.template operator()<1>(x1);
   if constexpr (FORCE) {  // momentum rows: s_c (j - u) - (1 - s_c/2) F = -F
-    row.template operator()<2>(V(-Fx));
-    row.template operator()<4>(V(-Fy));
-    row.template operator()<6>(V(-Fz));
+    row.template operator()<2>(V(-Fx * s.h[2]));
+    row.template operator()<4>(V(-Fy * s.h[4]));
+    row.template operator()<6>(V(-Fz * s.h[6]));
   }
   // q_eq = -7u/3 (Q14) or -2u/3 (Q18); sources -7F/3 or -2F/3
   constexpr double cq = Q == 14 ? 7.0 / 3.0 : 2.0 / 3.0;
-  V x3 = s.sq * (m.template operator()<3>() + R(cq) * ux);
-  V x5 = s.sq * (m.template operator()<5>() + R(cq) * uy);
-  V x7 = s.sq * (m.template operator()<7>() + R(cq) * uz);
+  V x3 = s.k[3] * (m.template operator()<3>() + R(cq) * ux);
+  V x5 = s.k[5] * (m.template operator()<5>() + R(cq) * uy);
+  V x7 = s.k[7] * (m.template operator()<7>() + R(cq) * uz);
   if constexpr (FORCE) {
-    x3 += hq * (R(cq) * Fx);
-    x5 += hq * (R(cq) * Fy);
-    x7 += hq * (R(cq) * Fz);
+    x3 += s.h[3] * (R(cq) * Fx);
+    x5 += s.h[5] * (R(cq) * Fy);
+    x7 += s.h[7] * (R(cq) * Fz);
   }
   row.template operator()<3>(x3);
   row.template operator()<5>(x5);
   row.template operator()<7>(x7);
   if constexpr (Q == 14) {
-    V x8 = s.snu * (m.template operator()<8>() - pxx_eq);
-    if constexpr (FORCE) x8 -= hnu * sxx;
+    V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
+    if constexpr (FORCE) x8 -= s.h[8] * sxx;
     row.template operator()<8>(x8);
-    V x9 = s.snu * (m.template operator()<9>() - pww_eq);
-    if constexpr (FORCE) x9 -= hnu * sww;
+    V x9 = s.k[9] * (m.template operator()<9>() - pww_eq);
+    if constexpr (FORCE) x9 -= s.h[9] * sww;
     row.template operator()<9>(x9);
-    V x10 = s.snu * (m.template operator()<10>() - uxy);
-    if constexpr (FORCE) x10 -= hnu * sxy;
+    V x10 = s.k[10] * (m.template operator()<10>() - uxy);
+    if constexpr (FORCE) x10 -= s.h[10] * sxy;
     row.template operator()<10>(x10);
-    V x11 = s.snu * (m.template operator()<11>() - uyz);
-    if constexpr (FORCE) x11 -= hnu * syz;
+    V x11 = s.k[11] * (m.template operator()<11>() - uyz);
+    if constexpr (FORCE) x11 -= s.h[11] * syz;
     row.template operator()<11>(x11);
-    V x12 = s.snu * (m.template operator()<12>() - uxz);
-    if constexpr (FORCE) x12 -= hnu * sxz;
+    V x12 = s.k[12] * (m.template operator()<12>() - uxz);
+    if constexpr (FORCE) x12 -= s.h[12] * sxz;
     row.template operator()<12>(x12);
-    row.template operator()<13>(s.st * m.template operator()<13>());
+    row.template operator()<13>(s.k[13] * m.template operator()<13>());
   } else {
     // 3pi_xx and pi_ww equilibria (and sources) are -1/2 of 3p_xx and p_ww
-    const R hpi = R(1) - R(0.5) * s.spi;
-    V x8 = s.snu * (m.template operator()<8>() - pxx_eq);
-    if constexpr (FORCE) x8 -= hnu * sxx;
+    V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
+    if constexpr (FORCE) x8 -= s.h[8] * sxx;
     row.template operator()<8>(x8);
-    V x9 = s.spi * (m.template operator()<9>() + R(0.5) * pxx_eq);
-    if constexpr (FORCE) x9 += hpi * (R(0.5) * sxx);
+    V x9 = s.k[9] * (m.template operator()<9>() + R(0.5) * pxx_eq);
+    if constexpr (FORCE) x9 += s.h[9] * (R(0.5) * sxx);
     row.template operator()<9>(x9);
-    V x10 = s.snu * (m.template operator()<10>() - pww_eq);
-    if constexpr (FORCE) x10 -= hnu * sww;
+    V x10 = s.k[10] * (m.template operator()<10>() - pww_eq);
+    if constexpr (FORCE) x10 -= s.h[10] * sww;
     row.template operator()<10>(x10);
-    V x11 = s.spi * (m.template operator()<11>() + R(0.5) * pww_eq);
-    if constexpr (FORCE) x11 += hpi * (R(0.5) * sww);
+    V x11 = s.k[11] * (m.template operator()<11>() + R(0.5) * pww_eq);
+    if constexpr (FORCE) x11 += s.h[11] * (R(0.5) * sww);
     row.template operator()<11>(x11);
-    V x12 = s.snu * (m.template operator()<12>() - uxy);
-    if constexpr (FORCE) x12 -= hnu * sxy;
+    V x12 = s.k[12] * (m.template operator()<12>() - uxy);
+    if constexpr (FORCE) x12 -= s.h[12] * sxy;
     row.template operator()<12>(x12);
-    V x13 = s.snu * (m.template operator()<13>() - uyz);
-    if constexpr (FORCE) x13 -= hnu * syz;
+    V x13 = s.k[13] * (m.template operator()<13>() - uyz);
+    if constexpr (FORCE) x13 -= s.h[13] * syz;
     row.template operator()<13>(x13);
-    V x14 = s.snu * (m.template operator()<14>() - uxz);
-    if constexpr (FORCE) x14 -= hnu * sxz;
+    V x14 = s.k[14] * (m.template operator()<14>() - uxz);
+    if constexpr (FORCE) x14 -= s.h[14] * sxz;
     row.template operator()<14>(x14);
-    row.template operator()<15>(s.st * m.template operator()<15>());
-    row.template operator()<16>(s.st * m.template operator()<16>());
-    row.template operator()<17>(s.st * m.template operator()<17>());
+    row.template operator()<15>(s.k[15] * m.template operator()<15>());
+    row.template operator()<16>(s.k[16] * m.template operator()<16>());
+    row.template operator()<17>(s.k[17] * m.template operator()<17>());
   }
   // f*_rep = f_rep - (E + O)_rows = E + O, f*_partner = E - O
   [&]<int... I>(std::integer_sequence<int, I...>) {

@@ -25,6 +25,8 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
   o.s.snu = R(d.s[3]);
   o.s.spi = R(d.s[4]);
   o.s.st = R(d.s[5]);
+  if (d.Q == 14) scale_rows<14>(o.s);
+  else scale_rows<18>(o.s);
   for (int k = 0; k < 3; ++k) o.F[k] = R(F[k]);
   o.key = 0;
   if (d.Q == 14) fill_offsets<14>(o);

@@ -24,6 +24,7 @@ static void step_typed(void* f, int nx, int ny, int nz, const int* per, int movi
     for (int k = 0; k < 3; ++k) d.uw[face][k] = R(uw[3 * face + k]);
   d.s.sc = R(s[0]); d.s.se = R(s[1]); d.s.sq = R(s[2]);
   d.s.snu = R(s[3]); d.s.spi = R(s[4]); d.s.st = R(s[5]);
+  scale_rows<Q>(d.s);
   for (int k = 0; k < 3; ++k) d.F[k] = R(F[k]);
   d.key = mix32(0x5eedu ^ uint32_t(n) * 0x632be5abu);
   fill_offsets<Q>(d);
@@ -140,10 +141,15 @@ int emu_canonical(int Q, void* f, int nx, int ny, int nz, const int* per, int mo
 }
 
 int emu_collide(int Q, const double* s, double* f, const double* F) {
-  Rates<double> r{s[0], s[1], s[2], s[3], s[4], s[5]};
+  Rates<double> r{s[0], s[1], s[2], s[3], s[4], s[5], {}, {}};
   double ux, uy, uz;
-  if (Q == 14) collide<14, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
-  else if (Q == 18) collide<18, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
+  if (Q == 14) {
+    scale_rows<14>(r);
+    collide<14, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
+  } else if (Q == 18) {
+    scale_rows<18>(r);
+    collide<18, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
+  }
   else return -1;
   return 0;
 }
