@@ -194,15 +194,19 @@ int lbm_read_stats(lbm_handle *h, lbm_stats *out);
 
 /* Launch shape of the step kernel.  Affects speed, and (cells_per_thread
  * only) the FP32 rounding pattern: bx and by never change results; the two
- * kernels behind cells_per_thread 1 and 2 run the same operations in the
- * same order, but the compiler may fuse multiply-adds differently, so their
- * results agree to FP32 rounding, not bit for bit. */
+ * cells of a pair are collided in packed FP32x2, where the compiler fuses
+ * multiply-adds differently than in the one-cell kernel, so results agree to
+ * FP32 rounding, not bit for bit. */
 typedef struct lbm_launch {
   int32_t bx, by;           /* threads along x (multiple of 32, so a warp never
                                spans two x-rows) and y; bx*by <= 256          */
-  int32_t cells_per_thread; /* 1, or 2 (cells x and x+32: the thread issues the
-                               loads of both before updating either, doubling
-                               the loads in flight; not for FP64 storage)     */
+  int32_t cells_per_thread; /* 1, or 2: on even steps with nx even and
+                               rounding to nearest, each thread updates the
+                               x-adjacent cells 2t, 2t+1, moving each
+                               population of the pair as one word (a warp
+                               touches 128 B per population with 2-byte
+                               storage instead of 64 B); odd steps run one
+                               cell per thread.  Not for FP64 storage.       */
 } lbm_launch;
 
 /* Set / read the launch shape.  EINVAL if out of range. */

@@ -7,11 +7,26 @@ namespace lbm {
 namespace batchk {
 namespace {
 
+// A domain without a body force runs the force-free update, as in the
+// single-domain and grouped kernels (so every mode computes bit-identical
+// results).
+// Each variant is a separate (not inlined) function: inlining all 24 of
+// them into one kernel makes its compilation take minutes.
+template <int Q, typename S, bool ODD, bool FORCE>
+__device__ __noinline__ void persist_tile(const Domain<float>& d, int tx, int ty, int tz) {
+  batch_tile<Q, S, ODD, false, true, FORCE>(d, tx, ty, tz);
+}
+
 template <int Q, typename S>
 __device__ __forceinline__ void batch_tile_persist(const Domain<float>& d, int tx, int ty, int tz,
-                                                   bool odd) {
-  if (odd) batch_tile<Q, S, true, false, true>(d, tx, ty, tz);
-  else batch_tile<Q, S, false, false, true>(d, tx, ty, tz);
+                                                   bool odd, bool force) {
+  if (force) {
+    if (odd) persist_tile<Q, S, true, true>(d, tx, ty, tz);
+    else persist_tile<Q, S, false, true>(d, tx, ty, tz);
+  } else {
+    if (odd) persist_tile<Q, S, true, false>(d, tx, ty, tz);
+    else persist_tile<Q, S, false, false>(d, tx, ty, tz);
+  }
 }
 
 
@@ -23,7 +38,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
                                                   int64_t total_tiles, int nsteps, int per,
                                                   GridBarrier* bar, long long spin_limit) {
   __shared__ Domain<float> sd;
-  __shared__ int s_meta[6];  // Q, storage, odd, sr, tiles_x, tiles_y
+  __shared__ int s_meta[7];  // Q, storage, odd, sr, tiles_x, tiles_y, force
   __shared__ int64_t s_begin, s_end;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
@@ -56,6 +71,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
           s_meta[3] = e.rounding == LBM_ROUND_STOCHASTIC;
           s_meta[4] = e.tiles_x;
           s_meta[5] = e.tiles_y;
+          s_meta[6] = e.force[0] != 0.0 || e.force[1] != 0.0 || e.force[2] != 0.0;
           s_begin = e.tile_begin;
           s_end = e.tile_begin + (int64_t)e.tiles_x * e.tiles_y * e.d.nz;
         }
@@ -63,15 +79,15 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchEntry* __restrict__
         end = s_end;
         cur.start((int)(t - s_begin), s_meta[4], s_meta[5]);
       }
-      const bool odd = s_meta[2] != 0;
+      const bool odd = s_meta[2] != 0, force = s_meta[6] != 0;
       if (s_meta[0] == 14) {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_persist<14, float>(sd, cur.tx, cur.ty, cur.tz, odd);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_persist<14, __half>(sd, cur.tx, cur.ty, cur.tz, odd);
-        else batch_tile_persist<14, __nv_bfloat16>(sd, cur.tx, cur.ty, cur.tz, odd);
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_persist<14, float>(sd, cur.tx, cur.ty, cur.tz, odd, force);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_persist<14, __half>(sd, cur.tx, cur.ty, cur.tz, odd, force);
+        else batch_tile_persist<14, __nv_bfloat16>(sd, cur.tx, cur.ty, cur.tz, odd, force);
       } else {
-        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_persist<18, float>(sd, cur.tx, cur.ty, cur.tz, odd);
-        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_persist<18, __half>(sd, cur.tx, cur.ty, cur.tz, odd);
-        else batch_tile_persist<18, __nv_bfloat16>(sd, cur.tx, cur.ty, cur.tz, odd);
+        if (s_meta[1] == LBM_STORAGE_F32) batch_tile_persist<18, float>(sd, cur.tx, cur.ty, cur.tz, odd, force);
+        else if (s_meta[1] == LBM_STORAGE_F16) batch_tile_persist<18, __half>(sd, cur.tx, cur.ty, cur.tz, odd, force);
+        else batch_tile_persist<18, __nv_bfloat16>(sd, cur.tx, cur.ty, cur.tz, odd, force);
       }
       cur.next();
     }

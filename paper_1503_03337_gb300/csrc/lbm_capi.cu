@@ -474,7 +474,8 @@ std::map<std::tuple<int, int, int, int, int>, std::pair<BlockShape, double>> g_t
 
 const BlockShape kCandidates[] = {{32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1},
                                   {64, 1, 1},  {64, 2, 1}, {64, 4, 1}, {128, 1, 1},
-                                  {128, 2, 1}, {256, 1, 1}, {32, 2, 2}, {64, 1, 2}};
+                                  {128, 2, 1}, {256, 1, 1}, {32, 2, 2}, {64, 1, 2},
+                                  {64, 2, 2},  {128, 1, 2}};
 }  // namespace
 
 int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) {

@@ -331,94 +331,57 @@ __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __re
   update_cell_at<Q, S, R, ODD, FORCE, SR, CG>(d, f, d.F, &d.key, x, y, z, x_lo, x_hi);
 }
 
-// Links of cell x of a warp spanning x_lo..x_hi on an odd step: the offset
-// tables for warps whose cells and neighbours are all interior, the x-only
-// selects in the bulk of y and z, else the full per-axis selects (the same
-// choice as update_cell, warp-uniform).
-template <typename R>
-__host__ __device__ __forceinline__ Links links_in_warp(const Domain<R>& d, int x, int y, int z,
-                                                        int x_lo, int x_hi) {
-  if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
-    if (x_lo > 0 && x_hi < d.nx - 1) return make_links_interior(d);
-    return make_links_x(d, x);
+// Two storage values of x-adjacent cells as one word (8 bytes for FP32,
+// 4 bytes for FP16 / BF16), unpacked to and packed from a pf2.
+template <typename S>
+struct Pair2;
+template <>
+struct Pair2<float> {
+  using type = float2;
+  __device__ static pf2 unpack(float2 v) { return pf2(v.x, v.y); }
+  __device__ static float2 pack(pf2 v) { return v.v; }
+};
+template <>
+struct Pair2<__half> {
+  using type = __half2;
+  __device__ static pf2 unpack(__half2 v) {
+    const float2 t = __half22float2(v);
+    return pf2(t.x, t.y);
   }
-  return make_links(d, x, y, z);
-}
-
-// Storage values of cell i's pre-collision populations: the gather's
-// addressing without the conversion and the wall terms.
-template <int Q, typename S, typename R, bool ODD>
-__host__ __device__ __forceinline__ void gather_raw(const Domain<R>& d, const S* __restrict__ f,
-                                                    int i, const Links& L, S* raw) {
-  const int N = (int)d.N;
-  const S* __restrict__ fc = f + i;
-  if constexpr (!ODD) {
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((raw[A] = fc[(size_t)A * d.N]), ...);
-    }(std::make_integer_sequence<int, Q>{});
-  } else if (L.interior) {
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((raw[A] = fc[d.pull[A]]), ...);
-    }(std::make_integer_sequence<int, Q>{});
-  } else {
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      (
-          [&] {
-            int off;
-            bool ghost;
-            link_of<Q, A, -1>(L, off, ghost);
-            raw[A] = f[ghost ? (A * N + i) : (opposite<Q>(A) * N + i + off)];
-          }(),
-          ...);
-    }(std::make_integer_sequence<int, Q>{});
+  __device__ static __half2 pack(pf2 v) { return __floats2half2_rn(v.v.x, v.v.y); }
+};
+template <>
+struct Pair2<__nv_bfloat16> {
+  using type = __nv_bfloat162;
+  __device__ static pf2 unpack(__nv_bfloat162 v) {
+    const float2 t = __bfloat1622float2(v);
+    return pf2(t.x, t.y);
   }
-}
+  __device__ static __nv_bfloat162 pack(pf2 v) { return __floats2bfloat162_rn(v.v.x, v.v.y); }
+};
 
-// The rest of the update of cell i from its gathered storage values: the
-// conversion and wall terms of gather, then collide and scatter.  Together
-// with gather_raw these are update_cell's operations in update_cell's order.
-template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
-__host__ __device__ __forceinline__ void finish_cell(const Domain<R>& d, S* __restrict__ f, int i,
-                                                     const Links& L, const S* raw) {
-  R fv[Q];
+// Even step of the two x-adjacent cells i, i + 1 (i even): each population
+// of the pair is one load and one store of a two-value word, so a warp's
+// access covers twice the bytes of one cell per thread (128 bytes for FP16
+// / BF16 storage, which one value per thread leaves at 64), and the two
+// cells collide together in packed FP32x2.  Needs nx even (then N is even
+// and a pair never straddles a row).  An even step touches only the cell's
+// own slots, so no links are needed.
+template <int Q, typename S, bool FORCE>
+__device__ __forceinline__ void update_pair_even(const Domain<float>& d, S* __restrict__ f,
+                                                 int i) {
+  using W = typename Pair2<S>::type;
+  W* __restrict__ g = reinterpret_cast<W*>(f);
+  const int M = (int)(d.N >> 1), j = i >> 1;
+  pf2 fv[Q];
   [&]<int... A>(std::integer_sequence<int, A...>) {
-    ((fv[A] = Codec<S, R>::value(raw[A])), ...);
+    ((fv[A] = Pair2<S>::unpack(g[j + A * M])), ...);
   }(std::make_integer_sequence<int, Q>{});
-  if constexpr (ODD)
-    if (!L.interior) add_pull_wall_terms<Q>(d, L, fv);
-  R ux, uy, uz;
+  pf2 ux, uy, uz;
   collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
-  scatter<Q, S, R, ODD, SR>(d, f, i, L, fv, d.key);
-}
-
-// Two cells per thread: the cells xa and xa + 32 of one x-row, so that a
-// warp on xa = x_lo..x_lo+31 covers the 64 cells x_lo..x_lo+63 and every
-// load and store still touches 32 consecutive values.  The thread issues the
-// loads of both cells before updating either, which doubles the loads a
-// warp keeps in flight (what bounds the step with 2-byte storage, where one
-// cell's loads are only 36 bytes).  Each cell's operations are update_cell's
-// in the same order (the compiler may still fuse multiply-adds differently
-// in this kernel, so results agree with one cell per thread to FP32
-// rounding).  In-place
-// safety: on either parity the locations a cell reads are the ones it
-// writes, so the loads of xa + 32 never see a store of xa.
-template <int Q, typename S, bool ODD, bool FORCE, bool SR>
-__device__ __forceinline__ void update_two(const Domain<float>& d, S* __restrict__ f, int xa, int y,
-                                           int z, int x_lo) {
-  const int xb = xa + 32;
-  const bool vb = xb < d.nx;
-  const int ia = xa + d.nx * (y + d.ny * z);
-  const int ib = ia + 32;
-  Links La{}, Lb{};
-  if constexpr (ODD) {
-    La = links_in_warp(d, xa, y, z, x_lo, x_lo + 31);
-    Lb = links_in_warp(d, xb, y, z, x_lo + 32, x_lo + 63);
-  }
-  S ra[Q], rb[Q];
-  gather_raw<Q, S, float, ODD>(d, f, ia, La, ra);
-  if (vb) gather_raw<Q, S, float, ODD>(d, f, ib, Lb, rb);
-  finish_cell<Q, S, float, ODD, FORCE, SR>(d, f, ia, La, ra);
-  if (vb) finish_cell<Q, S, float, ODD, FORCE, SR>(d, f, ib, Lb, rb);
+  [&]<int... A>(std::integer_sequence<int, A...>) {
+    ((g[j + opposite<Q>(A) * M] = Pair2<S>::pack(fv[A])), ...);
+  }(std::make_integer_sequence<int, Q>{});
 }
 
 // Inverse of gather: put canonical pre-collision values fv of cell (x,y,z)

@@ -349,6 +349,66 @@ struct Stochastic<__nv_bfloat16> {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Two adjacent cells at once (2-byte storage): a packed pair of FP32
+// values.  On the device every add, multiply and multiply-add is one packed
+// FP32x2 instruction (__fadd2_rn / __fmul2_rn / __ffma2_rn of sm_100 and
+// later), so the collision of two cells issues the instructions of one.
+// Arithmetic stays IEEE FP32, rounded to nearest, per component.
+// ---------------------------------------------------------------------------
+// (The scalar branches serve host builds of this header; device code is
+// only ever built for sm_103a.)
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define LBM_PACKED_F32X2 1
+#else
+#define LBM_PACKED_F32X2 0
+#endif
+
+struct pf2 {
+  float2 v;
+  pf2() = default;
+  __host__ __device__ pf2(float s) : v(make_float2(s, s)) {}  // broadcast
+  __host__ __device__ pf2(float a, float b) : v(make_float2(a, b)) {}
+};
+
+__host__ __device__ __forceinline__ pf2 pf2_from(float2 v) {
+  pf2 r;
+  r.v = v;
+  return r;
+}
+__host__ __device__ __forceinline__ pf2 operator+(pf2 a, pf2 b) {
+#if LBM_PACKED_F32X2
+  return pf2_from(__fadd2_rn(a.v, b.v));
+#else
+  return pf2(a.v.x + b.v.x, a.v.y + b.v.y);
+#endif
+}
+__host__ __device__ __forceinline__ pf2 operator*(pf2 a, pf2 b) {
+#if LBM_PACKED_F32X2
+  return pf2_from(__fmul2_rn(a.v, b.v));
+#else
+  return pf2(a.v.x * b.v.x, a.v.y * b.v.y);
+#endif
+}
+// a * b + c
+__host__ __device__ __forceinline__ pf2 fmadd(pf2 a, pf2 b, pf2 c) {
+#if LBM_PACKED_F32X2
+  return pf2_from(__ffma2_rn(a.v, b.v, c.v));
+#else
+  return pf2(std::fma(a.v.x, b.v.x, c.v.x), std::fma(a.v.y, b.v.y, c.v.y));
+#endif
+}
+__host__ __device__ __forceinline__ pf2 operator-(pf2 a, pf2 b) {
+  return fmadd(b, pf2(-1.0f), a);
+}
+__host__ __device__ __forceinline__ pf2 operator-(pf2 a) { return a * pf2(-1.0f); }
+__host__ __device__ __forceinline__ pf2 operator*(float s, pf2 a) { return pf2(s) * a; }
+__host__ __device__ __forceinline__ pf2 operator*(pf2 a, float s) { return a * pf2(s); }
+__host__ __device__ __forceinline__ pf2 operator+(pf2 a, float s) { return a + pf2(s); }
+__host__ __device__ __forceinline__ pf2 operator-(pf2 a, float s) { return a - pf2(s); }
+__host__ __device__ __forceinline__ pf2& operator+=(pf2& a, pf2 b) { return a = a + b; }
+__host__ __device__ __forceinline__ pf2& operator-=(pf2& a, pf2 b) { return a = a - b; }
+
 __host__ __device__ __forceinline__ float fmadd(float a, float b, float c) { return a * b + c; }
 __host__ __device__ __forceinline__ double fmadd(double a, double b, double c) {
   return a * b + c;

@@ -29,19 +29,19 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> 
   update_cell<Q, S, R, ODD, FORCE, SR>(d, static_cast<S*>(d.f), x, y, z, x_lo, x_hi);
 }
 
-// Two cells per thread (see update_two); blockDim.x threads cover
-// 2*blockDim.x cells of a row, each warp 64 consecutive cells.
-template <int Q, typename S, bool ODD, bool FORCE, bool SR>
-__global__ void __launch_bounds__(256, 3) k_step2(Domain<float> d) {
+// Even steps with two x-adjacent cells per thread (see update_pair_even; nx
+// even); blockDim.x threads cover 2*blockDim.x cells of a row.  The 36
+// packed values of a pair need more registers than one cell's 18, hence
+// the looser cap.
+template <int Q, typename S, bool FORCE>
+__global__ void __launch_bounds__(256, 3) k_step_pair(Domain<float> d) {
   pdl_release();
   pdl_acquire();
-  const int lane = threadIdx.x & 31;
-  const int x_lo = blockIdx.x * (2 * blockDim.x) + (threadIdx.x >> 5) * 64;
-  const int xa = x_lo + lane;
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (xa >= d.nx || y >= d.ny) return;
-  update_two<Q, S, ODD, FORCE, SR>(d, static_cast<S*>(d.f), xa, y, z, x_lo);
+  if (x0 >= d.nx || y >= d.ny) return;
+  update_pair_even<Q, S, FORCE>(d, static_cast<S*>(d.f), x0 + d.nx * (y + d.ny * z));
 }
 
 template <typename R>
@@ -53,16 +53,13 @@ void launch_one(void (*kernel)(Domain<R>), const Domain<R>& d, dim3 grid, dim3 b
 template <int Q, typename S, typename R, bool SR>
 void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 block,
                           const BlockShape& b, cudaStream_t st) {
-  if constexpr (sizeof(S) <= 4) {
-    if (b.cpt == 2) {
-      grid.x = (d.nx + 2 * block.x - 1) / (2 * block.x);
-      if (odd) {
-        if (force) launch_one(k_step2<Q, S, true, true, SR>, d, grid, block, b.pdl != 0, st);
-        else launch_one(k_step2<Q, S, true, false, SR>, d, grid, block, b.pdl != 0, st);
-      } else {
-        if (force) launch_one(k_step2<Q, S, false, true, SR>, d, grid, block, b.pdl != 0, st);
-        else launch_one(k_step2<Q, S, false, false, SR>, d, grid, block, b.pdl != 0, st);
-      }
+  // two cells per thread: even steps of FP32 / FP16 / BF16 storage with nx
+  // even and rounding to nearest; every other step runs one cell per thread
+  if constexpr (sizeof(S) <= 4 && !SR) {
+    if (b.cpt == 2 && !odd && d.nx % 2 == 0) {
+      grid.x = (d.nx / 2 + block.x - 1) / block.x;
+      if (force) launch_one(k_step_pair<Q, S, true>, d, grid, block, b.pdl != 0, st);
+      else launch_one(k_step_pair<Q, S, false>, d, grid, block, b.pdl != 0, st);
       return;
     }
   }
@@ -80,7 +77,9 @@ cudaError_t launch_typed(const DomainDesc& dd, int64_t n, BlockShape b,
                                 cudaStream_t st) {
   double F[3];
   force_at(dd, n, F);
-  const bool force = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0 || dd.period > 0.0;
+  // the force-carrying update whenever the amplitude is nonzero (also at the
+  // steps where a periodic force passes through zero), as the batch does
+  const bool force = dd.force[0] != 0.0 || dd.force[1] != 0.0 || dd.force[2] != 0.0;
   Domain<R> d = to_domain<R>(dd, F);
   d.key = step_key(n);
   dim3 block(b.bx, b.by, 1);
