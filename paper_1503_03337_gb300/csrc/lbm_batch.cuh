@@ -80,20 +80,6 @@ __device__ __forceinline__ void batch_tile(const Domain<float>& d, int tx, int t
                                                x_lo + 31);
 }
 
-template <int Q, typename S, bool CG>
-__device__ __forceinline__ void batch_tile_dispatch(const Domain<float>& d, int tx, int ty,
-                                                    int tz, bool odd, bool sr) {
-  if constexpr (Stochastic<S>::enabled) {
-    if (sr) {
-      if (odd) batch_tile<Q, S, true, true, CG>(d, tx, ty, tz);
-      else batch_tile<Q, S, false, true, CG>(d, tx, ty, tz);
-      return;
-    }
-  }
-  if (odd) batch_tile<Q, S, true, false, CG>(d, tx, ty, tz);
-  else batch_tile<Q, S, false, false, CG>(d, tx, ty, tz);
-}
-
 // Walks the tiles of one domain in order (x fastest) without divisions.
 struct TileCursor {
   int tx, ty, tz, nx, ny;
