@@ -172,3 +172,29 @@ def test_reduced_precision_cavity(Q, storage, max_bound, rms_bound):
     d = g["u"] - o["u"]
     assert np.max(np.abs(d)) <= max_bound * U, np.max(np.abs(d)) / U
     assert np.sqrt(np.mean(d ** 2)) <= rms_bound * U, np.sqrt(np.mean(d ** 2)) / U
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_fp64_lbgk_special_case(Q):
+    """S = (1/tau) I (every rate equal): the GPU path runs the LBGK special
+    case of the model (pinned against the LBGK step in the oracle tests) and
+    matches the oracle with the same rates, FP64, moving lid, 300 steps."""
+    import oracle
+    case = inputs.cavity(Q, 20, 100.0, storage="f64")
+    s = 1.0 / (3.0 * case.nu + 0.5)
+    g_or = oracle.make_grid(Q, case.nx, case.ny, case.nz, case.faces, case.u_wall)
+    prm = oracle.make_params(oracle.rates(Q, s, sc=s, se=s, sq=s, st=s, spi=s))
+    f = oracle.run(g_or, prm, oracle.init_equilibrium(g_or), 0, 300)
+    u_o, _ = oracle.macroscopic(g_or, prm, 300, f)
+    h = lbm.lbm_create(Q, case.nx, case.ny, case.nz, "f64", None)
+    try:
+        lbm.lbm_set_geometry(h, case.faces, case.u_wall)
+        lbm.lbm_set_params(h, nu=case.nu, s_c=s, s_e=s, s_q=s, s_pi=s, s_t=s)
+        lbm.lbm_init_equilibrium(h)
+        lbm.lbm_step(h, 300)
+        u = lbm.read_u(h, case.nx, case.ny, case.nz)
+        fg = lbm.read_populations(h, Q, case.nx, case.ny, case.nz)
+    finally:
+        lbm.lbm_destroy(h)
+    assert rel_max(u, u_o) <= 1e-12
+    assert rel_max(fg, f.reshape(fg.shape)) <= 1e-12
