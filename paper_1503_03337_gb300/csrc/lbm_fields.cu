@@ -130,6 +130,7 @@ struct ReduceArgs {
   double* partials;
   double F[3];
   double p_ref;
+  double uw[6][3];  // wall velocities in FP64 (the pair path's wall terms)
 };
 
 __device__ __forceinline__ void block_reduce(double (&v)[kNumStats], double* shm) {
@@ -187,6 +188,163 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(Domain<double> d, Red
     }
     v[9] += P + 3.0 * (1.0 - Lattice<Q>::w0) * a.p_ref;
   }
+  block_reduce(v, shm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kNumStats; ++k) a.partials[blockIdx.x * kNumStats + k] = v[k];
+}
+
+// A value kept as the unevaluated pair hi + lo of FP32 numbers.  Each
+// addition of an FP32 number is Knuth's TwoSum: the rounding error of
+// hi + x, which it computes exactly, goes into lo.  The pair carries about
+// 48 significant bits at the cost of FP32 instructions.  The reductions for
+// FP32 / FP16 / BF16 storage run entirely on such pairs (a cell's P and j,
+// u, the differences to the snapshot and the per-thread sums), because the
+// FP64 rate of this device is a small fraction of its FP32 rate; only the
+// per-thread totals are combined in FP64.  Every operation is a plain IEEE
+// add or subtract in a fixed order, so results are deterministic.
+struct PairSum {
+  float hi = 0.0f, lo = 0.0f;
+};
+__device__ __forceinline__ void add_exact(PairSum& s, float x) {
+  const float t = s.hi + x;
+  const float xv = t - s.hi;
+  const float e = (s.hi - (t - xv)) + (x - xv);
+  s.hi = t;
+  s.lo += e;
+}
+// s += p (p's low word only needs s.lo's precision)
+__device__ __forceinline__ void add_pair(PairSum& s, PairSum p) {
+  add_exact(s, p.hi);
+  s.lo += p.lo;
+}
+// hi + lo with |lo| at most half an ulp of hi (Fast2Sum; |hi| >= |lo|)
+__device__ __forceinline__ PairSum normalized(PairSum p) {
+  const float t = p.hi + p.lo;
+  return PairSum{t, p.lo - (t - p.hi)};
+}
+__device__ __forceinline__ PairSum negated(PairSum p) { return PairSum{-p.hi, -p.lo}; }
+__device__ __forceinline__ PairSum abs_of(PairSum p) {  // p normalized
+  return (p.hi < 0.0f || (p.hi == 0.0f && p.lo < 0.0f)) ? negated(p) : p;
+}
+__host__ __device__ inline PairSum pair_of(double x) {
+  const float h = (float)x;
+  return PairSum{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double value_of(PairSum s) { return (double)s.hi + (double)s.lo; }
+// a > b for normalized pairs
+__device__ __forceinline__ bool greater(PairSum a, PairSum b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+
+// P and j of cell (x, y, z) into pairs: the stored values (exact in FP32)
+// and, on odd steps, the moving-wall terms 6 w_a (c_a . u_w) of the links
+// whose source is a ghost beyond a moving face, evaluated in FP64 from the
+// FP64 wall velocities and added as pairs (the same canonical values that
+// the FP64 path of get_canonical forms).
+template <int Q, typename S, bool ODD>
+__device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __restrict__ f,
+                                             int x, int y, int z, const double (&uw)[6][3],
+                                             PairSum& sP, PairSum (&sj)[3]) {
+  const int i = x + d.nx * (y + d.ny * z);
+  const int N = (int)d.N;
+  Links L{};
+  if constexpr (ODD) L = make_links(d, x, y, z);
+  [&]<int... A>(std::integer_sequence<int, A...>) {
+    (
+        [&] {
+          constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
+                        cz = Lattice<Q>::c(A, 2);
+          int idx = A * N + i;
+          if constexpr (ODD) {
+            int off;
+            bool ghost;
+            link_of<Q, A, -1>(L, off, ghost);
+            if (!ghost) idx = opposite<Q>(A) * N + i + off;
+          }
+          const float v = Codec<S, float>::load(f + idx);
+          add_exact(sP, v);
+          if constexpr (cx != 0) add_exact(sj[0], cx > 0 ? v : -v);
+          if constexpr (cy != 0) add_exact(sj[1], cy > 0 ? v : -v);
+          if constexpr (cz != 0) add_exact(sj[2], cz > 0 ? v : -v);
+          if constexpr (ODD) {
+            const int hit = link_faces<Q, A, -1>(L) & d.moving;
+            if (hit) {
+              int face = 0;
+              while (!((hit >> face) & 1)) ++face;  // the first moving face
+              const double t = 6.0 * Lattice<Q>::w(A) *
+                               (cx * uw[face][0] + cy * uw[face][1] + cz * uw[face][2]);
+              const PairSum tp = pair_of(t);
+              add_pair(sP, tp);
+              if constexpr (cx != 0) add_pair(sj[0], cx > 0 ? tp : negated(tp));
+              if constexpr (cy != 0) add_pair(sj[1], cy > 0 ? tp : negated(tp));
+              if constexpr (cz != 0) add_pair(sj[2], cz > 0 ? tp : negated(tp));
+            }
+          }
+        }(),
+        ...);
+  }(std::make_integer_sequence<int, Q>{});
+}
+
+// k_reduce for FP32 / FP16 / BF16 storage on PairSum arithmetic (see
+// above); the statistics are those of k_reduce.  The snapshot holds each u
+// component as its (hi, lo) pair in the 8 bytes of its FP64 slot.  Cells
+// are numbered with 32-bit arithmetic (Q*N < 2^31).
+template <int Q, typename S, bool ODD>
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d, ReduceArgs a,
+                                                                 PairSum Fh0, PairSum Fh1,
+                                                                 PairSum Fh2, PairSum Pref) {
+  __shared__ double shm[(kReduceThreads / 32) * kNumStats];
+  PairSum sdu[3], su_abs[3], sup_abs[3], su[3], sPt, umax;
+  int nonfinite = 0;
+  const PairSum Fh[3] = {Fh0, Fh1, Fh2};
+  const int N = (int)d.N;
+  float2* snap = reinterpret_cast<float2*>(a.u_prev);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int x = i % d.nx;
+    const int r = i / d.nx;
+    const int y = r % d.ny, z = r / d.ny;
+    PairSum sP, sj[3];
+    cell_moments<Q, S, ODD>(d, static_cast<const S*>(d.f), x, y, z, a.uw, sP, sj);
+    PairSum u[3];
+    bool finite = isfinite(sP.hi) && isfinite(sP.lo);
+    for (int k = 0; k < 3; ++k) {
+      add_pair(sj[k], Fh[k]);  // u = j + F/2
+      u[k] = normalized(sj[k]);
+      finite = finite && isfinite(u[k].hi) && isfinite(u[k].lo);
+    }
+    if (!finite) {
+      ++nonfinite;
+      continue;
+    }
+    for (int k = 0; k < 3; ++k) {
+      PairSum up;
+      if (a.have_prev) {
+        const float2 t = snap[(int64_t)k * N + i];
+        up = PairSum{t.x, t.y};
+        PairSum du = u[k];
+        add_pair(du, negated(up));
+        add_pair(sdu[k], abs_of(normalized(du)));
+      }
+      const PairSum ua = abs_of(u[k]);
+      add_pair(su_abs[k], ua);
+      add_pair(sup_abs[k], abs_of(up));
+      add_pair(su[k], u[k]);
+      if (greater(ua, umax)) umax = ua;
+      if (a.u_prev) snap[(int64_t)k * N + i] = make_float2(u[k].hi, u[k].lo);
+    }
+    add_pair(sPt, normalized(sP));
+    add_pair(sPt, Pref);
+  }
+  double v[kNumStats];
+  for (int k = 0; k < 3; ++k) {
+    v[k] = value_of(sdu[k]);
+    v[3 + k] = value_of(su_abs[k]);
+    v[6 + k] = value_of(sup_abs[k]);
+    v[10 + k] = value_of(su[k]);
+  }
+  v[9] = value_of(sPt);
+  v[kNumSums - 1] = (double)nonfinite;
+  v[kNumSums] = value_of(umax);
   block_reduce(v, shm);
   if (threadIdx.x == 0)
     for (int k = 0; k < kNumStats; ++k) a.partials[blockIdx.x * kNumStats + k] = v[k];
@@ -300,13 +458,24 @@ cudaError_t launch_reduce(const DomainDesc& dd, int64_t n, double* u_prev, int h
   a.partials = partials;
   a.p_ref = dd.p_ref;
   for (int k = 0; k < 3; ++k) a.F[k] = F[k];
+  for (int face = 0; face < 6; ++face)
+    for (int k = 0; k < 3; ++k) a.uw[face][k] = dd.uw[face][k];
   int64_t g = (dd.N + kReduceThreads - 1) / kReduceThreads;
   if (g > kReduceBlocks) g = kReduceBlocks;
   if (g < 1) g = 1;
   const bool odd = n & 1;
+  const Domain<float> df = to_domain<float>(dd, F);
   cudaError_t e = dispatch(dd, [&]<int Q, typename S>() {
-    if (odd) k_reduce<Q, S, true><<<(int)g, kReduceThreads, 0, st>>>(d, a);
-    else k_reduce<Q, S, false><<<(int)g, kReduceThreads, 0, st>>>(d, a);
+    if constexpr (sizeof(S) <= 4) {
+      const PairSum f0 = pair_of(0.5 * F[0]), f1 = pair_of(0.5 * F[1]),
+                    f2 = pair_of(0.5 * F[2]);
+      const PairSum pr = pair_of(3.0 * (1.0 - Lattice<Q>::w0) * dd.p_ref);
+      if (odd) k_reduce_pair<Q, S, true><<<(int)g, kReduceThreads, 0, st>>>(df, a, f0, f1, f2, pr);
+      else k_reduce_pair<Q, S, false><<<(int)g, kReduceThreads, 0, st>>>(df, a, f0, f1, f2, pr);
+    } else {
+      if (odd) k_reduce<Q, S, true><<<(int)g, kReduceThreads, 0, st>>>(d, a);
+      else k_reduce<Q, S, false><<<(int)g, kReduceThreads, 0, st>>>(d, a);
+    }
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;

@@ -211,3 +211,40 @@ def test_overlap_does_not_change_results(storage):
     if storage == "f64":
         o = oracle_run(case, 101)
         assert rel_max(out[0], o["f"]) <= 1e-12
+
+
+@pytest.mark.parametrize("storage", ("f32", "f16", "bf16"))
+@pytest.mark.parametrize("Q", (14, 18))
+def test_pair_reductions_match_fields(Q, storage):
+    """The 32- and 16-bit storage reductions (FP32 pair arithmetic) against
+    FP64 sums of the read-back fields, on an odd and an even step, with a
+    body force and a moving lid: every statistic to 1e-11 relative (the
+    pair sums carry about 48 bits), the maximum to 1e-13."""
+    case = inputs.cavity(Q, 23, 150.0, storage=storage, ny=17, nz=11)
+    case.force = (1e-5, -2e-5, 3e-5)
+    h = gpu_open(case)
+    nx, ny, nz = case.nx, case.ny, case.nz
+    try:
+        lbm.lbm_init_equilibrium(h)
+        lbm.lbm_step(h, 41)
+        s0 = lbm.lbm_reductions(h)
+        ua = lbm.read_u(h, nx, ny, nz)
+        Pa = lbm.read_populations(h, Q, nx, ny, nz).sum()
+        lbm.lbm_step(h, 9)
+        s1 = lbm.lbm_reductions(h)
+        ub = lbm.read_u(h, nx, ny, nz)
+        Pb = lbm.read_populations(h, Q, nx, ny, nz).sum()
+    finally:
+        lbm.lbm_destroy(h)
+    tol = 1e-11
+    for s, u, P in ((s0, ua, Pa), (s1, ub, Pb)):
+        for k in range(3):
+            assert abs(s.sum_abs_u[k] - np.abs(u[k]).sum()) <= tol * np.abs(u[k]).sum()
+            assert abs(s.sum_u[k] - u[k].sum()) <= tol * np.abs(u[k]).sum()
+        assert abs(s.sum_P - P) <= 1e-12 * max(1.0, abs(P))
+        assert abs(s.max_abs_u - np.abs(u).max()) <= 1e-13 * np.abs(u).max()
+        assert s.nonfinite == 0
+    for k in range(3):
+        du = np.abs(ub[k] - ua[k]).sum()
+        assert abs(s1.sum_abs_du[k] - du) <= tol * np.abs(ub[k]).sum()
+        assert abs(s1.sum_abs_u_prev[k] - np.abs(ua[k]).sum()) <= tol * np.abs(ua[k]).sum()
