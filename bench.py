@@ -50,6 +50,8 @@ def parse():
                     help="cube side of the storage-precision comparison (0: skip); its "
                          "buffers are several times larger than L2, so steps run back to back")
     ap.add_argument("--precision-steps", type=int, default=200)
+    ap.add_argument("--reduction-n", type=int, default=256,
+                    help="cube side of the FP64-reduction timing (D3Q18 FP32 cavity; 0: skip)")
     ap.add_argument("--flushed-steps", type=int, default=400,
                     help="steps timed one by one after an L2 flush (secondary figure)")
     ap.add_argument("--e2e-chunk", type=int, default=100)
@@ -372,6 +374,35 @@ def run_gpu(a, rank, world, dist):
 
     # the step kernels plus, per residual check, the reduction kernel and its
     # final pass
+    # --- FP64 reductions (residuals, mass, flux, max) at a size far above L2 -----------
+    reductions = {}
+    if a.reduction_n > 0 and rank == 0:
+        cr = inputs.cavity(18, a.reduction_n, a.Re, U=0.05, storage="f32")
+        hr = lbm.lbm_create(18, cr.nx, cr.ny, cr.nz, "f32", sp)
+        lbm.lbm_set_geometry(hr, cr.faces, cr.u_wall)
+        lbm.lbm_set_params(hr, nu=cr.nu, residual_interval=0)
+        lbm.lbm_init_equilibrium(hr)
+        lbm.lbm_step(hr, 4)
+        for _ in range(3):  # snapshot allocated and filled
+            lbm.lbm_reductions(hr)
+        kr = 20
+        e0.record(stream)
+        for _ in range(kr):
+            lbm.lbm_reductions(hr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tr = e0.elapsed_time(e1) / kr
+        lbm.lbm_destroy(hr)
+        rbytes = cr.cells * (18 * 4 + 2 * 3 * 8)
+        reductions = {"workload": "lid-driven cavity %d^3 D3Q18 F32" % a.reduction_n,
+                      "ms_per_call": round(tr, 4),
+                      "algorithmic_bytes": rbytes,
+                      "hbm_gbs": round(rbytes / (tr * 1e-3) / 1e9, 1),
+                      "frac_of_measured_hbm": round(rbytes / (tr * 1e-3) / 1e9 / peak, 4),
+                      "note": "lbm_reductions (reduction kernel, final pass, host synchronisation) "
+                              "timed with CUDA events over %d calls; bytes: 18 FP32 populations "
+                              "read, FP64 u snapshot read and written, per cell" % kr}
+
     launches = a.steps + 2 * n_red
     res = {
         "metric": "D3Q18 MRT fused-step GLUPS (lattice updates/s) and HBM-roofline fraction",
@@ -406,6 +437,7 @@ def run_gpu(a, rank, world, dist):
         "residual_last": {"step": stats.step, "cavity": (lbm.residual_cavity(stats)
                                                          if stats.prev_step >= 0 else None)},
         "precision": precision,
+        "reductions": reductions,
         "flushed_per_step": flushed,
     }
     return res
