@@ -23,7 +23,7 @@ _LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PERIODIC, WALL, MOVING_WALL = 0, 1, 2
+PERIODIC, WALL, MOVING_WALL, SYMMETRY = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:

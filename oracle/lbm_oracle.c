@@ -268,30 +268,36 @@ static int n_axis(const oracle_grid *g, int d) {
 }
 
 /* Where does the pull source x - c_a of node (x,y,z) lie?  Returns 1 and the
- * wrapped source node if it is a fluid node; returns 0 if it is a ghost node
- * beyond a wall, and sets uw to that ghost node's wall velocity: the velocity
- * of the first moving face (x-, x+, y-, y+, z-, z+ order) the ghost lies
- * beyond, else zero (reading G6, edge and corner ghosts of a lid layer count
- * as lid). */
+ * source node if it is a fluid node (after periodic wraps and symmetry-plane
+ * mirrors); returns 0 if it is a ghost node beyond a wall, and sets uw to
+ * that ghost node's wall velocity: the velocity of the first moving face
+ * (x-, x+, y-, y+, z-, z+ order) the ghost lies beyond, else zero (reading
+ * G6, edge and corner ghosts of a lid layer count as lid).
+ *
+ * A symmetry face is a free-slip plane halfway between the last node and its
+ * ghost layer: the ghost mirrors the node across the plane, so a source
+ * beyond it is replaced by the mirrored node (the same coordinate as x along
+ * that axis) and *mirror gets the axis bit (the population arriving at x
+ * left that node with the normal component of its velocity reversed).  A
+ * source beyond a wall on any axis is a wall link even if it also lies
+ * beyond a symmetry face (reading G14). */
 static int pull_source(const oracle_grid *g, const int xyz[3], const int c[3],
-                       int src[3], double uw[3]) {
+                       int src[3], double uw[3], int *mirror) {
   int beyond[6] = {0, 0, 0, 0, 0, 0};
   int solid = 0;
+  *mirror = 0;
   for (int d = 0; d < 3; ++d) {
     const int n = n_axis(g, d);
     int v = xyz[d] - c[d];
-    if (v < 0) {
-      if (g->face[2 * d] == ORACLE_PERIODIC) {
-        v += n;
+    if (v < 0 || v >= n) {
+      const int face = v < 0 ? 2 * d : 2 * d + 1;
+      if (g->face[face] == ORACLE_PERIODIC) {
+        v += v < 0 ? n : -n;
+      } else if (g->face[face] == ORACLE_SYMMETRY) {
+        v = xyz[d];
+        *mirror |= 1 << d;
       } else {
-        beyond[2 * d] = 1;
-        solid = 1;
-      }
-    } else if (v >= n) {
-      if (g->face[2 * d + 1] == ORACLE_PERIODIC) {
-        v -= n;
-      } else {
-        beyond[2 * d + 1] = 1;
+        beyond[face] = 1;
         solid = 1;
       }
     }
@@ -308,6 +314,17 @@ static int pull_source(const oracle_grid *g, const int xyz[3], const int c[3],
     }
   }
   return 0;
+}
+
+/* The population whose velocity is c_a with the components of the axes in
+ * `mask` reversed. */
+static int mirrored(const model *m, int a, int mask) {
+  if (!mask) return a;
+  int c[3];
+  for (int d = 0; d < 3; ++d) c[d] = (mask >> d) & 1 ? -m->c[a][d] : m->c[a][d];
+  for (int b = 0; b < m->Q; ++b)
+    if (m->c[b][0] == c[0] && m->c[b][1] == c[1] && m->c[b][2] == c[2]) return b;
+  return a;  /* unreachable: both lattices are closed under axis reflections */
 }
 
 static double force_at(const oracle_params *prm, int64_t n, int d) {
@@ -432,11 +449,11 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
         const int xyz[3] = {x, y, z};
         const int64_t i = ((int64_t)z * ny + y) * nx + x;
         for (int a = 0; a < Q; ++a) {
-          int src[3];
+          int src[3], mirror;
           double uw[3];
-          if (pull_source(g, xyz, m.c[a], src, uw)) {
+          if (pull_source(g, xyz, m.c[a], src, uw, &mirror)) {
             const int64_t j = ((int64_t)src[2] * ny + src[1]) * nx + src[0];
-            f_out[a * N + i] = fpost[a * N + j];
+            f_out[a * N + i] = fpost[mirrored(&m, a, mirror) * N + j];
           } else {
             const double cu =
                 m.c[a][0] * uw[0] + m.c[a][1] * uw[1] + m.c[a][2] * uw[2];

@@ -12,7 +12,7 @@
 extern "C" {
 #endif
 
-enum { ORACLE_PERIODIC = 0, ORACLE_WALL = 1, ORACLE_MOVING_WALL = 2 };
+enum { ORACLE_PERIODIC = 0, ORACLE_WALL = 1, ORACLE_MOVING_WALL = 2, ORACLE_SYMMETRY = 3 };
 
 typedef struct {
   int Q;              /* 14 or 18 */
