@@ -55,7 +55,14 @@ enum lbm_storage { /* how populations are held in device memory */
 enum lbm_face_kind {
   LBM_PERIODIC = 0,    /* wraps to the opposite face (both must say so)   */
   LBM_WALL = 1,        /* halfway bounce-back, wall at rest               */
-  LBM_MOVING_WALL = 2  /* halfway bounce-back with wall velocity u_wall   */
+  LBM_MOVING_WALL = 2, /* halfway bounce-back with wall velocity u_wall   */
+  LBM_SYMMETRY = 3     /* free-slip mirror plane halfway beyond the face:
+                        * a population leaving through it returns as its
+                        * mirror image (normal velocity component
+                        * reversed) at the node it left.  Where a link also
+                        * crosses a wall face the wall's bounce-back
+                        * applies.  Like a wall, it cannot face a periodic
+                        * face.  Sec. 4.3's reduced domains use it. */
 };
 
 enum lbm_face { LBM_XM = 0, LBM_XP = 1, LBM_YM = 2, LBM_YP = 3, LBM_ZM = 4, LBM_ZP = 5 };

@@ -176,26 +176,14 @@ int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, Doma
   const int64_t N = (int64_t)desc->nx * desc->ny * desc->nz;
   if (N * desc->Q >= (int64_t(1) << 31) || desc->nz > 65535)
     return bfail(LBM_EINVAL, "domain too large (Q*N must be < 2^31)");
-  for (int f = 0; f < 6; ++f)
-    if (g->face[f] < LBM_PERIODIC || g->face[f] > LBM_MOVING_WALL)
-      return bfail(LBM_EINVAL, "unknown face kind");
   dd = DomainDesc{};
+  if (const char* why = set_faces(dd, g)) return bfail(LBM_EINVAL, why);
   dd.Q = desc->Q;
   dd.nx = desc->nx;
   dd.ny = desc->ny;
   dd.nz = desc->nz;
   dd.storage = desc->storage;
   dd.N = N;
-  for (int k = 0; k < 3; ++k) {
-    const bool lo = g->face[2 * k] == LBM_PERIODIC, hi = g->face[2 * k + 1] == LBM_PERIODIC;
-    if (lo != hi) return bfail(LBM_EINVAL, "opposite faces must both be periodic or neither");
-    dd.per[k] = lo;
-  }
-  for (int f = 0; f < 6; ++f) {
-    if (g->face[f] == LBM_MOVING_WALL) dd.moving |= 1 << f;
-    for (int k = 0; k < 3; ++k)
-      dd.uw[f][k] = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
-  }
   double s[6] = {p->s_c, p->s_e, p->s_q, p->s_nu, p->s_pi, p->s_t};
   if (p->nu > 0.0) s[3] = 1.0 / (3.0 * p->nu + 0.5);
   if (desc->Q == 14) s[4] = s[1];

@@ -104,25 +104,9 @@ int apply_params(lbm_handle* h, const lbm_params* p) {
 }
 
 int apply_geometry(lbm_handle* h, const lbm_geom* g) {
-  for (int f = 0; f < 6; ++f)
-    if (g->face[f] < LBM_PERIODIC || g->face[f] > LBM_MOVING_WALL)
-      return fail(LBM_EINVAL, "unknown face kind");
-  int per[3];
-  for (int k = 0; k < 3; ++k) {
-    const bool lo = g->face[2 * k] == LBM_PERIODIC, hi = g->face[2 * k + 1] == LBM_PERIODIC;
-    if (lo != hi) return fail(LBM_EINVAL, "opposite faces must both be periodic or neither");
-    per[k] = lo ? 1 : 0;
-  }
-  if (!finite_all(&g->u_wall[0][0], 18)) return fail(LBM_EINVAL, "wall velocity not finite");
-  // all checks passed: only now does the handle change
-  for (int k = 0; k < 3; ++k) h->d.per[k] = per[k];
+  // set_faces changes the handle only once every check has passed
+  if (const char* why = set_faces(h->d, g)) return fail(LBM_EINVAL, why);
   h->geom = *g;
-  h->d.moving = 0;
-  for (int f = 0; f < 6; ++f) {
-    if (g->face[f] == LBM_MOVING_WALL) h->d.moving |= 1 << f;
-    for (int k = 0; k < 3; ++k)
-      h->d.uw[f][k] = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
-  }
   return LBM_OK;
 }
 

@@ -256,10 +256,10 @@ __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __
                         cz = Lattice<Q>::c(A, 2);
           int idx = A * N + i;
           if constexpr (ODD) {
-            int off;
+            int off, mirror;
             bool ghost;
-            link_of<Q, A, -1>(L, off, ghost);
-            if (!ghost) idx = opposite<Q>(A) * N + i + off;
+            link_of<Q, A, -1>(L, off, ghost, mirror);
+            if (!ghost) idx = opposite_mirror_rt<Q, A>(mirror) * N + i + off;
           }
           const float v = Codec<S, float>::load(f + idx);
           add_exact(sP, v);

@@ -24,7 +24,8 @@ struct DomainDesc {
   int64_t N;
   void* f;
   int per[3];
-  int moving;
+  int moving;  // bit f: face f is a moving wall
+  int sym;     // bit f: face f is a symmetry plane
   double uw[6][3];
   double s[6];  // sc, se, sq, snu, spi, st
   double force[3];
@@ -40,6 +41,10 @@ struct BlockShape {
 };
 
 BlockShape default_block(int nx, int ny);
+
+// The face fields of d (per, moving, sym, uw) from a geometry.  Returns
+// nullptr, or the reason the geometry is invalid (then d is unchanged).
+const char* set_faces(DomainDesc& d, const lbm_geom* g);
 
 // Message returned by lbm_last_error() on the calling thread.
 void set_last_error(const std::string& msg);

@@ -28,6 +28,7 @@ struct Domain {
   int64_t N;         // nx*ny*nz
   int per[3];        // axis is periodic
   int moving;        // bit f set: face f is a moving wall
+  int sym;           // bit f set: face f is a symmetry (free-slip) plane
   R uw[6][3];        // velocity of each face (zero unless MOVING_WALL)
   Rates<R> s;
   R F[3];            // body force at the step's time level t_n
@@ -75,29 +76,40 @@ __host__ __device__ __forceinline__ R ghost_dot(const Domain<R>& d, int beyond, 
 // applied; 0 if that neighbour is a ghost node) and whether it is a ghost
 // node beyond a wall.  Computed once per cell; each link then costs a few
 // integer adds and one select, with no divergent branch.
+// Beyond a symmetry face the ghost mirrors the node across the halfway
+// plane: along that axis the neighbour is the node itself (offset 0) and the
+// population is the mirror one (flag sm / sp).  A link that also crosses a
+// wall on another axis is a wall link (gm / gp win).
 struct Links {
   int om[3], op[3];
-  bool gm[3], gp[3];
+  bool gm[3], gp[3];  // ghost beyond a wall
+  bool sm[3], sp[3];  // ghost beyond a symmetry face
   bool interior;  // every neighbour is a fluid, unwrapped node: use pull/push
 };
 
 template <typename R>
 __host__ __device__ __forceinline__ void axis_links(int v, int n, int stride, int per,
-                                                    int& om, int& op, bool& gm, bool& gp) {
+                                                    int sym_lo, int sym_hi, int& om, int& op,
+                                                    bool& gm, bool& gp, bool& sm, bool& sp) {
   const bool lo = v == 0, hi = v == n - 1;
   om = !lo ? -stride : (per ? (n - 1) * stride : 0);
   op = !hi ? stride : (per ? -(n - 1) * stride : 0);
-  gm = lo && !per;
-  gp = hi && !per;
+  sm = lo && !per && sym_lo;
+  sp = hi && !per && sym_hi;
+  gm = lo && !per && !sym_lo;
+  gp = hi && !per && !sym_hi;
 }
 
 template <typename R>
 __host__ __device__ __forceinline__ Links make_links(const Domain<R>& d, int x, int y, int z) {
   Links L;
   const int sy = d.nx, sz = d.nx * d.ny;
-  axis_links<R>(x, d.nx, 1, d.per[0], L.om[0], L.op[0], L.gm[0], L.gp[0]);
-  axis_links<R>(y, d.ny, sy, d.per[1], L.om[1], L.op[1], L.gm[1], L.gp[1]);
-  axis_links<R>(z, d.nz, sz, d.per[2], L.om[2], L.op[2], L.gm[2], L.gp[2]);
+  axis_links<R>(x, d.nx, 1, d.per[0], d.sym & 1, (d.sym >> 1) & 1, L.om[0], L.op[0], L.gm[0],
+                L.gp[0], L.sm[0], L.sp[0]);
+  axis_links<R>(y, d.ny, sy, d.per[1], (d.sym >> 2) & 1, (d.sym >> 3) & 1, L.om[1], L.op[1],
+                L.gm[1], L.gp[1], L.sm[1], L.sp[1]);
+  axis_links<R>(z, d.nz, sz, d.per[2], (d.sym >> 4) & 1, (d.sym >> 5) & 1, L.om[2], L.op[2],
+                L.gm[2], L.gp[2], L.sm[2], L.sp[2]);
   L.interior = false;
   return L;
 }
@@ -114,6 +126,7 @@ __host__ __device__ __forceinline__ Links make_links_interior(const Domain<R>& d
   L.om[2] = -sz;
   L.op[2] = sz;
   L.gm[0] = L.gp[0] = L.gm[1] = L.gp[1] = L.gm[2] = L.gp[2] = false;
+  L.sm[0] = L.sp[0] = L.sm[1] = L.sp[1] = L.sm[2] = L.sp[2] = false;
   L.interior = true;
   return L;
 }
@@ -124,7 +137,9 @@ template <typename R>
 __host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x) {
   Links L;
   const int sy = d.nx, sz = d.nx * d.ny;
-  axis_links<R>(x, d.nx, 1, d.per[0], L.om[0], L.op[0], L.gm[0], L.gp[0]);
+  axis_links<R>(x, d.nx, 1, d.per[0], d.sym & 1, (d.sym >> 1) & 1, L.om[0], L.op[0], L.gm[0],
+                L.gp[0], L.sm[0], L.sp[0]);
+  L.sm[1] = L.sp[1] = L.sm[2] = L.sp[2] = false;
   L.om[1] = -sy;
   L.op[1] = sy;
   L.om[2] = -sz;
@@ -134,22 +149,75 @@ __host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x
   return L;
 }
 
-// Offset and ghost flag of the node x + s*c_A (s = -1: pull source, +1:
-// push target).
+// Offset, wall-ghost flag and mirror axes (bit k: the link crosses a
+// symmetry face normal to axis k) of the node x + s*c_A (s = -1: pull
+// source, +1: push target).
 template <int Q, int A, int SIGN>
-__host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool& ghost) {
+__host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool& ghost,
+                                                 int& mirror) {
   off = 0;
   ghost = false;
+  mirror = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int c = SIGN * Lattice<Q>::c(A, k);
     if (c < 0) {
       off += L.om[k];
       ghost = ghost || L.gm[k];
+      if (L.sm[k]) mirror |= 1 << k;
     } else if (c > 0) {
       off += L.op[k];
       ghost = ghost || L.gp[k];
+      if (L.sp[k]) mirror |= 1 << k;
     }
+  }
+}
+
+// The population whose velocity is c_A with the components of the axes in
+// `mask` reversed (both lattices are closed under axis reflections).
+template <int Q>
+__host__ __device__ constexpr int mirror_of(int a, int mask) {
+  int c[3];
+  for (int k = 0; k < 3; ++k) c[k] = (mask >> k) & 1 ? -Lattice<Q>::c(a, k) : Lattice<Q>::c(a, k);
+  for (int b = 0; b < Q; ++b)
+    if (Lattice<Q>::c(b, 0) == c[0] && Lattice<Q>::c(b, 1) == c[1] && Lattice<Q>::c(b, 2) == c[2])
+      return b;
+  return -1;
+}
+template <int Q>
+__host__ __device__ constexpr bool mirrors_closed() {
+  for (int a = 0; a < Q; ++a)
+    for (int m = 0; m < 8; ++m)
+      if (mirror_of<Q>(a, m) < 0) return false;
+  return true;
+}
+static_assert(mirrors_closed<14>() && mirrors_closed<18>(), "lattice not closed under mirrors");
+
+// mirror_of<Q>(A, mask) for a runtime mask (a select among eight constants)
+template <int Q, int A>
+__host__ __device__ __forceinline__ int mirror_rt(int mask) {
+  switch (mask) {
+    case 1: return mirror_of<Q>(A, 1);
+    case 2: return mirror_of<Q>(A, 2);
+    case 3: return mirror_of<Q>(A, 3);
+    case 4: return mirror_of<Q>(A, 4);
+    case 5: return mirror_of<Q>(A, 5);
+    case 6: return mirror_of<Q>(A, 6);
+    case 7: return mirror_of<Q>(A, 7);
+    default: return A;
+  }
+}
+template <int Q, int A>
+__host__ __device__ __forceinline__ int opposite_mirror_rt(int mask) {
+  switch (mask) {
+    case 1: return opposite<Q>(mirror_of<Q>(A, 1));
+    case 2: return opposite<Q>(mirror_of<Q>(A, 2));
+    case 3: return opposite<Q>(mirror_of<Q>(A, 3));
+    case 4: return opposite<Q>(mirror_of<Q>(A, 4));
+    case 5: return opposite<Q>(mirror_of<Q>(A, 5));
+    case 6: return opposite<Q>(mirror_of<Q>(A, 6));
+    case 7: return opposite<Q>(mirror_of<Q>(A, 7));
+    default: return opposite<Q>(A);
   }
 }
 
@@ -210,14 +278,16 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
       ((fv[A] = load_pop<S, R, CG>(fc + d.pull[A])), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
-    // f_a(x) = A[abar][x - c_a], or A[a][x] if x - c_a is a ghost
+    // f_a(x) = A[abar][x - c_a], or A[a][x] if x - c_a is a wall ghost;
+    // beyond a symmetry face the source is the mirror node and population
     [&]<int... A>(std::integer_sequence<int, A...>) {
       (
           [&] {
-            int off;
+            int off, mirror;
             bool ghost;
-            link_of<Q, A, -1>(L, off, ghost);
-            const int idx = ghost ? (A * N + i) : (opposite<Q>(A) * N + i + off);
+            link_of<Q, A, -1>(L, off, ghost, mirror);
+            const int idx =
+                ghost ? (A * N + i) : (opposite_mirror_rt<Q, A>(mirror) * N + i + off);
             fv[A] = load_pop<S, R, CG>(f + idx);
           }(),
           ...);
@@ -266,14 +336,17 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
             ...);
       }(std::make_integer_sequence<int, Q>{});
     }
-    // f*_a goes to A[a][x + c_a], or back into A[abar][x] if x + c_a is a ghost
+    // f*_a goes to A[a][x + c_a], or back into A[abar][x] if x + c_a is a
+    // wall ghost; beyond a symmetry face it becomes the mirror population of
+    // the mirror node (the slot this cell's mirrored pull reads)
     [&]<int... A>(std::integer_sequence<int, A...>) {
       (
           [&] {
-            int off;
+            int off, mirror;
             bool ghost;
-            link_of<Q, A, 1>(L, off, ghost);
-            const int idx = ghost ? (opposite<Q>(A) * N + i) : (A * N + i + off);
+            link_of<Q, A, 1>(L, off, ghost, mirror);
+            const int idx =
+                ghost ? (opposite<Q>(A) * N + i) : (mirror_rt<Q, A>(mirror) * N + i + off);
             put<S, R, SR, A>(f + idx, fv[A], h);
           }(),
           ...);
@@ -400,16 +473,17 @@ __host__ __device__ __forceinline__ void put_canonical(const Domain<R>& d, S* __
     [&]<int... A>(std::integer_sequence<int, A...>) {
       (
           [&] {
-            int off;
+            int off, mirror;
             bool ghost;
-            link_of<Q, A, -1>(L, off, ghost);
+            link_of<Q, A, -1>(L, off, ghost, mirror);
             R v = fv[A];
             const int faces = link_faces<Q, A, -1>(L);
             if (faces)
               v -= R(6.0 * Lattice<Q>::w(A)) *
                    ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
                              Lattice<Q>::c(A, 2));
-            const int idx = ghost ? (A * N + i) : (opposite<Q>(A) * N + i + off);
+            const int idx =
+                ghost ? (A * N + i) : (opposite_mirror_rt<Q, A>(mirror) * N + i + off);
             Codec<S, R>::store(f + idx, v);
           }(),
           ...);

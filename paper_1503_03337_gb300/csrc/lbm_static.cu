@@ -182,14 +182,8 @@ extern "C" int lbm_reductions_static(const lbm_desc* desc, const lbm_geom* geom,
                        "domain has " + std::to_string(N) + " cells; the static scratch of "
                        "lbm_reductions_static holds at most " +
                            std::to_string(kStaticMaxCells) + " cells");
-  for (int f = 0; f < 6; ++f)
-    if (geom->face[f] < LBM_PERIODIC || geom->face[f] > LBM_MOVING_WALL)
-      return static_fail(LBM_EINVAL, "unknown face kind");
-  for (int k = 0; k < 3; ++k)
-    if ((geom->face[2 * k] == LBM_PERIODIC) != (geom->face[2 * k + 1] == LBM_PERIODIC))
-      return static_fail(LBM_EINVAL, "opposite faces must both be periodic or neither");
-
   DomainDesc dd{};
+  if (const char* why = set_faces(dd, geom)) return static_fail(LBM_EINVAL, why);
   dd.Q = desc->Q;
   dd.nx = desc->nx;
   dd.ny = desc->ny;
@@ -197,12 +191,6 @@ extern "C" int lbm_reductions_static(const lbm_desc* desc, const lbm_geom* geom,
   dd.storage = desc->storage;
   dd.N = N;
   dd.f = const_cast<void*>(populations);
-  for (int k = 0; k < 3; ++k) dd.per[k] = geom->face[2 * k] == LBM_PERIODIC ? 1 : 0;
-  for (int f = 0; f < 6; ++f) {
-    if (geom->face[f] == LBM_MOVING_WALL) dd.moving |= 1 << f;
-    for (int k = 0; k < 3; ++k)
-      dd.uw[f][k] = geom->face[f] == LBM_MOVING_WALL ? geom->u_wall[f][k] : 0.0;
-  }
   for (int k = 0; k < 3; ++k) dd.force[k] = params->force[k];
   dd.period = params->force_period;
   dd.p_ref = params->p_ref;

@@ -17,6 +17,7 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
   o.N = d.N;
   for (int k = 0; k < 3; ++k) o.per[k] = d.per[k];
   o.moving = d.moving;
+  o.sym = d.sym;
   for (int face = 0; face < 6; ++face)
     for (int k = 0; k < 3; ++k) o.uw[face][k] = R(d.uw[face][k]);
   o.s.sc = R(d.s[0]);
@@ -39,6 +40,28 @@ template Domain<float> to_domain<float>(const DomainDesc&, const double*);
 void force_at(const DomainDesc& d, int64_t n, double F[3]) {
   const double c = d.period > 0.0 ? std::cos(2.0 * M_PI * (double)n / d.period) : 1.0;
   for (int k = 0; k < 3; ++k) F[k] = d.force[k] * c;
+}
+
+const char* set_faces(DomainDesc& d, const lbm_geom* g) {
+  for (int f = 0; f < 6; ++f)
+    if (g->face[f] < LBM_PERIODIC || g->face[f] > LBM_SYMMETRY) return "unknown face kind";
+  int per[3];
+  for (int k = 0; k < 3; ++k) {
+    const bool lo = g->face[2 * k] == LBM_PERIODIC, hi = g->face[2 * k + 1] == LBM_PERIODIC;
+    if (lo != hi) return "opposite faces must both be periodic or neither";
+    per[k] = lo ? 1 : 0;
+  }
+  for (int f = 0; f < 6; ++f)
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(g->u_wall[f][k])) return "wall velocity not finite";
+  for (int k = 0; k < 3; ++k) d.per[k] = per[k];
+  d.moving = d.sym = 0;
+  for (int f = 0; f < 6; ++f) {
+    if (g->face[f] == LBM_MOVING_WALL) d.moving |= 1 << f;
+    if (g->face[f] == LBM_SYMMETRY) d.sym |= 1 << f;
+    for (int k = 0; k < 3; ++k) d.uw[f][k] = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
+  }
+  return nullptr;
 }
 
 BlockShape default_block(int nx, int ny) {

@@ -12,6 +12,7 @@ Recipes (lattice units, c = 1):
                   (pinned against the series in the oracle's tests).
   * cavity     -- cube with the y+ face moving at U along x, other faces walls,
                   nu = U L / Re.
+  * half_cavity -- the cavity's z <= 1/2 half, symmetry face on the mid-plane.
   * pulsatile  -- as duct but F_z(t) = A cos(2 pi t / T), nu = b^2 (2 pi/T) / eta^2.
 """
 from __future__ import annotations
@@ -23,7 +24,7 @@ import numpy as np
 
 SQUARE_DUCT_K = 0.2946854131
 
-PERIODIC, WALL, MOVING_WALL = 0, 1, 2
+PERIODIC, WALL, MOVING_WALL, SYMMETRY = 0, 1, 2, 3
 XM, XP, YM, YP, ZM, ZP = range(6)
 
 
@@ -65,6 +66,16 @@ def cavity(Q: int, n: int, Re: float, U: float = 0.05, storage: str = "f32",
     uw[YP] = (U, 0.0, 0.0)
     return Case("cavity", Q, n, ny, nz, tuple(faces), uw, nu=U * n / Re,
                 storage=storage, u_ref=U)
+
+
+def half_cavity(Q: int, n: int, Re: float, U: float = 0.05, storage: str = "f32") -> Case:
+    """The z <= 1/2 half of the cavity with a symmetry face on the mid-plane
+    z+ (the reduced domain of Sec. 4.3, Eq. z05symmetry): n x n x ceil(n/2)
+    nodes, so that the mirrored box is n x n x 2*ceil(n/2)."""
+    c = cavity(Q, n, Re, U, storage, nz=(n + 1) // 2)
+    c.name = "half_cavity"
+    c.faces = c.faces[:ZP] + (SYMMETRY,)
+    return c
 
 
 def duct(Q: int, n: int, nz: int, nu: float, u_max: float = 0.02,

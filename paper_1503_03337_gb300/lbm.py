@@ -18,7 +18,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EBUS
 # storage
 LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F16, LBM_STORAGE_BF16 = range(4)
 # faces
-LBM_PERIODIC, LBM_WALL, LBM_MOVING_WALL = range(3)
+LBM_PERIODIC, LBM_WALL, LBM_MOVING_WALL, LBM_SYMMETRY = range(4)
 LBM_XM, LBM_XP, LBM_YM, LBM_YP, LBM_ZM, LBM_ZP = range(6)
 # fields / dtypes
 LBM_FIELD_U, LBM_FIELD_P, LBM_FIELD_POPULATIONS = 1, 2, 4

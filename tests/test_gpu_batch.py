@@ -32,6 +32,8 @@ def mix():
         inputs.cavity(18, 20, 100.0, storage="f16"),
     ]
     cases[1].ny = 9  # a non-square duct cross-section
+    # a half cavity: symmetry face on the mid-plane z+
+    cases[2].faces = cases[2].faces[:5] + (inputs.SYMMETRY,)
     cases[4].rounding = lbm.LBM_ROUND_STOCHASTIC
     return cases
 

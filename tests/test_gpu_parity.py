@@ -2,6 +2,8 @@
 
 Bounds: FP64 build <= 1e-12 relative after 1000 steps; FP32 storage
 <= 1e-5 U; FP16 storage <= 1e-3 U (U the case's velocity scale)."""
+import zlib
+
 import numpy as np
 import pytest
 
@@ -62,14 +64,26 @@ EDGE = [
     ("thin_x_walls", (1, 4, 3), (1, 1, 2, 1, 0, 0)),
     ("two_cells", (2, 2, 2), (2, 2, 2, 2, 2, 2)),
     ("long_x", (67, 3, 3), (1, 1, 0, 0, 1, 2)),
+    # symmetry faces (3) against walls, moving walls, periodic axes and each
+    # other, on thin axes and on the x faces of long rows
+    ("sym_lid", (5, 6, 4), (1, 3, 1, 2, 3, 1)),
+    ("sym_corner", (4, 5, 6), (3, 1, 3, 2, 1, 3)),
+    ("sym_periodic", (6, 4, 5), (0, 0, 3, 3, 2, 1)),
+    ("sym_thin", (1, 5, 2), (3, 3, 2, 3, 3, 1)),
+    ("sym_long_x", (67, 3, 4), (3, 2, 1, 3, 0, 0)),
 ]
+
+
+def seed(*key):
+    """A seed that is the same in every process (str hashes are not)."""
+    return zlib.crc32(repr(key).encode())
 
 
 @pytest.mark.parametrize("Q", (14, 18))
 @pytest.mark.parametrize("name,shape,faces", EDGE)
 @pytest.mark.parametrize("steps", (1, 2, 37))
 def test_fp64_edge_cases(Q, name, shape, faces, steps):
-    rng = np.random.default_rng(hash((name, Q)) & 0xffff)
+    rng = np.random.default_rng(seed(name, Q))
     uw = rng.normal(size=(6, 3)) * 0.03
     case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
                        nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64",
@@ -83,6 +97,7 @@ def test_fp64_edge_cases(Q, name, shape, faces, steps):
 PAIR_CASES = EDGE + [
     ("wide_rows", (200, 6, 5), (1, 2, 1, 2, 0, 0)),
     ("wide_periodic", (131, 4, 4), (0, 0, 1, 1, 2, 1)),
+    ("wide_sym", (200, 5, 4), (1, 3, 3, 2, 0, 0)),
 ]
 
 
@@ -95,7 +110,7 @@ def test_two_cells_per_thread(Q, name, shape, faces, storage):
     differently in the two kernels, so the results agree to FP32 rounding
     (and, for the 2-byte formats with stochastic rounding, to a few storage
     ulps), on ragged rows, moving walls and periodic wraps."""
-    rng = np.random.default_rng(hash((name, Q, 2)) & 0xffff)
+    rng = np.random.default_rng(seed(name, Q, 2))
     uw = rng.normal(size=(6, 3)) * 0.03
     case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
                        nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage=storage,
@@ -115,7 +130,7 @@ def test_two_cells_per_thread(Q, name, shape, faces, storage):
 def test_fp32_launch_shapes(Q, name, shape, faces, launch):
     """Every launch shape, including two cells per thread, against the
     oracle from a seeded random state (odd step count)."""
-    rng = np.random.default_rng(hash((name, Q)) & 0xffff)
+    rng = np.random.default_rng(seed(name, Q))
     uw = rng.normal(size=(6, 3)) * 0.03
     case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
                        nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f32",

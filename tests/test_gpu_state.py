@@ -213,15 +213,18 @@ def test_overlap_does_not_change_results(storage):
         assert rel_max(out[0], o["f"]) <= 1e-12
 
 
+@pytest.mark.parametrize("sym", (False, True))
 @pytest.mark.parametrize("storage", ("f32", "f16", "bf16"))
 @pytest.mark.parametrize("Q", (14, 18))
-def test_pair_reductions_match_fields(Q, storage):
+def test_pair_reductions_match_fields(Q, storage, sym):
     """The 32- and 16-bit storage reductions (FP32 pair arithmetic) against
     FP64 sums of the read-back fields, on an odd and an even step, with a
     body force and a moving lid: every statistic to 1e-11 relative (the
     pair sums carry about 48 bits), the maximum to 1e-13."""
     case = inputs.cavity(Q, 23, 150.0, storage=storage, ny=17, nz=11)
     case.force = (1e-5, -2e-5, 3e-5)
+    if sym:  # mirrored links on the odd steps: symmetry faces at x- and z+
+        case.faces = (inputs.SYMMETRY,) + case.faces[1:5] + (inputs.SYMMETRY,)
     h = gpu_open(case)
     nx, ny, nz = case.nx, case.ny, case.nz
     try:

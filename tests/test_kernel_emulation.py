@@ -32,9 +32,10 @@ def emu():
     L = ctypes.CDLL(lib)
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
     L.emu_step.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
-                           ctypes.c_int, ip, ctypes.c_int, dp, dp, dp, ctypes.c_int64]
+                           ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                           ctypes.c_int64]
     L.emu_canonical.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip,
-                                ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int]
+                                ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int]
     L.emu_collide.argtypes = [ctypes.c_int, dp, dp, dp]
     return L
 
@@ -62,6 +63,7 @@ class EmuDomain:
         self.per = np.array([int(case.faces[2 * k] == inputs.PERIODIC) for k in range(3)],
                             dtype=np.int32)
         self.moving = sum(1 << f for f in range(6) if case.faces[f] == inputs.MOVING_WALL)
+        self.sym = sum(1 << f for f in range(6) if case.faces[f] == inputs.SYMMETRY)
         self.uw = np.ascontiguousarray(
             np.where(np.array(case.faces)[:, None] == inputs.MOVING_WALL, case.u_wall, 0.0))
         s = oracle.rates(case.Q, case.s_nu)
@@ -77,13 +79,13 @@ class EmuDomain:
         c = self.case
         canon = np.ascontiguousarray(f, dtype=np.float64)
         assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
-                                      self.moving, _d(self.uw), _d(canon), n, 1) == 0
+                                      self.moving, self.sym, _d(self.uw), _d(canon), n, 1) == 0
 
     def get(self):
         c = self.case
         out = np.zeros_like(self.A)
         assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
-                                      self.moving, _d(self.uw), _d(out), self.n, 0) == 0
+                                      self.moving, self.sym, _d(self.uw), _d(out), self.n, 0) == 0
         return out
 
     def step(self, k):
@@ -92,7 +94,7 @@ class EmuDomain:
             amp = np.cos(2 * np.pi * self.n / c.period) if c.period > 0 else 1.0
             F = np.array(c.force, dtype=np.float64) * amp
             assert self.emu.emu_step(c.Q, 0, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
-                                     self.moving, _d(self.uw), _d(self.s), _d(F), self.n) == 0
+                                     self.moving, self.sym, _d(self.uw), _d(self.s), _d(F), self.n) == 0
             self.n += 1
 
 
@@ -106,6 +108,13 @@ EDGE = [
     # wide enough for whole 32-cell x-ranges away from the x faces, which
     # take the interior offset tables
     ("wide_x", (70, 4, 3), (1, 2, 1, 2, 0, 0)),
+    # symmetry faces (3): against walls, moving walls and each other, on
+    # thin axes, and on the x faces of 32-cell x-ranges
+    ("sym_lid", (5, 6, 4), (1, 3, 1, 2, 3, 1)),
+    ("sym_corner", (4, 5, 6), (3, 1, 3, 2, 1, 3)),
+    ("sym_periodic", (6, 4, 5), (0, 0, 3, 3, 2, 1)),
+    ("sym_thin", (1, 5, 2), (3, 3, 2, 3, 3, 1)),
+    ("sym_wide_x", (70, 3, 4), (3, 2, 1, 3, 0, 0)),
 ]
 
 
