@@ -29,7 +29,8 @@ PERIODIC, WALL, MOVING_WALL, SYMMETRY = 0, 1, 2, 3
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fused multiply-add, OpenMP over z)."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(_SRC[:-2] + ".h"))):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
@@ -44,7 +45,9 @@ class Grid(ctypes.Structure):
     _fields_ = [("Q", ctypes.c_int), ("nx", ctypes.c_int),
                 ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("face", ctypes.c_int * 6),
-                ("u_wall", (ctypes.c_double * 3) * 6)]
+                ("u_wall", (ctypes.c_double * 3) * 6),
+                ("edge_axis", ctypes.c_int * 6),
+                ("edge_scale", (ctypes.c_double * 2) * 6)]
 
 
 class Rates(ctypes.Structure):
@@ -151,13 +154,18 @@ def collide(Q: int, r: Rates, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
 
 # ---- whole-grid operations -----------------------------------------------------
 
-def make_grid(Q, nx, ny, nz, faces=(WALL,) * 6, u_wall=None) -> Grid:
+def make_grid(Q, nx, ny, nz, faces=(WALL,) * 6, u_wall=None, edge=None) -> Grid:
+    """edge: {face: (axis, scale_first, scale_last)}, the edge profile of a
+    moving face (see lbm_oracle.h)."""
     g = Grid()
     g.Q, g.nx, g.ny, g.nz = Q, nx, ny, nz
     for i in range(6):
         g.face[i] = int(faces[i])
         for d in range(3):
             g.u_wall[i][d] = 0.0 if u_wall is None else float(u_wall[i][d])
+    for face, (axis, lo, hi) in (edge or {}).items():
+        g.edge_axis[face] = int(axis) + 1
+        g.edge_scale[face][0], g.edge_scale[face][1] = float(lo), float(hi)
     return g
 
 

@@ -307,9 +307,15 @@ static int pull_source(const oracle_grid *g, const int xyz[3], const int c[3],
   if (!solid) return 1;
   for (int face = 0; face < 6; ++face) {
     if (beyond[face] && g->face[face] == ORACLE_MOVING_WALL) {
-      uw[0] = g->u_wall[face][0];
-      uw[1] = g->u_wall[face][1];
-      uw[2] = g->u_wall[face][2];
+      double scale = 1.0;
+      const int k = g->edge_axis[face] - 1;
+      if (k >= 0 && k < 3) {
+        if (xyz[k] == 0) scale = g->edge_scale[face][0];
+        else if (xyz[k] == n_axis(g, k) - 1) scale = g->edge_scale[face][1];
+      }
+      uw[0] = g->u_wall[face][0] * scale;
+      uw[1] = g->u_wall[face][1] * scale;
+      uw[2] = g->u_wall[face][2] * scale;
       break;
     }
   }

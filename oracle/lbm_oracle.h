@@ -19,6 +19,12 @@ typedef struct {
   int nx, ny, nz;     /* fluid nodes per axis */
   int face[6];        /* x-, x+, y-, y+, z-, z+ : ORACLE_* kinds */
   double u_wall[6][3];/* wall velocity of each MOVING_WALL face */
+  /* Edge profile of a moving face (the corner velocities of Sec. 4.3): if
+   * edge_axis[f] = k + 1, the wall velocity of face f seen from the first
+   * (last) node column along axis k is u_wall[f] * edge_scale[f][0] ([1]);
+   * a one-node axis takes [0].  0 = uniform. */
+  int edge_axis[6];
+  double edge_scale[6][2];
 } oracle_grid;
 
 typedef struct {

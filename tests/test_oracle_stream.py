@@ -1,9 +1,11 @@
 """Pins of the oracle's streaming and boundary rules on tiny grids.
 
 Streaming is isolated by a collision that does nothing (S = 0, F = 0), then
-compared with a per-link table built here from the rules of readings G5/G6:
-a link whose source node lies beyond a wall carries the cell's own reflected
-population plus 6 w (c . u_wall).
+compared with a per-link table built here from the rules of readings G5/G6,
+G14 and G15: a link whose source node lies beyond a wall carries the cell's
+own reflected population plus 6 w (c . u_wall), u_wall scaled by the face's
+edge profile in the first and last node columns; across a symmetry face the
+source is the node's mirror image and the pulled population the mirror one.
 """
 import itertools
 
@@ -12,63 +14,78 @@ import pytest
 
 import oracle
 
-P, W, M = oracle.PERIODIC, oracle.WALL, oracle.MOVING_WALL
+P, W, M, S = oracle.PERIODIC, oracle.WALL, oracle.MOVING_WALL, oracle.SYMMETRY
 ZERO = oracle.Rates(0, 0, 0, 0, 0, 0)
 
 
-def link_table(Q, n, faces, u_wall):
+def link_table(Q, n, faces, u_wall, edge=None):
     """Expected pulled value of every (a, node) as ('src', b, node') or
     ('wall', abar, node, correction)."""
     c = oracle.velocities(Q)
     w, _ = oracle.weights(Q)
-    opp = [int(np.flatnonzero((c == -c[a]).all(axis=1))[0]) for a in range(Q)]
+    find = {tuple(v): b for b, v in enumerate(c)}
+    opp = [find[tuple(-c[a])] for a in range(Q)]
     table = {}
     for z, y, x in itertools.product(range(n[2]), range(n[1]), range(n[0])):
+        node = (x, y, z)
         for a in range(Q):
             src = [x - c[a][0], y - c[a][1], z - c[a][2]]
             beyond = []
+            cm = c[a].copy()  # velocity of the pulled population
             for d in range(3):
-                if src[d] < 0:
-                    if faces[2 * d] == P:
-                        src[d] += n[d]
-                    else:
-                        beyond.append(2 * d)
-                elif src[d] >= n[d]:
-                    if faces[2 * d + 1] == P:
-                        src[d] -= n[d]
-                    else:
-                        beyond.append(2 * d + 1)
+                out = 2 * d if src[d] < 0 else 2 * d + 1 if src[d] >= n[d] else None
+                if out is None:
+                    continue
+                if faces[out] == P:
+                    src[d] %= n[d]
+                elif faces[out] == S:
+                    src[d] = node[d]
+                    cm[d] = -cm[d]
+                else:
+                    beyond.append(out)
             if not beyond:
-                table[(a, z, y, x)] = ("src", a, (src[2], src[1], src[0]))
+                table[(a, z, y, x)] = ("src", find[tuple(cm)], (src[2], src[1], src[0]))
             else:
                 uw = np.zeros(3)
                 for face in sorted(beyond):
                     if faces[face] == M:
                         uw = np.asarray(u_wall[face], dtype=float)
+                        if edge and face in edge:
+                            k, first, last = edge[face]
+                            uw = uw * (first if node[k] == 0 else
+                                       last if node[k] == n[k] - 1 else 1.0)
                         break
                 table[(a, z, y, x)] = ("wall", opp[a], (z, y, x), 6.0 * w[a] * (c[a] @ uw))
     return table
 
 
 CASES = [
-    ((3, 3, 3), (W, W, W, W, W, W)),
-    ((4, 3, 5), (P, P, W, W, P, P)),
-    ((3, 4, 4), (W, W, W, M, W, W)),
-    ((4, 4, 3), (M, W, P, P, W, M)),
-    ((2, 3, 4), (P, P, P, P, P, P)),
+    ((3, 3, 3), (W, W, W, W, W, W), None),
+    ((4, 3, 5), (P, P, W, W, P, P), None),
+    ((3, 4, 4), (W, W, W, M, W, W), None),
+    ((4, 4, 3), (M, W, P, P, W, M), None),
+    ((2, 3, 4), (P, P, P, P, P, P), None),
+    # symmetry faces against walls, moving walls, periodic axes, each other
+    ((3, 4, 4), (W, S, W, M, S, W), None),
+    ((4, 3, 3), (S, S, P, P, M, S), None),
+    ((1, 3, 2), (S, S, S, M, W, S), None),
+    # edge profiles of moving faces (the lid corner velocities of Sec. 4.3)
+    ((5, 4, 3), (W, W, W, M, W, W), {3: (0, 0.3, 0.7)}),
+    ((4, 3, 5), (M, W, W, M, S, M), {3: (2, 0.2, 0.6), 0: (1, 1.5, -0.5), 5: (0, 0.0, 2.0)}),
+    ((1, 4, 3), (W, W, W, M, W, W), {3: (0, 0.4, 0.9)}),
 ]
 
 
 @pytest.mark.parametrize("Q", (14, 18))
-@pytest.mark.parametrize("n,faces", CASES)
-def test_streaming_matches_link_table(Q, n, faces):
+@pytest.mark.parametrize("n,faces,edge", CASES)
+def test_streaming_matches_link_table(Q, n, faces, edge):
     rng = np.random.default_rng(11)
     u_wall = rng.normal(size=(6, 3)) * 0.05
-    g = oracle.make_grid(Q, *n, faces=faces, u_wall=u_wall)
+    g = oracle.make_grid(Q, *n, faces=faces, u_wall=u_wall, edge=edge)
     prm = oracle.make_params(ZERO)
     f = rng.normal(size=(Q, n[2], n[1], n[0]))
     out = oracle.step(g, prm, 0, f)
-    for key, rule in link_table(Q, n, faces, u_wall).items():
+    for key, rule in link_table(Q, n, faces, u_wall, edge).items():
         if rule[0] == "src":
             expect = f[(rule[1],) + rule[2]]
         else:
