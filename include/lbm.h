@@ -91,10 +91,21 @@ typedef struct lbm_desc {
 
 /* Face order x-, x+, y-, y+, z-, z+.  A ghost node beyond several faces
  * (an edge or corner) takes the velocity of the first MOVING_WALL face among
- * them in that order, else zero. */
+ * them in that order, else zero.
+ *
+ * Edge profile of a MOVING_WALL face f (the lid corner velocities of Sec.
+ * 4.3): edge_axis[f] = k + 1 names an in-plane axis k of the face; the
+ * wall velocity seen from the first node column along k is
+ * u_wall[f] * edge_scale[f][0], from the last one u_wall[f] *
+ * edge_scale[f][1] (a one-node axis takes [0]), elsewhere u_wall[f].
+ * edge_axis[f] = 0 (a zero-initialised struct) leaves the face uniform.
+ * LBM_EINVAL: edge_axis outside 0..3, on a face that is not a moving wall,
+ * along the face's normal, or a non-finite scale. */
 typedef struct lbm_geom {
   int32_t face[6];
   double u_wall[6][3];
+  int32_t edge_axis[6];
+  double edge_scale[6][2];
 } lbm_geom;
 
 /* Relaxation rates of the diagonal collision matrix, Eq. sD3Q15meaning

@@ -131,6 +131,7 @@ struct ReduceArgs {
   double F[3];
   double p_ref;
   double uw[6][3];  // wall velocities in FP64 (the pair path's wall terms)
+  double edge_scale[6][2];  // their edge profiles (Domain::edge_scale)
 };
 
 __device__ __forceinline__ void block_reduce(double (&v)[kNumStats], double* shm) {
@@ -244,6 +245,7 @@ __device__ __forceinline__ bool greater(PairSum a, PairSum b) {
 template <int Q, typename S, bool ODD>
 __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __restrict__ f,
                                              int x, int y, int z, const double (&uw)[6][3],
+                                             const double (&es)[6][2],
                                              PairSum& sP, PairSum (&sj)[3]) {
   const int i = x + d.nx * (y + d.ny * z);
   const int N = (int)d.N;
@@ -271,8 +273,15 @@ __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __
             if (hit) {
               int face = 0;
               while (!((hit >> face) & 1)) ++face;  // the first moving face
+              double e = 1.0;  // edge profile (as edge_factor, in FP64)
+              const int k = d.edge_axis[face] - 1;
+              if (k >= 0) {
+                if ((L.edge >> (2 * k)) & 1) e = es[face][0];
+                else if ((L.edge >> (2 * k + 1)) & 1) e = es[face][1];
+              }
               const double t = 6.0 * Lattice<Q>::w(A) *
-                               (cx * uw[face][0] + cy * uw[face][1] + cz * uw[face][2]);
+                               (cx * (uw[face][0] * e) + cy * (uw[face][1] * e) +
+                                cz * (uw[face][2] * e));
               const PairSum tp = pair_of(t);
               add_pair(sP, tp);
               if constexpr (cx != 0) add_pair(sj[0], cx > 0 ? tp : negated(tp));
@@ -304,7 +313,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d,
     const int r = i / d.nx;
     const int y = r % d.ny, z = r / d.ny;
     PairSum sP, sj[3];
-    cell_moments<Q, S, ODD>(d, static_cast<const S*>(d.f), x, y, z, a.uw, sP, sj);
+    cell_moments<Q, S, ODD>(d, static_cast<const S*>(d.f), x, y, z, a.uw, a.edge_scale, sP,
+                            sj);
     PairSum u[3];
     bool finite = isfinite(sP.hi) && isfinite(sP.lo);
     for (int k = 0; k < 3; ++k) {
@@ -458,8 +468,10 @@ cudaError_t launch_reduce(const DomainDesc& dd, int64_t n, double* u_prev, int h
   a.partials = partials;
   a.p_ref = dd.p_ref;
   for (int k = 0; k < 3; ++k) a.F[k] = F[k];
-  for (int face = 0; face < 6; ++face)
+  for (int face = 0; face < 6; ++face) {
     for (int k = 0; k < 3; ++k) a.uw[face][k] = dd.uw[face][k];
+    for (int k = 0; k < 2; ++k) a.edge_scale[face][k] = dd.edge_scale[face][k];
+  }
   int64_t g = (dd.N + kReduceThreads - 1) / kReduceThreads;
   if (g > kReduceBlocks) g = kReduceBlocks;
   if (g < 1) g = 1;

@@ -27,6 +27,8 @@ struct DomainDesc {
   int moving;  // bit f: face f is a moving wall
   int sym;     // bit f: face f is a symmetry plane
   double uw[6][3];
+  int edge_axis[6];  // edge profiles of moving faces (lbm_geom)
+  double edge_scale[6][2];
   double s[6];  // sc, se, sq, snu, spi, st
   double force[3];
   double period;

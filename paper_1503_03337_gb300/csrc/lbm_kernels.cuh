@@ -30,6 +30,12 @@ struct Domain {
   int moving;        // bit f set: face f is a moving wall
   int sym;           // bit f set: face f is a symmetry (free-slip) plane
   R uw[6][3];        // velocity of each face (zero unless MOVING_WALL)
+  // Edge profile of a moving face f (the lid corner velocities of Sec.
+  // 4.3): with edge_axis[f] = k + 1, a cell in the first (last) node column
+  // along axis k sees uw[f] * edge_scale[f][0] ([1]); a one-node axis takes
+  // [0]; edge_axis[f] = 0: uniform.
+  int edge_axis[6];
+  R edge_scale[6][2];
   Rates<R> s;
   R F[3];            // body force at the step's time level t_n
   uint32_t key;      // per-step key of the stochastic-rounding hash
@@ -56,18 +62,33 @@ __host__ __device__ inline void fill_offsets(Domain<R>& d) {
   }
 }
 
-// c . u_wall for a ghost node beyond the faces in `beyond`: the first
-// moving face in x-, x+, y-, y+, z-, z+ order wins (edge and corner ghosts of
-// a lid layer belong to the lid).
+// Edge-profile factor of moving face `face` for a cell whose position bits
+// are `edge` (bit 2k: first node column along axis k; bit 2k+1: last, and
+// not first).
 template <typename R>
-__host__ __device__ __forceinline__ R ghost_dot(const Domain<R>& d, int beyond, int cx,
-                                       int cy, int cz) {
+__host__ __device__ __forceinline__ R edge_factor(const Domain<R>& d, int face, int edge) {
+  const int k = d.edge_axis[face] - 1;
+  if (k < 0) return R(1);
+  if ((edge >> (2 * k)) & 1) return d.edge_scale[face][0];
+  if ((edge >> (2 * k + 1)) & 1) return d.edge_scale[face][1];
+  return R(1);
+}
+
+// c . u_wall for a ghost node beyond the faces in `beyond`, seen from a cell
+// with position bits `edge`: the first moving face in x-, x+, y-, y+, z-,
+// z+ order wins (edge and corner ghosts of a lid layer belong to the lid).
+template <typename R>
+__host__ __device__ __forceinline__ R ghost_dot(const Domain<R>& d, int edge, int beyond,
+                                                int cx, int cy, int cz) {
   const int hit = beyond & d.moving;
   if (!hit) return R(0);
 #pragma unroll
   for (int face = 0; face < 6; ++face)
-    if ((hit >> face) & 1)
-      return R(cx) * d.uw[face][0] + R(cy) * d.uw[face][1] + R(cz) * d.uw[face][2];
+    if ((hit >> face) & 1) {
+      const R e = edge_factor(d, face, edge);
+      return R(cx) * (d.uw[face][0] * e) + R(cy) * (d.uw[face][1] * e) +
+             R(cz) * (d.uw[face][2] * e);
+    }
   return R(0);
 }
 
@@ -84,8 +105,13 @@ struct Links {
   int om[3], op[3];
   bool gm[3], gp[3];  // ghost beyond a wall
   bool sm[3], sp[3];  // ghost beyond a symmetry face
+  int edge;           // position bits of the cell (see edge_factor)
   bool interior;  // every neighbour is a fluid, unwrapped node: use pull/push
 };
+
+__host__ __device__ __forceinline__ int edge_bits(int v, int n, int k) {
+  return v == 0 ? 1 << (2 * k) : (v == n - 1 ? 2 << (2 * k) : 0);
+}
 
 template <typename R>
 __host__ __device__ __forceinline__ void axis_links(int v, int n, int stride, int per,
@@ -110,6 +136,7 @@ __host__ __device__ __forceinline__ Links make_links(const Domain<R>& d, int x, 
                 L.gm[1], L.gp[1], L.sm[1], L.sp[1]);
   axis_links<R>(z, d.nz, sz, d.per[2], (d.sym >> 4) & 1, (d.sym >> 5) & 1, L.om[2], L.op[2],
                 L.gm[2], L.gp[2], L.sm[2], L.sp[2]);
+  L.edge = edge_bits(x, d.nx, 0) | edge_bits(y, d.ny, 1) | edge_bits(z, d.nz, 2);
   L.interior = false;
   return L;
 }
@@ -127,6 +154,7 @@ __host__ __device__ __forceinline__ Links make_links_interior(const Domain<R>& d
   L.op[2] = sz;
   L.gm[0] = L.gp[0] = L.gm[1] = L.gp[1] = L.gm[2] = L.gp[2] = false;
   L.sm[0] = L.sp[0] = L.sm[1] = L.sp[1] = L.sm[2] = L.sp[2] = false;
+  L.edge = 0;
   L.interior = true;
   return L;
 }
@@ -140,6 +168,7 @@ __host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x
   axis_links<R>(x, d.nx, 1, d.per[0], d.sym & 1, (d.sym >> 1) & 1, L.om[0], L.op[0], L.gm[0],
                 L.gp[0], L.sm[0], L.sp[0]);
   L.sm[1] = L.sp[1] = L.sm[2] = L.sp[2] = false;
+  L.edge = edge_bits(x, d.nx, 0);
   L.om[1] = -sy;
   L.op[1] = sy;
   L.om[2] = -sz;
@@ -255,7 +284,7 @@ __host__ __device__ __forceinline__ void add_pull_wall_terms(const Domain<R>& d,
             const int faces = link_faces<Q, A, -1>(L);
             if (faces)
               fv[A] += R(6.0 * Lattice<Q>::w(A)) *
-                       ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
+                       ghost_dot(d, L.edge, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
                                  Lattice<Q>::c(A, 2));
           }(),
           ...);
@@ -330,7 +359,7 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
               const int faces = link_faces<Q, A, 1>(L);
               if (faces)
                 fv[A] -= R(6.0 * Lattice<Q>::w(A)) *
-                         ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
+                         ghost_dot(d, L.edge, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
                                    Lattice<Q>::c(A, 2));
             }(),
             ...);
@@ -480,7 +509,7 @@ __host__ __device__ __forceinline__ void put_canonical(const Domain<R>& d, S* __
             const int faces = link_faces<Q, A, -1>(L);
             if (faces)
               v -= R(6.0 * Lattice<Q>::w(A)) *
-                   ghost_dot(d, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
+                   ghost_dot(d, L.edge, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
                              Lattice<Q>::c(A, 2));
             const int idx =
                 ghost ? (A * N + i) : (opposite_mirror_rt<Q, A>(mirror) * N + i + off);

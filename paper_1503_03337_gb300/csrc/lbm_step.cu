@@ -18,8 +18,11 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
   for (int k = 0; k < 3; ++k) o.per[k] = d.per[k];
   o.moving = d.moving;
   o.sym = d.sym;
-  for (int face = 0; face < 6; ++face)
+  for (int face = 0; face < 6; ++face) {
     for (int k = 0; k < 3; ++k) o.uw[face][k] = R(d.uw[face][k]);
+    o.edge_axis[face] = d.edge_axis[face];
+    for (int k = 0; k < 2; ++k) o.edge_scale[face][k] = R(d.edge_scale[face][k]);
+  }
   o.s.sc = R(d.s[0]);
   o.s.se = R(d.s[1]);
   o.s.sq = R(d.s[2]);
@@ -51,15 +54,26 @@ const char* set_faces(DomainDesc& d, const lbm_geom* g) {
     if (lo != hi) return "opposite faces must both be periodic or neither";
     per[k] = lo ? 1 : 0;
   }
-  for (int f = 0; f < 6; ++f)
+  for (int f = 0; f < 6; ++f) {
     for (int k = 0; k < 3; ++k)
       if (!std::isfinite(g->u_wall[f][k])) return "wall velocity not finite";
+    const int k = g->edge_axis[f];
+    if (k == 0) continue;
+    if (k < 0 || k > 3) return "edge_axis must be 0 (none) or an axis + 1";
+    if (g->face[f] != LBM_MOVING_WALL) return "an edge profile needs a moving face";
+    if (k - 1 == f / 2) return "an edge profile runs along an in-plane axis of its face";
+    if (!std::isfinite(g->edge_scale[f][0]) || !std::isfinite(g->edge_scale[f][1]))
+      return "edge scale not finite";
+  }
   for (int k = 0; k < 3; ++k) d.per[k] = per[k];
   d.moving = d.sym = 0;
   for (int f = 0; f < 6; ++f) {
     if (g->face[f] == LBM_MOVING_WALL) d.moving |= 1 << f;
     if (g->face[f] == LBM_SYMMETRY) d.sym |= 1 << f;
     for (int k = 0; k < 3; ++k) d.uw[f][k] = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
+    d.edge_axis[f] = g->edge_axis[f];
+    d.edge_scale[f][0] = g->edge_axis[f] ? g->edge_scale[f][0] : 1.0;
+    d.edge_scale[f][1] = g->edge_axis[f] ? g->edge_scale[f][1] : 1.0;
   }
   return nullptr;
 }

@@ -46,6 +46,7 @@ class Case:
     init_u: Optional[np.ndarray] = None   # (3, nz, ny, nx) or None (rest)
     init_p: Optional[np.ndarray] = None   # (nz, ny, nx) or None
     rounding: int = 0             # 16-bit stores: 0 nearest, 1 stochastic
+    edge: Optional[dict] = None   # {face: (axis, scale_first, scale_last)}
 
     @property
     def cells(self) -> int:
@@ -68,13 +69,21 @@ def cavity(Q: int, n: int, Re: float, U: float = 0.05, storage: str = "f32",
                 storage=storage, u_ref=U)
 
 
-def half_cavity(Q: int, n: int, Re: float, U: float = 0.05, storage: str = "f32") -> Case:
+KU_LID_EDGE = (0.3, 1.0)  # lid velocity / U next to x = 0 and x = 1 (Sec. 4.3)
+
+
+def half_cavity(Q: int, n: int, Re: float, U: float = 0.05, storage: str = "f32",
+                ku_lid: bool = False) -> Case:
     """The z <= 1/2 half of the cavity with a symmetry face on the mid-plane
     z+ (the reduced domain of Sec. 4.3, Eq. z05symmetry): n x n x ceil(n/2)
-    nodes, so that the mirrored box is n x n x 2*ceil(n/2)."""
+    nodes, so that the mirrored box is n x n x 2*ceil(n/2).  ku_lid: the lid
+    velocity over the first and last x columns is scaled by KU_LID_EDGE (the
+    corner setting of Sec. 4.3)."""
     c = cavity(Q, n, Re, U, storage, nz=(n + 1) // 2)
     c.name = "half_cavity"
     c.faces = c.faces[:ZP] + (SYMMETRY,)
+    if ku_lid:
+        c.edge = {YP: (0,) + KU_LID_EDGE}
     return c
 
 

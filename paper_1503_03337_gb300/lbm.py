@@ -41,7 +41,8 @@ class lbm_desc(ctypes.Structure):
 
 
 class lbm_geom(ctypes.Structure):
-    _fields_ = [("face", ctypes.c_int32 * 6), ("u_wall", (ctypes.c_double * 3) * 6)]
+    _fields_ = [("face", ctypes.c_int32 * 6), ("u_wall", (ctypes.c_double * 3) * 6),
+                ("edge_axis", ctypes.c_int32 * 6), ("edge_scale", (ctypes.c_double * 2) * 6)]
 
 
 class lbm_params(ctypes.Structure):
@@ -177,17 +178,22 @@ def lbm_set_stream(h, stream):
     _check(load().lbm_set_stream(h, stream))
 
 
-def make_geom(faces, u_wall=None):
+def make_geom(faces, u_wall=None, edge=None):
+    """edge: {face: (axis, scale_first, scale_last)}, edge profiles of moving
+    faces (lbm_geom.edge_axis / edge_scale)."""
     g = lbm_geom()
     for i in range(6):
         g.face[i] = int(faces[i])
         for k in range(3):
             g.u_wall[i][k] = 0.0 if u_wall is None else float(u_wall[i][k])
+    for face, (axis, first, last) in (edge or {}).items():
+        g.edge_axis[face] = int(axis) + 1
+        g.edge_scale[face][0], g.edge_scale[face][1] = float(first), float(last)
     return g
 
 
-def lbm_set_geometry(h, faces, u_wall=None):
-    _check(load().lbm_set_geometry(h, ctypes.byref(make_geom(faces, u_wall))))
+def lbm_set_geometry(h, faces, u_wall=None, edge=None):
+    _check(load().lbm_set_geometry(h, ctypes.byref(make_geom(faces, u_wall, edge))))
 
 
 def make_params(nu=0.0, s_nu=0.0, s_c=1.0, s_e=1.19, s_q=1.2, s_pi=1.19, s_t=0.98,
@@ -276,11 +282,11 @@ def lbm_autotune(h, trials=8):
 
 
 def lbm_reductions_static(Q, nx, ny, nz, storage, faces, u_wall, params, step,
-                          populations, u_prev=None, prev_step=-1, stream=None):
+                          populations, u_prev=None, prev_step=-1, stream=None, edge=None):
     """Allocation-free FP64 reductions over caller-owned device buffers
     (populations in the storage layout of `step`, optional 3N snapshot)."""
     d = lbm_desc(Q, nx, ny, nz, STORAGE_NAMES.get(storage, storage))
-    g = make_geom(faces, u_wall)
+    g = make_geom(faces, u_wall, edge)
     s = lbm_stats()
     _check(load().lbm_reductions_static(ctypes.byref(d), ctypes.byref(g), ctypes.byref(params),
                                         int(step), _ptr(populations), _ptr(u_prev),
@@ -306,9 +312,9 @@ def lbm_batch_destroy(b):
     load().lbm_batch_destroy(b)
 
 
-def lbm_batch_add(b, Q, nx, ny, nz, storage, faces, u_wall=None, **params):
+def lbm_batch_add(b, Q, nx, ny, nz, storage, faces, u_wall=None, edge=None, **params):
     d = lbm_desc(Q, nx, ny, nz, STORAGE_NAMES.get(storage, storage))
-    g = make_geom(faces, u_wall)
+    g = make_geom(faces, u_wall, edge)
     p = make_params(**params)
     slot = ctypes.c_int32()
     _check(load().lbm_batch_add(b, ctypes.byref(d), ctypes.byref(g), ctypes.byref(p),

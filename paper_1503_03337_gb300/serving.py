@@ -75,7 +75,8 @@ class BatchBackend:
     def add(self, case: inputs.Case) -> int:
         try:
             slot = lbm.lbm_batch_add(self.b, case.Q, case.nx, case.ny, case.nz, case.storage,
-                                     case.faces, case.u_wall, nu=case.nu, force=case.force,
+                                     case.faces, case.u_wall, edge=case.edge, nu=case.nu,
+                                     force=case.force,
                                      force_period=case.period, rounding=case.rounding)
         except lbm.LBMError as e:
             if e.code == lbm.LBM_EBUSY:

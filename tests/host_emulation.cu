@@ -12,7 +12,7 @@ using namespace lbm;
 static int g_sr = 0;
 
 template <int Q, typename S, typename R>
-static void step_typed(void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
+static void step_typed(void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
                        const double* uw, const double* s, const double* F, int64_t n) {
   Domain<R> d{};
   d.f = f;
@@ -20,6 +20,11 @@ static void step_typed(void* f, int nx, int ny, int nz, const int* per, int movi
   d.N = (int64_t)nx * ny * nz;
   d.moving = moving;
   d.sym = sym;
+  for (int face = 0; face < 6; ++face) {
+    d.edge_axis[face] = eaxis ? eaxis[face] : 0;
+    d.edge_scale[face][0] = R(escale ? escale[2 * face] : 1.0);
+    d.edge_scale[face][1] = R(escale ? escale[2 * face + 1] : 1.0);
+  }
   for (int k = 0; k < 3; ++k) d.per[k] = per[k];
   for (int face = 0; face < 6; ++face)
     for (int k = 0; k < 3; ++k) d.uw[face][k] = R(uw[3 * face + k]);
@@ -53,7 +58,7 @@ static void step_typed(void* f, int nx, int ny, int nz, const int* per, int movi
 }
 
 template <int Q, typename S, typename R, bool ODD>
-static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
+static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
                             const double* uw, double* out, int to_storage) {
   Domain<R> d{};
   d.f = f;
@@ -62,6 +67,11 @@ static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int
   fill_offsets<Q>(d);
   d.moving = moving;
   d.sym = sym;
+  for (int face = 0; face < 6; ++face) {
+    d.edge_axis[face] = eaxis ? eaxis[face] : 0;
+    d.edge_scale[face][0] = R(escale ? escale[2 * face] : 1.0);
+    d.edge_scale[face][1] = R(escale ? escale[2 * face + 1] : 1.0);
+  }
   for (int k = 0; k < 3; ++k) d.per[k] = per[k];
   for (int face = 0; face < 6; ++face)
     for (int k = 0; k < 3; ++k) d.uw[face][k] = R(uw[3 * face + k]);
@@ -81,15 +91,15 @@ static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int
 }
 
 template <typename S, typename R>
-static int canon_any(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
+static int canon_any(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
                      const double* uw, double* canon, int64_t n, int to_storage) {
   const bool odd = n & 1;
   if (Q == 14) {
-    if (odd) canonical_typed<14, S, R, true>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
-    else canonical_typed<14, S, R, false>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
+    if (odd) canonical_typed<14, S, R, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
+    else canonical_typed<14, S, R, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
   } else if (Q == 18) {
-    if (odd) canonical_typed<18, S, R, true>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
-    else canonical_typed<18, S, R, false>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
+    if (odd) canonical_typed<18, S, R, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
+    else canonical_typed<18, S, R, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
   } else {
     return -1;
   }
@@ -100,42 +110,42 @@ extern "C" {
 void emu_set_stochastic(int on) { g_sr = on; }
 
 // storage: 0 double, 1 float, 2 half, 3 bfloat16
-int emu_step(int Q, int storage, void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
+int emu_step(int Q, int storage, void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
              const double* uw, const double* s, const double* F, int64_t n) {
-  if (Q == 14 && storage == 0) step_typed<14, double, double>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
-  else if (Q == 18 && storage == 0) step_typed<18, double, double>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
-  else if (Q == 14 && storage == 1) step_typed<14, float, float>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
-  else if (Q == 18 && storage == 1) step_typed<18, float, float>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
-  else if (Q == 14 && storage == 2) step_typed<14, __half, float>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
-  else if (Q == 18 && storage == 2) step_typed<18, __half, float>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
-  else if (Q == 14 && storage == 3) step_typed<14, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
-  else if (Q == 18 && storage == 3) step_typed<18, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, sym, uw, s, F, n);
+  if (Q == 14 && storage == 0) step_typed<14, double, double>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  else if (Q == 18 && storage == 0) step_typed<18, double, double>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  else if (Q == 14 && storage == 1) step_typed<14, float, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  else if (Q == 18 && storage == 1) step_typed<18, float, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  else if (Q == 14 && storage == 2) step_typed<14, __half, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  else if (Q == 18 && storage == 2) step_typed<18, __half, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  else if (Q == 14 && storage == 3) step_typed<14, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  else if (Q == 18 && storage == 3) step_typed<18, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
   else return -1;
   return 0;
 }
 
 // canonical f (FP64) <-> storage layout of parity n (double storage only)
 int emu_canonical_storage(int Q, int storage, void* f, int nx, int ny, int nz, const int* per,
-                          int moving, int sym, const double* uw, double* canon, int64_t n,
+                          int moving, int sym, const int* eaxis, const double* escale, const double* uw, double* canon, int64_t n,
                           int to_storage) {
   switch (storage) {
-    case 0: return canon_any<double, double>(Q, f, nx, ny, nz, per, moving, sym, uw, canon, n, to_storage);
-    case 1: return canon_any<float, float>(Q, f, nx, ny, nz, per, moving, sym, uw, canon, n, to_storage);
-    case 2: return canon_any<__half, float>(Q, f, nx, ny, nz, per, moving, sym, uw, canon, n, to_storage);
-    case 3: return canon_any<__nv_bfloat16, float>(Q, f, nx, ny, nz, per, moving, sym, uw, canon, n, to_storage);
+    case 0: return canon_any<double, double>(Q, f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, n, to_storage);
+    case 1: return canon_any<float, float>(Q, f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, n, to_storage);
+    case 2: return canon_any<__half, float>(Q, f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, n, to_storage);
+    case 3: return canon_any<__nv_bfloat16, float>(Q, f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, n, to_storage);
   }
   return -1;
 }
 
-int emu_canonical(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
+int emu_canonical(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
                   const double* uw, double* canon, int64_t n, int to_storage) {
   const bool odd = n & 1;
   if (Q == 14) {
-    if (odd) canonical_typed<14, double, double, true>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
-    else canonical_typed<14, double, double, false>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
+    if (odd) canonical_typed<14, double, double, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
+    else canonical_typed<14, double, double, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
   } else if (Q == 18) {
-    if (odd) canonical_typed<18, double, double, true>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
-    else canonical_typed<18, double, double, false>(f, nx, ny, nz, per, moving, sym, uw, canon, to_storage);
+    if (odd) canonical_typed<18, double, double, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
+    else canonical_typed<18, double, double, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
   } else {
     return -1;
   }

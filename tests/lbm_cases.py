@@ -7,7 +7,8 @@ from paper_1503_03337_gb300 import lbm
 
 
 def oracle_setup(case):
-    g = oracle.make_grid(case.Q, case.nx, case.ny, case.nz, case.faces, case.u_wall)
+    g = oracle.make_grid(case.Q, case.nx, case.ny, case.nz, case.faces, case.u_wall,
+                         edge=case.edge)
     r = oracle.rates(case.Q, case.s_nu)
     prm = oracle.make_params(r, force=case.force, period=case.period)
     return g, prm
@@ -27,7 +28,7 @@ def gpu_open(case, stream=None, residual_interval=0, launch=None):
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     h = lbm.lbm_create(case.Q, case.nx, case.ny, case.nz, case.storage, stream)
-    lbm.lbm_set_geometry(h, case.faces, case.u_wall)
+    lbm.lbm_set_geometry(h, case.faces, case.u_wall, case.edge)
     lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period,
                        residual_interval=residual_interval, rounding=case.rounding)
     if launch is not None:

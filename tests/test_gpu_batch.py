@@ -32,15 +32,17 @@ def mix():
         inputs.cavity(18, 20, 100.0, storage="f16"),
     ]
     cases[1].ny = 9  # a non-square duct cross-section
-    # a half cavity: symmetry face on the mid-plane z+
+    # a half cavity (symmetry face on the mid-plane z+) with the lid's
+    # corner velocities
     cases[2].faces = cases[2].faces[:5] + (inputs.SYMMETRY,)
+    cases[2].edge = {inputs.YP: (0,) + inputs.KU_LID_EDGE}
     cases[4].rounding = lbm.LBM_ROUND_STOCHASTIC
     return cases
 
 
 def add(b, c):
     return lbm.lbm_batch_add(b, c.Q, c.nx, c.ny, c.nz, c.storage, c.faces, c.u_wall,
-                             nu=c.nu, force=c.force, force_period=c.period, rounding=c.rounding)
+                             edge=c.edge, nu=c.nu, force=c.force, force_period=c.period, rounding=c.rounding)
 
 
 def batch_pops(torch, b, slot, c):

@@ -36,6 +36,15 @@ def test_rejected_calls_leave_handle_usable():
         einval(lbm.lbm_set_geometry, h, (P, W, W, W, W, W))      # opposite faces disagree
         einval(lbm.lbm_set_geometry, h, (W, W, W, W, W, 7))      # unknown face kind
         einval(lbm.lbm_set_geometry, h, (P, P, P, W, W, W))      # x fine, y disagrees
+        S, lid = lbm.LBM_SYMMETRY, (W, W, W, M, W, W)
+        einval(lbm.lbm_set_geometry, h, (P, S, W, W, W, W))      # symmetry facing periodic
+        uw = np.zeros((6, 3))
+        einval(lbm.lbm_set_geometry, h, lid, uw, {2: (0, 0.3, 1.0)})   # profile on a wall
+        einval(lbm.lbm_set_geometry, h, lid, uw, {3: (1, 0.3, 1.0)})   # along the normal
+        einval(lbm.lbm_set_geometry, h, lid, uw, {3: (3, 0.3, 1.0)})   # no such axis
+        einval(lbm.lbm_set_geometry, h, lid, uw, {3: (0, np.nan, 1.0)})
+        uw[0, 1] = np.inf
+        einval(lbm.lbm_set_geometry, h, lid, uw)                  # wall velocity not finite
         einval(lbm.lbm_set_params, h, nu=-0.1)                    # nu <= 0
         einval(lbm.lbm_set_params, h, nu=0.1, s_e=2.5)            # rate outside (0, 2)
         einval(lbm.lbm_set_params, h, nu=0.1, s_q=0.0)

@@ -223,8 +223,10 @@ def test_pair_reductions_match_fields(Q, storage, sym):
     pair sums carry about 48 bits), the maximum to 1e-13."""
     case = inputs.cavity(Q, 23, 150.0, storage=storage, ny=17, nz=11)
     case.force = (1e-5, -2e-5, 3e-5)
-    if sym:  # mirrored links on the odd steps: symmetry faces at x- and z+
+    if sym:  # mirrored links on the odd steps: symmetry faces at x- and z+;
+        # and an edge profile on the lid
         case.faces = (inputs.SYMMETRY,) + case.faces[1:5] + (inputs.SYMMETRY,)
+        case.edge = {inputs.YP: (2, 0.3, 0.7)}
     h = gpu_open(case)
     nx, ny, nz = case.nx, case.ny, case.nz
     try:

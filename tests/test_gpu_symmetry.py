@@ -1,6 +1,10 @@
-"""Symmetry (free-slip) faces on the GPU: the half cavity of Sec. 4.3 (Eq.
-z05symmetry) against the oracle's full, mirror-symmetric cavity, and the
-reduced-precision half domains against their own full boxes."""
+"""The cavity setups of Sec. 4.3 on the GPU.  Symmetry (free-slip) faces:
+the half cavity (Eq. z05symmetry) against the oracle's full, mirror-
+symmetric cavity, and the reduced-precision half domains against their own
+full boxes.  Edge profiles of moving faces (the lid corner velocities)
+against the oracle."""
+import zlib
+
 import numpy as np
 import pytest
 
@@ -77,3 +81,50 @@ def test_half_duct_with_two_symmetry_faces(Q):
     o = oracle_run(full, 400)
     assert rel_max(g["u"], o["u"][:, :, :6, :6]) <= 1e-12
     assert rel_max(g["f"], o["f"][:, :, :6, :6]) <= 1e-12
+
+
+EDGE_CASES = [
+    # (name, shape, faces, edge): a profiled lid over a half cavity, several
+    # profiled faces with symmetry faces, a one-column axis, long rows
+    ("ku_half", (9, 7, 5), (1, 1, 1, 2, 1, 3), {3: (0, 0.3, 1.0)}),
+    ("multi", (6, 5, 7), (2, 1, 1, 2, 3, 2), {3: (2, 0.2, 0.6), 0: (1, 1.5, -0.5),
+                                             5: (0, 0.0, 2.0)}),
+    ("thin", (1, 6, 4), (1, 1, 1, 2, 1, 1), {3: (0, 0.4, 0.9)}),
+    ("long_x", (67, 4, 3), (1, 1, 1, 2, 0, 0), {3: (0, 0.3, 1.0)}),
+]
+
+
+@pytest.mark.parametrize("steps", (1, 2, 37))
+@pytest.mark.parametrize("name,shape,faces,edge", EDGE_CASES)
+@pytest.mark.parametrize("Q", (14, 18))
+def test_fp64_edge_profiles(Q, name, shape, faces, edge, steps):
+    """Moving faces with edge profiles (the lid corner velocities of Sec.
+    4.3), FP64, from a seeded random state, against the oracle to 1e-12."""
+    rng = np.random.default_rng(zlib.crc32(repr((name, Q)).encode()))
+    uw = rng.normal(size=(6, 3)) * 0.03
+    case = inputs.Case(name, Q, *shape, tuple(faces), uw, nu=0.05, force=(1e-4, -2e-4, 5e-5),
+                       period=17.0, storage="f64", u_ref=0.03, edge=edge)
+    case.init_u, case.init_p = inputs.random_state(case, seed=3)
+    g, o = gpu_run(case, steps), oracle_run(case, steps)
+    assert rel_max(g["f"], o["f"]) <= 1e-12
+    assert rel_max(g["u"], o["u"]) <= 1e-12
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+def test_ku_half_cavity_fp64_and_fp32(Q):
+    """The Sec. 4.3 setup: half cavity 25 x 25 x 13, lid 0.1 with the corner
+    velocities, Re 400, 401 steps.  FP64 against the oracle to 1e-12; FP32
+    (one and two cells per thread) within 1e-5 U of it; and the profile
+    changes the flow next to the lid's first column."""
+    c64 = inputs.half_cavity(Q, 25, 400.0, U=0.1, storage="f64", ku_lid=True)
+    g = gpu_run(c64, 401)
+    o = oracle_run(c64, 401)
+    assert rel_max(g["f"], o["f"]) <= 1e-12
+    assert rel_max(g["u"], o["u"]) <= 1e-12
+    for launch in ((64, 1, 1), (64, 2, 2)):
+        c32 = inputs.half_cavity(Q, 25, 400.0, U=0.1, storage="f32", ku_lid=True)
+        g32 = gpu_run(c32, 401, launch=launch)
+        assert np.max(np.abs(g32["u"] - o["u"])) <= 1e-5 * c32.u_ref
+    plain = gpu_run(inputs.half_cavity(Q, 25, 400.0, U=0.1, storage="f64"), 401)
+    d = np.abs(plain["u"][0, :, -1, 0] - g["u"][0, :, -1, 0])
+    assert np.min(d) > 1e-3 * c64.u_ref

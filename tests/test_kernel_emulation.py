@@ -32,10 +32,11 @@ def emu():
     L = ctypes.CDLL(lib)
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
     L.emu_step.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
-                           ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                           ctypes.c_int, ip, ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp,
                            ctypes.c_int64]
     L.emu_canonical.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip,
-                                ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int64, ctypes.c_int]
+                                ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, ctypes.c_int64,
+                                ctypes.c_int]
     L.emu_collide.argtypes = [ctypes.c_int, dp, dp, dp]
     return L
 
@@ -64,6 +65,11 @@ class EmuDomain:
                             dtype=np.int32)
         self.moving = sum(1 << f for f in range(6) if case.faces[f] == inputs.MOVING_WALL)
         self.sym = sum(1 << f for f in range(6) if case.faces[f] == inputs.SYMMETRY)
+        self.eaxis = np.zeros(6, dtype=np.int32)
+        self.escale = np.ones((6, 2))
+        for face, (axis, first, last) in (case.edge or {}).items():
+            self.eaxis[face] = axis + 1
+            self.escale[face] = (first, last)
         self.uw = np.ascontiguousarray(
             np.where(np.array(case.faces)[:, None] == inputs.MOVING_WALL, case.u_wall, 0.0))
         s = oracle.rates(case.Q, case.s_nu)
@@ -71,21 +77,24 @@ class EmuDomain:
         self.A = np.zeros((case.Q, case.nz, case.ny, case.nx))
         self.n = 0
 
-    def _ip(self):
-        return self.per.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    def _geom(self):
+        """per, moving, sym, edge axes, edge scales, wall velocities"""
+        return (self.per.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), self.moving, self.sym,
+                self.eaxis.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(self.escale),
+                _d(self.uw))
 
     def put(self, f, n):
         self.n = n
         c = self.case
         canon = np.ascontiguousarray(f, dtype=np.float64)
-        assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
-                                      self.moving, self.sym, _d(self.uw), _d(canon), n, 1) == 0
+        assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, *self._geom(),
+                                      _d(canon), n, 1) == 0
 
     def get(self):
         c = self.case
         out = np.zeros_like(self.A)
-        assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
-                                      self.moving, self.sym, _d(self.uw), _d(out), self.n, 0) == 0
+        assert self.emu.emu_canonical(c.Q, self.A.ctypes.data, c.nx, c.ny, c.nz, *self._geom(),
+                                      _d(out), self.n, 0) == 0
         return out
 
     def step(self, k):
@@ -93,39 +102,47 @@ class EmuDomain:
         for _ in range(k):
             amp = np.cos(2 * np.pi * self.n / c.period) if c.period > 0 else 1.0
             F = np.array(c.force, dtype=np.float64) * amp
-            assert self.emu.emu_step(c.Q, 0, self.A.ctypes.data, c.nx, c.ny, c.nz, self._ip(),
-                                     self.moving, self.sym, _d(self.uw), _d(self.s), _d(F), self.n) == 0
+            assert self.emu.emu_step(c.Q, 0, self.A.ctypes.data, c.nx, c.ny, c.nz, *self._geom(),
+                                     _d(self.s), _d(F), self.n) == 0
             self.n += 1
 
 
 EDGE = [
-    ("ragged", (13, 7, 5), (1, 2, 0, 0, 2, 1)),
-    ("periodic", (6, 5, 4), (0, 0, 0, 0, 0, 0)),
-    ("thin_x_periodic", (1, 6, 5), (0, 0, 1, 2, 1, 1)),
-    ("thin_x_walls", (1, 4, 3), (1, 1, 2, 1, 0, 0)),
-    ("two_cells", (2, 2, 2), (2, 2, 2, 2, 2, 2)),
-    ("lid", (5, 6, 4), (1, 1, 1, 2, 1, 1)),
+    ("ragged", (13, 7, 5), (1, 2, 0, 0, 2, 1), None),
+    ("periodic", (6, 5, 4), (0, 0, 0, 0, 0, 0), None),
+    ("thin_x_periodic", (1, 6, 5), (0, 0, 1, 2, 1, 1), None),
+    ("thin_x_walls", (1, 4, 3), (1, 1, 2, 1, 0, 0), None),
+    ("two_cells", (2, 2, 2), (2, 2, 2, 2, 2, 2), None),
+    ("lid", (5, 6, 4), (1, 1, 1, 2, 1, 1), None),
     # wide enough for whole 32-cell x-ranges away from the x faces, which
     # take the interior offset tables
-    ("wide_x", (70, 4, 3), (1, 2, 1, 2, 0, 0)),
+    ("wide_x", (70, 4, 3), (1, 2, 1, 2, 0, 0), None),
     # symmetry faces (3): against walls, moving walls and each other, on
     # thin axes, and on the x faces of 32-cell x-ranges
-    ("sym_lid", (5, 6, 4), (1, 3, 1, 2, 3, 1)),
-    ("sym_corner", (4, 5, 6), (3, 1, 3, 2, 1, 3)),
-    ("sym_periodic", (6, 4, 5), (0, 0, 3, 3, 2, 1)),
-    ("sym_thin", (1, 5, 2), (3, 3, 2, 3, 3, 1)),
-    ("sym_wide_x", (70, 3, 4), (3, 2, 1, 3, 0, 0)),
+    ("sym_lid", (5, 6, 4), (1, 3, 1, 2, 3, 1), None),
+    ("sym_corner", (4, 5, 6), (3, 1, 3, 2, 1, 3), None),
+    ("sym_periodic", (6, 4, 5), (0, 0, 3, 3, 2, 1), None),
+    ("sym_thin", (1, 5, 2), (3, 3, 2, 3, 3, 1), None),
+    ("sym_wide_x", (70, 3, 4), (3, 2, 1, 3, 0, 0), None),
+    # edge profiles of moving faces (the lid corner velocities of Sec. 4.3),
+    # with symmetry faces, on thin axes and on long rows
+    ("edge_lid", (5, 6, 4), (1, 1, 1, 2, 1, 3), {3: (0, 0.3, 1.0)}),
+    ("edge_multi", (4, 3, 5), (2, 1, 1, 2, 3, 2), {3: (2, 0.2, 0.6), 0: (1, 1.5, -0.5),
+                                                   5: (0, 0.0, 2.0)}),
+    ("edge_thin", (1, 4, 3), (1, 1, 1, 2, 1, 1), {3: (0, 0.4, 0.9)}),
+    ("edge_wide_x", (70, 3, 4), (1, 1, 1, 2, 0, 0), {3: (0, 0.3, 1.0)}),
 ]
 
 
 @pytest.mark.parametrize("Q", (14, 18))
-@pytest.mark.parametrize("name,shape,faces", EDGE)
-def test_step_matches_oracle(emu, Q, name, shape, faces):
+@pytest.mark.parametrize("name,shape,faces,edge", EDGE)
+def test_step_matches_oracle(emu, Q, name, shape, faces, edge):
     rng = np.random.default_rng(5)
     uw = rng.normal(size=(6, 3)) * 0.03
     case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
-                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64")
-    g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw)
+                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64",
+                       edge=edge)
+    g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw, edge=edge)
     prm = oracle.make_params(oracle.rates(Q, case.s_nu), force=case.force, period=case.period)
     u0, p0 = inputs.random_state(case, seed=2)
     f0 = oracle.init_equilibrium(g, u0, p0)

@@ -106,6 +106,23 @@ def test_mass_conserved_with_walls(Q):
 
 
 @pytest.mark.parametrize("Q", (14, 18))
+def test_mass_conserved_with_profiled_lid(Q):
+    """A tangential lid whose velocity is scaled in its first and last
+    columns (reading G15: the scale belongs to the cell, so every link of a
+    cell sees one wall velocity) still conserves sum_x P exactly."""
+    rng = np.random.default_rng(13)
+    u_wall = np.zeros((6, 3))
+    u_wall[3] = (0.08, 0.0, 0.03)
+    g = oracle.make_grid(Q, 6, 5, 4, faces=(W, W, W, M, S, W), u_wall=u_wall,
+                         edge={3: (0, 0.3, 1.7)})
+    prm = oracle.make_params(oracle.rates(Q, 1.3))
+    f = 0.02 + 0.01 * rng.normal(size=(Q, 4, 5, 6))
+    m0 = f.sum()
+    f = oracle.run(g, prm, f, 0, 200, nthreads=1)
+    assert abs(f.sum() - m0) < 1e-12 * abs(m0)
+
+
+@pytest.mark.parametrize("Q", (14, 18))
 def test_rest_stays_at_rest(Q):
     g = oracle.make_grid(Q, 4, 5, 3, faces=(W, W, W, W, W, W))
     prm = oracle.make_params(oracle.rates(Q, 1.1))
