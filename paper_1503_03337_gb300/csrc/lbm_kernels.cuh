@@ -180,8 +180,9 @@ __host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x
 
 // Offset, wall-ghost flag and mirror axes (bit k: the link crosses a
 // symmetry face normal to axis k) of the node x + s*c_A (s = -1: pull
-// source, +1: push target).
-template <int Q, int A, int SIGN>
+// source, +1: push target).  SYM = false: the domain has no symmetry face
+// (mirror stays 0 and the mirrored indexing folds away).
+template <int Q, int A, int SIGN, bool SYM = true>
 __host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool& ghost,
                                                  int& mirror) {
   off = 0;
@@ -193,11 +194,11 @@ __host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool&
     if (c < 0) {
       off += L.om[k];
       ghost = ghost || L.gm[k];
-      if (L.sm[k]) mirror |= 1 << k;
+      if (SYM && L.sm[k]) mirror |= 1 << k;
     } else if (c > 0) {
       off += L.op[k];
       ghost = ghost || L.gp[k];
-      if (L.sp[k]) mirror |= 1 << k;
+      if (SYM && L.sp[k]) mirror |= 1 << k;
     }
   }
 }
@@ -292,8 +293,9 @@ __host__ __device__ __forceinline__ void add_pull_wall_terms(const Domain<R>& d,
   }
 }
 
-// Pre-collision populations f^n of cell i into fv (CG: L2-only loads).
-template <int Q, typename S, typename R, bool ODD, bool CG = false>
+// Pre-collision populations f^n of cell i into fv (CG: L2-only loads; SYM:
+// the domain may have symmetry faces).
+template <int Q, typename S, typename R, bool ODD, bool CG = false, bool SYM = true>
 __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
                                                 int i, const Links& L, R* fv) {
   const int N = (int)d.N;
@@ -314,7 +316,7 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
           [&] {
             int off, mirror;
             bool ghost;
-            link_of<Q, A, -1>(L, off, ghost, mirror);
+            link_of<Q, A, -1, SYM>(L, off, ghost, mirror);
             const int idx =
                 ghost ? (A * N + i) : (opposite_mirror_rt<Q, A>(mirror) * N + i + off);
             fv[A] = load_pop<S, R, CG>(f + idx);
@@ -336,8 +338,8 @@ __host__ __device__ __forceinline__ void put(S* p, R v, uint32_t h) {
 }
 
 // Post-collision populations f* of cell i from fv into storage (`key`: the
-// step's stochastic-rounding key).
-template <int Q, typename S, typename R, bool ODD, bool SR = false>
+// step's stochastic-rounding key; SYM as in gather).
+template <int Q, typename S, typename R, bool ODD, bool SR = false, bool SYM = true>
 __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
                                                  int i, const Links& L, R* fv, uint32_t key) {
   const int N = (int)d.N;
@@ -373,7 +375,7 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
           [&] {
             int off, mirror;
             bool ghost;
-            link_of<Q, A, 1>(L, off, ghost, mirror);
+            link_of<Q, A, 1, SYM>(L, off, ghost, mirror);
             const int idx =
                 ghost ? (opposite<Q>(A) * N + i) : (mirror_rt<Q, A>(mirror) * N + i + off);
             put<S, R, SR, A>(f + idx, fv[A], h);
@@ -383,23 +385,26 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
   }
 }
 
-template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR, bool CG = false>
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR, bool CG = false,
+          bool SYM = true>
 __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
                                                            S* __restrict__ f, int i,
                                                            const Links& L, const R* F,
                                                            const uint32_t* key) {
   R fv[Q];
-  gather<Q, S, R, ODD, CG>(d, f, i, L, fv);
+  gather<Q, S, R, ODD, CG, SYM>(d, f, i, L, fv);
   R ux, uy, uz;
   collide<Q, FORCE>(fv, d.s, F[0], F[1], F[2], ux, uy, uz);
-  scatter<Q, S, R, ODD, SR>(d, f, i, L, fv, SR ? *key : 0u);
+  scatter<Q, S, R, ODD, SR, SYM>(d, f, i, L, fv, SR ? *key : 0u);
 }
 
 // The whole fused update of one cell: gather (stream), collide, scatter.
 // Odd steps pick one of three addressing variants.  `x_lo`..`x_hi` is the
 // x-range of the calling warp: when a warp lies within one x-row (block
 // width a multiple of 32) every test below is uniform across the warp, so
-// the variants never diverge inside a warp.
+// the variants never diverge inside a warp.  The two boundary variants come
+// with and without the mirrored links of symmetry faces (d.sym is uniform
+// across the grid), so domains without one pay nothing for them.
 // update_cell_at reads the step's body force F[0..2] and rounding key *key
 // where they are used (F and key may live outside the descriptor);
 // update_cell takes them from the descriptor.
@@ -417,10 +422,18 @@ __host__ __device__ __forceinline__ void update_cell_at(const Domain<R>& d, S* _
       if (x_lo > 0 && x_hi < d.nx - 1)
         update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_interior(d), F,
                                                         key);
+      else if (d.sym)
+        update_with_links<Q, S, R, true, FORCE, SR, CG, true>(d, f, i, make_links_x(d, x), F,
+                                                              key);
       else
-        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_x(d, x), F, key);
+        update_with_links<Q, S, R, true, FORCE, SR, CG, false>(d, f, i, make_links_x(d, x), F,
+                                                               key);
+    } else if (d.sym) {
+      update_with_links<Q, S, R, true, FORCE, SR, CG, true>(d, f, i, make_links(d, x, y, z), F,
+                                                            key);
     } else {
-      update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links(d, x, y, z), F, key);
+      update_with_links<Q, S, R, true, FORCE, SR, CG, false>(d, f, i, make_links(d, x, y, z), F,
+                                                             key);
     }
   }
 }

@@ -5,7 +5,8 @@ nu = U L / Re (tau = 0.5091), 50000 steps of the fused FP32 step with the
 18-velocity model: every velocity stays finite and bounded by the lid speed
 scale, and the lid drives the primary vortex.  (With the halfway
 bounce-back walls used here the 14-velocity model diverges on this case;
-the paper's runs use its non-equilibrium extrapolation boundaries.)"""
+the paper's runs use its non-equilibrium extrapolation boundaries.)  And
+the half cavity of Sec. 4.3 at the paper's grid: MRT stable, LBGK not."""
 import numpy as np
 import pytest
 
@@ -43,3 +44,42 @@ def test_cavity_re3200_q18_stays_finite():
     assert np.max(np.abs(u)) < 1.5 * U
     # the lid drives a primary vortex: return flow along -x below the lid
     assert u[0, n // 2, n // 4, n // 2] < 0.0
+
+
+def run_until_unstable(case, steps, rates=None):
+    """Step in blocks of 1000 with the FP64 residual cadence; the step at
+    which a reduction first reports non-finite values, or None."""
+    h = gpu_open(case, residual_interval=1000)
+    try:
+        if rates is not None:
+            lbm.lbm_set_params(h, nu=case.nu, residual_interval=1000, **rates)
+        lbm.lbm_init_equilibrium(h)
+        for k in range(0, steps, 1000):
+            try:
+                lbm.lbm_step(h, 1000)
+                stats = lbm.lbm_reductions(h)
+            except lbm.LBMError as e:
+                assert e.code == lbm.LBM_EUNSTABLE, e
+                return k + 1000
+            if stats.nonfinite:
+                return k + 1000
+        u = lbm.read_u(h, case.nx, case.ny, case.nz)
+        assert np.all(np.isfinite(u)) and np.max(np.abs(u)) < 1.5 * case.u_ref
+        return None
+    finally:
+        lbm.lbm_destroy(h)
+
+
+def test_half_cavity_re3200_mrt_stable_lbgk_not():
+    """Sec. 4.3's stability comparison on its grid: the 97 x 97 x 49 half
+    cavity (symmetry face at z = 1/2, lid 0.1 with the corner velocities),
+    Re 3200, 50000 steps, 18-velocity model in FP32.  The MRT collision
+    stays finite; with every rate set to 1/tau (the LBGK special case of the
+    same model) the run diverges within the first few thousand steps."""
+    case = inputs.half_cavity(18, 97, 3200.0, U=0.1, storage="f32", ku_lid=True)
+    assert (case.nx, case.ny, case.nz) == (97, 97, 49)
+    assert run_until_unstable(case, 50000) is None
+    s = 1.0 / (3.0 * case.nu + 0.5)
+    lbgk = dict(s_c=s, s_e=s, s_q=s, s_pi=s, s_t=s)
+    div = run_until_unstable(case, 50000, rates=lbgk)
+    assert div is not None and div <= 5000, div
