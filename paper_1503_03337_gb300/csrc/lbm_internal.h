@@ -38,11 +38,17 @@ struct DomainDesc {
 
 struct BlockShape {
   int bx, by;
-  int cpt;      // cells per thread: 1, or 2 (pairs along x, FP32 arithmetic only)
+  int cpt;      // cells per thread: 1, 2 (pairs along x, FP32 arithmetic only), or
+                // 3 (row-staged through shared memory, lbm_staged.cuh)
   int pdl = 1;  // programmatic dependent launch of consecutive steps
 };
 
 BlockShape default_block(int nx, int ny);
+
+// Device view of the process-wide flag the row-staged kernel sets when a
+// wait for its bulk loads runs out (host-mapped memory), and its host value.
+int* stage_error_device();
+int stage_error_pending();
 
 // The face fields of d (per, moving, sym, uw) from a geometry.  Returns
 // nullptr, or the reason the geometry is invalid (then d is unchanged).

@@ -8,6 +8,7 @@
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 #include "lbm_launch.cuh"
+#include "lbm_staged.cuh"
 
 namespace lbm {
 
@@ -50,12 +51,107 @@ void launch_one(void (*kernel)(Domain<R>), const Domain<R>& d, dim3 grid, dim3 b
   launch_pdl(kernel, grid, block, pdl, st, d);
 }
 
+// Can the row-staged kernel run this domain?  Every bulk copy must start on
+// a 16-byte boundary and span a multiple of 16 bytes.
+inline bool stage_fits(const Domain<float>& d) {
+  return d.nx % 8 == 0 && d.nx >= 24 && reinterpret_cast<uintptr_t>(d.f) % 16 == 0;
+}
+
+// Units, segment length and per-cell work of one step of the row-staged
+// kernel (see lbm_staged.cuh).
+inline StagePlan stage_plan(const Domain<float>& d, bool odd) {
+  StagePlan p{};
+  int64_t rows;
+  if (!odd) {
+    p.x0 = 0;
+    p.xlen = d.nx;
+    p.row_lo = 0;
+    p.rows_y = d.ny;
+    rows = (int64_t)d.ny * d.nz;
+    p.general = 0;
+  } else {
+    const int iy = d.ny > 2 ? d.ny - 2 : 0, iz = d.nz > 2 ? d.nz - 2 : 0;
+    p.x0 = kStagePad;
+    p.xlen = d.nx - 2 * kStagePad;
+    p.row_lo = 1;
+    p.rows_y = iy > 0 ? iy : 1;
+    rows = (int64_t)iy * iz;
+    const int nzp = d.nz > 1 ? 2 : 1, nyp = d.ny > 1 ? 2 : 1;
+    const int64_t boundary_rows = (int64_t)nzp * d.ny + (int64_t)(d.nz > 2 ? d.nz - 2 : 0) * nyp;
+    p.general = rows * 2 * kStagePad + boundary_rows * d.nx;
+  }
+  // balanced segments of at most kStageSeg cells, each a multiple of 8
+  p.nseg = (p.xlen + kStageSeg - 1) / kStageSeg;
+  p.seg = ((p.xlen + p.nseg - 1) / p.nseg + 7) / 8 * 8;
+  p.nseg = (p.xlen + p.seg - 1) / p.seg;
+  p.units = rows * p.nseg;
+  p.error = stage_error_device();
+  return p;
+}
+
+template <int Q, typename S, bool ODD, bool FORCE>
+void launch_staged_kernel(const Domain<float>& d, const StagePlan& p, bool pdl, cudaStream_t st) {
+  auto kernel = k_step_staged<Q, S, ODD, FORCE>;
+  const int threads = ((p.seg / 2 + 31) / 32) * 32;
+  const size_t smem = stage_smem_bytes<Q, S>(p.seg);
+  static int per_sm[kStageSeg / 2 / 32 + 1] = {};  // resident CTAs per SM, by warps per CTA
+  static int sms = 0;
+  int& nb = per_sm[threads / 32];
+  if (nb == 0) {
+    // full-size buffers, so one answer serves every segment length
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads,
+                                                      stage_smem_bytes<Q, S>(kStageSeg)) !=
+            cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  int64_t want = p.units;
+  const int64_t general_ctas = (p.general + threads - 1) / threads;
+  if (want < general_ctas) want = general_ctas;
+  int64_t grid = (int64_t)nb * sms;
+  if (grid > want) grid = want;
+  if (grid < 1) grid = 1;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, d, p);
+}
+
+template <int Q, typename S>
+void launch_staged(const Domain<float>& d, bool odd, bool force, bool pdl, cudaStream_t st) {
+  const StagePlan p = stage_plan(d, odd);
+  if (odd) {
+    if (force) launch_staged_kernel<Q, S, true, true>(d, p, pdl, st);
+    else launch_staged_kernel<Q, S, true, false>(d, p, pdl, st);
+  } else {
+    if (force) launch_staged_kernel<Q, S, false, true>(d, p, pdl, st);
+    else launch_staged_kernel<Q, S, false, false>(d, p, pdl, st);
+  }
+}
+
 template <int Q, typename S, typename R, bool SR>
 void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 block,
                           const BlockShape& b, cudaStream_t st) {
-  // two cells per thread: even steps of FP32 / FP16 / BF16 storage with nx
-  // even and rounding to nearest; every other step runs one cell per thread
+  // row-staged (cells_per_thread 3): FP32 / FP16 / BF16 storage, rounding to
+  // nearest, nx a multiple of 8 and >= 24.  Two cells per thread: even steps
+  // of FP32 / FP16 / BF16 storage with nx even and rounding to nearest.
+  // Every other step runs one cell per thread.
   if constexpr (sizeof(S) <= 4 && !SR) {
+    if (b.cpt == 3 && stage_fits(d)) {
+      launch_staged<Q, S>(d, odd, force, b.pdl != 0, st);
+      return;
+    }
     if (b.cpt == 2 && !odd && d.nx % 2 == 0) {
       grid.x = (d.nx / 2 + block.x - 1) / block.x;
       if (force) launch_one(k_step_pair<Q, S, true>, d, grid, block, b.pdl != 0, st);
