@@ -232,7 +232,7 @@ typedef struct lbm_launch {
                                population array between HBM and shared
                                memory with bulk asynchronous copies (double
                                buffered) and update x-adjacent pairs there;
-                               needs nx a multiple of 8 and >= 24 and
+                               needs nx a multiple of 8 and >= 16 and
                                rounding to nearest, else the step runs one
                                cell per thread; bx, by are not used.  2 and
                                3 are not for FP64 storage.                   */

@@ -506,7 +506,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
     b.pdl = h->block.pdl;
     if (b.bx * b.cpt > xmax && b.bx > 32) continue;
     if (b.cpt >= 2 && h->d.storage == LBM_STORAGE_F64) continue;
-    if (b.cpt == 3 && (h->d.nx % 8 != 0 || h->d.nx < 24)) continue;  // falls back: same as 1
+    if (b.cpt == 3 && (h->d.nx % 8 != 0 || h->d.nx < 16)) continue;  // falls back: same as 1
     int64_t n = n0;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->d, n++, b, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);

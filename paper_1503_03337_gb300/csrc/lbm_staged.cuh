@@ -1,34 +1,33 @@
 // Row-staged step for FP32 / FP16 / BF16 storage (FP32 arithmetic).
 //
-// A unit of work is one segment of up to kStageSeg cells of one x-row.  For
-// every population array b the CTA copies, with one bulk copy, the part of
-// row b that the segment's cells read (and later write) into shared memory,
-// updates the cells there in place, two x-adjacent cells per thread in
-// packed FP32x2, and copies the part back with one bulk store.  Two buffers
-// alternate, so the next unit's loads are in flight while the current unit
-// collides; one thread issues all copies, so the bytes in flight per SM do
-// not depend on how many warps are resident.
+// A unit of work is one segment of one x-row.  For every population array b
+// the CTA copies, with one bulk copy, the part of row b that the segment's
+// cells read (and later write) into shared memory, updates the cells there
+// in place, two x-adjacent cells per thread in packed FP32x2, and copies the
+// part back with one bulk store.  A ring of buffers keeps the loads of the
+// next units in flight while the current unit collides; one thread issues
+// all copies, so the bytes in flight per SM do not depend on how many warps
+// are resident.
 //
 // Even steps (no neighbour access) stage every row, x = 0..nx-1, and need no
 // links.  Odd steps pull f_a(x) from slot abar of x - c_a and push f*_a to
 // slot a of x + c_a: array b is read and written at x + c_b for the same
 // cells, so the region staged for b is the segment shifted by c_b (the rows
-// y + c_by, z + c_bz, and one element along x, covered by an aligned
-// superset 8 elements wider).  Only interior rows are staged on odd steps,
-// and in them x = 8..nx-9, so that no staged cell has a wall, wrap or mirror
-// link; the other cells (boundary rows and the first and last 8 cells of
+// y + c_by, z + c_bz, and one element along x, covered by the aligned
+// superset on the 8-element grid).  Only interior rows are staged on odd
+// steps, and in them x = 1..nx-2, so that no staged cell has a wall, wrap or
+// mirror link; the other cells (boundary rows and the ends x = 0, nx-1 of
 // interior rows) take the per-cell path of update_cell_at in the same
-// launch.  The write region of an array with c_bx = +-1 starts or ends one
-// element off the 16-byte grid: its aligned middle goes out in the bulk
-// store and its 8 ragged end elements as plain stores.
+// launch.  A write region that starts or ends off the 16-byte grid goes out
+// as a bulk store of its aligned middle and plain stores of its ends.
 //
 // Cells only touch their own slots (the AA property), so the partition into
 // staged and per-cell cells needs no ordering, and the superset loads may
 // read slots owned by other cells (never used) while those are rewritten.
 //
-// Requirements (checked by stage_plan): nx a multiple of 8 and >= 24, every
-// copy address and size a multiple of 16 bytes (nx % 8 == 0 and the
-// population buffer 16-byte aligned make them so).
+// Requirements (stage_fits): nx a multiple of 8 and >= 16 and the population
+// buffer 16-byte aligned; then every copy address and size is a multiple of
+// 16 bytes.
 #pragma once
 
 #include <cstring>
@@ -39,16 +38,19 @@
 
 namespace lbm {
 
-constexpr int kStageSeg = 256;  // cells per segment at most (two per thread)
-constexpr int kStagePad = 8;    // elements of margin on each side of a buffer row
+constexpr int kStageSeg = 256;      // cells per segment at most (two per thread)
+constexpr int kStagePad = 8;        // elements of margin on each side of a buffer row
+constexpr int kStageMaxStages = 4;  // buffers in the ring
 constexpr uint64_t kStageWaitNs = 2000000000ull;  // bounded wait for a unit's loads
 
 struct StagePlan {
-  int seg;         // cells per segment (a multiple of 8, <= kStageSeg)
+  int seg;         // cells per segment (a multiple of 8, <= kStageSeg); segment j
+                   // of a row spans [j*seg, (j+1)*seg) clipped to the staged range
   int x0, xlen;    // staged x-range of a staged row: [x0, x0 + xlen)
   int nseg;        // segments per staged row
   int row_lo;      // 0 (even: every row) or 1 (odd: interior rows)
   int rows_y;      // staged rows per z-plane (ny or ny - 2)
+  int stages;      // buffers in the ring (2..kStageMaxStages)
   int64_t units;   // staged rows * nseg
   int64_t general; // cells of the per-cell path (odd steps)
   int* error;      // host-mapped flag, set when a unit's loads time out
@@ -58,16 +60,8 @@ struct StagePlan {
 __host__ __device__ constexpr int stage_row_len(int seg) { return seg + 2 * kStagePad; }
 
 template <int Q, typename S>
-__host__ __device__ constexpr size_t stage_smem_bytes(int seg) {
-  return 2 * (size_t)Q * stage_row_len(seg) * sizeof(S);
-}
-
-// Number of populations with c_x != 0 (their write regions have ragged ends).
-template <int Q>
-__host__ __device__ constexpr int num_x_movers() {
-  int n = 0;
-  for (int a = 0; a < Q; ++a) n += Lattice<Q>::c(a, 0) != 0;
-  return n;
+__host__ __device__ constexpr size_t stage_smem_bytes(int seg, int stages) {
+  return (size_t)stages * Q * stage_row_len(seg) * sizeof(S);
 }
 
 // The pair of values at element k of a staged row (MIS: k is odd, the pair
@@ -123,17 +117,39 @@ __device__ __forceinline__ void stage_row(const StagePlan& p, int64_t r, int& y,
   z = p.row_lo + (int)(r / p.rows_y);
 }
 
-// Thread 0: the loads of unit u into buf, announced on bar.
+__host__ __device__ __forceinline__ int floor8(int v) { return v & ~7; }
+__host__ __device__ __forceinline__ int ceil8(int v) { return (v + 7) & ~7; }
+
+// Unit u: its row, the aligned base xb of its segment, and its staged cells
+// [xa, xa + len).  Element x of a staged array row sits at buffer index
+// x - xb + kStagePad.
+struct StageUnit {
+  int y, z, xb, xa, len;
+};
+
+__device__ __forceinline__ StageUnit stage_unit(const StagePlan& p, int nx, int64_t u) {
+  StageUnit s;
+  stage_row(p, u / p.nseg, s.y, s.z);
+  s.xb = (int)(u % p.nseg) * p.seg;
+  s.xa = max(s.xb, p.x0);
+  s.len = min(s.xb + p.seg, p.x0 + p.xlen) - s.xa;
+  return s;
+}
+
+// Thread 0: the loads of unit u into buf, announced on bar.  Array b is
+// staged over the aligned superset of [xa + c, xa + len + c), c its shift.
 template <int Q, typename S, bool ODD>
 __device__ __forceinline__ void stage_issue_loads(const Domain<float>& d, const StagePlan& p,
                                                   int64_t u, S* buf, uint64_t* bar) {
   const int L = stage_row_len(p.seg);
-  int y, z;
-  stage_row(p, u / p.nseg, y, z);
-  const int xa = p.x0 + (int)(u % p.nseg) * p.seg;
-  const int len = min(p.seg, p.x0 + p.xlen - xa);
-  constexpr int wide = ODD ? num_x_movers<Q>() : 0;  // arrays loaded 8 elements wider
-  mbar_arrive_expect_tx(bar, (uint32_t)((Q * len + wide * kStagePad) * sizeof(S)));
+  const StageUnit t = stage_unit(p, d.nx, u);
+  int elems = 0;
+  [&]<int... B>(std::integer_sequence<int, B...>) {
+    ((elems += ceil8(t.xa + t.len + (ODD ? Lattice<Q>::c(B, 0) : 0)) -
+               floor8(t.xa + (ODD ? Lattice<Q>::c(B, 0) : 0))),
+     ...);
+  }(std::make_integer_sequence<int, Q>{});
+  mbar_arrive_expect_tx(bar, (uint32_t)(elems * sizeof(S)));
   const S* f = static_cast<const S*>(d.f);
   [&]<int... B>(std::integer_sequence<int, B...>) {
     (
@@ -141,27 +157,23 @@ __device__ __forceinline__ void stage_issue_loads(const Domain<float>& d, const 
           constexpr int cx = ODD ? Lattice<Q>::c(B, 0) : 0;
           constexpr int cy = ODD ? Lattice<Q>::c(B, 1) : 0;
           constexpr int cz = ODD ? Lattice<Q>::c(B, 2) : 0;
-          const int64_t row = ((int64_t)(z + cz) * d.ny + (y + cy)) * d.nx;
-          const int src_x = cx < 0 ? xa - kStagePad : xa;
-          const int dst = cx < 0 ? 0 : kStagePad;
-          const int n = len + (cx != 0 ? kStagePad : 0);
-          bulk_load(buf + B * L + dst, f + (int64_t)B * d.N + row + src_x,
-                    (uint32_t)(n * sizeof(S)), bar);
+          const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
+          const int lo = floor8(t.xa + cx), hi = ceil8(t.xa + t.len + cx);
+          bulk_load(buf + B * L + (lo - t.xb + kStagePad), f + (int64_t)B * d.N + row + lo,
+                    (uint32_t)((hi - lo) * sizeof(S)), bar);
         }(),
         ...);
   }(std::make_integer_sequence<int, Q>{});
 }
 
-// Thread 0: the bulk stores of unit u from buf (odd steps: the aligned part
-// of each write region).
+// Thread 0: the bulk stores of unit u from buf, the aligned middle
+// [ceil8(xa + c), floor8(xa + len + c)) of each write region (when it is
+// not empty).
 template <int Q, typename S, bool ODD>
 __device__ __forceinline__ void stage_issue_stores(const Domain<float>& d, const StagePlan& p,
                                                    int64_t u, const S* buf) {
   const int L = stage_row_len(p.seg);
-  int y, z;
-  stage_row(p, u / p.nseg, y, z);
-  const int xa = p.x0 + (int)(u % p.nseg) * p.seg;
-  const int len = min(p.seg, p.x0 + p.xlen - xa);
+  const StageUnit t = stage_unit(p, d.nx, u);
   S* f = static_cast<S*>(d.f);
   [&]<int... A>(std::integer_sequence<int, A...>) {
     (
@@ -169,49 +181,41 @@ __device__ __forceinline__ void stage_issue_stores(const Domain<float>& d, const
           constexpr int cx = ODD ? Lattice<Q>::c(A, 0) : 0;
           constexpr int cy = ODD ? Lattice<Q>::c(A, 1) : 0;
           constexpr int cz = ODD ? Lattice<Q>::c(A, 2) : 0;
-          const int64_t row = ((int64_t)(z + cz) * d.ny + (y + cy)) * d.nx;
-          // aligned part: cx = 0 all of [xa, xa+len); +1 [xa+8, xa+len);
-          // -1 [xa, xa+len-8)
-          const int x_first = cx > 0 ? xa + kStagePad : xa;
-          const int n = len - (cx != 0 ? kStagePad : 0);
-          if (n > 0)
-            bulk_store(f + (int64_t)A * d.N + row + x_first,
-                       buf + A * L + (x_first - xa + kStagePad), (uint32_t)(n * sizeof(S)));
+          const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
+          const int a0 = ceil8(t.xa + cx), a1 = floor8(t.xa + t.len + cx);
+          if (a1 > a0)
+            bulk_store(f + (int64_t)A * d.N + row + a0, buf + A * L + (a0 - t.xb + kStagePad),
+                       (uint32_t)((a1 - a0) * sizeof(S)));
         }(),
         ...);
   }(std::make_integer_sequence<int, Q>{});
 }
 
-// All threads, odd steps: the ragged ends of the write regions of the
-// populations with c_x != 0, 8 elements each: c_x = +1 owns
-// [xa+1, xa+len+1), whose elements xa+1..xa+7 and xa+len are outside the
-// bulk store; c_x = -1 owns [xa-1, xa+len-1): xa-1 and xa+len-8..xa+len-2.
-template <int Q, typename S>
+// All threads: the ragged ends of each write region (fewer than 8 elements
+// on either side of its aligned middle) as plain stores; slot j < 8 of an
+// array is the left end, j >= 8 the right end.
+template <int Q, typename S, bool ODD>
 __device__ __forceinline__ void stage_edge_stores(const Domain<float>& d, const StagePlan& p,
                                                   int64_t u, const S* buf) {
-  constexpr int M = num_x_movers<Q>();
   const int L = stage_row_len(p.seg);
-  int y, z;
-  stage_row(p, u / p.nseg, y, z);
-  const int xa = p.x0 + (int)(u % p.nseg) * p.seg;
-  const int len = min(p.seg, p.x0 + p.xlen - xa);
+  const StageUnit t = stage_unit(p, d.nx, u);
   S* f = static_cast<S*>(d.f);
-  for (int e = threadIdx.x; e < M * kStagePad; e += blockDim.x) {
-    const int rank = e / kStagePad, j = e % kStagePad;
+  for (int e = threadIdx.x; e < Q * 2 * kStagePad; e += blockDim.x) {
+    const int a_rt = e / (2 * kStagePad), j = e % (2 * kStagePad);
     [&]<int... A>(std::integer_sequence<int, A...>) {
-      int r = 0;  // rank of A among the populations with c_x != 0
       (
           [&] {
-            constexpr int cx = Lattice<Q>::c(A, 0);
-            if constexpr (cx != 0) {
-              if (r == rank) {
-                constexpr int cy = Lattice<Q>::c(A, 1), cz = Lattice<Q>::c(A, 2);
-                const int x = cx > 0 ? (j < kStagePad - 1 ? xa + 1 + j : xa + len)
-                                     : (j == 0 ? xa - 1 : xa + len - kStagePad - 1 + j);
-                const int64_t row = ((int64_t)(z + cz) * d.ny + (y + cy)) * d.nx;
-                f[(int64_t)A * d.N + row + x] = buf[A * L + (x - xa + kStagePad)];
-              }
-              ++r;
+            if (a_rt != A) return;
+            constexpr int cx = ODD ? Lattice<Q>::c(A, 0) : 0;
+            constexpr int cy = ODD ? Lattice<Q>::c(A, 1) : 0;
+            constexpr int cz = ODD ? Lattice<Q>::c(A, 2) : 0;
+            const int first = t.xa + cx, end = t.xa + t.len + cx;
+            const int a0 = ceil8(first), a1 = floor8(end);
+            const int x = j < kStagePad ? first + j : max(a0, a1) + (j - kStagePad);
+            const bool mine = j < kStagePad ? x < min(a0, end) : x < end;
+            if (mine) {
+              const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
+              f[(int64_t)A * d.N + row + x] = buf[A * L + (x - t.xb + kStagePad)];
             }
           }(),
           ...);
@@ -219,8 +223,10 @@ __device__ __forceinline__ void stage_edge_stores(const Domain<float>& d, const 
   }
 }
 
-// One thread's pair of cells (t: pair index within the unit's segment),
-// updated in place in the stage buffer.
+// One thread's pair of cells xb + 2t, xb + 2t + 1, updated in place in the
+// stage buffer.  A pair may hold one cell outside the unit's staged range
+// (the first or last cell of a row on odd steps): its values land only in
+// slots no staged cell reads and no store of this unit writes.
 template <int Q, typename S, bool ODD, bool FORCE>
 __device__ __forceinline__ void stage_update_pair(const Domain<float>& d, S* buf, int L,
                                                   int t) {
@@ -249,17 +255,16 @@ __device__ __forceinline__ void stage_update_pair(const Domain<float>& d, S* buf
   }(std::make_integer_sequence<int, Q>{});
 }
 
-// Cell g of the per-cell path of an odd step: the first and last 8 cells of
-// the interior rows, then every cell of the boundary rows (the z = 0 and
+// Cell g of the per-cell path of an odd step: x = 0 and x = nx-1 of the
+// interior rows, then every cell of the boundary rows (the z = 0 and
 // z = nz-1 planes, then y = 0 and y = ny-1 of the planes between).
 __device__ __forceinline__ void stage_general_cell(const Domain<float>& d, int64_t g, int& x,
                                                    int& y, int& z) {
   const int iy = max(d.ny - 2, 0), iz = max(d.nz - 2, 0);
-  const int64_t ends = (int64_t)iy * iz * 2 * kStagePad;
+  const int64_t ends = (int64_t)iy * iz * 2;
   if (g < ends) {
-    const int64_t r = g / (2 * kStagePad);
-    const int j = (int)(g % (2 * kStagePad));
-    x = j < kStagePad ? j : d.nx - 2 * kStagePad + j;
+    const int64_t r = g >> 1;
+    x = (g & 1) ? d.nx - 1 : 0;
     y = 1 + (int)(r % iy);
     z = 1 + (int)(r / iy);
     return;
@@ -284,52 +289,60 @@ template <int Q, typename S, bool ODD, bool FORCE>
 __global__ void __launch_bounds__(kStageSeg / 2, 4)
     k_step_staged(Domain<float> d, StagePlan p) {
   extern __shared__ __align__(128) unsigned char stage_smem[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[kStageMaxStages];
   const int L = stage_row_len(p.seg);
-  S* const buf0 = reinterpret_cast<S*>(stage_smem);
-  S* const buf1 = buf0 + Q * L;
+  const int K = p.stages;
+  S* const base = reinterpret_cast<S*>(stage_smem);
   const int tid = threadIdx.x;
   pdl_release();
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int s = 0; s < K; ++s) mbar_init(&bar[s], 1);
     mbar_init_fence();
   }
   __syncthreads();
   pdl_acquire();
   const int64_t stride = gridDim.x;
-  if (tid == 0 && (int64_t)blockIdx.x < p.units)
-    stage_issue_loads<Q, S, ODD>(d, p, blockIdx.x, buf0, &bar[0]);
-  uint32_t phase = 0;  // bit b: parity of the next completion of bar[b]
-  int it = 0;
-  for (int64_t u = blockIdx.x; u < p.units; u += stride, ++it) {
-    const int b = it & 1;
-    S* const buf = b ? buf1 : buf0;
-    const bool next = u + stride < p.units;
-    if (tid == 0 && next) {
-      bulk_wait_read_all();  // the other buffer's stores (previous unit) have read it
-      stage_issue_loads<Q, S, ODD>(d, p, u + stride, b ? buf0 : buf1, &bar[b ^ 1]);
+  if (tid == 0)
+    for (int s = 0; s < K - 1; ++s) {
+      const int64_t v = blockIdx.x + s * stride;
+      if (v < p.units) stage_issue_loads<Q, S, ODD>(d, p, v, base + s * Q * L, &bar[s]);
     }
-    const bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, kStageWaitNs);
-    phase ^= 1u << b;
+  uint32_t phase = 0;  // bit s: parity of the next completion of bar[s]
+  int s = 0;           // stage of the current unit
+  for (int64_t u = blockIdx.x; u < p.units; u += stride) {
+    S* const buf = base + s * Q * L;
+    const int ahead = s == 0 ? K - 1 : s - 1;  // stage of unit u + (K-1)*stride
+    const int64_t v = u + (K - 1) * stride;
+    if (tid == 0 && v < p.units) {
+      bulk_wait_read_all();  // that stage's stores (previous unit) have read it
+      stage_issue_loads<Q, S, ODD>(d, p, v, base + ahead * Q * L, &bar[ahead]);
+    }
+    const bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u, kStageWaitNs);
+    phase ^= 1u << s;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         *(volatile int*)p.error = 1;
-        // let the loads already issued for the next unit land before exiting
-        if (next) mbar_wait_bounded(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u, kStageWaitNs);
+        // let the loads already issued for later units land before exiting
+        for (int k = 1; k < K; ++k) {
+          const int s2 = (s + k) % K;
+          if (u + k * stride < p.units)
+            mbar_wait_bounded(&bar[s2], (phase >> s2) & 1u, kStageWaitNs);
+        }
       }
       break;
     }
-    const int len = min(p.seg, p.x0 + p.xlen - (p.x0 + (int)(u % p.nseg) * p.seg));
-    if (2 * tid < len) stage_update_pair<Q, S, ODD, FORCE>(d, buf, L, tid);
+    const StageUnit t = stage_unit(p, d.nx, u);
+    if (t.xb + 2 * tid + 1 >= t.xa && t.xb + 2 * tid < t.xa + t.len)
+      stage_update_pair<Q, S, ODD, FORCE>(d, buf, L, tid);
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       stage_issue_stores<Q, S, ODD>(d, p, u, buf);
       bulk_commit();
     }
-    if constexpr (ODD) stage_edge_stores<Q, S>(d, p, u, buf);
-    __syncthreads();  // buf is reloaded two units on
+    stage_edge_stores<Q, S, ODD>(d, p, u, buf);
+    __syncthreads();  // buf is reloaded K-1 units on
+    s = s + 1 == K ? 0 : s + 1;
   }
   if (tid == 0) bulk_wait_all();
   if constexpr (ODD) {

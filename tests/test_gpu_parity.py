@@ -219,13 +219,14 @@ STAGED_CASES = [
     # row-staged kernel (cells_per_thread 3): walls, moving walls, periodic
     # axes, symmetry faces and an edge profile on its per-cell cells; rows of
     # several segments (the last one short); no interior rows (ny = 2); the
-    # smallest staged row (nx = 24: one 8-cell segment)
+    # shortest rows it stages (nx = 16)
     ("st_walls", (64, 6, 5), (1, 2, 0, 0, 2, 1), None),
     ("st_periodic", (32, 5, 4), (0, 0, 0, 0, 0, 0), None),
     ("st_sym_edge", (48, 5, 6), (3, 1, 1, 2, 3, 2), {3: (0, 0.3, 1.0)}),
     ("st_long", (520, 3, 4), (1, 2, 1, 2, 0, 0), None),
     ("st_flat", (40, 2, 3), (2, 1, 1, 2, 0, 0), None),
-    ("st_24", (24, 4, 4), (1, 1, 0, 0, 2, 1), None),
+    ("st_16", (16, 4, 4), (1, 1, 0, 0, 2, 1), None),
+    ("st_136", (136, 3, 4), (0, 0, 1, 2, 3, 1), {3: (2, 0.5, 0.2)}),
 ]
 
 
