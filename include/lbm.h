@@ -228,10 +228,10 @@ typedef struct lbm_launch {
                                touches 128 B per population with 2-byte
                                storage instead of 64 B); odd steps run one
                                cell per thread.  Or 3, row-staged: both
-                               parities move whole row segments of every
+                               parities copy row segments of every
                                population array between HBM and shared
-                               memory with bulk asynchronous copies (double
-                               buffered) and update x-adjacent pairs there;
+                               memory in 16-byte chunks (a ring of four
+                               buffers) and update x-adjacent pairs there;
                                needs nx a multiple of 8 and >= 16 and
                                rounding to nearest, else the step runs one
                                cell per thread; bx, by are not used.  2 and

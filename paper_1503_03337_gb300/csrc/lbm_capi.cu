@@ -323,8 +323,6 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
   if (static_cast<volatile double*>(h->stats_host)[kNumSums - 1] > 0.0)
     return fail(LBM_EUNSTABLE, "a reduction found non-finite values");
-  if (stage_error_pending())
-    return fail(LBM_ETIMEOUT, "a row-staged step timed out waiting for its bulk loads");
   DeviceGuard dg(h->device);
   const int K = h->params.residual_interval;
   for (int64_t k = 0; k < nsteps; ++k) {

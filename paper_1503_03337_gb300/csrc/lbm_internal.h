@@ -45,11 +45,6 @@ struct BlockShape {
 
 BlockShape default_block(int nx, int ny);
 
-// Device view of the process-wide flag the row-staged kernel sets when a
-// wait for its bulk loads runs out (host-mapped memory), and its host value.
-int* stage_error_device();
-int stage_error_pending();
-
 // The face fields of d (per, moving, sym, uw) from a geometry.  Returns
 // nullptr, or the reason the geometry is invalid (then d is unchanged).
 const char* set_faces(DomainDesc& d, const lbm_geom* g);

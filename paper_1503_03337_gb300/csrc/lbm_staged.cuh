@@ -1,13 +1,13 @@
 // Row-staged step for FP32 / FP16 / BF16 storage (FP32 arithmetic).
 //
 // A unit of work is one segment of one x-row.  For every population array b
-// the CTA copies, with one bulk copy, the part of row b that the segment's
-// cells read (and later write) into shared memory, updates the cells there
-// in place, two x-adjacent cells per thread in packed FP32x2, and copies the
-// part back with one bulk store.  A ring of buffers keeps the loads of the
-// next units in flight while the current unit collides; one thread issues
-// all copies, so the bytes in flight per SM do not depend on how many warps
-// are resident.
+// the CTA's threads copy the part of row b that the segment's cells read
+// (and later write) into shared memory in 16-byte chunks (cp.async, one
+// chunk per thread and instruction, so a warp moves 512 bytes where the
+// per-cell kernels move 64 or 128), update the cells there in place, two
+// x-adjacent cells per thread in packed FP32x2, and write the part back in
+// 16-byte chunks.  A ring of buffers keeps the copies of the next units in
+// flight (commit groups) while the current unit collides.
 //
 // Even steps (no neighbour access) stage every row, x = 0..nx-1, and need no
 // links.  Odd steps pull f_a(x) from slot abar of x - c_a and push f*_a to
@@ -19,20 +19,18 @@
 // mirror link; the other cells (boundary rows and the ends x = 0, nx-1 of
 // interior rows) take the per-cell path of update_cell_at in the same
 // launch.  A write region that starts or ends off the 16-byte grid goes out
-// as a bulk store of its aligned middle and plain stores of its ends.
+// as chunks of its aligned middle and plain stores of its ends.
 //
 // Cells only touch their own slots (the AA property), so the partition into
 // staged and per-cell cells needs no ordering, and the superset loads may
 // read slots owned by other cells (never used) while those are rewritten.
 //
 // Requirements (stage_fits): nx a multiple of 8 and >= 16 and the population
-// buffer 16-byte aligned; then every copy address and size is a multiple of
-// 16 bytes.
+// buffer 16-byte aligned; then every chunk address is a multiple of 16 bytes.
 #pragma once
 
 #include <cstring>
 
-#include "lbm_bulk.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_launch.cuh"
 
@@ -41,7 +39,6 @@ namespace lbm {
 constexpr int kStageSeg = 256;      // cells per segment at most (two per thread)
 constexpr int kStagePad = 8;        // elements of margin on each side of a buffer row
 constexpr int kStageMaxStages = 4;  // buffers in the ring
-constexpr uint64_t kStageWaitNs = 2000000000ull;  // bounded wait for a unit's loads
 
 struct StagePlan {
   int seg;         // cells per segment (a multiple of 8, <= kStageSeg); segment j
@@ -53,8 +50,22 @@ struct StagePlan {
   int stages;      // buffers in the ring (2..kStageMaxStages)
   int64_t units;   // staged rows * nseg
   int64_t general; // cells of the per-cell path (odd steps)
-  int* error;      // host-mapped flag, set when a unit's loads time out
 };
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// This thread's copies older than its newest N groups are complete.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Elements per array in a stage buffer.
 __host__ __device__ constexpr int stage_row_len(int seg) { return seg + 2 * kStagePad; }
@@ -136,20 +147,15 @@ __device__ __forceinline__ StageUnit stage_unit(const StagePlan& p, int nx, int6
   return s;
 }
 
-// Thread 0: the loads of unit u into buf, announced on bar.  Array b is
-// staged over the aligned superset of [xa + c, xa + len + c), c its shift.
+// All threads: the copies of unit u into buf.  Array b is staged over the
+// aligned superset of [xa + c, xa + len + c), c its shift, in chunks of
+// V = 16 / sizeof(S) elements.
 template <int Q, typename S, bool ODD>
 __device__ __forceinline__ void stage_issue_loads(const Domain<float>& d, const StagePlan& p,
-                                                  int64_t u, S* buf, uint64_t* bar) {
+                                                  int64_t u, S* buf) {
+  constexpr int V = 16 / sizeof(S);
   const int L = stage_row_len(p.seg);
   const StageUnit t = stage_unit(p, d.nx, u);
-  int elems = 0;
-  [&]<int... B>(std::integer_sequence<int, B...>) {
-    ((elems += ceil8(t.xa + t.len + (ODD ? Lattice<Q>::c(B, 0) : 0)) -
-               floor8(t.xa + (ODD ? Lattice<Q>::c(B, 0) : 0))),
-     ...);
-  }(std::make_integer_sequence<int, Q>{});
-  mbar_arrive_expect_tx(bar, (uint32_t)(elems * sizeof(S)));
   const S* f = static_cast<const S*>(d.f);
   [&]<int... B>(std::integer_sequence<int, B...>) {
     (
@@ -157,21 +163,22 @@ __device__ __forceinline__ void stage_issue_loads(const Domain<float>& d, const 
           constexpr int cx = ODD ? Lattice<Q>::c(B, 0) : 0;
           constexpr int cy = ODD ? Lattice<Q>::c(B, 1) : 0;
           constexpr int cz = ODD ? Lattice<Q>::c(B, 2) : 0;
-          const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
           const int lo = floor8(t.xa + cx), hi = ceil8(t.xa + t.len + cx);
-          bulk_load(buf + B * L + (lo - t.xb + kStagePad), f + (int64_t)B * d.N + row + lo,
-                    (uint32_t)((hi - lo) * sizeof(S)), bar);
+          const S* src = f + (int64_t)B * d.N + ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
+          S* dst = buf + B * L + (kStagePad - t.xb);
+          for (int x = lo + V * (int)threadIdx.x; x < hi; x += V * (int)blockDim.x)
+            cp_async16(dst + x, src + x);
         }(),
         ...);
   }(std::make_integer_sequence<int, Q>{});
 }
 
-// Thread 0: the bulk stores of unit u from buf, the aligned middle
-// [ceil8(xa + c), floor8(xa + len + c)) of each write region (when it is
-// not empty).
+// All threads: the aligned middle [ceil8(xa + c), floor8(xa + len + c)) of
+// each write region, in 16-byte chunks.
 template <int Q, typename S, bool ODD>
-__device__ __forceinline__ void stage_issue_stores(const Domain<float>& d, const StagePlan& p,
+__device__ __forceinline__ void stage_store_chunks(const Domain<float>& d, const StagePlan& p,
                                                    int64_t u, const S* buf) {
+  constexpr int V = 16 / sizeof(S);
   const int L = stage_row_len(p.seg);
   const StageUnit t = stage_unit(p, d.nx, u);
   S* f = static_cast<S*>(d.f);
@@ -181,11 +188,11 @@ __device__ __forceinline__ void stage_issue_stores(const Domain<float>& d, const
           constexpr int cx = ODD ? Lattice<Q>::c(A, 0) : 0;
           constexpr int cy = ODD ? Lattice<Q>::c(A, 1) : 0;
           constexpr int cz = ODD ? Lattice<Q>::c(A, 2) : 0;
-          const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
           const int a0 = ceil8(t.xa + cx), a1 = floor8(t.xa + t.len + cx);
-          if (a1 > a0)
-            bulk_store(f + (int64_t)A * d.N + row + a0, buf + A * L + (a0 - t.xb + kStagePad),
-                       (uint32_t)((a1 - a0) * sizeof(S)));
+          S* dst = f + (int64_t)A * d.N + ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
+          const S* src = buf + A * L + (kStagePad - t.xb);
+          for (int x = a0 + V * (int)threadIdx.x; x < a1; x += V * (int)blockDim.x)
+            *reinterpret_cast<uint4*>(dst + x) = *reinterpret_cast<const uint4*>(src + x);
         }(),
         ...);
   }(std::make_integer_sequence<int, Q>{});
@@ -289,62 +296,41 @@ template <int Q, typename S, bool ODD, bool FORCE>
 __global__ void __launch_bounds__(kStageSeg / 2, 4)
     k_step_staged(Domain<float> d, StagePlan p) {
   extern __shared__ __align__(128) unsigned char stage_smem[];
-  __shared__ __align__(8) uint64_t bar[kStageMaxStages];
   const int L = stage_row_len(p.seg);
   const int K = p.stages;
   S* const base = reinterpret_cast<S*>(stage_smem);
   const int tid = threadIdx.x;
   pdl_release();
-  if (tid == 0) {
-    for (int s = 0; s < K; ++s) mbar_init(&bar[s], 1);
-    mbar_init_fence();
-  }
-  __syncthreads();
   pdl_acquire();
   const int64_t stride = gridDim.x;
-  if (tid == 0)
-    for (int s = 0; s < K - 1; ++s) {
-      const int64_t v = blockIdx.x + s * stride;
-      if (v < p.units) stage_issue_loads<Q, S, ODD>(d, p, v, base + s * Q * L, &bar[s]);
-    }
-  uint32_t phase = 0;  // bit s: parity of the next completion of bar[s]
-  int s = 0;           // stage of the current unit
+  // prologue: units 0..K-2 of this CTA into stages 0..K-2, one group each
+  for (int s = 0; s < K - 1; ++s) {
+    const int64_t v = blockIdx.x + s * stride;
+    if (v < p.units) stage_issue_loads<Q, S, ODD>(d, p, v, base + s * Q * L);
+    cp_async_commit();
+  }
+  int s = 0;  // stage of the current unit
   for (int64_t u = blockIdx.x; u < p.units; u += stride) {
     S* const buf = base + s * Q * L;
     const int ahead = s == 0 ? K - 1 : s - 1;  // stage of unit u + (K-1)*stride
     const int64_t v = u + (K - 1) * stride;
-    if (tid == 0 && v < p.units) {
-      bulk_wait_read_all();  // that stage's stores (previous unit) have read it
-      stage_issue_loads<Q, S, ODD>(d, p, v, base + ahead * Q * L, &bar[ahead]);
-    }
-    const bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u, kStageWaitNs);
-    phase ^= 1u << s;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        *(volatile int*)p.error = 1;
-        // let the loads already issued for later units land before exiting
-        for (int k = 1; k < K; ++k) {
-          const int s2 = (s + k) % K;
-          if (u + k * stride < p.units)
-            mbar_wait_bounded(&bar[s2], (phase >> s2) & 1u, kStageWaitNs);
-        }
-      }
-      break;
-    }
+    if (v < p.units) stage_issue_loads<Q, S, ODD>(d, p, v, base + ahead * Q * L);
+    cp_async_commit();
+    // all but the newest K-1 groups done: this unit's copies have landed
+    if (K == 4) cp_async_wait<3>();
+    else if (K == 3) cp_async_wait<2>();
+    else cp_async_wait<1>();
+    __syncthreads();
     const StageUnit t = stage_unit(p, d.nx, u);
     if (t.xb + 2 * tid + 1 >= t.xa && t.xb + 2 * tid < t.xa + t.len)
       stage_update_pair<Q, S, ODD, FORCE>(d, buf, L, tid);
-    fence_proxy_async_smem();
     __syncthreads();
-    if (tid == 0) {
-      stage_issue_stores<Q, S, ODD>(d, p, u, buf);
-      bulk_commit();
-    }
+    stage_store_chunks<Q, S, ODD>(d, p, u, buf);
     stage_edge_stores<Q, S, ODD>(d, p, u, buf);
-    __syncthreads();  // buf is reloaded K-1 units on
+    __syncthreads();  // buf is refilled by the next iteration's copies
     s = s + 1 == K ? 0 : s + 1;
   }
-  if (tid == 0) bulk_wait_all();
+  cp_async_wait<0>();
   if constexpr (ODD) {
     S* f = static_cast<S*>(d.f);
     const int64_t step = (int64_t)gridDim.x * blockDim.x;

@@ -78,33 +78,6 @@ const char* set_faces(DomainDesc& d, const lbm_geom* g) {
   return nullptr;
 }
 
-namespace {
-int* g_stage_error_host = nullptr;  // host-mapped, written by the staged kernel
-int* g_stage_error_dev = nullptr;
-}  // namespace
-
-int* stage_error_device() {
-  if (!g_stage_error_host) {
-    int* h = nullptr;
-    if (cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(int), cudaHostAllocMapped) !=
-        cudaSuccess)
-      return nullptr;
-    *h = 0;
-    int* dptr = nullptr;
-    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&dptr), h, 0) != cudaSuccess) {
-      cudaFreeHost(h);
-      return nullptr;
-    }
-    g_stage_error_dev = dptr;
-    g_stage_error_host = h;
-  }
-  return g_stage_error_dev;
-}
-
-int stage_error_pending() {
-  return g_stage_error_host ? *static_cast<volatile int*>(g_stage_error_host) : 0;
-}
-
 BlockShape default_block(int nx, int ny) {
   int bx = 32;
   while (bx < nx && bx < 128) bx *= 2;

@@ -89,7 +89,6 @@ inline StagePlan stage_plan(const Domain<float>& d, bool odd) {
   p.nseg = (d.nx + p.seg - 1) / p.seg;
   p.units = rows * p.nseg;
   p.stages = kStageMaxStages;
-  p.error = stage_error_device();
   return p;
 }
 
