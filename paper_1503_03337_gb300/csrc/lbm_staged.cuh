@@ -48,7 +48,7 @@ struct StagePlan {
   int row_lo;      // 0 (even: every row) or 1 (odd: interior rows)
   int rows_y;      // staged rows per z-plane (ny or ny - 2)
   int stages;      // buffers in the ring (2..kStageMaxStages)
-  int64_t units;   // staged rows * nseg
+  int64_t units;   // staged rows * nseg (< 2^31)
   int64_t general; // cells of the per-cell path (odd steps)
 };
 
@@ -122,11 +122,6 @@ __device__ __forceinline__ void stage_put(S* row, int k, pf2 v) {
   }
 }
 
-// (y, z) of staged row r.
-__device__ __forceinline__ void stage_row(const StagePlan& p, int64_t r, int& y, int& z) {
-  y = p.row_lo + (int)(r % p.rows_y);
-  z = p.row_lo + (int)(r / p.rows_y);
-}
 
 __host__ __device__ __forceinline__ int floor8(int v) { return v & ~7; }
 __host__ __device__ __forceinline__ int ceil8(int v) { return (v + 7) & ~7; }
@@ -138,10 +133,12 @@ struct StageUnit {
   int y, z, xb, xa, len;
 };
 
-__device__ __forceinline__ StageUnit stage_unit(const StagePlan& p, int nx, int64_t u) {
+__device__ __forceinline__ StageUnit stage_unit(const StagePlan& p, int u) {
   StageUnit s;
-  stage_row(p, u / p.nseg, s.y, s.z);
-  s.xb = (int)(u % p.nseg) * p.seg;
+  const int r = u / p.nseg;
+  s.y = p.row_lo + r % p.rows_y;
+  s.z = p.row_lo + r / p.rows_y;
+  s.xb = (u - r * p.nseg) * p.seg;
   s.xa = max(s.xb, p.x0);
   s.len = min(s.xb + p.seg, p.x0 + p.xlen) - s.xa;
   return s;
@@ -152,10 +149,9 @@ __device__ __forceinline__ StageUnit stage_unit(const StagePlan& p, int nx, int6
 // V = 16 / sizeof(S) elements.
 template <int Q, typename S, bool ODD>
 __device__ __forceinline__ void stage_issue_loads(const Domain<float>& d, const StagePlan& p,
-                                                  int64_t u, S* buf) {
+                                                  const StageUnit& t, S* buf) {
   constexpr int V = 16 / sizeof(S);
   const int L = stage_row_len(p.seg);
-  const StageUnit t = stage_unit(p, d.nx, u);
   const S* f = static_cast<const S*>(d.f);
   [&]<int... B>(std::integer_sequence<int, B...>) {
     (
@@ -177,10 +173,9 @@ __device__ __forceinline__ void stage_issue_loads(const Domain<float>& d, const 
 // each write region, in 16-byte chunks.
 template <int Q, typename S, bool ODD>
 __device__ __forceinline__ void stage_store_chunks(const Domain<float>& d, const StagePlan& p,
-                                                   int64_t u, const S* buf) {
+                                                   const StageUnit& t, const S* buf) {
   constexpr int V = 16 / sizeof(S);
   const int L = stage_row_len(p.seg);
-  const StageUnit t = stage_unit(p, d.nx, u);
   S* f = static_cast<S*>(d.f);
   [&]<int... A>(std::integer_sequence<int, A...>) {
     (
@@ -198,36 +193,33 @@ __device__ __forceinline__ void stage_store_chunks(const Domain<float>& d, const
   }(std::make_integer_sequence<int, Q>{});
 }
 
-// All threads: the ragged ends of each write region (fewer than 8 elements
-// on either side of its aligned middle) as plain stores; slot j < 8 of an
-// array is the left end, j >= 8 the right end.
-template <int Q, typename S, bool ODD>
+// Odd steps, all threads: the ragged ends of each write region (fewer
+// than 8 elements on either side of its aligned middle) as plain stores.
+// Groups of 16 threads take the arrays in turn; within a group slot j < 8 is
+// the left end, j >= 8 the right end.  (Even-step regions are aligned.)
+template <int Q, typename S>
 __device__ __forceinline__ void stage_edge_stores(const Domain<float>& d, const StagePlan& p,
-                                                  int64_t u, const S* buf) {
+                                                  const StageUnit& t, const S* buf) {
   const int L = stage_row_len(p.seg);
-  const StageUnit t = stage_unit(p, d.nx, u);
+  const int groups = blockDim.x / (2 * kStagePad);
+  const int group = threadIdx.x / (2 * kStagePad), j = threadIdx.x % (2 * kStagePad);
   S* f = static_cast<S*>(d.f);
-  for (int e = threadIdx.x; e < Q * 2 * kStagePad; e += blockDim.x) {
-    const int a_rt = e / (2 * kStagePad), j = e % (2 * kStagePad);
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      (
-          [&] {
-            if (a_rt != A) return;
-            constexpr int cx = ODD ? Lattice<Q>::c(A, 0) : 0;
-            constexpr int cy = ODD ? Lattice<Q>::c(A, 1) : 0;
-            constexpr int cz = ODD ? Lattice<Q>::c(A, 2) : 0;
-            const int first = t.xa + cx, end = t.xa + t.len + cx;
-            const int a0 = ceil8(first), a1 = floor8(end);
-            const int x = j < kStagePad ? first + j : max(a0, a1) + (j - kStagePad);
-            const bool mine = j < kStagePad ? x < min(a0, end) : x < end;
-            if (mine) {
-              const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
-              f[(int64_t)A * d.N + row + x] = buf[A * L + (x - t.xb + kStagePad)];
-            }
-          }(),
-          ...);
-    }(std::make_integer_sequence<int, Q>{});
-  }
+  [&]<int... A>(std::integer_sequence<int, A...>) {
+    (
+        [&] {
+          if (A % groups != group) return;
+          constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
+                        cz = Lattice<Q>::c(A, 2);
+          const int first = t.xa + cx, end = t.xa + t.len + cx;
+          const int a0 = ceil8(first), a1 = floor8(end);
+          const int x = j < kStagePad ? first + j : max(a0, a1) + (j - kStagePad);
+          if (j < kStagePad ? x < min(a0, end) : x < end) {
+            const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
+            f[(int64_t)A * d.N + row + x] = buf[A * L + (x - t.xb + kStagePad)];
+          }
+        }(),
+        ...);
+  }(std::make_integer_sequence<int, Q>{});
 }
 
 // One thread's pair of cells xb + 2t, xb + 2t + 1, updated in place in the
@@ -302,31 +294,31 @@ __global__ void __launch_bounds__(kStageSeg / 2, 4)
   const int tid = threadIdx.x;
   pdl_release();
   pdl_acquire();
-  const int64_t stride = gridDim.x;
+  const int stride = gridDim.x, units = (int)p.units;
   // prologue: units 0..K-2 of this CTA into stages 0..K-2, one group each
   for (int s = 0; s < K - 1; ++s) {
-    const int64_t v = blockIdx.x + s * stride;
-    if (v < p.units) stage_issue_loads<Q, S, ODD>(d, p, v, base + s * Q * L);
+    const int v = blockIdx.x + s * stride;
+    if (v < units) stage_issue_loads<Q, S, ODD>(d, p, stage_unit(p, v), base + s * Q * L);
     cp_async_commit();
   }
   int s = 0;  // stage of the current unit
-  for (int64_t u = blockIdx.x; u < p.units; u += stride) {
+  for (int u = blockIdx.x; u < units; u += stride) {
     S* const buf = base + s * Q * L;
     const int ahead = s == 0 ? K - 1 : s - 1;  // stage of unit u + (K-1)*stride
-    const int64_t v = u + (K - 1) * stride;
-    if (v < p.units) stage_issue_loads<Q, S, ODD>(d, p, v, base + ahead * Q * L);
+    const int v = u + (K - 1) * stride;
+    if (v < units) stage_issue_loads<Q, S, ODD>(d, p, stage_unit(p, v), base + ahead * Q * L);
     cp_async_commit();
     // all but the newest K-1 groups done: this unit's copies have landed
     if (K == 4) cp_async_wait<3>();
     else if (K == 3) cp_async_wait<2>();
     else cp_async_wait<1>();
     __syncthreads();
-    const StageUnit t = stage_unit(p, d.nx, u);
+    const StageUnit t = stage_unit(p, u);
     if (t.xb + 2 * tid + 1 >= t.xa && t.xb + 2 * tid < t.xa + t.len)
       stage_update_pair<Q, S, ODD, FORCE>(d, buf, L, tid);
     __syncthreads();
-    stage_store_chunks<Q, S, ODD>(d, p, u, buf);
-    stage_edge_stores<Q, S, ODD>(d, p, u, buf);
+    stage_store_chunks<Q, S, ODD>(d, p, t, buf);
+    if constexpr (ODD) stage_edge_stores<Q, S>(d, p, t, buf);
     __syncthreads();  // buf is refilled by the next iteration's copies
     s = s + 1 == K ? 0 : s + 1;
   }

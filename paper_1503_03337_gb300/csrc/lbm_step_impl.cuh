@@ -61,7 +61,7 @@ constexpr int kStageSegTarget = 128;  // cells per segment aimed at (64 threads)
 
 // Units, segment length, ring depth and per-cell work of one step of the
 // row-staged kernel (see lbm_staged.cuh).
-inline StagePlan stage_plan(const Domain<float>& d, bool odd) {
+inline StagePlan stage_plan(const Domain<float>& d, bool odd, int elem_bytes) {
   StagePlan p{};
   int64_t rows;
   if (!odd) {
@@ -88,7 +88,9 @@ inline StagePlan stage_plan(const Domain<float>& d, bool odd) {
   p.seg = ((d.nx + p.nseg - 1) / p.nseg + 7) / 8 * 8;
   p.nseg = (d.nx + p.seg - 1) / p.seg;
   p.units = rows * p.nseg;
-  p.stages = kStageMaxStages;
+  // ring depth: about half the shared memory of an SM holds copies in
+  // flight with either depth; the shallower ring fits more CTAs (warps)
+  p.stages = elem_bytes == 4 ? 2 : 3;
   return p;
 }
 
@@ -135,7 +137,7 @@ void launch_staged_kernel(const Domain<float>& d, const StagePlan& p, bool pdl, 
 
 template <int Q, typename S>
 void launch_staged(const Domain<float>& d, bool odd, bool force, bool pdl, cudaStream_t st) {
-  const StagePlan p = stage_plan(d, odd);
+  const StagePlan p = stage_plan(d, odd, (int)sizeof(S));
   if (odd) {
     if (force) launch_staged_kernel<Q, S, true, true>(d, p, pdl, st);
     else launch_staged_kernel<Q, S, true, false>(d, p, pdl, st);
