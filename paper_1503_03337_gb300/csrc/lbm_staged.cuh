@@ -144,82 +144,79 @@ __device__ __forceinline__ StageUnit stage_unit(const StagePlan& p, int u) {
   return s;
 }
 
-// All threads: the copies of unit u into buf.  Array b is staged over the
-// aligned superset of [xa + c, xa + len + c), c its shift, in chunks of
-// V = 16 / sizeof(S) elements.
-template <int Q, typename S, bool ODD>
+// Per-array shift of the staged regions, in shared memory for the whole
+// kernel: the element offset of array b's staged row from the unit's row
+// (b*N plus the y and z shifts on odd steps) and its x shift.
+template <int Q>
+struct StageShift {
+  long long goff[Q];
+  int cx[Q];
+};
+
+template <int Q, bool ODD>
+__device__ __forceinline__ void stage_fill_shift(StageShift<Q>& t, const Domain<float>& d) {
+  for (int b = threadIdx.x; b < Q; b += blockDim.x) {
+    int cx = 0, cy = 0, cz = 0;
+    if constexpr (ODD) {
+      [&]<int... B>(std::integer_sequence<int, B...>) {
+        ((b == B ? (cx = Lattice<Q>::c(B, 0), cy = Lattice<Q>::c(B, 1),
+                    cz = Lattice<Q>::c(B, 2), 0)
+                 : 0),
+         ...);
+      }(std::make_integer_sequence<int, Q>{});
+    }
+    t.goff[b] = (long long)b * d.N + ((long long)cz * d.ny + cy) * d.nx;
+    t.cx[b] = cx;
+  }
+}
+
+// All threads: the copies of unit t into buf.  Array b is staged over the
+// aligned superset [floor8(xa + c), ceil8(xa + len + c)) of its region, c
+// its x shift; chunk j of a buffer row holds elements xb - 8 + j*V .. + V-1
+// (V = 16 / sizeof(S)).
+template <int Q, typename S>
 __device__ __forceinline__ void stage_issue_loads(const Domain<float>& d, const StagePlan& p,
-                                                  const StageUnit& t, S* buf) {
+                                                  const StageShift<Q>& sh, const StageUnit& t,
+                                                  S* buf) {
   constexpr int V = 16 / sizeof(S);
-  const int L = stage_row_len(p.seg);
-  const S* f = static_cast<const S*>(d.f);
-  [&]<int... B>(std::integer_sequence<int, B...>) {
-    (
-        [&] {
-          constexpr int cx = ODD ? Lattice<Q>::c(B, 0) : 0;
-          constexpr int cy = ODD ? Lattice<Q>::c(B, 1) : 0;
-          constexpr int cz = ODD ? Lattice<Q>::c(B, 2) : 0;
-          const int lo = floor8(t.xa + cx), hi = ceil8(t.xa + t.len + cx);
-          const S* src = f + (int64_t)B * d.N + ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
-          S* dst = buf + B * L + (kStagePad - t.xb);
-          for (int x = lo + V * (int)threadIdx.x; x < hi; x += V * (int)blockDim.x)
-            cp_async16(dst + x, src + x);
-        }(),
-        ...);
-  }(std::make_integer_sequence<int, Q>{});
+  const int L = stage_row_len(p.seg), CH = L / V;
+  const S* f = static_cast<const S*>(d.f) + ((long long)t.z * d.ny + t.y) * d.nx;
+  for (int e = threadIdx.x; e < Q * CH; e += blockDim.x) {
+    const int b = e / CH, j = e - b * CH;
+    const int x = t.xb - kStagePad + j * V, c = sh.cx[b];
+    if (x >= floor8(t.xa + c) && x < ceil8(t.xa + t.len + c))
+      cp_async16(buf + b * L + j * V, f + sh.goff[b] + x);
+  }
 }
 
 // All threads: the aligned middle [ceil8(xa + c), floor8(xa + len + c)) of
-// each write region, in 16-byte chunks.
+// each write region in 16-byte chunks, then (odd steps) its ragged ends,
+// fewer than 8 elements on either side, as plain stores (slot j < 8 of an
+// array: left end, j >= 8: right end).
 template <int Q, typename S, bool ODD>
-__device__ __forceinline__ void stage_store_chunks(const Domain<float>& d, const StagePlan& p,
-                                                   const StageUnit& t, const S* buf) {
+__device__ __forceinline__ void stage_stores(const Domain<float>& d, const StagePlan& p,
+                                             const StageShift<Q>& sh, const StageUnit& t,
+                                             const S* buf) {
   constexpr int V = 16 / sizeof(S);
-  const int L = stage_row_len(p.seg);
-  S* f = static_cast<S*>(d.f);
-  [&]<int... A>(std::integer_sequence<int, A...>) {
-    (
-        [&] {
-          constexpr int cx = ODD ? Lattice<Q>::c(A, 0) : 0;
-          constexpr int cy = ODD ? Lattice<Q>::c(A, 1) : 0;
-          constexpr int cz = ODD ? Lattice<Q>::c(A, 2) : 0;
-          const int a0 = ceil8(t.xa + cx), a1 = floor8(t.xa + t.len + cx);
-          S* dst = f + (int64_t)A * d.N + ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
-          const S* src = buf + A * L + (kStagePad - t.xb);
-          for (int x = a0 + V * (int)threadIdx.x; x < a1; x += V * (int)blockDim.x)
-            *reinterpret_cast<uint4*>(dst + x) = *reinterpret_cast<const uint4*>(src + x);
-        }(),
-        ...);
-  }(std::make_integer_sequence<int, Q>{});
-}
-
-// Odd steps, all threads: the ragged ends of each write region (fewer
-// than 8 elements on either side of its aligned middle) as plain stores.
-// Groups of 16 threads take the arrays in turn; within a group slot j < 8 is
-// the left end, j >= 8 the right end.  (Even-step regions are aligned.)
-template <int Q, typename S>
-__device__ __forceinline__ void stage_edge_stores(const Domain<float>& d, const StagePlan& p,
-                                                  const StageUnit& t, const S* buf) {
-  const int L = stage_row_len(p.seg);
-  const int groups = blockDim.x / (2 * kStagePad);
-  const int group = threadIdx.x / (2 * kStagePad), j = threadIdx.x % (2 * kStagePad);
-  S* f = static_cast<S*>(d.f);
-  [&]<int... A>(std::integer_sequence<int, A...>) {
-    (
-        [&] {
-          if (A % groups != group) return;
-          constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
-                        cz = Lattice<Q>::c(A, 2);
-          const int first = t.xa + cx, end = t.xa + t.len + cx;
-          const int a0 = ceil8(first), a1 = floor8(end);
-          const int x = j < kStagePad ? first + j : max(a0, a1) + (j - kStagePad);
-          if (j < kStagePad ? x < min(a0, end) : x < end) {
-            const int64_t row = ((int64_t)(t.z + cz) * d.ny + (t.y + cy)) * d.nx;
-            f[(int64_t)A * d.N + row + x] = buf[A * L + (x - t.xb + kStagePad)];
-          }
-        }(),
-        ...);
-  }(std::make_integer_sequence<int, Q>{});
+  const int L = stage_row_len(p.seg), CH = L / V;
+  S* f = static_cast<S*>(d.f) + ((long long)t.z * d.ny + t.y) * d.nx;
+  for (int e = threadIdx.x; e < Q * CH; e += blockDim.x) {
+    const int a = e / CH, j = e - a * CH;
+    const int x = t.xb - kStagePad + j * V, c = sh.cx[a];
+    if (x >= ceil8(t.xa + c) && x < floor8(t.xa + t.len + c))
+      *reinterpret_cast<uint4*>(f + sh.goff[a] + x) =
+          *reinterpret_cast<const uint4*>(buf + a * L + j * V);
+  }
+  if constexpr (ODD) {
+    for (int e = threadIdx.x; e < Q * 2 * kStagePad; e += blockDim.x) {
+      const int a = e / (2 * kStagePad), j = e % (2 * kStagePad);
+      const int first = t.xa + sh.cx[a], end = t.xa + t.len + sh.cx[a];
+      const int a0 = ceil8(first), a1 = floor8(end);
+      const int x = j < kStagePad ? first + j : max(a0, a1) + (j - kStagePad);
+      if (j < kStagePad ? x < min(a0, end) : x < end)
+        f[sh.goff[a] + x] = buf[a * L + (x - t.xb + kStagePad)];
+    }
+  }
 }
 
 // One thread's pair of cells xb + 2t, xb + 2t + 1, updated in place in the
@@ -288,17 +285,20 @@ template <int Q, typename S, bool ODD, bool FORCE>
 __global__ void __launch_bounds__(kStageSeg / 2, 4)
     k_step_staged(Domain<float> d, StagePlan p) {
   extern __shared__ __align__(128) unsigned char stage_smem[];
+  __shared__ StageShift<Q> sh;
   const int L = stage_row_len(p.seg);
   const int K = p.stages;
   S* const base = reinterpret_cast<S*>(stage_smem);
   const int tid = threadIdx.x;
   pdl_release();
+  stage_fill_shift<Q, ODD>(sh, d);
+  __syncthreads();
   pdl_acquire();
   const int stride = gridDim.x, units = (int)p.units;
   // prologue: units 0..K-2 of this CTA into stages 0..K-2, one group each
   for (int s = 0; s < K - 1; ++s) {
     const int v = blockIdx.x + s * stride;
-    if (v < units) stage_issue_loads<Q, S, ODD>(d, p, stage_unit(p, v), base + s * Q * L);
+    if (v < units) stage_issue_loads<Q, S>(d, p, sh, stage_unit(p, v), base + s * Q * L);
     cp_async_commit();
   }
   int s = 0;  // stage of the current unit
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kStageSeg / 2, 4)
     S* const buf = base + s * Q * L;
     const int ahead = s == 0 ? K - 1 : s - 1;  // stage of unit u + (K-1)*stride
     const int v = u + (K - 1) * stride;
-    if (v < units) stage_issue_loads<Q, S, ODD>(d, p, stage_unit(p, v), base + ahead * Q * L);
+    if (v < units) stage_issue_loads<Q, S>(d, p, sh, stage_unit(p, v), base + ahead * Q * L);
     cp_async_commit();
     // all but the newest K-1 groups done: this unit's copies have landed
     if (K == 4) cp_async_wait<3>();
@@ -317,8 +317,7 @@ __global__ void __launch_bounds__(kStageSeg / 2, 4)
     if (t.xb + 2 * tid + 1 >= t.xa && t.xb + 2 * tid < t.xa + t.len)
       stage_update_pair<Q, S, ODD, FORCE>(d, buf, L, tid);
     __syncthreads();
-    stage_store_chunks<Q, S, ODD>(d, p, t, buf);
-    if constexpr (ODD) stage_edge_stores<Q, S>(d, p, t, buf);
+    stage_stores<Q, S, ODD>(d, p, sh, t, buf);
     __syncthreads();  // buf is refilled by the next iteration's copies
     s = s + 1 == K ? 0 : s + 1;
   }
