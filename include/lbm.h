@@ -227,15 +227,7 @@ typedef struct lbm_launch {
                                population of the pair as one word (a warp
                                touches 128 B per population with 2-byte
                                storage instead of 64 B); odd steps run one
-                               cell per thread.  Or 3, row-staged: both
-                               parities copy row segments of every
-                               population array between HBM and shared
-                               memory in 16-byte chunks (a ring of four
-                               buffers) and update x-adjacent pairs there;
-                               needs nx a multiple of 8 and >= 16 and
-                               rounding to nearest, else the step runs one
-                               cell per thread; bx, by are not used.  2 and
-                               3 are not for FP64 storage.                   */
+                               cell per thread.  Not for FP64 storage.       */
 } lbm_launch;
 
 /* Set / read the launch shape.  EINVAL if out of range. */

@@ -441,11 +441,10 @@ int lbm_set_launch(lbm_handle* h, const lbm_launch* l) {
   if (!l) return fail(LBM_EINVAL, "null launch");
   if (l->bx < 32 || l->bx % 32 != 0 || l->by < 1 || (int64_t)l->bx * l->by > 256)
     return fail(LBM_EINVAL, "block must be bx (multiple of 32) x by with bx*by <= 256");
-  if (l->cells_per_thread < 1 || l->cells_per_thread > 3)
-    return fail(LBM_EINVAL, "cells_per_thread must be 1, 2 or 3");
-  if (l->cells_per_thread > 1 && h->d.storage == LBM_STORAGE_F64)
-    return fail(LBM_EINVAL,
-                "two cells per thread and row staging need FP32 arithmetic (not FP64 storage)");
+  if (l->cells_per_thread != 1 && l->cells_per_thread != 2)
+    return fail(LBM_EINVAL, "cells_per_thread must be 1 or 2");
+  if (l->cells_per_thread == 2 && h->d.storage == LBM_STORAGE_F64)
+    return fail(LBM_EINVAL, "two cells per thread needs FP32 arithmetic (not FP64 storage)");
   h->block = {l->bx, l->by, l->cells_per_thread, h->block.pdl};
   return LBM_OK;
 }
@@ -463,7 +462,7 @@ std::map<std::tuple<int, int, int, int, int>, std::pair<BlockShape, double>> g_t
 const BlockShape kCandidates[] = {{32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1},
                                   {64, 1, 1},  {64, 2, 1}, {64, 4, 1}, {128, 1, 1},
                                   {128, 2, 1}, {256, 1, 1}, {32, 2, 2}, {64, 1, 2},
-                                  {64, 2, 2},  {128, 1, 2}, {128, 1, 3}};
+                                  {64, 2, 2},  {128, 1, 2}};
 }  // namespace
 
 int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) {
@@ -503,8 +502,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
     if (e != cudaSuccess) break;
     b.pdl = h->block.pdl;
     if (b.bx * b.cpt > xmax && b.bx > 32) continue;
-    if (b.cpt >= 2 && h->d.storage == LBM_STORAGE_F64) continue;
-    if (b.cpt == 3 && (h->d.nx % 8 != 0 || h->d.nx < 16)) continue;  // falls back: same as 1
+    if (b.cpt == 2 && h->d.storage == LBM_STORAGE_F64) continue;
     int64_t n = n0;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->d, n++, b, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);

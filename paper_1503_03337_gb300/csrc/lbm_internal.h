@@ -38,8 +38,7 @@ struct DomainDesc {
 
 struct BlockShape {
   int bx, by;
-  int cpt;      // cells per thread: 1, 2 (pairs along x, FP32 arithmetic only), or
-                // 3 (row-staged through shared memory, lbm_staged.cuh)
+  int cpt;      // cells per thread: 1, or 2 (pairs along x, FP32 arithmetic only)
   int pdl = 1;  // programmatic dependent launch of consecutive steps
 };
 

@@ -51,7 +51,7 @@ def test_rejected_calls_leave_handle_usable():
         einval(lbm.lbm_set_params, h, nu=0.1, rounding=9)         # unknown rounding mode
         einval(lbm.lbm_set_launch, h, 48, 2, 1)                   # bx not a multiple of 32
         einval(lbm.lbm_set_launch, h, 128, 4, 1)                  # more than 256 threads
-        einval(lbm.lbm_set_launch, h, 64, 2, 4)                   # cells per thread
+        einval(lbm.lbm_set_launch, h, 64, 2, 3)                   # cells per thread
         out = np.zeros(3 * case.cells)
         einval(lbm.lbm_read_fields, h, 0, out)                    # empty field mask
         einval(lbm.lbm_read_fields, h, 64, out)                   # unknown field bit

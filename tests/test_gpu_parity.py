@@ -213,71 +213,3 @@ def test_fp64_lbgk_special_case(Q):
         lbm.lbm_destroy(h)
     assert rel_max(u, u_o) <= 1e-12
     assert rel_max(fg, f.reshape(fg.shape)) <= 1e-12
-
-
-STAGED_CASES = [
-    # row-staged kernel (cells_per_thread 3): walls, moving walls, periodic
-    # axes, symmetry faces and an edge profile on its per-cell cells; rows of
-    # several segments (the last one short); no interior rows (ny = 2); the
-    # shortest rows it stages (nx = 16)
-    ("st_walls", (64, 6, 5), (1, 2, 0, 0, 2, 1), None),
-    ("st_periodic", (32, 5, 4), (0, 0, 0, 0, 0, 0), None),
-    ("st_sym_edge", (48, 5, 6), (3, 1, 1, 2, 3, 2), {3: (0, 0.3, 1.0)}),
-    ("st_long", (520, 3, 4), (1, 2, 1, 2, 0, 0), None),
-    ("st_flat", (40, 2, 3), (2, 1, 1, 2, 0, 0), None),
-    ("st_16", (16, 4, 4), (1, 1, 0, 0, 2, 1), None),
-    ("st_136", (136, 3, 4), (0, 0, 1, 2, 3, 1), {3: (2, 0.5, 0.2)}),
-]
-
-
-@pytest.mark.parametrize("Q", (14, 18))
-@pytest.mark.parametrize("name,shape,faces,edge", STAGED_CASES)
-def test_fp32_row_staged(Q, name, shape, faces, edge):
-    """The row-staged kernel against the oracle from a seeded random state,
-    odd step count, FP32 storage: to FP32 rounding."""
-    rng = np.random.default_rng(seed(name, Q, 3))
-    uw = rng.normal(size=(6, 3)) * 0.03
-    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
-                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f32",
-                       u_ref=0.03, edge=edge)
-    case.init_u, case.init_p = inputs.random_state(case, seed=4)
-    g, o = gpu_run(case, 37, launch=(128, 1, 3)), oracle_run(case, 37)
-    assert rel_max(g["f"], o["f"]) <= 2e-6
-    assert np.max(np.abs(g["u"] - o["u"])) <= 1e-5 * case.u_ref
-
-
-@pytest.mark.parametrize("storage", ("f16", "bf16"))
-@pytest.mark.parametrize("Q", (14, 18))
-@pytest.mark.parametrize("name,shape,faces,edge", STAGED_CASES)
-def test_16bit_row_staged(Q, name, shape, faces, edge, storage):
-    """FP16 / BF16 storage, rounding to nearest: the row-staged kernel
-    against one cell per thread to a few storage ulps (the two collide in
-    packed and in scalar FP32, whose multiply-adds may fuse differently)."""
-    rng = np.random.default_rng(seed(name, Q, 4))
-    uw = rng.normal(size=(6, 3)) * 0.03
-    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
-                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage=storage,
-                       u_ref=0.03, edge=edge)
-    case.init_u, case.init_p = inputs.random_state(case, seed=5)
-    one = gpu_run(case, 37, launch=(64, 1, 1))
-    staged = gpu_run(case, 37, launch=(128, 1, 3))
-    tol = {"f16": 2e-3, "bf16": 1.6e-2}[storage]
-    assert rel_max(staged["f"], one["f"]) <= tol
-
-
-def test_row_staged_falls_back_and_rejects():
-    """cells_per_thread 3 on a domain it cannot stage (nx not a multiple of
-    8) runs one cell per thread, bit for bit; FP64 storage rejects it."""
-    case = inputs.Case("fb", 18, 13, 7, 5, (1, 2, 0, 0, 2, 1), np.full((6, 3), 0.01),
-                       nu=0.05, storage="f32", u_ref=0.01)
-    case.init_u, case.init_p = inputs.random_state(case, seed=6)
-    a = gpu_run(case, 9, launch=(32, 1, 3))
-    b = gpu_run(case, 9, launch=(32, 1, 1))
-    np.testing.assert_array_equal(a["f"], b["f"])
-    h = lbm.lbm_create(18, 16, 8, 8, "f64", None)
-    try:
-        with pytest.raises(lbm.LBMError) as ei:
-            lbm.lbm_set_launch(h, 128, 1, 3)
-        assert ei.value.code == lbm.LBM_EINVAL
-    finally:
-        lbm.lbm_destroy(h)
