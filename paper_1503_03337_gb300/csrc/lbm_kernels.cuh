@@ -398,62 +398,13 @@ __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
   scatter<Q, S, R, ODD, SR, SYM>(d, f, i, L, fv, SR ? *key : 0u);
 }
 
-// Odd step of a cell in an interior row (y, z away from their faces) whose
-// warp touches x = 0 or x = nx-1, when neither x face is moving or a
-// symmetry plane: the interior offset tables, with each link that leaves
-// through an x face redirected (wall: the cell's own slot, as in gather and
-// scatter; periodic: wrapped by nx).
-template <int Q, typename S, typename R, bool FORCE, bool SR, bool CG>
-__host__ __device__ __forceinline__ void update_x_edge(const Domain<R>& d, S* __restrict__ f,
-                                                       int i, int x, const R* F,
-                                                       const uint32_t* key) {
-  const int N = (int)d.N, nx = d.nx;
-  const bool lo = x == 0, hi = x == nx - 1, per = d.per[0] != 0;
-  const S* __restrict__ fc = f + i;
-  R fv[Q];
-  [&]<int... A>(std::integer_sequence<int, A...>) {
-    (
-        [&] {
-          constexpr int cx = Lattice<Q>::c(A, 0);
-          int off = d.pull[A];
-          if constexpr (cx > 0) {
-            if (lo) off = per ? off + nx : A * N;
-          } else if constexpr (cx < 0) {
-            if (hi) off = per ? off - nx : A * N;
-          }
-          fv[A] = load_pop<S, R, CG>(fc + off);
-        }(),
-        ...);
-  }(std::make_integer_sequence<int, Q>{});
-  R ux, uy, uz;
-  collide<Q, FORCE>(fv, d.s, F[0], F[1], F[2], ux, uy, uz);
-  const uint32_t h = SR ? mix32(uint32_t(i) ^ *key) : 0u;
-  S* __restrict__ fw = f + i;
-  [&]<int... A>(std::integer_sequence<int, A...>) {
-    (
-        [&] {
-          constexpr int cx = Lattice<Q>::c(A, 0);
-          int off = d.push[A];
-          if constexpr (cx > 0) {
-            if (hi) off = per ? off - nx : opposite<Q>(A) * N;
-          } else if constexpr (cx < 0) {
-            if (lo) off = per ? off + nx : opposite<Q>(A) * N;
-          }
-          put<S, R, SR, A>(fw + off, fv[A], h);
-        }(),
-        ...);
-  }(std::make_integer_sequence<int, Q>{});
-}
-
 // The whole fused update of one cell: gather (stream), collide, scatter.
 // Odd steps pick one of three addressing variants.  `x_lo`..`x_hi` is the
 // x-range of the calling warp: when a warp lies within one x-row (block
 // width a multiple of 32) every test below is uniform across the warp, so
-// the variants never diverge inside a warp.  Warps at the ends of interior
-// rows take update_x_edge when the x faces are stationary walls or periodic.
-// The general boundary variants come with and without the mirrored links of
-// symmetry faces (d.sym is uniform across the grid), so domains without one
-// pay nothing for them.
+// the variants never diverge inside a warp.  The two boundary variants come
+// with and without the mirrored links of symmetry faces (d.sym is uniform
+// across the grid), so domains without one pay nothing for them.
 // update_cell_at reads the step's body force F[0..2] and rounding key *key
 // where they are used (F and key may live outside the descriptor);
 // update_cell takes them from the descriptor.
@@ -471,8 +422,6 @@ __host__ __device__ __forceinline__ void update_cell_at(const Domain<R>& d, S* _
       if (x_lo > 0 && x_hi < d.nx - 1)
         update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_interior(d), F,
                                                         key);
-      else if (!((d.moving | d.sym) & 3))
-        update_x_edge<Q, S, R, FORCE, SR, CG>(d, f, i, x, F, key);
       else if (d.sym)
         update_with_links<Q, S, R, true, FORCE, SR, CG, true>(d, f, i, make_links_x(d, x), F,
                                                               key);
