@@ -44,65 +44,6 @@ __global__ void __launch_bounds__(256, 3) k_step_pair(Domain<float> d) {
   update_pair_even<Q, S, FORCE>(d, static_cast<S*>(d.f), x0 + d.nx * (y + d.ny * z));
 }
 
-// Odd steps with the cells ordered by kind.  Threads 0 .. interior-1 take
-// the cells whose neighbours are all fluid and unwrapped (1 <= x <= nx-2,
-// likewise y and z) in linear order, so every warp there runs the interior
-// offset tables; a warp may span two rows, whose cells stay a few elements
-// apart.  The threads after them take the other cells (update_cell_at's
-// boundary variants): first x = 0 and x = nx-1 of the interior rows, then
-// every cell of the boundary rows (the z = 0 and z = nz-1 planes, then y = 0
-// and y = ny-1 of the planes between).  Needs nx, ny, nz >= 3.
-struct OddSplit {
-  int ix, iy;     // nx - 2, ny - 2
-  int interior;   // (nx-2)(ny-2)(nz-2)
-  int other;      // N - interior
-};
-
-__device__ __forceinline__ void odd_split_other(int nx, int ny, int nz, int g, int& x, int& y,
-                                                int& z) {
-  const int iy = ny - 2, ends = iy * (nz - 2) * 2;
-  if (g < ends) {
-    const int r = g >> 1;
-    x = (g & 1) ? nx - 1 : 0;
-    y = 1 + r % iy;
-    z = 1 + r / iy;
-    return;
-  }
-  g -= ends;
-  int r = g / nx;
-  x = g - r * nx;
-  if (r < 2 * ny) {
-    y = r % ny;
-    z = r < ny ? 0 : nz - 1;
-    return;
-  }
-  r -= 2 * ny;
-  z = 1 + (r >> 1);
-  y = (r & 1) ? ny - 1 : 0;
-}
-
-template <int Q, typename S, typename R, bool FORCE, bool SR>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4)
-    k_step_odd_split(Domain<R> d, OddSplit p) {
-  pdl_release();
-  pdl_acquire();
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  S* f = static_cast<S*>(d.f);
-  if (g < p.interior) {
-    const int r = g / p.ix;
-    const int x = 1 + (g - r * p.ix);
-    const int y = 1 + r % p.iy, z = 1 + r / p.iy;
-    update_with_links<Q, S, R, true, FORCE, SR>(d, f, x + d.nx * (y + d.ny * z),
-                                                make_links_interior(d), d.F, &d.key);
-  } else if (g - p.interior < p.other) {
-    int x, y, z;
-    odd_split_other(d.nx, d.ny, d.nz, g - p.interior, x, y, z);
-    update_cell_at<Q, S, R, true, FORCE, SR>(d, f, d.F, &d.key, x, y, z, -1, -1);
-  }
-}
-
-constexpr bool kOddSplit = true;  // odd steps of domains with nx, ny, nz >= 3
-
 template <typename R>
 void launch_one(void (*kernel)(Domain<R>), const Domain<R>& d, dim3 grid, dim3 block, bool pdl,
                 cudaStream_t st) {
@@ -122,16 +63,7 @@ void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 blo
       return;
     }
   }
-  if (odd && kOddSplit && d.nx >= 3 && d.ny >= 3 && d.nz >= 3) {
-    OddSplit p;
-    p.ix = d.nx - 2;
-    p.iy = d.ny - 2;
-    p.interior = p.ix * p.iy * (d.nz - 2);
-    p.other = (int)d.N - p.interior;
-    const dim3 g1((unsigned)((d.N + 255) / 256)), b1(256);
-    if (force) launch_pdl(k_step_odd_split<Q, S, R, true, SR>, g1, b1, b.pdl != 0, st, d, p);
-    else launch_pdl(k_step_odd_split<Q, S, R, false, SR>, g1, b1, b.pdl != 0, st, d, p);
-  } else if (odd) {
+  if (odd) {
     if (force) launch_one(k_step<Q, S, R, true, true, SR>, d, grid, block, b.pdl != 0, st);
     else launch_one(k_step<Q, S, R, true, false, SR>, d, grid, block, b.pdl != 0, st);
   } else {
