@@ -61,10 +61,12 @@ def parse():
     ap.add_argument("--launch", default="",
                     help="fixed launch shape bx,by,cells_per_thread instead of the autotuner")
     ap.add_argument("--workload", default="cavity128",
-                    choices=("cavity128", "batch256", "serving"),
+                    choices=("cavity128", "batch256", "serving", "half_cavity97"),
                     help="cavity128: the fused-step throughput line (default); batch256: "
                          "256 uneven domains, batched vs one launch per domain; serving: "
-                         "request trace, batched server vs one domain at a time")
+                         "request trace, batched server vs one domain at a time; "
+                         "half_cavity97: the Sec. 4.3 half cavity 97x97x49 at Re 3200, "
+                         "throughput and the MRT / LBGK stability comparison")
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-steps", type=int, default=1000)
     ap.add_argument("--saturation-cells", type=int, default=8 << 20,
@@ -603,6 +605,86 @@ def run_serving(a):
             "batched": out["batched"], "one_at_a_time": out["one_at_a_time"]}
 
 
+def run_half_cavity(a):
+    """The cavity of Sec. 4.3 on its grid: the 97 x 97 x 49 half cavity
+    (symmetry face at z = 1/2, lid 0.1 with the corner velocities), Re 3200,
+    D3Q18 FP32.  Throughput of a.steps back-to-back steps under CUDA events,
+    then the stability comparison: 50000 steps each with the MRT rates and
+    with every rate 1/tau (LBGK), checked every 1000 steps."""
+    import torch
+
+    from paper_1503_03337_gb300 import lbm
+    lbm.load()
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    case = inputs.half_cavity(18, 97, 3200.0, U=0.1, storage="f32", ku_lid=True)
+    s_lbgk = 1.0 / (3.0 * case.nu + 0.5)
+    lbgk = dict(s_c=s_lbgk, s_e=s_lbgk, s_q=s_lbgk, s_pi=s_lbgk, s_t=s_lbgk)
+
+    def open_case(rates, interval):
+        h = lbm.lbm_create(case.Q, case.nx, case.ny, case.nz, case.storage, sp)
+        lbm.lbm_set_geometry(h, case.faces, case.u_wall, case.edge)
+        lbm.lbm_set_params(h, nu=case.nu, residual_interval=interval, **rates)
+        lbm.lbm_autotune(h)
+        lbm.lbm_init_equilibrium(h)
+        return h
+
+    out = {}
+    with torch.cuda.stream(stream):
+        # the 33 MB population buffer fits in L2: each timed step follows a
+        # 256 MiB flush (write, then read), outside its event pair
+        steps = max(2, min(a.steps, 400) + (min(a.steps, 400) & 1))
+        flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+        sink = torch.empty(1, dtype=torch.float32, device="cuda")
+        h = open_case({}, 0)
+        lbm.lbm_step(h, max(4, a.warmup))
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            sink.copy_(flush.sum().reshape(1))
+            ev[k][0].record(stream)
+            lbm.lbm_step(h, 1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        launch = lbm.lbm_get_launch(h)
+        lbm.lbm_destroy(h)
+        for name, rates in (("mrt", {}), ("lbgk", lbgk)):
+            h = open_case(rates, 1000)
+            diverged = None
+            for k in range(0, 50000, 1000):
+                try:
+                    lbm.lbm_step(h, 1000)
+                    st = lbm.lbm_reductions(h)
+                except lbm.LBMError:
+                    diverged = k + 1000
+                    break
+                if st.nonfinite:
+                    diverged = k + 1000
+                    break
+            out[name] = {"steps": 50000, "diverged_by_step": diverged,
+                         "max_abs_u": None if diverged else st.max_abs_u}
+            lbm.lbm_destroy(h)
+    peak, peak_kind = measured_hbm_peak()
+    bytes_per_step = 2 * case.Q * 4 * case.cells
+    achieved = bytes_per_step / (ms * 1e-3) / 1e9
+    return {"metric": "half-cavity GLUPS and MRT/LBGK stability at Re 3200",
+            "value": round(case.cells / (ms * 1e-3) / 1e9, 3), "unit": "GLUPS",
+            "higher_is_better": True, "n_gpus": 1, "steps": steps, "ms_per_step": ms,
+            "dtype": "f32", "data": "synthetic (half cavity from rest)",
+            "config": {"workload": "half cavity 97x97x49 D3Q18 F32 Re=3200 lid=0.1, "
+                                   "symmetry face z+, lid corner velocities 0.3/1.0",
+                       "launch": list(launch),
+                       "l2": "population buffer 33 MB fits in L2: each timed step follows "
+                             "a 256 MiB L2 flush (write then read), outside its events"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_kind": peak_kind},
+            "stability": out}
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -625,7 +707,8 @@ def main():
         print(json.dumps(out))
         return
     if a.workload != "cavity128":
-        fn = run_batch256 if a.workload == "batch256" else run_serving
+        fn = {"batch256": run_batch256, "serving": run_serving,
+              "half_cavity97": run_half_cavity}[a.workload]
         if rank == 0:
             print(json.dumps(fn(a)))
         return
