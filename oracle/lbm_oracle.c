@@ -12,15 +12,15 @@
  *
  * The update follows the paper's order (Sec. 3, Eq. mrteqvT):
  *   1. P = sum f, j = sum c f                       (Eq. hgl)
- *   2. u = j + F/2, p from P and |u|^2               (Eq. hgl; forcing reading G4)
+ *   2. u = j + F/2, p from P and |u|^2               (Eq. hgl; Guo forcing)
  *   3. m = T f with the printed T                    (Eq. T14 / App. B)
  *   4. m_eq from the printed closed forms            (Eq. meq / App. B)
- *   5. S_F = T Fbar, P row dropped                   (forcing reading G4)
+ *   5. S_F = T Fbar, P row dropped                   (Guo forcing)
  *   6. m* = m - S (m - m_eq) + (I - S/2) S_F         (Eq. mrteqvT, diagonal S)
  *   7. f* = T^-1 m* with T^-1 = T' D^-1              (rows of T are orthogonal)
  *   8. pull streaming; a link whose source lies beyond a wall takes the
  *      cell's own reflected population plus 6 w (c . u_wall)
- *      (halfway and moving-wall bounce-back, readings G5/G6)
+ *      (halfway and moving-wall bounce-back)
  *
  * Layout of every population array: f[a][z][y][x], a = 0..Q-1 holding the
  * paper's 1-based direction a+1, x fastest.
@@ -102,7 +102,7 @@ static int model_init(int Q, model *m) {
     m->Q = 14;
     m->c = C14;
     m->T = &T14[0][0];
-    /* Reading G1: the weights printed beside Eq. edf belong to D3Q19; the
+    /* The weights printed beside Eq. edf belong to D3Q19; the
      * Q14 equilibria of Eq. meq hold only with the D3Q15 weights
      * w0 = 2/9, 1/9 on the axes and 1/72 on the cube diagonals. */
     m->w0 = 2.0 / 9.0;
@@ -229,7 +229,7 @@ static void collide_cell(const model *m, const double *s, const double *f,
   moment_equilibrium(m, p, u, meq);
 
   /* Guo source in velocity space, Fbar_a = w_a [3 c.F + 9 (c.u)(c.F) - 3 u.F],
-   * projected with T; the P row is dropped (reading G4). */
+   * projected with T; the P row is dropped. */
   double Fbar[18];
   const double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
   for (int a = 0; a < Q; ++a) {
@@ -271,8 +271,8 @@ static int n_axis(const oracle_grid *g, int d) {
  * source node if it is a fluid node (after periodic wraps and symmetry-plane
  * mirrors); returns 0 if it is a ghost node beyond a wall, and sets uw to
  * that ghost node's wall velocity: the velocity of the first moving face
- * (x-, x+, y-, y+, z-, z+ order) the ghost lies beyond, else zero (reading
- * G6, edge and corner ghosts of a lid layer count as lid).
+ * (x-, x+, y-, y+, z-, z+ order) the ghost lies beyond, else zero (so
+ * edge and corner ghosts of a lid layer count as lid).
  *
  * A symmetry face is a free-slip plane halfway between the last node and its
  * ghost layer: the ghost mirrors the node across the plane, so a source
@@ -280,7 +280,7 @@ static int n_axis(const oracle_grid *g, int d) {
  * that axis) and *mirror gets the axis bit (the population arriving at x
  * left that node with the normal component of its velocity reversed).  A
  * source beyond a wall on any axis is a wall link even if it also lies
- * beyond a symmetry face (reading G14). */
+ * beyond a symmetry face (the wall extends across the mirror plane). */
 static int pull_source(const oracle_grid *g, const int xyz[3], const int c[3],
                        int src[3], double uw[3], int *mirror) {
   int beyond[6] = {0, 0, 0, 0, 0, 0};

@@ -79,7 +79,7 @@ def test_c3_pulsatile_gre(storage):
     omega = 2 * np.pi / T
     xs = an.lattice_coords(N)
     Y, X = np.meshgrid(xs, xs, indexing="ij")
-    Uc = an.pulsatile_amplitude(X, Y, b, b, case.nu, omega, -A)  # G = -A (reading G10)
+    Uc = an.pulsatile_amplitude(X, Y, b, b, case.nu, omega, -A)  # G = -A (F = -dp/dx)
     U = float(np.max(np.abs(Uc)))
     assert abs(U - 0.03) < 1e-4
     u0 = np.zeros((3, nz, N, N))

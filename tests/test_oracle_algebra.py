@@ -76,7 +76,7 @@ def test_transform_orthogonal_and_inverse(Q):
 @pytest.mark.parametrize("Q", QS)
 def test_weights_isotropy(Q):
     """With the rest weight w0, the weights satisfy the standard lattice
-    isotropy conditions up to fourth order with c_s^2 = 1/3 (reading G1)."""
+    isotropy conditions up to fourth order with c_s^2 = 1/3."""
     w, w0 = oracle.weights(Q)
     c = oracle.velocities(Q).astype(float)
     cs2 = 1.0 / 3.0
@@ -176,7 +176,7 @@ def test_equilibrium_is_fixed_point(Q):
 @pytest.mark.parametrize("Q", QS)
 def test_force_adds_exact_momentum(Q):
     """With u = j + F/2 and the (I - S/2) Guo source, j* = j + F for any s_c,
-    and P is unchanged (reading G4)."""
+    and P is unchanged (the P row of the Guo source is dropped)."""
     rng = np.random.default_rng(6)
     c = oracle.velocities(Q).astype(float)
     for _ in range(20):
@@ -190,7 +190,7 @@ def test_force_adds_exact_momentum(Q):
 @pytest.mark.parametrize("Q", QS)
 def test_force_source_second_moment(Q):
     """Guo's source gives the momentum flux u F + F u.  With the P row of the
-    source dropped (reading G4) the deviatoric part is untouched, mass is not
+    source dropped the deviatoric part is untouched, mass is not
     injected, and the trace loses exactly the P-row share
     3 w0 (u.F) sum|c|^2 / Q.  Checked at S = 0 so that only the source acts."""
     rng = np.random.default_rng(7)
@@ -214,7 +214,7 @@ def test_force_source_second_moment(Q):
 
 @pytest.mark.parametrize("Q", QS)
 def test_pressure_shift_invariance(Q):
-    """f -> f + 3 w dp commutes with the collision (reading G7)."""
+    """f -> f + 3 w dp commutes with the collision."""
     rng = np.random.default_rng(8)
     w, _ = oracle.weights(Q)
     for _ in range(10):

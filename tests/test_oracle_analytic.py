@@ -143,7 +143,7 @@ def test_pulsatile_gre(Q):
     omega = 2 * np.pi / T
     nu = b * b * omega / eta ** 2
     A = 1e-4
-    G = -A  # F = -dp/dx, dp/dx = G cos(w t)  (reading G10)
+    G = -A  # F = -dp/dx, dp/dx = G cos(w t)
     xs = an.lattice_coords(N)
     Y, X = np.meshgrid(xs, xs, indexing="ij")
     Uc = an.pulsatile_amplitude(X, Y, b, b, nu, omega, G)

@@ -1,8 +1,7 @@
 """Pins of the oracle's streaming and boundary rules on tiny grids.
 
 Streaming is isolated by a collision that does nothing (S = 0, F = 0), then
-compared with a per-link table built here from the rules of readings G5/G6,
-G14 and G15: a link whose source node lies beyond a wall carries the cell's
+compared with a per-link table built here from the boundary rules: a link whose source node lies beyond a wall carries the cell's
 own reflected population plus 6 w (c . u_wall), u_wall scaled by the face's
 edge profile in the first and last node columns; across a symmetry face the
 source is the node's mirror image and the pulled population the mirror one.
@@ -108,8 +107,8 @@ def test_mass_conserved_with_walls(Q):
 @pytest.mark.parametrize("Q", (14, 18))
 def test_mass_conserved_with_profiled_lid(Q):
     """A tangential lid whose velocity is scaled in its first and last
-    columns (reading G15: the scale belongs to the cell, so every link of a
-    cell sees one wall velocity) still conserves sum_x P exactly."""
+    columns (the scale belongs to the cell, so every link of a cell sees
+    one wall velocity) still conserves sum_x P exactly."""
     rng = np.random.default_rng(13)
     u_wall = np.zeros((6, 3))
     u_wall[3] = (0.08, 0.0, 0.03)

@@ -1,8 +1,7 @@
 """Symmetry (free-slip) faces of the oracle, pinned against its wall
 streaming: a box that is mirror-symmetric about a mid-plane computes, in its
 lower half, what the half box computes with a symmetry face on that plane
-(reading G14: the ghost beyond a symmetry face mirrors the node across the
-plane)."""
+(the ghost beyond a symmetry face mirrors the node across the plane)."""
 import numpy as np
 import pytest
 
