@@ -37,6 +37,10 @@ def emu():
     L.emu_canonical.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip,
                                 ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, ctypes.c_int64,
                                 ctypes.c_int]
+    L.emu_canonical_storage.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ip, ctypes.c_int,
+                                        ctypes.c_int, ip, dp, dp, dp, ctypes.c_int64,
+                                        ctypes.c_int]
     L.emu_collide.argtypes = [ctypes.c_int, dp, dp, dp]
     return L
 
@@ -167,3 +171,39 @@ def test_restore_at_odd_parity(emu, Q):
     f = inputs.random_populations(Q, (3, 4, 5), seed=1)
     d.put(f, 7)
     np.testing.assert_allclose(d.get(), f, atol=1e-17)
+
+
+@pytest.mark.parametrize("storage,dtype,tol", ((1, np.float32, 2e-6), (2, np.float16, 3e-3)))
+@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("name,shape,faces,edge", [e for e in EDGE if e[0] in
+                                                   ("sym_lid", "sym_corner", "edge_multi",
+                                                    "sym_wide_x")])
+def test_reduced_storage_step_matches_oracle(emu, Q, name, shape, faces, edge, storage, dtype,
+                                             tol):
+    """FP32 and FP16 storage (FP32 arithmetic) of the kernel's per-cell code
+    with symmetry faces and edge profiles: 7 steps from a seeded state
+    against the FP64 oracle, to the storage precision."""
+    rng = np.random.default_rng(8)
+    uw = rng.normal(size=(6, 3)) * 0.03
+    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
+                       nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64",
+                       edge=edge)
+    g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw, edge=edge)
+    prm = oracle.make_params(oracle.rates(Q, case.s_nu), force=case.force, period=case.period)
+    u0, p0 = inputs.random_state(case, seed=2)
+    f0 = oracle.init_equilibrium(g, u0, p0)
+    d = EmuDomain(emu, case)
+    A = np.zeros(d.A.shape, dtype=dtype)
+    canon = np.ascontiguousarray(f0, dtype=np.float64)
+    assert emu.emu_canonical_storage(Q, storage, A.ctypes.data, *shape, *d._geom(), _d(canon),
+                                     0, 1) == 0
+    for n in range(7):
+        amp = np.cos(2 * np.pi * n / case.period)
+        F = np.array(case.force, dtype=np.float64) * amp
+        assert emu.emu_step(Q, storage, A.ctypes.data, *shape, *d._geom(), _d(d.s), _d(F),
+                            n) == 0
+    out = np.zeros_like(canon)
+    assert emu.emu_canonical_storage(Q, storage, A.ctypes.data, *shape, *d._geom(), _d(out),
+                                     7, 0) == 0
+    ref = oracle.run(g, prm, f0, 0, 7, nthreads=1)
+    assert np.max(np.abs(out - ref)) <= tol * np.max(np.abs(ref))
