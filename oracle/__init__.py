@@ -23,7 +23,7 @@ _LIB_PATH = os.path.join(_HERE, "liblbm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PERIODIC, WALL, MOVING_WALL, SYMMETRY = 0, 1, 2, 3
+PERIODIC, WALL, MOVING_WALL, SYMMETRY, NEQ_VELOCITY, NEQ_PRESSURE = 0, 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -58,7 +58,8 @@ class Rates(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("rates", Rates), ("force", ctypes.c_double * 3),
-                ("period", ctypes.c_double)]
+                ("period", ctypes.c_double), ("p_face", ctypes.c_double * 6),
+                ("p_amp", ctypes.c_double * 6), ("p_period", ctypes.c_double)]
 
 
 def lib():
@@ -138,6 +139,12 @@ def feq(Q: int, p: float, u) -> np.ndarray:
     return out
 
 
+def s_nu_of(nu: float) -> float:
+    """Eq. vis: nu = c_s^2 (tau - 1/2) with c_s^2 = 1/3 and s_nu = 1/tau, so
+    s_nu = 1 / (3 nu + 1/2) in lattice units."""
+    return 1.0 / (3.0 * nu + 0.5)
+
+
 def rates(Q: int, snu: float, sc=1.0, se=1.19, sq=1.2, st=0.98, spi=None) -> Rates:
     """Relaxation rates of Sec. 4 (sc=1, se=1.19, sq=1.2, st=0.98, snu=1/tau);
     for Q18 the paper leaves s_pi open and the default reading is s_pi = se."""
@@ -169,12 +176,19 @@ def make_grid(Q, nx, ny, nz, faces=(WALL,) * 6, u_wall=None, edge=None) -> Grid:
     return g
 
 
-def make_params(r: Rates, force=(0.0, 0.0, 0.0), period=0.0) -> Params:
+def make_params(r: Rates, force=(0.0, 0.0, 0.0), period=0.0, p_face=None, p_amp=None,
+                p_period=0.0) -> Params:
+    """p_face / p_amp: pressure of each NEQ_PRESSURE face,
+    p_face + p_amp cos(2 pi n / p_period) (constant if p_period <= 0)."""
     p = Params()
     p.rates = r
     for d in range(3):
         p.force[d] = float(force[d])
     p.period = float(period)
+    for f in range(6):
+        p.p_face[f] = 0.0 if p_face is None else float(p_face[f])
+        p.p_amp[f] = 0.0 if p_amp is None else float(p_amp[f])
+    p.p_period = float(p_period)
     return p
 
 

@@ -21,6 +21,11 @@
  *   8. pull streaming; a link whose source lies beyond a wall takes the
  *      cell's own reflected population plus 6 w (c . u_wall)
  *      (halfway and moving-wall bounce-back)
+ *   9. non-equilibrium extrapolation (Sec. 4, the boundary scheme the paper
+ *      always applies): every node on a face of kind ORACLE_NEQ_* takes
+ *      f = f_eq(p_b, u_b) + [f(x_f) - f_eq(p_f, u_f)] from its inward
+ *      neighbour x_f, with u_b given on velocity faces (p_b = p_f) and p_b
+ *      given on pressure faces (u_b = u_f)
  *
  * Layout of every population array: f[a][z][y][x], a = 0..Q-1 holding the
  * paper's 1-based direction a+1, x fastest.
@@ -339,6 +344,76 @@ static double force_at(const oracle_params *prm, int64_t n, int d) {
   return prm->force[d];
 }
 
+static int is_neq(int kind) {
+  return kind == ORACLE_NEQ_VELOCITY || kind == ORACLE_NEQ_PRESSURE;
+}
+
+static double face_pressure(const oracle_params *prm, int face, int64_t n) {
+  if (prm->p_period > 0.0)
+    return prm->p_face[face] + prm->p_amp[face] * cos(2.0 * M_PI * (double)n / prm->p_period);
+  return prm->p_face[face];
+}
+
+/* Equilibrium populations, Eq. edf with lambda_a = w_a p / c_s^2 (c_s^2 = 1/3) */
+static void feq_cell(const model *m, double p, const double u[3], double *feq) {
+  const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int a = 0; a < m->Q; ++a) {
+    const double cu = m->c[a][0] * u[0] + m->c[a][1] * u[1] + m->c[a][2] * u[2];
+    feq[a] = m->w[a] * 3.0 * p + m->w[a] * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+  }
+}
+
+/* Non-equilibrium extrapolation of every node on an ORACLE_NEQ_* face, on
+ * the pre-collision populations f of step n (in place).  The inward
+ * neighbour x_f of a node is one node inward along the normal of every such
+ * face the node lies on (diagonally inward on edges and corners); it is
+ * never itself on such a face when those axes have at least 3 nodes, so the
+ * order of the nodes does not matter.  A node on a velocity face takes the
+ * velocity of the first such face in x-, x+, y-, y+, z-, z+ order and the
+ * pressure of x_f; a node only on pressure faces takes the pressure of the
+ * first one and the velocity of x_f. */
+static void neq_extrapolate(const model *m, const oracle_grid *g, const oracle_params *prm,
+                            int64_t n, double *f) {
+  const int Q = m->Q, nx = g->nx, ny = g->ny, nz = g->nz;
+  const int64_t N = (int64_t)nx * ny * nz;
+  const double F[3] = {force_at(prm, n, 0), force_at(prm, n, 1), force_at(prm, n, 2)};
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int xyz[3] = {x, y, z};
+        int xf[3] = {x, y, z};
+        int vel_face = -1, pre_face = -1;
+        for (int d = 0; d < 3; ++d) {
+          const int nd = n_axis(g, d);
+          for (int side = 0; side < 2; ++side) {
+            const int face = 2 * d + side;
+            const int on = side == 0 ? xyz[d] == 0 : xyz[d] == nd - 1;
+            if (!on || !is_neq(g->face[face])) continue;
+            xf[d] = side == 0 ? 1 : nd - 2;
+            if (g->face[face] == ORACLE_NEQ_VELOCITY && vel_face < 0) vel_face = face;
+            if (g->face[face] == ORACLE_NEQ_PRESSURE && pre_face < 0) pre_face = face;
+          }
+        }
+        if (vel_face < 0 && pre_face < 0) continue;
+        const int64_t ib = ((int64_t)z * ny + y) * nx + x;
+        const int64_t jf = ((int64_t)xf[2] * ny + xf[1]) * nx + xf[0];
+        double P = 0.0, uf[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < Q; ++a) {
+          P += f[a * N + jf];
+          for (int d = 0; d < 3; ++d) uf[d] += (double)m->c[a][d] * f[a * N + jf];
+        }
+        for (int d = 0; d < 3; ++d) uf[d] += 0.5 * F[d];
+        const double pf = pressure(m, P, uf);
+        double ub[3], pb;
+        for (int d = 0; d < 3; ++d) ub[d] = vel_face >= 0 ? g->u_wall[vel_face][d] : uf[d];
+        pb = pre_face >= 0 ? face_pressure(prm, pre_face, n) : pf;
+        double eb[18], ef[18];
+        feq_cell(m, pb, ub, eb);
+        feq_cell(m, pf, uf, ef);
+        for (int a = 0; a < Q; ++a) f[a * N + ib] = eb[a] + (f[a * N + jf] - ef[a]);
+      }
+}
+
 /* ---- public entry points --------------------------------------------------- */
 
 int oracle_velocities(int Q, int *c_out) {
@@ -425,6 +500,9 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
   const int Q = m.Q;
   const int nx = g->nx, ny = g->ny, nz = g->nz;
   const int64_t N = (int64_t)nx * ny * nz;
+  for (int d = 0; d < 3; ++d)
+    if ((is_neq(g->face[2 * d]) || is_neq(g->face[2 * d + 1])) && n_axis(g, d) < 3)
+      return -3; /* an extrapolation boundary needs an inward neighbour */
   double s[18];
   relaxation_diag(&m, &prm->rates, s);
   int opp[18];
@@ -469,6 +547,9 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
       }
   }
   free(fpost);
+  int any_neq = 0;
+  for (int face = 0; face < 6; ++face) any_neq |= is_neq(g->face[face]);
+  if (any_neq) neq_extrapolate(&m, g, prm, n + 1, f_out);
   return 0;
 }
 

@@ -12,7 +12,18 @@
 extern "C" {
 #endif
 
-enum { ORACLE_PERIODIC = 0, ORACLE_WALL = 1, ORACLE_MOVING_WALL = 2, ORACLE_SYMMETRY = 3 };
+enum {
+  ORACLE_PERIODIC = 0,
+  ORACLE_WALL = 1,
+  ORACLE_MOVING_WALL = 2,
+  ORACLE_SYMMETRY = 3,
+  /* Non-equilibrium extrapolation boundaries (Sec. 4, after Guo, Zheng and
+   * Shi): the outermost node layer lies on the boundary.  After each step
+   * every boundary node takes f = f_eq(p_b, u_b) + f(x_f) - f_eq(p_f, u_f),
+   * x_f its inward neighbour, (p_f, u_f) the macroscopic values there. */
+  ORACLE_NEQ_VELOCITY = 4, /* u_b = u_wall of the face, p_b = p_f        */
+  ORACLE_NEQ_PRESSURE = 5  /* p_b = the face's pressure, u_b = u_f       */
+};
 
 typedef struct {
   int Q;              /* 14 or 18 */
@@ -35,6 +46,11 @@ typedef struct {
   oracle_rates rates;
   double force[3]; /* body force amplitude (lattice units) */
   double period;   /* > 0: F(t_n) = force cos(2 pi n / period); else constant */
+  /* pressure of each ORACLE_NEQ_PRESSURE face at step n:
+   * p_face[f] + p_amp[f] cos(2 pi n / p_period) (p_period > 0), else p_face[f] */
+  double p_face[6];
+  double p_amp[6];
+  double p_period;
 } oracle_params;
 
 int oracle_velocities(int Q, int *c_out);           /* Q*3 ints */
