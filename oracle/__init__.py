@@ -47,7 +47,8 @@ class Grid(ctypes.Structure):
                 ("face", ctypes.c_int * 6),
                 ("u_wall", (ctypes.c_double * 3) * 6),
                 ("edge_axis", ctypes.c_int * 6),
-                ("edge_scale", (ctypes.c_double * 2) * 6)]
+                ("edge_scale", (ctypes.c_double * 2) * 6),
+                ("solid", ctypes.c_void_p)]
 
 
 class Rates(ctypes.Structure):
@@ -161,10 +162,15 @@ def collide(Q: int, r: Rates, f, F=(0.0, 0.0, 0.0)) -> np.ndarray:
 
 # ---- whole-grid operations -----------------------------------------------------
 
-def make_grid(Q, nx, ny, nz, faces=(WALL,) * 6, u_wall=None, edge=None) -> Grid:
+def make_grid(Q, nx, ny, nz, faces=(WALL,) * 6, u_wall=None, edge=None, solid=None) -> Grid:
     """edge: {face: (axis, scale_first, scale_last)}, the edge profile of a
-    moving face (see lbm_oracle.h)."""
+    moving face (see lbm_oracle.h); solid: None or an (nz, ny, nx) array,
+    nonzero at solid nodes (kept alive by the returned grid)."""
     g = Grid()
+    if solid is not None:
+        mask = np.ascontiguousarray(np.asarray(solid).reshape(nz, ny, nx) != 0, dtype=np.uint8)
+        g._solid = mask  # the C side holds a pointer into it
+        g.solid = mask.ctypes.data
     g.Q, g.nx, g.ny, g.nz = Q, nx, ny, nz
     for i in range(6):
         g.face[i] = int(faces[i])

@@ -21,6 +21,8 @@
  *   8. pull streaming; a link whose source lies beyond a wall takes the
  *      cell's own reflected population plus 6 w (c . u_wall)
  *      (halfway and moving-wall bounce-back)
+ *      A source that is a solid node of the grid's solid mask is a wall
+ *      link at rest (halfway bounce-back off an arbitrary solid)
  *   9. non-equilibrium extrapolation (Sec. 4, the boundary scheme the paper
  *      always applies): every node on a face of kind ORACLE_NEQ_* takes
  *      f = f_eq(p_b, u_b) + [f(x_f) - f_eq(p_f, u_f)] from its inward
@@ -309,7 +311,11 @@ static int pull_source(const oracle_grid *g, const int xyz[3], const int c[3],
     src[d] = v;
   }
   uw[0] = uw[1] = uw[2] = 0.0;
-  if (!solid) return 1;
+  if (!solid) {
+    if (g->solid && g->solid[((int64_t)src[2] * g->ny + src[1]) * g->nx + src[0]])
+      return 0; /* a solid node: bounce-back off a wall at rest */
+    return 1;
+  }
   for (int face = 0; face < 6; ++face) {
     if (beyond[face] && g->face[face] == ORACLE_MOVING_WALL) {
       double scale = 1.0;
@@ -488,7 +494,8 @@ int oracle_init_equilibrium(const oracle_grid *g, const double *u,
     const double pi = p ? p[i] : 0.0;
     double feq[18];
     oracle_feq(g->Q, pi, ui, feq);
-    for (int a = 0; a < g->Q; ++a) f[a * N + i] = feq[a];
+    const int solid = g->solid && g->solid[i];
+    for (int a = 0; a < g->Q; ++a) f[a * N + i] = solid ? 0.0 : feq[a];
   }
   return 0;
 }
@@ -503,6 +510,8 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
   for (int d = 0; d < 3; ++d)
     if ((is_neq(g->face[2 * d]) || is_neq(g->face[2 * d + 1])) && n_axis(g, d) < 3)
       return -3; /* an extrapolation boundary needs an inward neighbour */
+  for (int face = 0; face < 6; ++face)
+    if (g->solid && is_neq(g->face[face])) return -4; /* not combined */
   double s[18];
   relaxation_diag(&m, &prm->rates, s);
   int opp[18];
@@ -520,6 +529,10 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         const int64_t i = ((int64_t)z * ny + y) * nx + x;
+        if (g->solid && g->solid[i]) {
+          for (int a = 0; a < Q; ++a) fpost[a * N + i] = 0.0;
+          continue;
+        }
         for (int a = 0; a < Q; ++a) fc[a] = f_in[a * N + i];
         collide_cell(&m, s, fc, F, fp, NULL, NULL);
         for (int a = 0; a < Q; ++a) fpost[a * N + i] = fp[a];
@@ -532,6 +545,10 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
       for (int x = 0; x < nx; ++x) {
         const int xyz[3] = {x, y, z};
         const int64_t i = ((int64_t)z * ny + y) * nx + x;
+        if (g->solid && g->solid[i]) {
+          for (int a = 0; a < Q; ++a) f_out[a * N + i] = 0.0;
+          continue;
+        }
         for (int a = 0; a < Q; ++a) {
           int src[3], mirror;
           double uw[3];
@@ -578,6 +595,12 @@ int oracle_macroscopic(const oracle_grid *g, const oracle_params *prm,
   const double F[3] = {force_at(prm, n, 0), force_at(prm, n, 1),
                        force_at(prm, n, 2)};
   for (int64_t i = 0; i < N; ++i) {
+    if (g->solid && g->solid[i]) {
+      if (u)
+        for (int d = 0; d < 3; ++d) u[d * N + i] = 0.0;
+      if (p) p[i] = 0.0;
+      continue;
+    }
     double P = 0.0, j[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < m.Q; ++a) {
       P += f[a * N + i];

@@ -36,6 +36,12 @@ typedef struct {
    * a one-node axis takes [0].  0 = uniform. */
   int edge_axis[6];
   double edge_scale[6][2];
+  /* Solid nodes (general geometry): NULL, or nx*ny*nz bytes, x fastest,
+   * nonzero = solid.  A fluid node whose pull source is a solid node
+   * bounces the population back as from a wall at rest halfway between
+   * the two nodes; solid nodes hold no flow (their populations, velocity
+   * and pressure are reported as zero). */
+  const unsigned char *solid;
 } oracle_grid;
 
 typedef struct {
