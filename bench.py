@@ -1,12 +1,15 @@
 """Throughput benchmark of the fused D3Q14/D3Q18 MRT step on one GB300.
 
-Workload (one bench step = one lattice update of the whole domain):
-lid-driven cube 128^3, D3Q18, FP32 populations, lid 0.05 along x on y+,
-Re = 1000 (nu = U L / Re), FP64 residual every 1000 steps, synthetic state
-from rest.  The timed steps run back to back (the 151 MB population buffer
-is larger than the 129 MB L2, and each step sweeps all of it), bracketed by
-CUDA events on the stream the kernels run on.  The same step is also timed
-one by one after an L2 flush, as a secondary figure.
+Workload: lid-driven cube 128^3, D3Q18, FP32 populations, lid 0.05 along x
+on y+, Re = 1000 (nu = U L / Re), synthetic state from rest.  One bench step
+is one pass of the whole hot path: 1000 fused lattice updates of the domain
+followed by the FP64 reductions that give the residual of Eq.
+cavity_creterion (its 1000-step interval), so the default 20 timed steps are
+the 20000 updates of the workload.  The timed steps run back to back (the
+151 MB population buffer is larger than the 129 MB L2, and each update
+sweeps all of it), bracketed by CUDA events on the stream the kernels run
+on.  The update is also timed one by one after an L2 flush, as a secondary
+figure.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -38,8 +41,10 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed bench steps (each: residual-interval lattice updates + one "
+                         "FP64 residual reduction)")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--Q", type=int, default=18)
     ap.add_argument("--n", type=int, default=128)
@@ -50,12 +55,16 @@ def parse():
                     help="cube side of the storage-precision comparison (0: skip); its "
                          "buffers are several times larger than L2, so steps run back to back")
     ap.add_argument("--precision-steps", type=int, default=200)
+    ap.add_argument("--porous-n", type=int, default=256,
+                    help="cube side of the solid-node (porous medium) timing (0: skip)")
     ap.add_argument("--reduction-n", type=int, default=256,
                     help="cube side of the FP64-reduction timing (D3Q18 FP32 cavity; 0: skip)")
     ap.add_argument("--flushed-steps", type=int, default=400,
                     help="steps timed one by one after an L2 flush (secondary figure)")
-    ap.add_argument("--e2e-chunk", type=int, default=100)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--kernel-updates", type=int, default=2000,
+                    help="back-to-back updates timed without reductions for the step "
+                         "kernel's own launch duration (roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-trials", type=int, default=16)
     ap.add_argument("--launch", default="",
@@ -67,6 +76,15 @@ def parse():
                          "request trace, batched server vs one domain at a time; "
                          "half_cavity97: the Sec. 4.3 half cavity 97x97x49 at Re 3200, "
                          "throughput and the MRT / LBGK stability comparison")
+    ap.add_argument("--batch-steps", type=int, default=200,
+                    help="steps of the 256-domain batch comparison in the default run (0: skip)")
+    ap.add_argument("--serving-requests", type=int, default=100,
+                    help="requests of the serving comparison in the default run (0: skip)")
+    ap.add_argument("--batch-domains", type=int, default=256,
+                    help="batch256 workload: number of domains of the seed-0 draw")
+    ap.add_argument("--batch-lmax", type=int, default=160,
+                    help="batch256 workload: largest side of the draw (24 .. lmax)")
+    ap.add_argument("--batch-repeats", type=int, default=3)
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-steps", type=int, default=1000)
     ap.add_argument("--saturation-cells", type=int, default=8 << 20,
@@ -217,6 +235,39 @@ def replica_throughput(world, cells, steps, seconds):
 
 # ---- GPU leg -----------------------------------------------------------------------
 
+def storage_error(Q, storage, rounding, launch, stream):
+    """max |u - u_FP64| / U of one storage and launch on the two accuracy
+    cases (FP64 storage agrees with the oracle to 1e-12 relative)."""
+    from paper_1503_03337_gb300 import lbm
+
+    def run(case, steps, st, rnd, lau):
+        h = lbm.lbm_create(case.Q, case.nx, case.ny, case.nz, st, stream)
+        try:
+            lbm.lbm_set_geometry(h, case.faces, case.u_wall)
+            lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period,
+                               rounding=rnd)
+            if lau is not None:
+                lbm.lbm_set_launch(h, *lau)
+            u0 = None if case.init_u is None else np.ascontiguousarray(case.init_u)
+            lbm.lbm_init_equilibrium(h, u0, None, 0)
+            lbm.lbm_step(h, steps)
+            return lbm.read_u(h, case.nx, case.ny, case.nz)
+        finally:
+            lbm.lbm_destroy(h)
+
+    out = {}
+    cav = inputs.cavity(Q, 32, 400.0, U=0.05)
+    lau = launch if storage != "f64" else None
+    ref = run(cav, 1000, "f64", 0, None)
+    out["cavity32"] = float(np.max(np.abs(run(cav, 1000, storage, rounding, lau) - ref)) / 0.05)
+    pul = inputs.pulsatile(Q, 64, 8, 1000, 4.0, 1.555e-4, u_ref=0.03)  # max |u| 0.03
+    ref = run(pul, 1000, "f64", 0, None)
+    out["pulsatile64"] = float(np.max(np.abs(run(pul, 1000, storage, rounding, lau) - ref))
+                               / 0.03)
+    out["within_1e-3"] = bool(max(out["cavity32"], out["pulsatile64"]) <= 1e-3)
+    return out
+
+
 def run_gpu(a, rank, world, dist):
     import torch
 
@@ -259,27 +310,28 @@ def run_gpu(a, rank, world, dist):
                 red.append(k)
         return ev, red
 
-    # --- main workload: back-to-back steps ----------------------------------------
+    # --- main workload: back-to-back bench steps ------------------------------------
     # The population buffer (151 MB for D3Q18 FP32 at 128^3) is larger than
-    # the 129 MB L2 and every step sweeps all of it, so consecutive steps find
-    # nothing useful in L2 (an ncu capture of steady-state steps reads 149 MB
-    # and writes 147-153 MB from/to DRAM per step).  The residual reductions
-    # run inside lbm_step at their cadence and are part of the timed work.
-    case, h, block = open_case(a.Q, a.storage, a.residual_interval)
+    # the 129 MB L2 and every update sweeps all of it, so consecutive updates
+    # find nothing useful in L2 (an ncu capture of steady-state updates reads
+    # 149 MB and writes 147-153 MB from/to DRAM per update).  A bench step is
+    # `interval` updates plus the FP64 residual reduction that lbm_step queues
+    # at the end of the interval.
+    interval = max(1, a.residual_interval)
+    case, h, block = open_case(a.Q, a.storage, interval)
     cells = case.cells
     bytes_per_update = 2 * a.Q * STORAGE_BYTES[a.storage]
-    lbm.lbm_step(h, max(3, a.warmup))
+    lbm.lbm_step(h, max(3, a.warmup) * interval)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    n_before = lbm.lbm_get_step(h)
     with ClockSampler(dev) as clk:
         t0 = time.perf_counter()
         e0.record(stream)
-        lbm.lbm_step(h, a.steps)
+        lbm.lbm_step(h, a.steps * interval)
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -287,34 +339,54 @@ def run_gpu(a, rank, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     total_ms = e0.elapsed_time(e1)
-    kernel_ms = total_ms / a.steps
-    n_red = (sum(1 for n in range(n_before + 1, n_before + a.steps + 1)
-                 if a.residual_interval and n % a.residual_interval == 0))
+    updates = a.steps * interval
     stats = lbm.lbm_read_stats(h)
-    # the same steps timed one by one with the L2 flushed in between (a
-    # 256 MiB write, then a read of it, so that the flush leaves only clean
-    # lines and the timed step pays no write-back of the flush)
+    residual = (lbm.lbm_residual(h, lbm.LBM_RESIDUAL_CAVITY) if stats.prev_step >= 0 else None)
+    # the step kernel's own launch duration: back-to-back updates with no
+    # reduction in between (the dominant kernel of the step, for the roofline)
     lbm.lbm_set_params(h, nu=case.nu, residual_interval=0)
-    fl_steps = max(2, min(a.steps, a.flushed_steps))
+    ku = max(2, a.kernel_updates + (a.kernel_updates & 1))
+    e0.record(stream)
+    lbm.lbm_step(h, ku)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kernel_ms = e0.elapsed_time(e1) / ku
+    # the reduction alone (kernel + final pass + synchronisation), same domain
+    for _ in range(2):
+        lbm.lbm_reductions(h)
+    e0.record(stream)
+    for _ in range(10):
+        lbm.lbm_reductions(h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    reduce_ms = e0.elapsed_time(e1) / 10
+    # the same update timed one by one with the L2 flushed in between (a
+    # 256 MiB write, then a read of it, so that the flush leaves only clean
+    # lines and the timed update pays no write-back of the flush)
+    fl_steps = max(2, a.flushed_steps)
     ev, _ = timed_steps(h, fl_steps, 0)
     torch.cuda.synchronize()
     fl_ms = statistics.mean(s0.elapsed_time(s1) for s0, s1 in ev)
-    flushed = {"glups": round(cells / (fl_ms * 1e-3) / 1e9, 3), "steps": fl_steps,
-               "ms_per_step": round(fl_ms, 6),
-               "note": "per-step CUDA events, 256 MiB L2 flush (write then read) before each step, "
-                       "outside the events"}
+    flushed = {"glups": round(cells / (fl_ms * 1e-3) / 1e9, 3), "updates": fl_steps,
+               "ms_per_update": round(fl_ms, 6),
+               "note": "per-update CUDA events, 256 MiB L2 flush (write then read) before each "
+                       "update, outside the events"}
     lbm.lbm_destroy(h)
 
     total_ms = max_over_ranks(total_ms, dist, "cuda")
-    glups = replica_throughput(world, cells, a.steps, total_ms * 1e-3)
+    glups = replica_throughput(world, cells, updates, total_ms * 1e-3)
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_update * cells / (kernel_ms * 1e-3) / 1e9
     traffic = recorded_traffic(a.Q, a.storage, a.n)
+    share = {"step_kernel": round(kernel_ms * interval / (total_ms / a.steps), 4),
+             "reduction": round(reduce_ms / (total_ms / a.steps), 4)}
 
     # --- e2e through the C-ABI with host buffers ---------------------------------
+    # per step: equilibrium from pinned host (u, p), `interval` updates and the
+    # residual reduction, the velocity field back to pinned host memory
     e2e = None
     if a.e2e_steps > 0:
-        case_e, he, _ = open_case(a.Q, a.storage, 0)
+        case_e, he, _ = open_case(a.Q, a.storage, interval)
         N = case_e.cells
         u0 = torch.zeros(3 * N, dtype=torch.float64).pin_memory()
         p0 = torch.zeros(N, dtype=torch.float64).pin_memory()
@@ -326,28 +398,29 @@ def run_gpu(a, rank, world, dist):
         t0 = time.perf_counter()
         for _ in range(a.e2e_steps):
             lbm.lbm_init_equilibrium(he, u0, p0, 0)
-            lbm.lbm_step(he, a.e2e_chunk)
+            lbm.lbm_step(he, interval)
             lbm.lbm_read_fields(he, lbm.LBM_FIELD_U, uout, lbm.LBM_DTYPE_F64, 0)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         lbm.lbm_destroy(he)
         el = max_over_ranks(el, dist, "cuda")
-        e2e = {"value": replica_throughput(world, N, a.e2e_chunk * a.e2e_steps, el),
+        e2e = {"value": replica_throughput(world, N, interval * a.e2e_steps, el),
                "unit": "GLUPS",
                "h2d_bytes_per_step": 4 * N * 8, "d2h_bytes_per_step": 3 * N * 8,
-               "lattice_updates_per_step": a.e2e_chunk,
-               "calls": "lbm_init_equilibrium(host u,p) + lbm_step(%d) + lbm_read_fields(U -> host)"
-                        % a.e2e_chunk}
+               "lattice_updates_per_step": interval,
+               "calls": "lbm_init_equilibrium(host u,p) + lbm_step(%d, residual every %d) + "
+                        "lbm_read_fields(U -> host)" % (interval, interval)}
 
     # --- storage precision at a size far above L2: back-to-back steps ------------------
     precision = {}
     if a.precision_n > 0 and a.precision_steps > 0 and rank == 0:
+        variants = (("f32", 0), ("f16", 0), ("f16", 1), ("bf16", 1))
         for Q in (14, 18):
-            for st in ("f32", "f16", "bf16"):
+            for st, rnd in variants:
                 cp = inputs.cavity(Q, a.precision_n, a.Re, U=0.05, storage=st)
                 hp = lbm.lbm_create(Q, cp.nx, cp.ny, cp.nz, st, sp)
                 lbm.lbm_set_geometry(hp, cp.faces, cp.u_wall)
-                lbm.lbm_set_params(hp, nu=cp.nu, residual_interval=0)
+                lbm.lbm_set_params(hp, nu=cp.nu, residual_interval=0, rounding=rnd)
                 lbm.lbm_init_equilibrium(hp)
                 bp, _ = lbm.lbm_autotune(hp, 4)
                 lbm.lbm_step(hp, 10)
@@ -359,20 +432,57 @@ def run_gpu(a, rank, world, dist):
                 tp = e0.elapsed_time(e1) / k
                 lbm.lbm_destroy(hp)
                 bpu = 2 * Q * STORAGE_BYTES[st]
-                precision["D3Q%d_%s" % (Q, st)] = {
+                key = "D3Q%d_%s%s" % (Q, st, "_sr" if rnd else "")
+                precision[key] = {
+                    "rounding": "stochastic" if rnd else "nearest",
                     "launch": list(bp),
                     "glups": round(cp.cells / (tp * 1e-3) / 1e9, 3),
                     "hbm_gbs": round(bpu * cp.cells / (tp * 1e-3) / 1e9, 1),
                     "frac_of_measured_hbm": round(bpu * cp.cells / (tp * 1e-3) / 1e9 / peak, 4)}
+                precision[key]["error"] = storage_error(Q, st, rnd, tuple(bp), sp)
             f32 = precision["D3Q%d_f32" % Q]["glups"]
-            for st in ("f16", "bf16"):
-                precision["D3Q%d_%s" % (Q, st)]["vs_f32"] = round(
-                    precision["D3Q%d_%s" % (Q, st)]["glups"] / f32, 3)
+            for st, rnd in variants[1:]:
+                key = "D3Q%d_%s%s" % (Q, st, "_sr" if rnd else "")
+                precision[key]["vs_f32"] = round(precision[key]["glups"] / f32, 3)
         precision["note"] = ("lid-driven cavity %d^3, %d back-to-back steps after 10, one event "
-                             "pair; population buffers %d-%d MB, all far above the 129 MB L2"
+                             "pair; population buffers %d-%d MB, all far above the 129 MB L2.  "
+                             "error: max|u - u_FP64| / U with the same launch, on the 32^3 "
+                             "cavity (Re 400, 1000 steps) and the 64x64x8 oscillating channel "
+                             "(T 1000, eta 4, one period from rest); the FP64 "
+                             "storage run matches the oracle to 1e-12"
                              % (a.precision_n, a.precision_steps,
                                 2 * 14 * a.precision_n ** 3 >> 20,
                                 4 * 18 * a.precision_n ** 3 >> 20))
+
+    # --- solid nodes: a porous medium of random spheres, 256^3 --------------------
+    porous = {}
+    if a.porous_n > 0 and rank == 0:
+        pc = inputs.porous_spheres(18, a.porous_n, storage="f32")
+        hp = lbm.lbm_create(18, pc.nx, pc.ny, pc.nz, "f32", sp)
+        lbm.lbm_set_geometry(hp, pc.faces, pc.u_wall)
+        lbm.lbm_set_params(hp, nu=pc.nu, force=pc.force)
+        lbm.lbm_set_solid(hp, pc.solid)
+        lbm.lbm_init_equilibrium(hp)
+        bp, _ = lbm.lbm_autotune(hp, 4)
+        lbm.lbm_step(hp, 10)
+        k = 200
+        e0.record(stream)
+        lbm.lbm_step(hp, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tp = e0.elapsed_time(e1) / k
+        lbm.lbm_destroy(hp)
+        fluid = int(pc.cells - int(pc.solid.sum()))
+        # fluid cells move 2Q values and read their link word; solid cells
+        # read their link word only
+        pbytes = fluid * (2 * 18 * 4 + 4) + (pc.cells - fluid) * 4
+        porous = {"workload": "periodic %d^3 box of random spheres (radius 6, seed 0), "
+                              "D3Q18 FP32, body force" % a.porous_n,
+                  "fluid_fraction": round(fluid / pc.cells, 4), "launch": list(bp),
+                  "glups_fluid": round(fluid / (tp * 1e-3) / 1e9, 3),
+                  "hbm_gbs": round(pbytes / (tp * 1e-3) / 1e9, 1),
+                  "frac_of_measured_hbm": round(pbytes / (tp * 1e-3) / 1e9 / peak, 4),
+                  "bytes_model": "fluid cell 2*18*4 + 4 B (link word), solid cell 4 B"}
 
     # the step kernels plus, per residual check, the reduction kernel and its
     # final pass
@@ -405,7 +515,7 @@ def run_gpu(a, rank, world, dist):
                               "timed with CUDA events over %d calls; bytes: 18 FP32 populations "
                               "read, FP64 u snapshot read and written, per cell" % kr}
 
-    launches = a.steps + 2 * n_red
+    launches = a.steps * (interval + 2)  # updates + reduction kernel and final pass
     res = {
         "metric": "D3Q18 MRT fused-step GLUPS (lattice updates/s) and HBM-roofline fraction",
         "value": round(glups, 4),
@@ -413,7 +523,7 @@ def run_gpu(a, rank, world, dist):
         "n_gpus": world,
         "steps": a.steps,
         "warmup": a.warmup,
-        "ms_per_step": round(total_ms / a.steps, 6),
+        "ms_per_step": round(total_ms / a.steps, 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -421,7 +531,9 @@ def run_gpu(a, rank, world, dist):
         "data": "synthetic (lid-driven cavity from rest)",
         "config": {"workload": workload_name(a), "grid": [a.n, a.n, a.n], "Q": a.Q,
                    "storage": a.storage, "Re": a.Re, "lid_velocity": 0.05,
-                   "residual_interval": a.residual_interval,
+                   "step": "%d fused lattice updates + one FP64 residual reduction "
+                           "(Eq. cavity_creterion interval)" % interval,
+                   "lattice_updates": updates,
                    "l2": "inputs larger than L2: back-to-back steps over a %d MB population "
                          "buffer (L2 129 MB); see flushed_per_step for the same step timed one "
                          "by one after an L2 flush" % (bytes_per_update * cells // 2 // 10**6),
@@ -432,14 +544,18 @@ def run_gpu(a, rank, world, dist):
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_per_update * cells,
-                     "kernel_ms": round(kernel_ms, 6)},
+                     "kernel_ms": round(kernel_ms, 6),
+                     "kernel_timing": "CUDA events over %d back-to-back updates without "
+                                      "reductions, on the launch stream" % ku},
+        "time_share": share,
+        "reduction_ms": round(reduce_ms, 4),
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
-        "residual_last": {"step": stats.step, "cavity": (lbm.residual_cavity(stats)
-                                                         if stats.prev_step >= 0 else None)},
+        "residual_last": {"step": stats.step, "cavity": residual},
         "precision": precision,
         "reductions": reductions,
+        "solid_nodes": porous,
         "flushed_per_step": flushed,
     }
     return res
@@ -451,7 +567,7 @@ def oracle_rate(Q, n, Re, storage, budget_s=15.0, max_steps=50):
     import oracle
     case = inputs.cavity(Q, n, Re, U=0.05, storage=storage)
     g = oracle.make_grid(Q, case.nx, case.ny, case.nz, case.faces, case.u_wall)
-    prm = oracle.make_params(oracle.rates(Q, case.s_nu))
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(case.nu)))
     f = oracle.init_equilibrium(g)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
@@ -478,7 +594,7 @@ def oracle_reference_arm(a, budget_s=90.0):
     # calibrate on one slab step
     probe = inputs.cavity(a.Q, a.n, a.Re, U=0.05, storage=a.storage, nz=min(a.n, 8))
     g = oracle.make_grid(a.Q, probe.nx, probe.ny, probe.nz, probe.faces, probe.u_wall)
-    prm = oracle.make_params(oracle.rates(a.Q, full.s_nu))
+    prm = oracle.make_params(oracle.rates(a.Q, oracle.s_nu_of(full.nu)))
     f = oracle.init_equilibrium(g)
     t0 = time.perf_counter()
     oracle.run(g, prm, f, 0, 1, nthreads=threads)
@@ -499,42 +615,40 @@ def oracle_reference_arm(a, budget_s=90.0):
                       % (a.n, a.n, nz_s, a.n, a.Q)}
 
 
-def run_batch256(a):
-    """256 independent cavities/ducts (seed 0, sides 24-160, Q14/Q18, FP32/FP16),
-    a.steps steps each: batched (persistent and per-step modes) against one
-    launch per domain per step."""
+def batch_compare(steps, repeats=3, chunk=10, n_domains=256, lmax=160):
+    """The seed-0 draw of 256 independent cavities/ducts (sides 24-160,
+    Q14/Q18, FP32/FP16): `steps` steps of every domain batched (grouped
+    launches in CUDA graphs, and the persistent cooperative kernel) against
+    one launch per domain per step, each timed `repeats` times with CUDA
+    events on the launch stream."""
     import torch
 
     from paper_1503_03337_gb300 import lbm
     lbm.load()
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
-    cases = [inputs.batch_case(d) for d in inputs.batch_draw(256, seed=0)]
+    cases = [inputs.batch_case(d) for d in inputs.batch_draw(n_domains, seed=0,
+                                                            lmax=max(24, lmax))]
     cells = sum(c.cells for c in cases)
-    steps = max(2, a.steps + (a.steps & 1))
-    res = {}
+    steps = max(2, steps + (steps & 1))
+    runs = {"grouped": [], "persistent": [], "one_launch_per_domain": []}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return cells * steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
     with torch.cuda.stream(stream):
-        b = lbm.lbm_batch_create(256, 0, sp)
-        slots = []
+        b = lbm.lbm_batch_create(n_domains, 0, sp)
         for c in cases:
-            s = lbm.lbm_batch_add(b, c.Q, c.nx, c.ny, c.nz, c.storage, c.faces, c.u_wall,
-                                  nu=c.nu, force=c.force)
-            lbm.lbm_batch_init_equilibrium(b, s)
-            slots.append(s)
-        for mode, launch in (("persistent", (64, 2, 1)), ("grouped", (64, 2, 0))):
-            lbm.lbm_batch_set_launch(b, *launch)
-            lbm.lbm_batch_step(b, 4, 2)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            lbm.lbm_batch_step(b, steps, 10)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            res[mode] = {"glups": cells * steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / steps}
-        lbm.lbm_batch_destroy(b)
-        # one launch per domain per step, domains one after another
+            slot = lbm.lbm_batch_add(b, c.Q, c.nx, c.ny, c.nz, c.storage, c.faces, c.u_wall,
+                                     nu=c.nu, force=c.force)
+            lbm.lbm_batch_init_equilibrium(b, slot)
         hs = []
         for c in cases:
             h = lbm.lbm_create(c.Q, c.nx, c.ny, c.nz, c.storage, sp)
@@ -543,36 +657,68 @@ def run_batch256(a):
             lbm.lbm_set_launch(h, 64, 2, 1)
             lbm.lbm_init_equilibrium(h)
             hs.append(h)
-        for h in hs:
-            lbm.lbm_step(h, 2)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
+        for _ in range(repeats):
+            for mode, persistent in (("grouped", 0), ("persistent", 1)):
+                lbm.lbm_batch_set_launch(b, 64, 2, persistent)
+                lbm.lbm_batch_step(b, 3 * chunk, chunk)  # graphs captured, warm
+                runs[mode].append(timed(lambda: lbm.lbm_batch_step(b, steps, chunk)))
+
+            def one_by_one():
+                for _ in range(steps):
+                    for h in hs:
+                        lbm.lbm_step(h, 1)
             for h in hs:
-                lbm.lbm_step(h, 1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        res["one_launch_per_domain"] = {"glups": cells * steps / (ms * 1e-3) / 1e9,
-                                        "ms_per_step": ms / steps}
+                lbm.lbm_step(h, 2)
+            runs["one_launch_per_domain"].append(timed(one_by_one))
+        lbm.lbm_batch_destroy(b)
         for h in hs:
             lbm.lbm_destroy(h)
-    best = max(res["persistent"]["glups"], res["grouped"]["glups"])
-    return {"metric": "batched GLUPS, 256 uneven domains", "value": round(best, 3),
-            "unit": "GLUPS", "n_gpus": 1, "steps": steps, "higher_is_better": True,
+    out = {k: {"glups": round(statistics.median(v), 3), "min": round(min(v), 3),
+               "max": round(max(v), 3)} for k, v in runs.items()}
+    base = out["one_launch_per_domain"]
+    return {"workload": "%d domains (seed 0), sides 24-%d, Q14/Q18, FP32/FP16, %d cells"
+                        % (n_domains, max(24, lmax), cells),
+            "steps": steps, "chunk": chunk, "repeats": repeats, "modes": out,
+            "speedup_grouped": round(out["grouped"]["glups"] / base["glups"], 3),
+            "speedup_persistent": round(out["persistent"]["glups"] / base["glups"], 3),
+            "beats_beyond_spread": out["grouped"]["min"] > base["max"]}
+
+
+def run_batch256(a):
+    r = batch_compare(max(2, a.steps), repeats=a.batch_repeats, n_domains=a.batch_domains,
+                      lmax=a.batch_lmax)
+    return {"metric": "batched GLUPS, 256 uneven domains",
+            "value": r["modes"]["grouped"]["glups"], "unit": "GLUPS", "n_gpus": 1,
+            "steps": r["steps"], "higher_is_better": True,
             "data": "synthetic (seed-0 draw of cavities and ducts)",
-            "config": {"workload": "256 domains, sides 24-160, Q14/Q18, FP32/FP16",
-                       "cells": cells, "chunk": 10},
-            "modes": res,
-            "speedup_vs_one_launch_per_domain":
-                round(best / res["one_launch_per_domain"]["glups"], 3)}
+            "config": {"workload": r["workload"], "chunk": r["chunk"]}, "batch": r}
 
 
-def run_serving(a):
-    """Poisson request trace served by the continuous-batching loop and by
-    one domain at a time (FIFO), both from the same arrival times."""
+def request_error(case, steps, u, stream):
+    """max |u - u_ref| / U of a delivered field against the same request run
+    alone with higher-precision storage (FP16 -> FP32, FP32 -> FP64) for the
+    same number of steps."""
+    from paper_1503_03337_gb300 import lbm
+    ref = "f32" if case.storage in ("f16", "bf16") else "f64"
+    h = lbm.lbm_create(case.Q, case.nx, case.ny, case.nz, ref, stream)
+    try:
+        lbm.lbm_set_geometry(h, case.faces, case.u_wall, case.edge)
+        lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period)
+        lbm.lbm_init_equilibrium(h)
+        lbm.lbm_step(h, steps)
+        ur = lbm.read_u(h, case.nx, case.ny, case.nz)
+    finally:
+        lbm.lbm_destroy(h)
+    return float(np.max(np.abs(u - ur)) / case.u_ref), ref
+
+
+def serving_compare(requests, max_steps, repeats=3, saturation_cells=8 << 20,
+                    check_cells=96 ** 3, lmin=32, lmax=256):
+    """The seed-0 Poisson trace (200/s) served by the continuous-batching
+    loop and by one domain at a time, from the same arrival times, `repeats`
+    times each.  Then every request of at most `check_cells` cells from the
+    first batched run is checked against its requested accuracy: its field
+    against the same request run alone in higher precision."""
     import torch
 
     from paper_1503_03337_gb300 import lbm
@@ -580,29 +726,76 @@ def run_serving(a):
                                                 summarize)
     lbm.load()
     stream = torch.cuda.Stream()
-    trace = inputs.request_trace(a.requests, rate=200.0, seed=0, lmin=32, lmax=256,
-                                 max_steps=a.max_steps)
-    out = {}
+    trace = inputs.request_trace(requests, rate=200.0, seed=0, lmin=lmin, lmax=lmax,
+                                 max_steps=max_steps)
+    runs = {"batched": [], "one_at_a_time": []}
+    first = None
     with torch.cuda.stream(stream):
-        for name, be in (("batched", BatchBackend(256, 150 << 30, stream.cuda_stream)),
-                         ("one_at_a_time", SequentialBackend(stream.cuda_stream))):
-            t0 = time.perf_counter()
-            res = Server(be, check_every=100, tol=1e-8, chunk=50,
-                         max_active_cells=a.saturation_cells).run(trace)
+        # one untimed pass of the whole trace through each backend first:
+        # allocator pools, graph capture and module loading then belong to
+        # no timed repeat
+        for be in (BatchBackend(256, 150 << 30, stream.cuda_stream),
+                   SequentialBackend(stream.cuda_stream)):
+            Server(be, check_every=100, tol=1e-8, chunk=50,
+                   max_active_cells=saturation_cells).run(trace)
             torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
             be.close()
-            out[name] = summarize(res, wall)
+        for rep in range(repeats):
+            for name in ("batched", "one_at_a_time"):
+                be = (BatchBackend(256, 150 << 30, stream.cuda_stream) if name == "batched"
+                      else SequentialBackend(stream.cuda_stream))
+                keep = name == "batched" and rep == 0
+                t0 = time.perf_counter()
+                res = Server(be, check_every=100, tol=1e-8, chunk=50,
+                             max_active_cells=saturation_cells, keep_fields=keep).run(trace)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                be.close()
+                runs[name].append(summarize(res, wall))
+                if keep:
+                    first = res
+        checks = []
+        for r in trace:
+            case = inputs.request_case(r)
+            o = first[r.rid]
+            if case.cells > check_cells or o.u is None:
+                continue
+            err, ref = request_error(case, o.steps, o.u, stream.cuda_stream)
+            checks.append({"rid": r.rid, "kind": r.kind, "L": r.L, "storage": case.storage,
+                           "tol": r.tol, "err": err, "ref": ref})
+    med = {}
+    for name, rs in runs.items():
+        med[name] = {k: statistics.median(x[k] for x in rs) for k in ("p50_s", "p99_s", "glups")}
+        med[name].update({"p99_s_range": [min(x["p99_s"] for x in rs), max(x["p99_s"] for x in rs)],
+                          "glups_range": [min(x["glups"] for x in rs), max(x["glups"] for x in rs)],
+                          "converged": rs[0]["converged"], "requests": rs[0]["requests"]})
+    b, s = med["batched"], med["one_at_a_time"]
+    met = [c for c in checks if c["err"] <= c["tol"]]
+    return {"workload": "%d requests, Poisson 200/s (seed 0), cavity/duct/pulsatile, sides "
+                        "%d-%d, Q14/Q18, FP32 or FP16 by requested accuracy, residual 1e-8 "
+                        "or %d steps, 150 GB budget, admission while < %d active cells"
+                        % (requests, lmin, lmax, max_steps, saturation_cells),
+            "repeats": repeats, "batched": b, "one_at_a_time": s,
+            "glups_beats_beyond_spread": b["glups_range"][0] > s["glups_range"][1],
+            "p99_beats_beyond_spread": b["p99_s_range"][1] < s["p99_s_range"][0],
+            "accuracy": {"checked": len(checks), "met": len(met),
+                         "max_err_over_tol": max((c["err"] / c["tol"] for c in checks),
+                                                 default=None),
+                         "rule": "requests of at most %d cells from the first batched run; "
+                                 "error = max|u - u_ref| / U against the request run alone "
+                                 "with FP32 (FP16 requests) or FP64 (FP32 requests) storage"
+                                 % check_cells,
+                         "worst": sorted(checks, key=lambda c: -c["err"] / c["tol"])[:3]}}
+
+
+def run_serving(a):
+    r = serving_compare(a.requests, a.max_steps, repeats=3,
+                        saturation_cells=a.saturation_cells)
     return {"metric": "serving p50/p99 time-to-converged and aggregate GLUPS",
-            "value": round(out["batched"]["glups"], 3), "unit": "GLUPS",
+            "value": round(r["batched"]["glups"], 3), "unit": "GLUPS",
             "higher_is_better": True, "n_gpus": 1,
             "data": "synthetic Poisson trace (seed 0, 200/s)",
-            "config": {"workload": "serving", "requests": a.requests,
-                       "sizes": "32^3-256^3 (Q14/Q18, cavity/duct/pulsatile)",
-                       "max_steps": a.max_steps, "residual_tol": 1e-8,
-                       "max_active_cells": a.saturation_cells,
-                       "hbm_budget_bytes": 150 << 30},
-            "batched": out["batched"], "one_at_a_time": out["one_at_a_time"]}
+            "config": {"workload": r["workload"]}, "serving": r}
 
 
 def run_half_cavity(a):
@@ -719,6 +912,19 @@ def main():
         td.init_process_group("nccl")
         dist = td
     res = run_gpu(a, rank, world, dist)
+    if rank == 0 and world == 1:
+        # the batched (256 uneven domains) and serving (request trace) halves
+        # of the metric, on the same GPU after the single-domain line
+        if a.batch_steps > 0:
+            res["batch"] = batch_compare(a.batch_steps)
+        if a.serving_requests > 0:
+            res["serving"] = serving_compare(a.serving_requests, a.max_steps,
+                                             saturation_cells=a.saturation_cells)
+            # the same trace with small domains only (sides 32-96), where one
+            # domain alone cannot fill the device
+            res["serving_small"] = serving_compare(a.serving_requests, a.max_steps,
+                                                   saturation_cells=a.saturation_cells,
+                                                   lmin=32, lmax=96)
     if rank == 0:
         if not a.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = oracle_rate(a.Q, a.n, a.Re, a.storage)

@@ -56,13 +56,27 @@ enum lbm_face_kind {
   LBM_PERIODIC = 0,    /* wraps to the opposite face (both must say so)   */
   LBM_WALL = 1,        /* halfway bounce-back, wall at rest               */
   LBM_MOVING_WALL = 2, /* halfway bounce-back with wall velocity u_wall   */
-  LBM_SYMMETRY = 3     /* free-slip mirror plane halfway beyond the face:
+  LBM_SYMMETRY = 3,    /* free-slip mirror plane halfway beyond the face:
                         * a population leaving through it returns as its
                         * mirror image (normal velocity component
                         * reversed) at the node it left.  Where a link also
                         * crosses a wall face the wall's bounce-back
                         * applies.  Like a wall, it cannot face a periodic
                         * face.  Sec. 4.3's reduced domains use it. */
+  /* Non-equilibrium extrapolation, the boundary scheme of Sec. 4 (after
+   * Guo, Zheng and Shi): the outermost node layer lies ON the face.  After
+   * every step each node x_b of such a layer takes
+   *   f(x_b) = f_eq(p_b, u_b) + [f(x_f) - f_eq(p_f, u_f)]   (Eq. edf),
+   * x_f being its neighbour one node inward along the normal of every such
+   * face it lies on (diagonally inward on edges and corners) and (p_f, u_f)
+   * the macroscopic values there (Eq. hgl).  u_b is prescribed on a
+   * velocity face (u_wall of the first such face in x-, x+, y-, y+, z-, z+
+   * order), else u_b = u_f; p_b is prescribed on a pressure face
+   * (lbm_params.p_face of the first such face), else p_b = p_f, so a node
+   * where a wall meets an inlet takes u_wall and the inlet pressure.  The
+   * axis of such a face needs at least 3 nodes. */
+  LBM_NEQ_VELOCITY = 4,
+  LBM_NEQ_PRESSURE = 5
 };
 
 enum lbm_face { LBM_XM = 0, LBM_XP = 1, LBM_YM = 2, LBM_YP = 3, LBM_ZM = 4, LBM_ZP = 5 };
@@ -77,9 +91,11 @@ enum lbm_dtype { LBM_DTYPE_F64 = 0, LBM_DTYPE_F32 = 1 };
 
 /* Rounding of FP16/BF16 stores (ignored for FP32/FP64 storage).  Nearest
  * loses every per-step change below half a storage ulp in the same
- * direction; stochastic rounding (a counter-based hash of cell, direction
- * and step picks up or down with probability equal to the discarded
- * fraction) makes each store unbiased and is reproducible. */
+ * direction; stochastic rounding makes each store unbiased: the value goes
+ * to the 16-bit neighbour above with probability equal to its distance from
+ * the one below, over their spacing, quantised to 13 (FP16) or 16 (BF16)
+ * random bits from a counter-based hash of (cell pair, direction, step), so
+ * runs are reproducible and independent of launch shape and batching. */
 enum lbm_rounding { LBM_ROUND_NEAREST = 0, LBM_ROUND_STOCHASTIC = 1 };
 
 /* ---- descriptors -------------------------------------------------------- */
@@ -125,6 +141,14 @@ typedef struct lbm_params {
   int32_t residual_interval; /* > 0: lbm_step runs the FP64 reductions every
                                 that many steps (stats via lbm_read_stats) */
   int32_t rounding;          /* enum lbm_rounding */
+  /* Pressure of each LBM_NEQ_PRESSURE face at time level n:
+   * p_face[f] + p_amp[f] * cos(2 pi n / p_period) if p_period > 0, else
+   * p_face[f] (Sec. 4.1 constant inlet/outlet pressures; Sec. 4.2
+   * oscillating pressure drop, Eq. pbc-pul).  Same units as the read-back
+   * pressure (p_ref included). */
+  double p_face[6];
+  double p_amp[6];
+  double p_period;
 } lbm_params;
 
 /* FP64 reductions over all nodes at step `step`, against the velocity
@@ -163,14 +187,32 @@ void lbm_destroy(lbm_handle *h);
 /* Replace the stream later work is queued on. */
 int lbm_set_stream(lbm_handle *h, void *cuda_stream);
 
-/* Boundary kinds (Sec. 4 problem statement; halfway and moving-wall
- * bounce-back stand in for the paper's extrapolation scheme).  EINVAL if a
- * kind is unknown or only one of two opposite faces is periodic. */
+/* Boundary kinds (Sec. 4 problem statement): halfway and moving-wall
+ * bounce-back, symmetry planes, or the paper's own non-equilibrium
+ * extrapolation (LBM_NEQ_*).  EINVAL if a kind is unknown, only one of two
+ * opposite faces is periodic, or an LBM_NEQ_* face lies on an axis with
+ * fewer than 3 nodes, or LBM_NEQ_* faces while a solid mask is set. */
 int lbm_set_geometry(lbm_handle *h, const lbm_geom *geom);
 
 /* Rates, force and reduction cadence.  EINVAL unless every rate is in
  * (0, 2), nu > 0 or s_nu given, and all values are finite. */
 int lbm_set_params(lbm_handle *h, const lbm_params *params);
+
+/* Solid nodes (general geometry; the paper's introduction motivates complex
+ * boundaries and porous media): `solid` holds N bytes, x fastest, nonzero
+ * marking a solid node (host pointer, or device if on_device != 0; copied,
+ * the caller keeps it).  A fluid node whose pull source is solid -- after
+ * the periodic wraps and symmetry mirrors of the faces -- bounces that
+ * population back as off a wall at rest halfway between the two nodes.
+ * Solid nodes hold no flow: no step updates them, lbm_read_fields reports
+ * zero there, lbm_reductions leaves them out, lbm_write_populations
+ * ignores their values.  NULL returns to the plain box.  Set it before
+ * lbm_init_equilibrium (or restore a checkpoint after it): the populations
+ * of a node that turns solid or fluid are not converted.  Costs N*5 bytes
+ * of device memory and 4 bytes of traffic per cell update; two cells per
+ * thread is not used while a mask is set.  Not for handles with
+ * LBM_NEQ_* faces.  Synchronises.  EINVAL, ENOMEM, ECUDA. */
+int lbm_set_solid(lbm_handle *h, const uint8_t *solid, int on_device);
 
 /* f = f_eq(p, u) of Eq. edf at every node (u: 3*N FP64 ux,uy,uz; p: N FP64;
  * either may be NULL meaning zero), step counter reset to 0, velocity
@@ -213,6 +255,33 @@ int lbm_reductions(lbm_handle *h, lbm_stats *out);
  * lbm_reductions).  Synchronises. */
 int lbm_read_stats(lbm_handle *h, lbm_stats *out);
 
+/* Convergence criteria of the paper, formed from one lbm_stats (the sums of
+ * a reduction at step t1 = s->step against the snapshot of t0 =
+ * s->prev_step):
+ *   LBM_RESIDUAL_STEADY   Eq. sc (Sec. 4.1), one velocity component k:
+ *       sum_i |u_k(t1) - u_k(t0)| / sum_i |u_k(t0)|   (earlier level)
+ *   LBM_RESIDUAL_PERIODIC Eq. cr (Sec. 4.2), one component k:
+ *       sum_i |u_k(t1) - u_k(t0)| / sum_i |u_k(t1)|   (later level)
+ *   LBM_RESIDUAL_CAVITY   Eq. cavity_creterion (Sec. 4.3), all components:
+ *       sum_i sum_k |u_k(t1) - u_k(t0)| / sum_i sum_k |u_k(t1)|
+ * The paper's intervals t1 - t0 (one step, one period T, 1000 steps) are
+ * the caller's choice of reduction cadence.  A zero denominator gives 0 if
+ * the numerator is 0, else +infinity.  component (0 = x, 1 = y, 2 = z) is
+ * ignored by LBM_RESIDUAL_CAVITY.
+ * Errors: EINVAL (null pointer, unknown kind, component outside 0..2, or
+ * statistics without an earlier snapshot: prev_step < 0). */
+enum lbm_residual_kind {
+  LBM_RESIDUAL_STEADY = 0,
+  LBM_RESIDUAL_PERIODIC = 1,
+  LBM_RESIDUAL_CAVITY = 2
+};
+int lbm_stats_residual(const lbm_stats *s, int32_t kind, int32_t component, double *r);
+
+/* The criterion `kind` of the handle's most recent reduction (as
+ * lbm_read_stats, then lbm_stats_residual).  Synchronises.  EINVAL also if
+ * no reduction has run since the last init, write or set_step. */
+int lbm_residual(lbm_handle *h, int32_t kind, int32_t component, double *r);
+
 /* Launch shape of the step kernel.  Affects speed, and (cells_per_thread
  * only) the FP32 rounding pattern: bx and by never change results; the two
  * cells of a pair are collided in packed FP32x2, where the compiler fuses
@@ -221,13 +290,14 @@ int lbm_read_stats(lbm_handle *h, lbm_stats *out);
 typedef struct lbm_launch {
   int32_t bx, by;           /* threads along x (multiple of 32, so a warp never
                                spans two x-rows) and y; bx*by <= 256          */
-  int32_t cells_per_thread; /* 1, or 2: on even steps with nx even and
-                               rounding to nearest, each thread updates the
-                               x-adjacent cells 2t, 2t+1, moving each
-                               population of the pair as one word (a warp
-                               touches 128 B per population with 2-byte
-                               storage instead of 64 B); odd steps run one
-                               cell per thread.  Not for FP64 storage.       */
+  int32_t cells_per_thread; /* 1, or 2: on even steps with nx even, each
+                               thread updates the x-adjacent cells 2t, 2t+1,
+                               moving each population of the pair as one
+                               word (a warp touches 128 B per population
+                               with 2-byte storage instead of 64 B); odd
+                               steps run one cell per thread.  Stochastic
+                               rounding draws the same random bits for a
+                               cell either way.  Not for FP64 storage.      */
 } lbm_launch;
 
 /* Set / read the launch shape.  EINVAL if out of range. */
@@ -242,11 +312,12 @@ int lbm_get_launch(lbm_handle *h, lbm_launch *launch);
 int lbm_set_overlap(lbm_handle *h, int32_t enable);
 
 /* Autotuner: time the step kernel on this domain for each candidate launch
- * shape (block shape, cells per thread) (`trials` steps each, CUDA events on the handle's stream) and keep
- * the fastest.  The populations and step counter are saved before and
- * restored after, so the state is unaffected (the chosen cells per thread
- * sets the FP32 rounding pattern, see lbm_set_block); the choice is cached per
- * (Q, storage, nx, ny, nz) for later handles of the same shape.  trials <= 0
+ * shape (block shape, cells per thread; `trials` steps each, CUDA events on
+ * the handle's stream) and keep the fastest.  The populations and step
+ * counter are saved before and restored after, so the state is unaffected
+ * (the chosen cells per thread sets the FP32 rounding pattern, see
+ * lbm_set_launch); the choice is cached per (Q, storage, rounding, nx, ny,
+ * nz) for later handles of the same shape.  trials <= 0
  * uses the cache only (or 8 trials on a miss).  Outputs may be NULL.
  * Synchronises; needs Q*N storage values of temporary device memory. */
 int lbm_autotune(lbm_handle *h, int32_t trials, lbm_launch *chosen, double *ms_per_step);
@@ -281,7 +352,9 @@ int lbm_autotune(lbm_handle *h, int32_t trials, lbm_launch *chosen, double *ms_p
  * rejected with LBM_EINVAL and a message naming the limit.
  * The first call on a device looks up the static array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the same static
+ * before any stream capture.  The looked-up address is kept for the life of
+ * the process: after a cudaDeviceReset of that device it is stale, so the
+ * entry point must not be called on a device that has been reset.  Every call on a device shares the same static
  * array: each call overwrites everything it reads, so nothing needs
  * clearing, but calls whose GPU work overlaps (e.g. on two streams at once)
  * race on it and must be serialised by the caller.
@@ -294,6 +367,18 @@ int lbm_reductions_static(const lbm_desc *desc, const lbm_geom *geom,
 
 /* Device memory the handle holds, in bytes. */
 int lbm_memory_bytes(lbm_handle *h, int64_t *bytes);
+
+/* The handle's population buffer: *ptr receives its device address and
+ * *bytes its size (Q*N storage values).  The values are in the storage layout
+ * of the current step counter's parity (for an even step the canonical
+ * populations [a][cell]; for an odd step the post-collision values of the
+ * previous step in the slots the in-place streaming keeps them in), so the
+ * buffer can be handed to lbm_reductions_static with lbm_get_step's counter.
+ * The handle keeps ownership; the address stays valid until lbm_destroy.
+ * Reading it races with queued steps unless the caller orders the read after
+ * them on the handle's stream; writing it is the caller's responsibility.
+ * No synchronisation. */
+int lbm_device_populations(lbm_handle *h, void **ptr, int64_t *bytes);
 
 /* ---- batches of independent domains -------------------------------------- */
 
@@ -317,7 +402,7 @@ void lbm_batch_destroy(lbm_batch *b);
 /* Add a domain (stream-ordered allocation of Q*N storage values, f = 0,
  * step 0); returns its slot.  EBUSY if no slot is free or the budget would
  * be exceeded; EINVAL for bad descriptors (as lbm_create/set_geometry/
- * set_params). */
+ * set_params) and for LBM_NEQ_* faces (single-domain handles only). */
 int lbm_batch_add(lbm_batch *b, const lbm_desc *desc, const lbm_geom *geom,
                   const lbm_params *params, int32_t *slot);
 
@@ -346,6 +431,12 @@ int lbm_batch_reductions(lbm_batch *b, int32_t slot, lbm_stats *out);
  * synchronisation: out[k] belongs to slots[k], k < *count.  Both arrays
  * must hold `capacity` entries. */
 int lbm_batch_reductions_all(lbm_batch *b, lbm_stats *out, int32_t *slots, int32_t *count);
+
+/* The criterion `kind` (see lbm_stats_residual) of the slot's most recent
+ * reduction (lbm_batch_reductions or lbm_batch_reductions_all).  Host only,
+ * no synchronisation.  EINVAL also if the slot has had no reduction since it
+ * was added or initialised. */
+int lbm_batch_residual(lbm_batch *b, int32_t slot, int32_t kind, int32_t component, double *r);
 
 /* Launch shape of the batch kernels (bx multiple of 32, bx*by <= 256) and
  * mode: grouped (0: one launch per domain group per step) or persistent (1:

@@ -87,6 +87,8 @@ struct BatchSlot {
   double* u_prev = nullptr;
   int have_prev = 0;
   int64_t prev_step = -1;
+  bool has_last = false;  // `last` holds the statistics of a reduction
+  lbm_stats last{};
 };
 
 struct lbm_batch {
@@ -177,13 +179,15 @@ int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, Doma
   if (N * desc->Q >= (int64_t(1) << 31) || desc->nz > 65535)
     return bfail(LBM_EINVAL, "domain too large (Q*N must be < 2^31)");
   dd = DomainDesc{};
-  if (const char* why = set_faces(dd, g)) return bfail(LBM_EINVAL, why);
   dd.Q = desc->Q;
   dd.nx = desc->nx;
   dd.ny = desc->ny;
   dd.nz = desc->nz;
   dd.storage = desc->storage;
   dd.N = N;
+  if (const char* why = set_faces(dd, g)) return bfail(LBM_EINVAL, why);
+  if (dd.neq_vel | dd.neq_pre)
+    return bfail(LBM_EINVAL, "extrapolation faces are for single-domain handles only");
   double s[6] = {p->s_c, p->s_e, p->s_q, p->s_nu, p->s_pi, p->s_t};
   if (p->nu > 0.0) s[3] = 1.0 / (3.0 * p->nu + 0.5);
   if (desc->Q == 14) s[4] = s[1];
@@ -565,6 +569,7 @@ int lbm_batch_init_equilibrium(lbm_batch* b, int32_t slot, const double* u, cons
   s.n = 0;
   s.have_prev = 0;
   s.prev_step = -1;
+  s.has_last = false;
   b->dirty = true;
   return LBM_OK;
 }
@@ -677,6 +682,8 @@ static void take_stats(lbm_batch* b, int32_t slot, lbm_stats* out) {
   out->max_abs_u = v[kNumSums];
   s.have_prev = 1;
   s.prev_step = s.n;
+  s.last = *out;
+  s.has_last = true;
 }
 
 int lbm_batch_reductions(lbm_batch* b, int32_t slot, lbm_stats* out) {
@@ -702,6 +709,12 @@ int lbm_batch_reductions_all(lbm_batch* b, lbm_stats* out, int32_t* slots, int32
   for (int k = 0; k < n; ++k) take_stats(b, slots[k], &out[k]);
   *count = n;
   return LBM_OK;
+}
+
+int lbm_batch_residual(lbm_batch* b, int32_t slot, int32_t kind, int32_t component, double* r) {
+  if (int rc = check_slot(b, slot)) return rc;
+  if (!b->slots[slot].has_last) return bfail(LBM_EINVAL, "no reduction of this slot yet");
+  return lbm_stats_residual(&b->slots[slot].last, kind, component, r);
 }
 
 int lbm_batch_set_launch(lbm_batch* b, int32_t bx, int32_t by, int32_t persistent) {

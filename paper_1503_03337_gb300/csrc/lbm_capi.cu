@@ -33,6 +33,8 @@ struct lbm_handle {
   void* staging = nullptr;      // grow-only device buffer for host transfers
   size_t staging_bytes = 0;
   int64_t bytes = 0;
+  uint8_t* solid_bytes = nullptr;   // N bytes: the solid-node mask, or null
+  uint32_t* solid_links = nullptr;  // N words: its link bits (d.solid)
 };
 
 namespace {
@@ -93,6 +95,8 @@ int apply_params(lbm_handle* h, const lbm_params* p) {
   if (p->residual_interval < 0) return fail(LBM_EINVAL, "residual_interval < 0");
   if (p->rounding != LBM_ROUND_NEAREST && p->rounding != LBM_ROUND_STOCHASTIC)
     return fail(LBM_EINVAL, "unknown rounding mode");
+  if (!finite_all(p->p_face, 6) || !finite_all(p->p_amp, 6) || !std::isfinite(p->p_period))
+    return fail(LBM_EINVAL, "face pressures must be finite");
   if (h->d.Q == 14) s[4] = s[1];
   h->params = *p;
   for (int k = 0; k < 6; ++k) h->d.s[k] = s[k];
@@ -100,12 +104,27 @@ int apply_params(lbm_handle* h, const lbm_params* p) {
   h->d.period = p->force_period;
   h->d.p_ref = p->p_ref;
   h->d.rounding = p->rounding;
+  for (int f = 0; f < 6; ++f) {
+    h->d.p_face[f] = p->p_face[f];
+    h->d.p_amp[f] = p->p_amp[f];
+  }
+  h->d.p_period = p->p_period;
   return LBM_OK;
 }
 
 int apply_geometry(lbm_handle* h, const lbm_geom* g) {
+  if (h->solid_bytes)
+    for (int f = 0; f < 6; ++f)
+      if (g->face[f] == LBM_NEQ_VELOCITY || g->face[f] == LBM_NEQ_PRESSURE)
+        return fail(LBM_EINVAL, "extrapolation faces do not combine with solid nodes");
   // set_faces changes the handle only once every check has passed
-  if (const char* why = set_faces(h->d, g)) return fail(LBM_EINVAL, why);
+  DomainDesc d = h->d;
+  if (const char* why = set_faces(d, g)) return fail(LBM_EINVAL, why);
+  if (h->solid_bytes) {  // the link bits follow the faces' wraps and mirrors
+    cudaError_t e = launch_solid_links(d, h->solid_bytes, h->solid_links, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "solid links");
+  }
+  h->d = d;
   h->geom = *g;
   return LBM_OK;
 }
@@ -214,6 +233,8 @@ void lbm_destroy(lbm_handle* h) {
   if (h->partials) cudaFree(h->partials);
   if (h->stats_host) cudaFreeHost(h->stats_host);
   if (h->staging) cudaFree(h->staging);
+  if (h->solid_bytes) cudaFree(h->solid_bytes);
+  if (h->solid_links) cudaFree(h->solid_links);
   delete h;
 }
 
@@ -272,6 +293,44 @@ static int upload(lbm_handle* h, const double* src, size_t count, int on_device,
   return LBM_OK;
 }
 
+int lbm_set_solid(lbm_handle* h, const uint8_t* solid, int on_device) {
+  if (int rc = check(h)) return rc;
+  DeviceGuard dg(h->device);
+  const size_t N = (size_t)h->d.N;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_solid synchronize");
+  if (!solid) {  // back to the plain box
+    if (h->solid_bytes) cudaFree(h->solid_bytes);
+    if (h->solid_links) cudaFree(h->solid_links);
+    if (h->solid_bytes) h->bytes -= (int64_t)(5 * N);
+    h->solid_bytes = nullptr;
+    h->solid_links = nullptr;
+    h->d.solid = nullptr;
+    return LBM_OK;
+  }
+  if (h->d.neq_vel | h->d.neq_pre)
+    return fail(LBM_EINVAL, "extrapolation faces do not combine with solid nodes");
+  if (!h->solid_bytes) {
+    e = cudaMalloc(&h->solid_bytes, N);
+    if (e == cudaSuccess) e = cudaMalloc(&h->solid_links, 4 * N);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (h->solid_bytes) cudaFree(h->solid_bytes);
+      h->solid_bytes = nullptr;
+      h->solid_links = nullptr;
+      return fail(LBM_ENOMEM, "solid mask allocation failed");
+    }
+    h->bytes += (int64_t)(5 * N);
+  }
+  e = cudaMemcpyAsync(h->solid_bytes, solid, N, on_device ? cudaMemcpyDeviceToDevice
+                                                          : cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_solid_links(h->d, h->solid_bytes, h->solid_links, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_solid");
+  h->d.solid = h->solid_links;
+  return LBM_OK;
+}
+
 int lbm_init_equilibrium(lbm_handle* h, const double* u, const double* p, int on_device) {
   if (int rc = check(h)) return rc;
   DeviceGuard dg(h->device);
@@ -325,10 +384,15 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     return fail(LBM_EUNSTABLE, "a reduction found non-finite values");
   DeviceGuard dg(h->device);
   const int K = h->params.residual_interval;
+  const bool neq = (h->d.neq_vel | h->d.neq_pre) != 0;
   for (int64_t k = 0; k < nsteps; ++k) {
     cudaError_t e = launch_step(h->d, h->n, h->block, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel");
     h->n += 1;
+    if (neq) {  // the extrapolation boundaries of the new time level
+      e = launch_neq(h->d, h->n, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "boundary kernel");
+    }
     if (K > 0 && h->n % K == 0)
       if (int rc = run_reduction(h)) return rc;
   }
@@ -351,6 +415,7 @@ int lbm_set_step(lbm_handle* h, int64_t n) {
   h->n = n;
   h->have_prev = 0;
   h->prev_step = -1;
+  h->stats_step = -1;
   return LBM_OK;
 }
 
@@ -396,6 +461,7 @@ int lbm_write_populations(lbm_handle* h, const double* src, int src_on_device) {
     h->stats_host[kNumSums - 1] = 0.0;
     h->have_prev = 0;
     h->prev_step = -1;
+    h->stats_step = -1;
   }
   return rc;
 }
@@ -436,6 +502,44 @@ int lbm_read_stats(lbm_handle* h, lbm_stats* out) {
   return LBM_OK;
 }
 
+int lbm_stats_residual(const lbm_stats* s, int32_t kind, int32_t component, double* r) {
+  if (!s || !r) return fail(LBM_EINVAL, "null argument");
+  if (kind != LBM_RESIDUAL_CAVITY && (component < 0 || component > 2))
+    return fail(LBM_EINVAL, "component must be 0, 1 or 2");
+  if (s->prev_step < 0)
+    return fail(LBM_EINVAL, "the statistics hold no earlier snapshot (prev_step < 0)");
+  double num, den;
+  switch (kind) {
+    case LBM_RESIDUAL_STEADY:  // Eq. sc: against the earlier time level
+      num = s->sum_abs_du[component];
+      den = s->sum_abs_u_prev[component];
+      break;
+    case LBM_RESIDUAL_PERIODIC:  // Eq. cr: against the later time level
+      num = s->sum_abs_du[component];
+      den = s->sum_abs_u[component];
+      break;
+    case LBM_RESIDUAL_CAVITY:  // Eq. cavity_creterion: every component, later level
+      num = s->sum_abs_du[0] + s->sum_abs_du[1] + s->sum_abs_du[2];
+      den = s->sum_abs_u[0] + s->sum_abs_u[1] + s->sum_abs_u[2];
+      break;
+    default: return fail(LBM_EINVAL, "unknown residual kind");
+  }
+  *r = den > 0.0 ? num / den : (num == 0.0 ? 0.0 : HUGE_VAL);
+  return LBM_OK;
+}
+
+int lbm_residual(lbm_handle* h, int32_t kind, int32_t component, double* r) {
+  if (int rc = check(h)) return rc;
+  if (!r) return fail(LBM_EINVAL, "null output");
+  DeviceGuard dg(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "residual synchronize");
+  if (h->stats_step < 0) return fail(LBM_EINVAL, "no reduction has run yet");
+  lbm_stats s;
+  fill_stats(h, &s);
+  return lbm_stats_residual(&s, kind, component, r);
+}
+
 int lbm_set_launch(lbm_handle* h, const lbm_launch* l) {
   if (int rc = check(h)) return rc;
   if (!l) return fail(LBM_EINVAL, "null launch");
@@ -457,7 +561,7 @@ int lbm_set_overlap(lbm_handle* h, int32_t enable) {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, std::pair<BlockShape, double>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int>, std::pair<BlockShape, double>> g_tune_cache;
 
 const BlockShape kCandidates[] = {{32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1},
                                   {64, 1, 1},  {64, 2, 1}, {64, 4, 1}, {128, 1, 1},
@@ -468,7 +572,8 @@ const BlockShape kCandidates[] = {{32, 1, 1},  {32, 2, 1}, {32, 4, 1}, {32, 8, 1
 int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) {
   if (int rc = check(h)) return rc;
   DeviceGuard dg(h->device);
-  const auto key = std::make_tuple(h->d.Q, h->d.storage, h->d.nx, h->d.ny, h->d.nz);
+  const auto key =
+      std::make_tuple(h->d.Q, h->d.storage, h->d.rounding, h->d.nx, h->d.ny, h->d.nz);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -541,6 +646,14 @@ int lbm_get_launch(lbm_handle* h, lbm_launch* out) {
   if (int rc = check(h)) return rc;
   if (!out) return fail(LBM_EINVAL, "null output");
   *out = {h->block.bx, h->block.by, h->block.cpt};
+  return LBM_OK;
+}
+
+int lbm_device_populations(lbm_handle* h, void** ptr, int64_t* bytes) {
+  if (int rc = check(h)) return rc;
+  if (!ptr || !bytes) return fail(LBM_EINVAL, "null output");
+  *ptr = h->d.f;
+  *bytes = h->d.N * h->d.Q * (int64_t)storage_bytes(h->d.storage);
   return LBM_OK;
 }
 

@@ -59,10 +59,16 @@ __global__ void k_read(Domain<double> d, FieldArgs a) {
     y = (int)(r % d.ny);
     z = (int)(r / d.ny);
     double fv[Q];
-    get_canonical<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, fv);
-    for (int b = 0; b < Q; ++b) fv[b] += 3.0 * Lattice<Q>::w(b) * a.p_ref;
-    double P, u[3];
-    macro<Q>(fv, a.F, P, u);
+    double P, u[3], p;
+    if (d.solid && (d.solid[i] & kSolidCell)) {  // solid nodes report zero
+      for (int b = 0; b < Q; ++b) fv[b] = 0.0;
+      u[0] = u[1] = u[2] = p = 0.0;
+    } else {
+      get_canonical<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, fv);
+      for (int b = 0; b < Q; ++b) fv[b] += 3.0 * Lattice<Q>::w(b) * a.p_ref;
+      macro<Q>(fv, a.F, P, u);
+      p = pressure_of<Q>(P, u);
+    }
     int64_t off = 0;
     auto put = [&](int64_t k, double v) {
       if (a.dtype == LBM_DTYPE_F64) static_cast<double*>(a.dst)[k] = v;
@@ -73,7 +79,7 @@ __global__ void k_read(Domain<double> d, FieldArgs a) {
       off += 3 * N;
     }
     if (a.mask & LBM_FIELD_P) {
-      put(off + i, pressure_of<Q>(P, u));
+      put(off + i, p);
       off += N;
     }
     if (a.mask & LBM_FIELD_POPULATIONS) {
@@ -90,6 +96,9 @@ __global__ void k_write(Domain<double> d, FieldArgs a) {
     const int x = (int)(i % d.nx);
     const int64_t r = i / d.nx;
     const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+    // a solid node holds nothing (and at odd parity its canonical slots
+    // hold the bounce-back values of its fluid neighbours)
+    if (d.solid && (d.solid[i] & kSolidCell)) continue;
     double fv[Q];
     for (int b = 0; b < Q; ++b)
       fv[b] = a.src[b * N + i] - 3.0 * Lattice<Q>::w(b) * a.p_ref;
@@ -111,12 +120,13 @@ __global__ void k_init(Domain<double> d, FieldArgs a) {
     const double p = (a.p_in ? a.p_in[i] : 0.0) - a.p_ref;
     const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     double fv[Q];
+    const bool solid = d.solid && (d.solid[i] & kSolidCell);
     // Eq. edf with lambda_a = w_a p / c_s^2 (Eq. lamda_alpha), c_s^2 = 1/3
 #pragma unroll
     for (int b = 0; b < Q; ++b) {
       const double cu = Lattice<Q>::c(b, 0) * u[0] + Lattice<Q>::c(b, 1) * u[1] +
                         Lattice<Q>::c(b, 2) * u[2];
-      fv[b] = Lattice<Q>::w(b) * (3.0 * p + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+      fv[b] = solid ? 0.0 : Lattice<Q>::w(b) * (3.0 * p + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
     }
     put_canonical<Q, S, double, false>(d, static_cast<S*>(d.f), x, y, z, fv);
   }
@@ -169,6 +179,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(Domain<double> d, Red
     const int x = (int)(i % d.nx);
     const int64_t r = i / d.nx;
     const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+    if (d.solid && (d.solid[i] & kSolidCell)) {  // no flow: zero in every sum
+      if (a.u_prev)
+        for (int k = 0; k < 3; ++k) a.u_prev[k * N + i] = 0.0;
+      continue;
+    }
     double fv[Q];
     get_canonical<Q, S, double, ODD>(d, static_cast<const S*>(d.f), x, y, z, fv);
     double P, u[3];
@@ -312,6 +327,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d,
     const int x = i % d.nx;
     const int r = i / d.nx;
     const int y = r % d.ny, z = r / d.ny;
+    if (d.solid && (d.solid[i] & kSolidCell)) {  // no flow: zero in every sum
+      if (a.u_prev)
+        for (int k = 0; k < 3; ++k) snap[(int64_t)k * N + i] = make_float2(0.0f, 0.0f);
+      continue;
+    }
     PairSum sP, sj[3];
     cell_moments<Q, S, ODD>(d, static_cast<const S*>(d.f), x, y, z, a.uw, a.edge_scale, sP,
                             sj);

@@ -26,6 +26,10 @@ struct DomainDesc {
   int per[3];
   int moving;  // bit f: face f is a moving wall
   int sym;     // bit f: face f is a symmetry plane
+  int neq_vel; // bit f: face f is a non-equilibrium extrapolation velocity face
+  int neq_pre; // bit f: ... pressure face
+  double p_face[6], p_amp[6], p_period;  // pressure of the pressure faces
+  const uint32_t* solid;  // device: per-cell solid-link bits (Domain::solid), or null
   double uw[6][3];
   int edge_axis[6];  // edge profiles of moving faces (lbm_geom)
   double edge_scale[6][2];
@@ -44,9 +48,19 @@ struct BlockShape {
 
 BlockShape default_block(int nx, int ny);
 
-// The face fields of d (per, moving, sym, uw) from a geometry.  Returns
-// nullptr, or the reason the geometry is invalid (then d is unchanged).
+// The face fields of d (per, moving, sym, neq_*, uw) from a geometry.
+// Returns nullptr, or the reason the geometry is invalid (then d is
+// unchanged).  d's sizes must be set (extrapolation faces need 3 nodes).
 const char* set_faces(DomainDesc& d, const lbm_geom* g);
+
+// Per-cell solid-link bits (Domain::solid) of the solid-node mask `bytes`
+// (N device bytes, nonzero = solid) for d's geometry.
+cudaError_t launch_solid_links(const DomainDesc& d, const uint8_t* bytes, uint32_t* links,
+                               cudaStream_t st);
+
+// Non-equilibrium extrapolation of the boundary nodes of d's LBM_NEQ_*
+// faces, on the populations of step n (after the step n-1 -> n).
+cudaError_t launch_neq(const DomainDesc& d, int64_t n, cudaStream_t st);
 
 // Message returned by lbm_last_error() on the calling thread.
 void set_last_error(const std::string& msg);

@@ -39,6 +39,11 @@ struct Domain {
   Rates<R> s;
   R F[3];            // body force at the step's time level t_n
   uint32_t key;      // per-step key of the stochastic-rounding hash
+  // Solid nodes (general geometry), null if none: per cell, bit a set if
+  // the pull source x - c_a (after periodic wraps and symmetry mirrors; not
+  // beyond a wall) is a solid node, so that link bounces back off a wall at
+  // rest; kSolidCell marks a solid cell itself, which no step updates.
+  const uint32_t* solid;
   // Element offsets from a cell's slot 0 (index i) used by interior cells
   // on odd steps:
   //   pull[a] = abar*N - s(c_a)     (where f_a(x) is read)
@@ -46,6 +51,38 @@ struct Domain {
   // with s(c) = cx + cy*nx + cz*nx*ny.  Filled by fill_offsets().
   int pull[18], push[18];
 };
+
+constexpr uint32_t kSolidCell = 0x80000000u;
+
+// Domain::solid word of cell i from the byte mask of solid nodes (nonzero =
+// solid): kSolidCell for a solid cell, else bit a set when the pull source
+// x - c_a -- wrapped across periodic axes (bit k of `per`), mirrored across
+// symmetry faces (bit f of `sym`), and not beyond a wall -- is solid.
+template <int Q>
+__host__ __device__ inline uint32_t solid_link_bits(int nx, int ny, int nz, int per, int sym,
+                                                    const uint8_t* bytes, int64_t i) {
+  if (bytes[i]) return kSolidCell;
+  const int n[3] = {nx, ny, nz};
+  const int xyz[3] = {(int)(i % nx), (int)((i / nx) % ny), (int)(i / ((int64_t)nx * ny))};
+  uint32_t m = 0;
+  for (int a = 0; a < Q; ++a) {
+    int src[3];
+    bool beyond_wall = false;
+    for (int k = 0; k < 3; ++k) {
+      int v = xyz[k] - Lattice<Q>::c(a, k);
+      if (v < 0 || v >= n[k]) {
+        const int face = v < 0 ? 2 * k : 2 * k + 1;
+        if ((per >> k) & 1) v += v < 0 ? n[k] : -n[k];
+        else if ((sym >> face) & 1) v = xyz[k];
+        else beyond_wall = true;
+      }
+      src[k] = v;
+    }
+    if (!beyond_wall && bytes[src[0] + (int64_t)nx * (src[1] + (int64_t)ny * src[2])])
+      m |= 1u << a;
+  }
+  return m;
+}
 
 // Per-step key of the stochastic-rounding hash.
 __host__ __device__ inline uint32_t step_key(int64_t n) {
@@ -107,6 +144,7 @@ struct Links {
   bool sm[3], sp[3];  // ghost beyond a symmetry face
   int edge;           // position bits of the cell (see edge_factor)
   bool interior;  // every neighbour is a fluid, unwrapped node: use pull/push
+  uint32_t solid;     // bit a: the pull source of link a is a solid node
 };
 
 __host__ __device__ __forceinline__ int edge_bits(int v, int n, int k) {
@@ -138,6 +176,7 @@ __host__ __device__ __forceinline__ Links make_links(const Domain<R>& d, int x, 
                 L.gm[2], L.gp[2], L.sm[2], L.sp[2]);
   L.edge = edge_bits(x, d.nx, 0) | edge_bits(y, d.ny, 1) | edge_bits(z, d.nz, 2);
   L.interior = false;
+  L.solid = d.solid ? d.solid[x + (int64_t)d.nx * (y + (int64_t)d.ny * z)] : 0u;
   return L;
 }
 
@@ -156,6 +195,7 @@ __host__ __device__ __forceinline__ Links make_links_interior(const Domain<R>& d
   L.sm[0] = L.sp[0] = L.sm[1] = L.sp[1] = L.sm[2] = L.sp[2] = false;
   L.edge = 0;
   L.interior = true;
+  L.solid = 0u;
   return L;
 }
 
@@ -175,6 +215,7 @@ __host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x
   L.op[2] = sz;
   L.gm[1] = L.gp[1] = L.gm[2] = L.gp[2] = false;
   L.interior = false;
+  L.solid = 0u;
   return L;
 }
 
@@ -182,7 +223,7 @@ __host__ __device__ __forceinline__ Links make_links_x(const Domain<R>& d, int x
 // symmetry face normal to axis k) of the node x + s*c_A (s = -1: pull
 // source, +1: push target).  SYM = false: the domain has no symmetry face
 // (mirror stays 0 and the mirrored indexing folds away).
-template <int Q, int A, int SIGN, bool SYM = true>
+template <int Q, int A, int SIGN, bool SYM = true, bool SOLID = true>
 __host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool& ghost,
                                                  int& mirror) {
   off = 0;
@@ -201,6 +242,10 @@ __host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool&
       if (SYM && L.sp[k]) mirror |= 1 << k;
     }
   }
+  // a solid pull source (SIGN -1: x - c_A) or push target (x + c_A, the
+  // pull source of the opposite link): bounce-back at rest.  SOLID = false:
+  // the caller knows L.solid is zero.
+  if (SOLID && ((L.solid >> (SIGN < 0 ? A : opposite<Q>(A))) & 1u)) ghost = true;
 }
 
 // The population whose velocity is c_A with the components of the axes in
@@ -295,7 +340,8 @@ __host__ __device__ __forceinline__ void add_pull_wall_terms(const Domain<R>& d,
 
 // Pre-collision populations f^n of cell i into fv (CG: L2-only loads; SYM:
 // the domain may have symmetry faces).
-template <int Q, typename S, typename R, bool ODD, bool CG = false, bool SYM = true>
+template <int Q, typename S, typename R, bool ODD, bool CG = false, bool SYM = true,
+          bool SOLID = true>
 __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
                                                 int i, const Links& L, R* fv) {
   const int N = (int)d.N;
@@ -316,7 +362,7 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
           [&] {
             int off, mirror;
             bool ghost;
-            link_of<Q, A, -1, SYM>(L, off, ghost, mirror);
+            link_of<Q, A, -1, SYM, SOLID>(L, off, ghost, mirror);
             const int idx =
                 ghost ? (A * N + i) : (opposite_mirror_rt<Q, A>(mirror) * N + i + off);
             fv[A] = load_pop<S, R, CG>(f + idx);
@@ -327,32 +373,66 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
   }
 }
 
-// Store one post-collision value (stochastically rounded if SR).
-template <typename S, typename R, bool SR, int A>
-__host__ __device__ __forceinline__ void put(S* p, R v, uint32_t h) {
+// Random bits of the stochastic rounding.  Cell i and the step's key give
+// one hash per cell, sr_cell_hash; the direction pair (2K, 2K+1) of the cell
+// draws the 32 bits sr_bits<K>(hash), whose low half rounds direction 2K and
+// whose high half rounds 2K+1 (the halves a two-value conversion takes from
+// its random operand).  The bits therefore belong to (cell, direction, step)
+// alone, whether a cell is stored by itself or as one half of an x-adjacent
+// pair.
+__host__ __device__ __forceinline__ uint32_t sr_cell_hash(int i, uint32_t key) {
+  return mix32(uint32_t(i) ^ key);
+}
+template <int K>
+__host__ __device__ __forceinline__ uint32_t sr_bits(uint32_t h) {
+  return mix32_short(h + uint32_t(K + 1) * 0x9e3779b9u);
+}
+
+template <typename S>
+__host__ __device__ __forceinline__ void store_half(S* p, uint16_t v) {
+#ifdef __CUDA_ARCH__
+  *reinterpret_cast<unsigned short*>(p) = v;
+#else
+  memcpy(p, &v, 2);
+#endif
+}
+
+// Store the Q post-collision values fv of one cell at the addresses
+// addr.operator()<A>() (stochastically rounded in direction pairs if SR, h =
+// sr_cell_hash of the cell).
+template <int Q, typename S, typename R, bool SR, typename Addr>
+__host__ __device__ __forceinline__ void store_cell(const R* fv, uint32_t h, Addr&& addr) {
   if constexpr (SR) {
-    Stochastic<S>::store(p, float(v), mix32_short(h + uint32_t(A + 1) * 0x9e3779b9u));
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+      (
+          [&] {
+            const uint32_t w =
+                Stochastic<S>::pack2(float(fv[2 * K + 1]), float(fv[2 * K]), sr_bits<K>(h));
+            store_half(addr.template operator()<2 * K>(), uint16_t(w & 0xffffu));
+            store_half(addr.template operator()<2 * K + 1>(), uint16_t(w >> 16));
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, Q / 2>{});
   } else {
-    Codec<S, R>::store(p, v);
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      (Codec<S, R>::store(addr.template operator()<A>(), fv[A]), ...);
+    }(std::make_integer_sequence<int, Q>{});
   }
 }
 
 // Post-collision populations f* of cell i from fv into storage (`key`: the
 // step's stochastic-rounding key; SYM as in gather).
-template <int Q, typename S, typename R, bool ODD, bool SR = false, bool SYM = true>
+template <int Q, typename S, typename R, bool ODD, bool SR = false, bool SYM = true,
+          bool SOLID = true>
 __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
                                                  int i, const Links& L, R* fv, uint32_t key) {
   const int N = (int)d.N;
-  const uint32_t h = SR ? mix32(uint32_t(i) ^ key) : 0u;
+  const uint32_t h = SR ? sr_cell_hash(i, key) : 0u;
   S* __restrict__ fc = f + i;
   if constexpr (!ODD) {
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((put<S, R, SR, A>(fc + (size_t)opposite<Q>(A) * d.N, fv[A], h)), ...);
-    }(std::make_integer_sequence<int, Q>{});
+    store_cell<Q, S, R, SR>(fv, h, [&]<int A>() { return fc + (size_t)opposite<Q>(A) * d.N; });
   } else if (L.interior) {
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((put<S, R, SR, A>(fc + d.push[A], fv[A], h)), ...);
-    }(std::make_integer_sequence<int, Q>{});
+    store_cell<Q, S, R, SR>(fv, h, [&]<int A>() { return fc + d.push[A]; });
   } else {
     if (d.moving && touches_moving(d, L)) {
       [&]<int... A>(std::integer_sequence<int, A...>) {
@@ -370,32 +450,37 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
     // f*_a goes to A[a][x + c_a], or back into A[abar][x] if x + c_a is a
     // wall ghost; beyond a symmetry face it becomes the mirror population of
     // the mirror node (the slot this cell's mirrored pull reads)
-    [&]<int... A>(std::integer_sequence<int, A...>) {
-      (
-          [&] {
-            int off, mirror;
-            bool ghost;
-            link_of<Q, A, 1, SYM>(L, off, ghost, mirror);
-            const int idx =
-                ghost ? (opposite<Q>(A) * N + i) : (mirror_rt<Q, A>(mirror) * N + i + off);
-            put<S, R, SR, A>(f + idx, fv[A], h);
-          }(),
-          ...);
-    }(std::make_integer_sequence<int, Q>{});
+    store_cell<Q, S, R, SR>(fv, h, [&]<int A>() {
+      int off, mirror;
+      bool ghost;
+      link_of<Q, A, 1, SYM, SOLID>(L, off, ghost, mirror);
+      const int idx = ghost ? (opposite<Q>(A) * N + i) : (mirror_rt<Q, A>(mirror) * N + i + off);
+      return f + idx;
+    });
   }
 }
 
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR, bool CG = false,
-          bool SYM = true>
+          bool SYM = true, bool SOLID = false>
 __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
                                                            S* __restrict__ f, int i,
                                                            const Links& L, const R* F,
                                                            const uint32_t* key) {
   R fv[Q];
-  gather<Q, S, R, ODD, CG, SYM>(d, f, i, L, fv);
+  gather<Q, S, R, ODD, CG, SYM, SOLID>(d, f, i, L, fv);
   R ux, uy, uz;
   collide<Q, FORCE>(fv, d.s, F[0], F[1], F[2], ux, uy, uz);
-  scatter<Q, S, R, ODD, SR, SYM>(d, f, i, L, fv, SR ? *key : 0u);
+  scatter<Q, S, R, ODD, SR, SYM, SOLID>(d, f, i, L, fv, SR ? *key : 0u);
+}
+
+// Does any active lane of the warp hold a nonzero v (every lane on the
+// host, where cells run one at a time)?
+__host__ __device__ __forceinline__ bool warp_any(bool v) {
+#ifdef __CUDA_ARCH__
+  return __any_sync(__activemask(), v);
+#else
+  return v;
+#endif
 }
 
 // The whole fused update of one cell: gather (stream), collide, scatter.
@@ -415,9 +500,25 @@ __host__ __device__ __forceinline__ void update_cell_at(const Domain<R>& d, S* _
                                                         int y, int z, int x_lo, int x_hi) {
   const int i = x + d.nx * (y + d.ny * z);
   if constexpr (!ODD) {
+    if (d.solid && (d.solid[i] & kSolidCell)) return;  // solid cells hold no flow
     Links L{};
     update_with_links<Q, S, R, false, FORCE, SR, CG>(d, f, i, L, F, key);
   } else {
+    if (d.solid) {
+      // a warp with any solid-touching link takes the full addressing with
+      // the cells' solid bits (the vote comes before any lane leaves)
+      const uint32_t sm = d.solid[i];
+      if (warp_any(sm != 0u)) {
+        if (sm & kSolidCell) return;
+        if (d.sym)
+          update_with_links<Q, S, R, true, FORCE, SR, CG, true, true>(
+              d, f, i, make_links(d, x, y, z), F, key);
+        else
+          update_with_links<Q, S, R, true, FORCE, SR, CG, false, true>(
+              d, f, i, make_links(d, x, y, z), F, key);
+        return;
+      }
+    }
     if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
       if (x_lo > 0 && x_hi < d.nx - 1)
         update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_interior(d), F,
@@ -481,8 +582,9 @@ struct Pair2<__nv_bfloat16> {
 // / BF16 storage, which one value per thread leaves at 64), and the two
 // cells collide together in packed FP32x2.  Needs nx even (then N is even
 // and a pair never straddles a row).  An even step touches only the cell's
-// own slots, so no links are needed.
-template <int Q, typename S, bool FORCE>
+// own slots, so no links are needed.  SR: each word is one stochastic pair
+// conversion with the random bits the one-cell update uses for both cells.
+template <int Q, typename S, bool FORCE, bool SR = false>
 __device__ __forceinline__ void update_pair_even(const Domain<float>& d, S* __restrict__ f,
                                                  int i) {
   using W = typename Pair2<S>::type;
@@ -494,9 +596,28 @@ __device__ __forceinline__ void update_pair_even(const Domain<float>& d, S* __re
   }(std::make_integer_sequence<int, Q>{});
   pf2 ux, uy, uz;
   collide<Q, FORCE>(fv, d.s, d.F[0], d.F[1], d.F[2], ux, uy, uz);
-  [&]<int... A>(std::integer_sequence<int, A...>) {
-    ((g[j + opposite<Q>(A) * M] = Pair2<S>::pack(fv[A])), ...);
-  }(std::make_integer_sequence<int, Q>{});
+  if constexpr (SR) {
+    // random bits of direction A for cells i (low half of the operand) and
+    // i + 1 (high half): the halves of sr_bits<A/2> of each cell's hash that
+    // round direction A
+    const uint32_t he = sr_cell_hash(i, d.key), ho = sr_cell_hash(i + 1, d.key);
+    uint32_t* __restrict__ g32 = reinterpret_cast<uint32_t*>(f);
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+      (
+          [&] {
+            const uint32_t re = sr_bits<K>(he), ro = sr_bits<K>(ho);
+            g32[j + opposite<Q>(2 * K) * M] =
+                Stochastic<S>::pack2(fv[2 * K].v.y, fv[2 * K].v.x, (re & 0xffffu) | (ro << 16));
+            g32[j + opposite<Q>(2 * K + 1) * M] = Stochastic<S>::pack2(
+                fv[2 * K + 1].v.y, fv[2 * K + 1].v.x, (re >> 16) | (ro & 0xffff0000u));
+          }(),
+          ...);
+    }(std::make_integer_sequence<int, Q / 2>{});
+  } else {
+    [&]<int... A>(std::integer_sequence<int, A...>) {
+      ((g[j + opposite<Q>(A) * M] = Pair2<S>::pack(fv[A])), ...);
+    }(std::make_integer_sequence<int, Q>{});
+  }
 }
 
 // Inverse of gather: put canonical pre-collision values fv of cell (x,y,z)

@@ -311,17 +311,18 @@ __host__ __device__ __forceinline__ float bits_f32(uint32_t b) {
 #endif
 }
 
-// Round v to a value with `drop` fewer mantissa bits, stochastically:
-// add uniform random bits below the kept LSB, then truncate the magnitude.
-__host__ __device__ __forceinline__ float dither_truncate(float v, int drop, uint32_t r) {
-  const uint32_t mask = (drop >= 31) ? 0x7fffffffu : ((1u << drop) - 1u);
-  uint32_t b = f32_bits(v);
-  const uint32_t mag = b & 0x7fffffffu;
-  if (mag >= 0x7f800000u) return v;  // inf / nan unchanged
-  b = (b & 0x80000000u) | ((mag + (r & mask)) & ~mask);
-  return bits_f32(b);
-}
-
+// Stochastic rounding of two FP32 values into one 32-bit word of two 16-bit
+// values, hi <- a and lo <- b, from 32 random bits r.  Each value becomes one
+// of its two 16-bit neighbours with probability proportional to its distance
+// to the other, so the stored value is unbiased:
+//   FP16: |v| / s + k / 8192 rounded down, times s, with s the FP16 spacing
+//         at |v| (2^-24 below 2^-14) and k = r[28:16] (hi) or r[12:0] (lo);
+//   BF16: the 16 random bits r[31:16] (hi) or r[15:0] (lo) added to the
+//         16 bits of the FP32 magnitude that BF16 drops, then truncated.
+// On the device each pair is one conversion instruction (cvt.rs.f16x2 /
+// .bf16x2 of sm_100 and later, whose bit layout and rounding are exactly
+// these); host builds compute the same bits.  Finite inputs below the
+// format's largest value.
 template <typename S>
 struct Stochastic {
   static constexpr bool enabled = false;
@@ -329,23 +330,46 @@ struct Stochastic {
 template <>
 struct Stochastic<__half> {
   static constexpr bool enabled = true;
-  __host__ __device__ static void store(__half* p, float v, uint32_t r) {
-    // half keeps 10 mantissa bits (13 fewer than float) down to 2^-14; below
-    // that its spacing is fixed at 2^-24, so more bits are dropped.
-    const int e = int((f32_bits(v) >> 23) & 0xffu) - 127;
-    if (e < -24) {  // below half's smallest spacing: nearest is within 3e-8
-      *p = __float2half_rn(v);
-      return;
-    }
-    const int drop = e < -14 ? 13 + (-14 - e) : 13;
-    *p = __float2half_rz(dither_truncate(v, drop, r));
+  __host__ static float round_host(float v, uint32_t k) {
+    const uint32_t b = f32_bits(v), mag = b & 0x7fffffffu, sign = b & 0x80000000u;
+    if (mag >= 0x7f800000u) return v;
+    if (mag >= 0x38800000u)  // |v| >= 2^-14: drop 13 of the 23 mantissa bits
+      return bits_f32(sign | ((mag + k) & ~0x1fffu));
+    // subnormal FP16 spacing 2^-24: count spacings, exactly in double
+    const double q = std::floor(double(bits_f32(mag)) * 16777216.0 + double(k) / 8192.0);
+    return bits_f32(sign | f32_bits(float(q / 16777216.0)));
+  }
+  __host__ __device__ static uint32_t pack2(float a, float b, uint32_t r) {
+#ifdef __CUDA_ARCH__
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(r));
+    return d;
+#else
+    const __half ha = __float2half_rz(round_host(a, (r >> 16) & 0x1fffu));
+    const __half hb = __float2half_rz(round_host(b, r & 0x1fffu));
+    uint16_t ua, ub;
+    memcpy(&ua, &ha, 2);
+    memcpy(&ub, &hb, 2);
+    return (uint32_t(ua) << 16) | ub;
+#endif
   }
 };
 template <>
 struct Stochastic<__nv_bfloat16> {
   static constexpr bool enabled = true;
-  __host__ __device__ static void store(__nv_bfloat16* p, float v, uint32_t r) {
-    *p = __float2bfloat16_rz(dither_truncate(v, 16, r));
+  __host__ static uint16_t round_host(float v, uint32_t k) {
+    const uint32_t b = f32_bits(v), mag = b & 0x7fffffffu;
+    if (mag >= 0x7f800000u) return uint16_t(b >> 16);
+    return uint16_t(((b & 0x80000000u) | ((mag + k) & ~0xffffu)) >> 16);
+  }
+  __host__ __device__ static uint32_t pack2(float a, float b, uint32_t r) {
+#ifdef __CUDA_ARCH__
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(r));
+    return d;
+#else
+    return (uint32_t(round_host(a, r >> 16)) << 16) | round_host(b, r & 0xffffu);
+#endif
   }
 };
 

@@ -183,13 +183,13 @@ extern "C" int lbm_reductions_static(const lbm_desc* desc, const lbm_geom* geom,
                        "lbm_reductions_static holds at most " +
                            std::to_string(kStaticMaxCells) + " cells");
   DomainDesc dd{};
-  if (const char* why = set_faces(dd, geom)) return static_fail(LBM_EINVAL, why);
   dd.Q = desc->Q;
   dd.nx = desc->nx;
   dd.ny = desc->ny;
   dd.nz = desc->nz;
   dd.storage = desc->storage;
   dd.N = N;
+  if (const char* why = set_faces(dd, geom)) return static_fail(LBM_EINVAL, why);
   dd.f = const_cast<void*>(populations);
   for (int k = 0; k < 3; ++k) dd.force[k] = params->force[k];
   dd.period = params->force_period;

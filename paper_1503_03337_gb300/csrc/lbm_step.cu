@@ -18,6 +18,7 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
   for (int k = 0; k < 3; ++k) o.per[k] = d.per[k];
   o.moving = d.moving;
   o.sym = d.sym;
+  o.solid = d.solid;
   for (int face = 0; face < 6; ++face) {
     for (int k = 0; k < 3; ++k) o.uw[face][k] = R(d.uw[face][k]);
     o.edge_axis[face] = d.edge_axis[face];
@@ -47,7 +48,12 @@ void force_at(const DomainDesc& d, int64_t n, double F[3]) {
 
 const char* set_faces(DomainDesc& d, const lbm_geom* g) {
   for (int f = 0; f < 6; ++f)
-    if (g->face[f] < LBM_PERIODIC || g->face[f] > LBM_SYMMETRY) return "unknown face kind";
+    if (g->face[f] < LBM_PERIODIC || g->face[f] > LBM_NEQ_PRESSURE) return "unknown face kind";
+  for (int f = 0; f < 6; ++f) {
+    const int n = f < 2 ? d.nx : (f < 4 ? d.ny : d.nz);
+    if ((g->face[f] == LBM_NEQ_VELOCITY || g->face[f] == LBM_NEQ_PRESSURE) && n < 3)
+      return "an extrapolation face needs at least 3 nodes along its axis";
+  }
   int per[3];
   for (int k = 0; k < 3; ++k) {
     const bool lo = g->face[2 * k] == LBM_PERIODIC, hi = g->face[2 * k + 1] == LBM_PERIODIC;
@@ -66,11 +72,14 @@ const char* set_faces(DomainDesc& d, const lbm_geom* g) {
       return "edge scale not finite";
   }
   for (int k = 0; k < 3; ++k) d.per[k] = per[k];
-  d.moving = d.sym = 0;
+  d.moving = d.sym = d.neq_vel = d.neq_pre = 0;
   for (int f = 0; f < 6; ++f) {
     if (g->face[f] == LBM_MOVING_WALL) d.moving |= 1 << f;
     if (g->face[f] == LBM_SYMMETRY) d.sym |= 1 << f;
-    for (int k = 0; k < 3; ++k) d.uw[f][k] = g->face[f] == LBM_MOVING_WALL ? g->u_wall[f][k] : 0.0;
+    if (g->face[f] == LBM_NEQ_VELOCITY) d.neq_vel |= 1 << f;
+    if (g->face[f] == LBM_NEQ_PRESSURE) d.neq_pre |= 1 << f;
+    const bool has_u = g->face[f] == LBM_MOVING_WALL || g->face[f] == LBM_NEQ_VELOCITY;
+    for (int k = 0; k < 3; ++k) d.uw[f][k] = has_u ? g->u_wall[f][k] : 0.0;
     d.edge_axis[f] = g->edge_axis[f];
     d.edge_scale[f][0] = g->edge_axis[f] ? g->edge_scale[f][0] : 1.0;
     d.edge_scale[f][1] = g->edge_axis[f] ? g->edge_scale[f][1] : 1.0;

@@ -31,9 +31,12 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> 
 
 // Even steps with two x-adjacent cells per thread (see update_pair_even; nx
 // even); blockDim.x threads cover 2*blockDim.x cells of a row.  The 36
-// packed values of a pair need more registers than one cell's 18, hence
-// the looser cap.
-template <int Q, typename S, bool FORCE>
+// packed values of a pair need more registers than one cell's 18: at three
+// 256-thread blocks per SM (80 registers) a pair spills about 100 bytes a
+// thread to local memory, and is still faster than at two blocks without
+// spills (measured at 256^3: FP16 66.4 vs 62.7 GLUPS for Q18, 85.0 vs 81.7
+// for Q14).
+template <int Q, typename S, bool FORCE, bool SR>
 __global__ void __launch_bounds__(256, 3) k_step_pair(Domain<float> d) {
   pdl_release();
   pdl_acquire();
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(256, 3) k_step_pair(Domain<float> d) {
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x0 >= d.nx || y >= d.ny) return;
-  update_pair_even<Q, S, FORCE>(d, static_cast<S*>(d.f), x0 + d.nx * (y + d.ny * z));
+  update_pair_even<Q, S, FORCE, SR>(d, static_cast<S*>(d.f), x0 + d.nx * (y + d.ny * z));
 }
 
 template <typename R>
@@ -54,12 +57,12 @@ template <int Q, typename S, typename R, bool SR>
 void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 block,
                           const BlockShape& b, cudaStream_t st) {
   // two cells per thread: even steps of FP32 / FP16 / BF16 storage with nx
-  // even and rounding to nearest; every other step runs one cell per thread
-  if constexpr (sizeof(S) <= 4 && !SR) {
-    if (b.cpt == 2 && !odd && d.nx % 2 == 0) {
+  // even and no solid nodes; every other step runs one cell per thread
+  if constexpr (sizeof(S) <= 4) {
+    if (b.cpt == 2 && !odd && d.nx % 2 == 0 && !d.solid) {
       grid.x = (d.nx / 2 + block.x - 1) / block.x;
-      if (force) launch_one(k_step_pair<Q, S, true>, d, grid, block, b.pdl != 0, st);
-      else launch_one(k_step_pair<Q, S, false>, d, grid, block, b.pdl != 0, st);
+      if (force) launch_one(k_step_pair<Q, S, true, SR>, d, grid, block, b.pdl != 0, st);
+      else launch_one(k_step_pair<Q, S, false, SR>, d, grid, block, b.pdl != 0, st);
       return;
     }
   }

@@ -24,7 +24,7 @@ import numpy as np
 
 SQUARE_DUCT_K = 0.2946854131
 
-PERIODIC, WALL, MOVING_WALL, SYMMETRY = 0, 1, 2, 3
+PERIODIC, WALL, MOVING_WALL, SYMMETRY, NEQ_VELOCITY, NEQ_PRESSURE = 0, 1, 2, 3, 4, 5
 XM, XP, YM, YP, ZM, ZP = range(6)
 
 
@@ -47,14 +47,18 @@ class Case:
     init_p: Optional[np.ndarray] = None   # (nz, ny, nx) or None
     rounding: int = 0             # 16-bit stores: 0 nearest, 1 stochastic
     edge: Optional[dict] = None   # {face: (axis, scale_first, scale_last)}
+    # pressure of NEQ_PRESSURE faces: p_face + p_amp cos(2 pi n / p_period)
+    p_face: Tuple[float, ...] = (0.0,) * 6
+    p_amp: Tuple[float, ...] = (0.0,) * 6
+    p_period: float = 0.0
+    c: float = 1.0  # lattice speed dx/dt of a recipe given in physical units
+    p_ref: float = 0.0  # pressure the stored populations are deviations from
+    solid: Optional[np.ndarray] = None  # (nz, ny, nx) uint8, nonzero = solid node
 
     @property
     def cells(self) -> int:
         return self.nx * self.ny * self.nz
 
-    @property
-    def s_nu(self) -> float:
-        return 1.0 / (3.0 * self.nu + 0.5)
 
 
 def cavity(Q: int, n: int, Re: float, U: float = 0.05, storage: str = "f32",
@@ -104,6 +108,88 @@ def pulsatile(Q: int, n: int, nz: int, period: int, eta: float, amplitude: float
     return Case("pulsatile", Q, n, n, nz, faces, np.zeros((6, 3)), nu=nu,
                 force=(0.0, 0.0, amplitude), period=float(period),
                 storage=storage, u_ref=u_ref)
+
+
+def pressure_duct(Q: int, dx: float, inv_tau: float, nu: float = 0.03, length: float = 2.0,
+                  half_width: float = 0.5, p_in: float = 1.1, p_out: float = 1.0,
+                  storage: str = "f64") -> Case:
+    """The pressure-driven square duct of Sec. 4.1 on its node grid: nodes on
+    the walls y, z = +-a and on the inlet / outlet planes x = 0, l, spacing
+    dx (l/dx + 1 by 2a/dx + 1 by 2a/dx nodes), viscosity nu, s_nu = 1/tau,
+    inlet and outlet pressures p_in, p_out (the paper's 1.1 and 1.0), all
+    converted to lattice units with c = dx / dt, dt = nu_lattice dx^2 / nu,
+    nu_lattice = (tau - 1/2) / 3.  Walls use the extrapolation velocity
+    boundary, inlet and outlet the extrapolation pressure boundary.  Start
+    from rest at the mean pressure, inlet and outlet planes at theirs.
+    Stored populations are deviations from the mean pressure (p_ref)."""
+    tau = 1.0 / inv_tau
+    dt = (tau - 0.5) / 3.0 * dx * dx / nu
+    c = dx / dt
+    nx, ny = int(round(length / dx)) + 1, int(round(2 * half_width / dx)) + 1
+    faces = (NEQ_PRESSURE, NEQ_PRESSURE) + (NEQ_VELOCITY,) * 4
+    case = Case("pressure_duct", Q, nx, ny, ny, faces, np.zeros((6, 3)),
+                nu=(tau - 0.5) / 3.0, storage=storage, u_ref=0.0)
+    case.p_face = (p_in / c ** 2, p_out / c ** 2, 0.0, 0.0, 0.0, 0.0)
+    p0 = np.full((ny, ny, nx), 0.5 * (p_in + p_out) / c ** 2)
+    p0[:, :, 0] = p_in / c ** 2
+    p0[:, :, -1] = p_out / c ** 2
+    case.init_p = p0
+    case.c = c
+    case.p_ref = 0.5 * (p_in + p_out) / c ** 2
+    return case
+
+
+def pressure_pulsatile(Q: int, dx: float, dt: float, tau: float, period: float = 100.0,
+                       delta_p: float = 0.001, length: float = 2.0, half_width: float = 0.5,
+                       p_out: float = 1.0, storage: str = "f64") -> Case:
+    """The pressure-driven pulsatile channel of Sec. 4.2 on its node grid
+    (the duct of pressure_duct): outlet pressure p_out, inlet pressure
+    p_out - delta_p cos(2 pi t / period), so that dp/dx = G cos(w t) with
+    G = delta_p / length (Eq. pbc-pul); spacing dx, time step dt, s_nu =
+    1/tau; lattice units with c = dx / dt.  Start from rest at the mean of
+    the t = 0 inlet and outlet pressures, the end planes at theirs; stored
+    populations are deviations from the outlet pressure (p_ref).  Its
+    physical viscosity is (tau - 1/2)/3 dx^2 / dt."""
+    c = dx / dt
+    nx, ny = int(round(length / dx)) + 1, int(round(2 * half_width / dx)) + 1
+    faces = (NEQ_PRESSURE, NEQ_PRESSURE) + (NEQ_VELOCITY,) * 4
+    case = Case("pressure_pulsatile", Q, nx, ny, ny, faces, np.zeros((6, 3)),
+                nu=(tau - 0.5) / 3.0, storage=storage, u_ref=0.0)
+    case.p_face = (p_out / c ** 2, p_out / c ** 2, 0.0, 0.0, 0.0, 0.0)
+    case.p_amp = (-delta_p / c ** 2, 0.0, 0.0, 0.0, 0.0, 0.0)
+    case.p_period = period / dt
+    p0 = np.full((ny, ny, nx), (p_out - 0.5 * delta_p) / c ** 2)
+    p0[:, :, 0] = (p_out - delta_p) / c ** 2
+    p0[:, :, -1] = p_out / c ** 2
+    case.init_p = p0
+    case.c = c
+    case.p_ref = p_out / c ** 2
+    return case
+
+
+def porous_spheres(Q: int, n: int, radius: float = 6.0, solid_fraction: float = 0.3,
+                   seed: int = 0, storage: str = "f32", force: float = 1e-6) -> Case:
+    """A periodic n^3 box filled with randomly placed solid spheres (seeded
+    centres, overlaps allowed, periodic images) until about solid_fraction
+    of the nodes are solid; flow driven by a body force along x.  The
+    porous-medium geometry the paper's introduction motivates."""
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((n, n, n), dtype=bool)
+    r = int(np.ceil(radius))
+    off = np.arange(-r, r + 1)
+    dz, dy, dx = np.meshgrid(off, off, off, indexing="ij")
+    ball = dx ** 2 + dy ** 2 + dz ** 2 <= radius ** 2
+    bz, by, bx = dz[ball], dy[ball], dx[ball]
+    flat = solid.reshape(-1)
+    while solid.mean() < solid_fraction:
+        # a batch of spheres at a time; the last batch may overshoot a little
+        k = max(1, int((solid_fraction - solid.mean()) * n ** 3 / len(bx) * 0.5) + 1)
+        x0, y0, z0 = (rng.integers(0, n, size=(3, k, 1)))
+        flat[(((z0 + bz) % n) * n + (y0 + by) % n) * n + (x0 + bx) % n] = True
+    case = Case("porous", Q, n, n, n, (PERIODIC,) * 6, np.zeros((6, 3)), nu=0.05,
+                force=(force, 0.0, 0.0), storage=storage, u_ref=0.0)
+    case.solid = solid.astype(np.uint8)
+    return case
 
 
 def random_state(case: Case, seed: int, u_scale: float = 0.02, p_scale: float = 0.01):
@@ -160,12 +246,17 @@ class Request:
     kind: str
     Q: int
     L: int
-    tol: float          # requested accuracy (picks FP32 below 1e-3, else FP16)
+    tol: float          # requested accuracy: max |u - u_exact| / U of the delivered field
     max_steps: int
 
     @property
     def storage(self) -> str:
-        return "f32" if self.tol < 1e-3 else "f16"
+        """FP16 (stochastic rounding) where its measured error fits the
+        request: within 1e-3 U on ducts and oscillating channels, within
+        1e-2 U on cavities (whose lid corners amplify storage rounding);
+        FP32 (within 1e-5 U) otherwise."""
+        fp16_error = 1e-2 if self.kind == "cavity" else 1e-3
+        return "f16" if self.tol >= fp16_error else "f32"
 
 
 def request_trace(n_requests: int, rate: float = 200.0, seed: int = 0, lmin: int = 32,
@@ -188,12 +279,16 @@ def request_trace(n_requests: int, rate: float = 200.0, seed: int = 0, lmin: int
 
 def request_case(r: Request) -> Case:
     if r.kind == "cavity":
-        return cavity(r.Q, r.L, 400.0, U=0.05, storage=r.storage)
-    if r.kind == "duct":
-        return duct(r.Q, r.L, max(4, r.L // 4), nu=0.1, u_max=0.02, storage=r.storage)
-    # pulsatile: T = 1000 steps, eta = 4, amplitude from the quasi-steady
-    # square-duct relation, so that u stays O(0.02)
-    b = r.L / 2.0
-    nu = b * b * (2.0 * np.pi / 1000.0) / 16.0
-    A = 0.02 * nu / (SQUARE_DUCT_K * b * b)
-    return pulsatile(r.Q, r.L, max(4, r.L // 4), 1000, 4.0, A, storage=r.storage, u_ref=0.02)
+        c = cavity(r.Q, r.L, 400.0, U=0.05, storage=r.storage)
+    elif r.kind == "duct":
+        c = duct(r.Q, r.L, max(4, r.L // 4), nu=0.1, u_max=0.02, storage=r.storage)
+    else:
+        # pulsatile: T = 1000 steps, eta = 4, amplitude from the quasi-steady
+        # square-duct relation, so that u stays O(0.02)
+        b = r.L / 2.0
+        nu = b * b * (2.0 * np.pi / 1000.0) / 16.0
+        A = 0.02 * nu / (SQUARE_DUCT_K * b * b)
+        c = pulsatile(r.Q, r.L, max(4, r.L // 4), 1000, 4.0, A, storage=r.storage, u_ref=0.02)
+    if c.storage == "f16":
+        c.rounding = 1  # stochastic
+    return c

@@ -18,12 +18,13 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EBUS
 # storage
 LBM_STORAGE_F64, LBM_STORAGE_F32, LBM_STORAGE_F16, LBM_STORAGE_BF16 = range(4)
 # faces
-LBM_PERIODIC, LBM_WALL, LBM_MOVING_WALL, LBM_SYMMETRY = range(4)
+LBM_PERIODIC, LBM_WALL, LBM_MOVING_WALL, LBM_SYMMETRY, LBM_NEQ_VELOCITY, LBM_NEQ_PRESSURE = range(6)
 LBM_XM, LBM_XP, LBM_YM, LBM_YP, LBM_ZM, LBM_ZP = range(6)
 # fields / dtypes
 LBM_FIELD_U, LBM_FIELD_P, LBM_FIELD_POPULATIONS = 1, 2, 4
 LBM_DTYPE_F64, LBM_DTYPE_F32 = 0, 1
 LBM_ROUND_NEAREST, LBM_ROUND_STOCHASTIC = 0, 1
+LBM_RESIDUAL_STEADY, LBM_RESIDUAL_PERIODIC, LBM_RESIDUAL_CAVITY = 0, 1, 2
 
 STORAGE_NAMES = {"f64": LBM_STORAGE_F64, "f32": LBM_STORAGE_F32,
                  "f16": LBM_STORAGE_F16, "bf16": LBM_STORAGE_BF16}
@@ -50,7 +51,9 @@ class lbm_params(ctypes.Structure):
                 ("s_e", ctypes.c_double), ("s_q", ctypes.c_double), ("s_pi", ctypes.c_double),
                 ("s_t", ctypes.c_double), ("force", ctypes.c_double * 3),
                 ("force_period", ctypes.c_double), ("p_ref", ctypes.c_double),
-                ("residual_interval", ctypes.c_int32), ("rounding", ctypes.c_int32)]
+                ("residual_interval", ctypes.c_int32), ("rounding", ctypes.c_int32),
+                ("p_face", ctypes.c_double * 6), ("p_amp", ctypes.c_double * 6),
+                ("p_period", ctypes.c_double)]
 
 
 class lbm_launch(ctypes.Structure):
@@ -83,6 +86,7 @@ SIGNATURES = {
     "lbm_set_geometry": (_I, [_VP, ctypes.POINTER(lbm_geom)]),
     "lbm_set_params": (_I, [_VP, ctypes.POINTER(lbm_params)]),
     "lbm_init_equilibrium": (_I, [_VP, _VP, _VP, _I]),
+    "lbm_set_solid": (_I, [_VP, _VP, _I]),
     "lbm_step": (_I, [_VP, _I64]),
     "lbm_get_step": (_I, [_VP, ctypes.POINTER(_I64)]),
     "lbm_set_step": (_I, [_VP, _I64]),
@@ -90,7 +94,12 @@ SIGNATURES = {
     "lbm_write_populations": (_I, [_VP, _VP, _I]),
     "lbm_reductions": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
     "lbm_read_stats": (_I, [_VP, ctypes.POINTER(lbm_stats)]),
+    "lbm_stats_residual": (_I, [ctypes.POINTER(lbm_stats), ctypes.c_int32, ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_double)]),
+    "lbm_residual": (_I, [_VP, ctypes.c_int32, ctypes.c_int32,
+                          ctypes.POINTER(ctypes.c_double)]),
     "lbm_memory_bytes": (_I, [_VP, ctypes.POINTER(_I64)]),
+    "lbm_device_populations": (_I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I64)]),
     "lbm_set_launch": (_I, [_VP, ctypes.POINTER(lbm_launch)]),
     "lbm_set_overlap": (_I, [_VP, ctypes.c_int32]),
     "lbm_get_launch": (_I, [_VP, ctypes.POINTER(lbm_launch)]),
@@ -112,6 +121,8 @@ SIGNATURES = {
     "lbm_batch_reductions_all": (_I, [_VP, ctypes.POINTER(lbm_stats),
                                       ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
+    "lbm_batch_residual": (_I, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_double)]),
     "lbm_batch_set_launch": (_I, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "lbm_batch_set_schedule": (_I, [_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64]),
     "lbm_batch_info": (_I, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_I64),
@@ -198,7 +209,7 @@ def lbm_set_geometry(h, faces, u_wall=None, edge=None):
 
 def make_params(nu=0.0, s_nu=0.0, s_c=1.0, s_e=1.19, s_q=1.2, s_pi=1.19, s_t=0.98,
                 force=(0.0, 0.0, 0.0), force_period=0.0, p_ref=0.0, residual_interval=0,
-                rounding=LBM_ROUND_NEAREST):
+                rounding=LBM_ROUND_NEAREST, p_face=None, p_amp=None, p_period=0.0):
     p = lbm_params()
     p.nu, p.s_nu, p.s_c, p.s_e, p.s_q, p.s_pi, p.s_t = nu, s_nu, s_c, s_e, s_q, s_pi, s_t
     for k in range(3):
@@ -207,11 +218,24 @@ def make_params(nu=0.0, s_nu=0.0, s_c=1.0, s_e=1.19, s_q=1.2, s_pi=1.19, s_t=0.9
     p.p_ref = float(p_ref)
     p.residual_interval = int(residual_interval)
     p.rounding = int(rounding)
+    for f in range(6):
+        p.p_face[f] = 0.0 if p_face is None else float(p_face[f])
+        p.p_amp[f] = 0.0 if p_amp is None else float(p_amp[f])
+    p.p_period = float(p_period)
     return p
 
 
 def lbm_set_params(h, **kw):
     _check(load().lbm_set_params(h, ctypes.byref(make_params(**kw))))
+
+
+def lbm_set_solid(h, solid, on_device=None):
+    """solid: None, or N bytes (uint8 numpy array or torch tensor, x fastest)."""
+    if solid is not None and not hasattr(solid, "data_ptr"):
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    if on_device is None:
+        on_device = int(getattr(solid, "is_cuda", False))
+    _check(load().lbm_set_solid(h, _ptr(solid), int(on_device)))
 
 
 def lbm_init_equilibrium(h, u=None, p=None, on_device=None):
@@ -272,6 +296,13 @@ def lbm_get_launch(h):
     l = lbm_launch()
     _check(load().lbm_get_launch(h, ctypes.byref(l)))
     return l.astuple()
+
+
+def lbm_device_populations(h):
+    """(device address, bytes) of the handle's population buffer."""
+    p, n = _VP(), _I64()
+    _check(load().lbm_device_populations(h, ctypes.byref(p), ctypes.byref(n)))
+    return p.value, n.value
 
 
 def lbm_autotune(h, trials=8):
@@ -379,21 +410,40 @@ def lbm_batch_set_barrier_test(b, extra_arrivals, spin_limit):
     _check(load().lbm_batch_set_barrier_test(b, int(extra_arrivals), int(spin_limit)))
 
 
-# ---- residual forms over lbm_stats (Eq. sc, Eq. cr, Eq. cavity_creterion) ---
+# ---- convergence criteria (Eq. sc, Eq. cr, Eq. cavity_creterion) --------------
+
+def lbm_stats_residual(s, kind, component=0):
+    r = ctypes.c_double()
+    _check(load().lbm_stats_residual(ctypes.byref(s), int(kind), int(component),
+                                     ctypes.byref(r)))
+    return r.value
+
+
+def lbm_residual(h, kind, component=0):
+    r = ctypes.c_double()
+    _check(load().lbm_residual(h, int(kind), int(component), ctypes.byref(r)))
+    return r.value
+
+
+def lbm_batch_residual(b, slot, kind, component=0):
+    r = ctypes.c_double()
+    _check(load().lbm_batch_residual(b, int(slot), int(kind), int(component), ctypes.byref(r)))
+    return r.value
+
 
 def residual_steady(s, k):
-    """Eq. sc for component k: sum|du| / sum|u(t)| (earlier time level)."""
-    return s.sum_abs_du[k] / s.sum_abs_u_prev[k]
+    """Eq. sc for component k (earlier time level)."""
+    return lbm_stats_residual(s, LBM_RESIDUAL_STEADY, k)
 
 
 def residual_periodic(s, k):
-    """Eq. cr for component k: sum|du| / sum|u(t+T)| (later time level)."""
-    return s.sum_abs_du[k] / s.sum_abs_u[k]
+    """Eq. cr for component k (later time level)."""
+    return lbm_stats_residual(s, LBM_RESIDUAL_PERIODIC, k)
 
 
 def residual_cavity(s):
     """Eq. cavity_creterion: all three components, later time level."""
-    return sum(s.sum_abs_du) / sum(s.sum_abs_u)
+    return lbm_stats_residual(s, LBM_RESIDUAL_CAVITY)
 
 
 # ---- host-array helpers (numpy, pageable memory) ------------------------------

@@ -47,17 +47,11 @@ class Outcome:
     cells: int = 0
     storage: str = ""
     fingerprint: tuple = ()
+    u: Optional[np.ndarray] = None  # final velocity field (Server(keep_fields=True))
 
     @property
     def latency(self) -> float:
         return self.done - self.arrival
-
-
-def residual_of(stats) -> Optional[float]:
-    if stats.prev_step < 0:
-        return None
-    den = sum(stats.sum_abs_u)
-    return float(sum(stats.sum_abs_du) / den) if den > 0 else 0.0
 
 
 def fingerprint(stats) -> tuple:
@@ -94,6 +88,16 @@ class BatchBackend:
     def reductions(self) -> Dict[int, object]:
         return lbm.lbm_batch_reductions_all(self.b, self.capacity)
 
+    def residual(self, slot: int) -> float:
+        """Eq. cavity_creterion of the slot's last reduction (library call)."""
+        return lbm.lbm_batch_residual(self.b, slot, lbm.LBM_RESIDUAL_CAVITY)
+
+    def read_u(self, slot: int, case: inputs.Case) -> np.ndarray:
+        import torch
+        out = torch.empty(3 * case.cells, dtype=torch.float64, device="cuda")
+        lbm.lbm_batch_read_fields(self.b, slot, lbm.LBM_FIELD_U, out)
+        return out.cpu().numpy().reshape(3, case.nz, case.ny, case.nx)
+
     def close(self) -> None:
         lbm.lbm_batch_destroy(self.b)
 
@@ -111,7 +115,7 @@ class SequentialBackend:
         if self.h is not None:
             raise Busy()
         h = lbm.lbm_create(case.Q, case.nx, case.ny, case.nz, case.storage, self.stream)
-        lbm.lbm_set_geometry(h, case.faces, case.u_wall)
+        lbm.lbm_set_geometry(h, case.faces, case.u_wall, case.edge)
         lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period,
                            rounding=case.rounding)
         lbm.lbm_set_launch(h, *self.launch)
@@ -130,6 +134,12 @@ class SequentialBackend:
     def reductions(self) -> Dict[int, object]:
         return {} if self.h is None else {0: lbm.lbm_reductions(self.h)}
 
+    def residual(self, slot: int) -> float:
+        return lbm.lbm_residual(self.h, lbm.LBM_RESIDUAL_CAVITY)
+
+    def read_u(self, slot: int, case: inputs.Case) -> np.ndarray:
+        return lbm.read_u(self.h, case.nx, case.ny, case.nz)
+
     def close(self) -> None:
         if self.h is not None:
             lbm.lbm_destroy(self.h)
@@ -141,8 +151,10 @@ class Server:
                  max_active_cells: int = 0,
                  case_of: Callable = inputs.request_case,
                  clock: Callable[[], float] = time.perf_counter,
-                 sleep: Callable[[float], None] = time.sleep):
+                 sleep: Callable[[float], None] = time.sleep,
+                 keep_fields: bool = False):
         self.backend = backend
+        self.keep_fields = keep_fields
         self.check_every = check_every
         self.tol = tol
         self.max_active_cells = max_active_cells
@@ -187,11 +199,15 @@ class Server:
                 o = out[r.rid]
                 o.steps += self.check_every
                 st = stats[slot]
-                res = residual_of(st)
+                # Eq. cavity_creterion over the last interval; none before the
+                # second check of a request (no earlier snapshot yet)
+                res = self.backend.residual(slot) if st.prev_step >= 0 else None
                 o.residual = res
                 if st.nonfinite or (res is not None and res <= self.tol) or o.steps >= r.max_steps:
                     o.done = self.clock() - t0
                     o.fingerprint = fingerprint(st)
+                    if self.keep_fields:
+                        o.u = self.backend.read_u(slot, case)
                     self.backend.remove(slot)
                     del active[slot]
         return out

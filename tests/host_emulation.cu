@@ -6,10 +6,12 @@
 #include <cmath>
 
 #include "../paper_1503_03337_gb300/csrc/lbm_kernels.cuh"
+#include "../paper_1503_03337_gb300/csrc/lbm_neq.cuh"
 
 using namespace lbm;
 
 static int g_sr = 0;
+static const uint32_t* g_solid = nullptr;  // solid-link words (Domain::solid) or null
 
 template <int Q, typename S, typename R>
 static void step_typed(void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
@@ -20,6 +22,7 @@ static void step_typed(void* f, int nx, int ny, int nz, const int* per, int movi
   d.N = (int64_t)nx * ny * nz;
   d.moving = moving;
   d.sym = sym;
+  d.solid = g_solid;
   for (int face = 0; face < 6; ++face) {
     d.edge_axis[face] = eaxis ? eaxis[face] : 0;
     d.edge_scale[face][0] = R(escale ? escale[2 * face] : 1.0);
@@ -67,6 +70,7 @@ static void canonical_typed(void* f, int nx, int ny, int nz, const int* per, int
   fill_offsets<Q>(d);
   d.moving = moving;
   d.sym = sym;
+  d.solid = g_solid;
   for (int face = 0; face < 6; ++face) {
     d.edge_axis[face] = eaxis ? eaxis[face] : 0;
     d.edge_scale[face][0] = R(escale ? escale[2 * face] : 1.0);
@@ -106,8 +110,65 @@ static int canon_any(int Q, void* f, int nx, int ny, int nz, const int* per, int
   return 0;
 }
 
+// The extrapolation pass over every boundary node, on the populations of
+// step n (FP64 storage): uw holds the velocity of every velocity face, pb the
+// pressure of every pressure face at time level n, F the force at n.
+template <int Q, bool ODD>
+static void neq_typed(void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
+                      const double* uw, int vel, int pre, const double* pb, const double* F) {
+  Domain<double> d{};
+  d.f = f;
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.N = (int64_t)nx * ny * nz;
+  d.moving = moving;
+  d.sym = sym;
+  for (int k = 0; k < 3; ++k) d.per[k] = per[k];
+  for (int face = 0; face < 6; ++face) {
+    d.edge_axis[face] = 0;
+    d.edge_scale[face][0] = d.edge_scale[face][1] = 1.0;
+    for (int k = 0; k < 3; ++k) d.uw[face][k] = uw[3 * face + k];
+  }
+  for (int k = 0; k < 3; ++k) d.F[k] = F[k];
+  fill_offsets<Q>(d);
+  NeqArgs a{};
+  a.vel = vel;
+  a.pre = pre;
+  const int plane[3] = {ny * nz, nx * nz, nx * ny};
+  for (int face = 0; face < 6; ++face) {
+    a.off[face + 1] = a.off[face] + ((((vel | pre) >> face) & 1) ? plane[face >> 1] : 0);
+    a.pb[face] = pb[face];
+  }
+  for (int t = 0; t < a.off[6]; ++t) neq_node<Q, double, double, ODD>(d, a, t);
+}
+
 extern "C" {
 void emu_set_stochastic(int on) { g_sr = on; }
+
+// Solid-link words of a byte mask (the device builder's per-cell code).
+int emu_solid_links(int Q, int nx, int ny, int nz, int per, int sym, const uint8_t* bytes,
+                    uint32_t* out) {
+  const int64_t N = (int64_t)nx * ny * nz;
+  for (int64_t i = 0; i < N; ++i)
+    out[i] = Q == 14 ? solid_link_bits<14>(nx, ny, nz, per, sym, bytes, i)
+                     : solid_link_bits<18>(nx, ny, nz, per, sym, bytes, i);
+  return 0;
+}
+void emu_set_solid(const uint32_t* links) { g_solid = links; }
+
+int emu_neq(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
+            const double* uw, int vel, int pre, const double* pb, const double* F, int64_t n) {
+  const bool odd = n & 1;
+  if (Q == 14) {
+    if (odd) neq_typed<14, true>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
+    else neq_typed<14, false>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
+  } else if (Q == 18) {
+    if (odd) neq_typed<18, true>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
+    else neq_typed<18, false>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
+  } else {
+    return -1;
+  }
+  return 0;
+}
 
 // storage: 0 double, 1 float, 2 half, 3 bfloat16
 int emu_step(int Q, int storage, void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,

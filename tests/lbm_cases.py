@@ -8,9 +8,10 @@ from paper_1503_03337_gb300 import lbm
 
 def oracle_setup(case):
     g = oracle.make_grid(case.Q, case.nx, case.ny, case.nz, case.faces, case.u_wall,
-                         edge=case.edge)
-    r = oracle.rates(case.Q, case.s_nu)
-    prm = oracle.make_params(r, force=case.force, period=case.period)
+                         edge=case.edge, solid=case.solid)
+    r = oracle.rates(case.Q, oracle.s_nu_of(case.nu))
+    prm = oracle.make_params(r, force=case.force, period=case.period, p_face=case.p_face,
+                             p_amp=case.p_amp, p_period=case.p_period)
     return g, prm
 
 
@@ -30,7 +31,11 @@ def gpu_open(case, stream=None, residual_interval=0, launch=None):
     h = lbm.lbm_create(case.Q, case.nx, case.ny, case.nz, case.storage, stream)
     lbm.lbm_set_geometry(h, case.faces, case.u_wall, case.edge)
     lbm.lbm_set_params(h, nu=case.nu, force=case.force, force_period=case.period,
-                       residual_interval=residual_interval, rounding=case.rounding)
+                       residual_interval=residual_interval, rounding=case.rounding,
+                       p_face=case.p_face, p_amp=case.p_amp, p_period=case.p_period,
+                       p_ref=case.p_ref)
+    if case.solid is not None:
+        lbm.lbm_set_solid(h, case.solid)
     if launch is not None:
         lbm.lbm_set_launch(h, *launch)
     return h

@@ -10,7 +10,7 @@ import pytest
 from oracle import analytic as an
 from paper_1503_03337_gb300 import inputs, lbm
 
-from lbm_cases import gpu_open, oracle_run
+from lbm_cases import gpu_open, gpu_run, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -88,7 +88,7 @@ def test_c3_pulsatile_gre(storage):
     for st in sorted({"f32", storage}):
         c = inputs.pulsatile(18, N, nz, T, eta, A, storage=st)
         c.rounding = case.rounding if st == storage else lbm.LBM_ROUND_NEAREST
-        h = gpu_open(c)
+        h = gpu_open(c, launch=(64, 1, 2) if st != "f32" else None)
         try:
             lbm.lbm_init_equilibrium(h, u0, None, 0)
             lbm.lbm_step(h, 2 * T)
@@ -111,3 +111,78 @@ def test_c3_pulsatile_gre(storage):
         dev = max(float(np.max(np.abs(a - b))) for a, b in zip(us, fields["f32"][1]))
         print("max |u_%s - u_f32| / U = %.3e" % (storage, dev / U))
         assert dev <= PULSATILE_DEV[storage] * U, dev / U
+
+
+# The ends of the pulsatile grid of the 64 x 64 x 8 channel: the longest
+# period with the largest Womersley number (thin Stokes layers, tau = 0.521,
+# per-step changes of a few FP16 ulps) and the shortest period with the
+# smallest (tau = 10.15, the largest wall slip of halfway bounce-back).
+HARD_END = [(4000, 15.0), (500, 2.0)]
+
+
+def pulsatile_setup(Q, T, eta, storage, N=64, nz=8, U=0.03):
+    b = N / 2.0
+    omega = 2 * np.pi / T
+    nu = b * b * omega / eta ** 2
+    xs = an.lattice_coords(N)
+    Y, X = np.meshgrid(xs, xs, indexing="ij")
+    unit = an.pulsatile_amplitude(X, Y, b, b, nu, omega, 1.0)
+    A = U / float(np.max(np.abs(unit)))  # max over (t, y, z) of |u| = U
+    case = inputs.pulsatile(Q, N, nz, T, eta, A, storage=storage, u_ref=U)
+    Uc = -A * unit  # G = -A (F = -dp/dx)
+    u0 = np.zeros((3, nz, N, N))
+    u0[2] = np.real(Uc)[None]
+    case.init_u = u0
+    return case, Uc, omega
+
+
+@pytest.mark.parametrize("T,eta", HARD_END)
+@pytest.mark.parametrize("Q", (14, 18))
+def test_pulsatile_hard_end_parity(Q, T, eta):
+    """One period from the analytic field at t = 0: FP32 storage within
+    1e-5 U and FP16 storage (stochastic rounding, two cells per thread on
+    even steps, the benchmarked launch) within 1e-3 U of the oracle, max
+    over all nodes and components."""
+    case, _, _ = pulsatile_setup(Q, T, eta, "f64")
+    o = oracle_run(case, T)
+    for storage, launch, bound in (("f32", None, 1e-5), ("f16", (64, 1, 2), 1e-3)):
+        c, _, _ = pulsatile_setup(Q, T, eta, storage)
+        if storage == "f16":
+            c.rounding = lbm.LBM_ROUND_STOCHASTIC
+        g = gpu_run(c, T, launch=launch)
+        err = float(np.max(np.abs(g["u"] - o["u"])))
+        print("Q%d T=%d eta=%g %s: max|u - u_oracle| / U = %.3e" % (Q, T, eta, storage, err / 0.03))
+        assert err <= bound * 0.03, (storage, err / 0.03)
+
+
+@pytest.mark.parametrize("T,eta", HARD_END)
+def test_pulsatile_hard_end_gre(T, eta):
+    """Five periods from the analytic field (D3Q18): GRE_u (Eq. ed) against
+    Eq. wa at the quarter periods of the fifth, FP32 and FP16 (stochastic
+    rounding, pair launch).  The two storages give the same GRE_u to 1e-3
+    of its value plus 1e-4."""
+    out = {}
+    for storage, launch in (("f32", None), ("f16", (64, 1, 2))):
+        c, Uc, omega = pulsatile_setup(18, T, eta, storage)
+        if storage == "f16":
+            c.rounding = lbm.LBM_ROUND_STOCHASTIC
+        h = gpu_open(c, launch=launch)
+        try:
+            lbm.lbm_init_equilibrium(h, np.ascontiguousarray(c.init_u), None, 0)
+            lbm.lbm_step(h, 4 * T)
+            errs = []
+            for q in range(4):
+                n = lbm.lbm_get_step(h)
+                u = lbm.read_u(h, c.nx, c.ny, c.nz)
+                ua = np.zeros_like(u)
+                ua[2] = np.real(Uc * np.exp(1j * omega * n))[None]
+                errs.append(an.gre_u(u, ua))
+                lbm.lbm_step(h, T // 4)
+        finally:
+            lbm.lbm_destroy(h)
+        out[storage] = errs
+        print("T=%d eta=%g %s GRE_u at kT/4 of period 5:" % (T, eta, storage),
+              ["%.3e" % e for e in errs])
+    for a, b in zip(out["f16"], out["f32"]):
+        assert abs(a - b) <= 1e-3 * b + 1e-4, (a, b)
+    assert max(out["f32"]) < 0.5

@@ -157,36 +157,56 @@ def test_fp32_duct(Q):
     assert err <= 1e-5 * case.u_ref, err
 
 
+@pytest.mark.parametrize("launch", ((64, 1, 2), (64, 1, 1)))
 @pytest.mark.parametrize("Q", (14, 18))
-def test_fp16_pulsatile_stochastic_within_1e3(Q):
-    """FP16 storage with stochastic rounding on the oscillating-force channel:
+def test_fp16_pulsatile_stochastic_within_1e3(Q, launch):
+    """FP16 storage with stochastic rounding on the oscillating-force channel,
+    two cells per thread on even steps (the benchmarked launch) and one:
     max |u - u_oracle| <= 1e-3 U_max after 1000 steps (two periods)."""
     case = inputs.pulsatile(Q, 32, 4, 500, 4.0, 3e-4, storage="f16")
     case.rounding = lbm.LBM_ROUND_STOCHASTIC
-    g, o = both(case, 1000)
+    g, o = gpu_run(case, 1000, launch=launch), oracle_run(case, 1000)
     U = np.max(np.abs(o["u"]))
     err = np.max(np.abs(g["u"] - o["u"]))
     assert err <= 1e-3 * U, err / U
 
 
-# Measured error of 16-bit storage with round-to-nearest on the lid-driven
-# cavity after 1000 steps (max over cells, and root-mean-square, both over
-# U_max).  The max-norm error sits at the singular lid corners and moves with
-# every change of FP32 rounding in the collision (2e-3 .. 5e-3 U for Q14,
-# ~1e-3 U for Q18); the RMS error is ~1e-4 U.  BF16 (8-bit mantissa) is not
-# within 1e-3 in max norm.
-REDUCED = [("f16", 1e-2, 1e-3), ("bf16", 6e-2, 3e-3)]
+# 16-bit storage on the lid-driven cavity.  The largest errors sit in the few
+# cells where the lid meets the downstream side wall: the flow there amplifies
+# any storage rounding by about 10^3 (FP32 storage shows the same
+# amplification, of its own unit roundoff, and a 16-bit fixed-point format
+# with a five times finer grid than FP16 at these magnitudes still errs by
+# 3e-3 U there).  So the max-norm error of a storage format is its unit
+# roundoff times the amplification that FP32 measures on the same case: the
+# test bounds the 16-bit max-norm error by RATIO * (u_32 / u_16 roundoff
+# ratio) * the FP32 max-norm error, and the root-mean-square error over the
+# cavity by RMS_BOUND (measured: FP16 4e-5 .. 1.4e-4 U, BF16 4e-4 .. 1.4e-3 U).
+ROUNDOFF = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+RATIO = 3.0
+RMS_BOUND = {"f16": 3e-4, "bf16": 3e-3}
 
 
-@pytest.mark.parametrize("storage,max_bound,rms_bound", REDUCED)
+@pytest.mark.parametrize("storage,rounding,launch", [
+    ("f16", "nearest", (64, 1, 2)), ("f16", "stochastic", (64, 1, 2)),
+    ("f16", "stochastic", (64, 1, 1)), ("bf16", "stochastic", (64, 1, 2)),
+    ("bf16", "nearest", (64, 1, 1))])
 @pytest.mark.parametrize("Q", (14, 18))
-def test_reduced_precision_cavity(Q, storage, max_bound, rms_bound):
-    case = inputs.cavity(Q, 32, 400.0, storage=storage)
-    g, o = both(case, 1000)
+def test_reduced_precision_cavity(Q, storage, rounding, launch):
+    case = inputs.cavity(Q, 32, 400.0, storage="f64")
+    o = oracle_run(case, 1000)
     U = np.max(np.abs(o["u"]))
-    d = g["u"] - o["u"]
-    assert np.max(np.abs(d)) <= max_bound * U, np.max(np.abs(d)) / U
-    assert np.sqrt(np.mean(d ** 2)) <= rms_bound * U, np.sqrt(np.mean(d ** 2)) / U
+    e32 = float(np.max(np.abs(gpu_run(inputs.cavity(Q, 32, 400.0, storage="f32"), 1000)["u"]
+                              - o["u"])))
+    c = inputs.cavity(Q, 32, 400.0, storage=storage)
+    c.rounding = lbm.LBM_ROUND_STOCHASTIC if rounding == "stochastic" else lbm.LBM_ROUND_NEAREST
+    d = gpu_run(c, 1000, launch=launch)["u"] - o["u"]
+    emax, erms = float(np.max(np.abs(d))), float(np.sqrt(np.mean(d ** 2)))
+    bound = RATIO * ROUNDOFF[storage] / 2.0 ** -24 * e32
+    print("Q%d %s %s %s: max %.3e U (bound %.3e U), rms %.3e U; FP32 max %.3e U"
+          % (Q, storage, rounding, launch, emax / U, bound / U, erms / U, e32 / U))
+    assert e32 <= 1e-5 * U
+    assert emax <= bound, (emax / U, bound / U)
+    assert erms <= RMS_BOUND[storage] * U, erms / U
 
 
 @pytest.mark.parametrize("Q", (14, 18))
@@ -196,7 +216,7 @@ def test_fp64_lbgk_special_case(Q):
     matches the oracle with the same rates, FP64, moving lid, 300 steps."""
     import oracle
     case = inputs.cavity(Q, 20, 100.0, storage="f64")
-    s = 1.0 / (3.0 * case.nu + 0.5)
+    s = oracle.s_nu_of(case.nu)
     g_or = oracle.make_grid(Q, case.nx, case.ny, case.nz, case.faces, case.u_wall)
     prm = oracle.make_params(oracle.rates(Q, s, sc=s, se=s, sq=s, st=s, spi=s))
     f = oracle.run(g_or, prm, oracle.init_equilibrium(g_or), 0, 300)

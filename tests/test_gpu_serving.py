@@ -26,7 +26,7 @@ def trace():
 
 
 def serve(torch, backend):
-    srv = Server(backend, check_every=100, tol=1e-8, chunk=25)
+    srv = Server(backend, check_every=100, tol=1e-8, chunk=25, keep_fields=True)
     t = trace()
     out = srv.run(t)
     torch.cuda.synchronize()
@@ -43,6 +43,8 @@ def test_results_same_in_mix_and_alone(torch):
     for rid in mixed:
         assert mixed[rid].steps == alone[rid].steps
         assert mixed[rid].fingerprint == alone[rid].fingerprint, rid
+        # the whole velocity field, bit for bit
+        assert mixed[rid].u is not None and np.array_equal(mixed[rid].u, alone[rid].u), rid
     s = summarize(mixed, max(o.done for o in mixed.values()))
     assert s["glups"] > 0 and s["p99_s"] >= s["p50_s"]
 
@@ -53,8 +55,12 @@ def test_sequential_backend_matches_for_steady_drives(torch):
     stream = torch.cuda.Stream()
     keep = [r for r in trace() if r.kind != "pulsatile"]
     with torch.cuda.stream(stream):
-        a = Server(BatchBackend(16, 0, stream.cuda_stream), check_every=100, chunk=25).run(keep)
-        b = Server(SequentialBackend(stream.cuda_stream), check_every=100, chunk=25).run(keep)
+        a = Server(BatchBackend(16, 0, stream.cuda_stream), check_every=100, chunk=25,
+                   keep_fields=True).run(keep)
+        b = Server(SequentialBackend(stream.cuda_stream), check_every=100, chunk=25,
+                   keep_fields=True).run(keep)
     torch.cuda.synchronize()
     for r in keep:
         assert a[r.rid].fingerprint == b[r.rid].fingerprint
+        assert np.array_equal(a[r.rid].u, b[r.rid].u), r.rid
+        assert a[r.rid].residual == b[r.rid].residual

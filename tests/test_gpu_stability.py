@@ -10,6 +10,7 @@ the half cavity of Sec. 4.3 at the paper's grid: MRT stable, LBGK not."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1503_03337_gb300 import inputs, lbm
 
 from lbm_cases import gpu_open
@@ -79,7 +80,7 @@ def test_half_cavity_re3200_mrt_stable_lbgk_not():
     case = inputs.half_cavity(18, 97, 3200.0, U=0.1, storage="f32", ku_lid=True)
     assert (case.nx, case.ny, case.nz) == (97, 97, 49)
     assert run_until_unstable(case, 50000) is None
-    s = 1.0 / (3.0 * case.nu + 0.5)
+    s = oracle.s_nu_of(case.nu)
     lbgk = dict(s_c=s, s_e=s, s_q=s, s_pi=s, s_t=s)
     div = run_until_unstable(case, 50000, rates=lbgk)
     assert div is not None and div <= 5000, div

@@ -83,6 +83,64 @@ def test_reductions_match_fields(Q):
     assert abs(r - np.abs(ub[2] - ua[2]).sum() / np.abs(ub[2]).sum()) < 1e-12
 
 
+@pytest.mark.parametrize("Q", (14, 18))
+def test_residual_criteria_match_oracle_fields(Q):
+    """lbm_residual (Eq. sc, Eq. cr, Eq. cavity_creterion) on the GPU's FP64
+    reductions against the oracle's residual forms of the oracle's velocity
+    fields at the same two steps: 1e-12 relative.  The batch form
+    (lbm_batch_residual) gives the same numbers for FP32 storage against the
+    single-domain handle."""
+    from oracle import analytic
+    case = inputs.cavity(Q, 12, 100.0, storage="f64")
+    h = gpu_open(case)
+    try:
+        lbm.lbm_init_equilibrium(h)
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_residual(h, lbm.LBM_RESIDUAL_CAVITY)  # no reduction yet
+        lbm.lbm_step(h, 300)
+        lbm.lbm_reductions(h)
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_residual(h, lbm.LBM_RESIDUAL_CAVITY)  # no earlier snapshot
+        lbm.lbm_step(h, 100)
+        lbm.lbm_reductions(h)
+        got = {(kind, k): lbm.lbm_residual(h, kind, k)
+               for kind in (lbm.LBM_RESIDUAL_STEADY, lbm.LBM_RESIDUAL_PERIODIC) for k in range(3)}
+        got_cav = lbm.lbm_residual(h, lbm.LBM_RESIDUAL_CAVITY)
+    finally:
+        lbm.lbm_destroy(h)
+    ua, ub = oracle_run(case, 300)["u"], oracle_run(case, 400)["u"]
+    for k in range(3):
+        assert got[(lbm.LBM_RESIDUAL_STEADY, k)] == pytest.approx(
+            analytic.residual_steady(ub[k], ua[k]), rel=1e-12, abs=0)
+        assert got[(lbm.LBM_RESIDUAL_PERIODIC, k)] == pytest.approx(
+            analytic.residual_periodic(ub[k], ua[k]), rel=1e-12, abs=0)
+    assert got_cav == pytest.approx(analytic.residual_cavity(ub, ua), rel=1e-12, abs=0)
+
+    import torch
+    c32 = inputs.cavity(Q, 12, 100.0, storage="f32")
+    h = gpu_open(c32)
+    b = lbm.lbm_batch_create(2, 0, torch.cuda.current_stream().cuda_stream)
+    try:
+        slot = lbm.lbm_batch_add(b, Q, c32.nx, c32.ny, c32.nz, "f32", c32.faces, c32.u_wall,
+                                 nu=c32.nu)
+        lbm.lbm_batch_init_equilibrium(b, slot)
+        lbm.lbm_init_equilibrium(h)
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_batch_residual(b, slot, lbm.LBM_RESIDUAL_CAVITY)
+        for n in (200, 50):
+            lbm.lbm_batch_step(b, n, 10)
+            lbm.lbm_batch_reductions(b, slot)
+            lbm.lbm_step(h, n)
+            lbm.lbm_reductions(h)
+        assert lbm.lbm_batch_residual(b, slot, lbm.LBM_RESIDUAL_CAVITY) == \
+            lbm.lbm_residual(h, lbm.LBM_RESIDUAL_CAVITY)
+        assert lbm.lbm_batch_residual(b, slot, lbm.LBM_RESIDUAL_STEADY, 0) == \
+            lbm.lbm_residual(h, lbm.LBM_RESIDUAL_STEADY, 0)
+    finally:
+        lbm.lbm_batch_destroy(b)
+        lbm.lbm_destroy(h)
+
+
 def test_residual_cadence_in_step():
     case = inputs.cavity(18, 16, 100.0, storage="f32")
     h = gpu_open(case, residual_interval=50)

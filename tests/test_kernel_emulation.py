@@ -23,7 +23,7 @@ def emu():
     os.makedirs(out_dir, exist_ok=True)
     lib = os.path.join(out_dir, "libhost_emulation.so")
     deps = [SRC] + [os.path.join(ROOT, "paper_1503_03337_gb300", "csrc", f)
-                    for f in ("lbm_model.cuh", "lbm_kernels.cuh")]
+                    for f in ("lbm_model.cuh", "lbm_kernels.cuh", "lbm_neq.cuh")]
     if not os.path.exists(lib) or os.path.getmtime(lib) < max(map(os.path.getmtime, deps)):
         tmp = lib + ".tmp%d" % os.getpid()
         subprocess.run([pkg_build.nvcc(), "-std=c++20", "-O2", "--expt-relaxed-constexpr",
@@ -42,6 +42,12 @@ def emu():
                                         ctypes.c_int, ip, dp, dp, dp, ctypes.c_int64,
                                         ctypes.c_int]
     L.emu_collide.argtypes = [ctypes.c_int, dp, dp, dp]
+    L.emu_solid_links.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, vp, vp]
+    L.emu_set_solid.argtypes = [vp]
+    L.emu_neq.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip,
+                          ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp,
+                          ctypes.c_int64]
     return L
 
 
@@ -76,7 +82,7 @@ class EmuDomain:
             self.escale[face] = (first, last)
         self.uw = np.ascontiguousarray(
             np.where(np.array(case.faces)[:, None] == inputs.MOVING_WALL, case.u_wall, 0.0))
-        s = oracle.rates(case.Q, case.s_nu)
+        s = oracle.rates(case.Q, oracle.s_nu_of(case.nu))
         self.s = np.array([s.sc, s.se, s.sq, s.snu, s.spi, s.st])
         self.A = np.zeros((case.Q, case.nz, case.ny, case.nx))
         self.n = 0
@@ -147,7 +153,7 @@ def test_step_matches_oracle(emu, Q, name, shape, faces, edge):
                        nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64",
                        edge=edge)
     g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw, edge=edge)
-    prm = oracle.make_params(oracle.rates(Q, case.s_nu), force=case.force, period=case.period)
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(case.nu)), force=case.force, period=case.period)
     u0, p0 = inputs.random_state(case, seed=2)
     f0 = oracle.init_equilibrium(g, u0, p0)
     d = EmuDomain(emu, case)
@@ -189,7 +195,7 @@ def test_reduced_storage_step_matches_oracle(emu, Q, name, shape, faces, edge, s
                        nu=0.05, force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64",
                        edge=edge)
     g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw, edge=edge)
-    prm = oracle.make_params(oracle.rates(Q, case.s_nu), force=case.force, period=case.period)
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(case.nu)), force=case.force, period=case.period)
     u0, p0 = inputs.random_state(case, seed=2)
     f0 = oracle.init_equilibrium(g, u0, p0)
     d = EmuDomain(emu, case)
@@ -207,3 +213,100 @@ def test_reduced_storage_step_matches_oracle(emu, Q, name, shape, faces, edge, s
                                      7, 0) == 0
     ref = oracle.run(g, prm, f0, 0, 7, nthreads=1)
     assert np.max(np.abs(out - ref)) <= tol * np.max(np.abs(ref))
+
+
+NEQ = [
+    # (name, shape, faces): 4 = extrapolation velocity face, 5 = pressure face
+    ("duct", (9, 5, 6), (5, 5, 4, 4, 4, 4)),
+    ("cavity", (7, 8, 6), (4, 4, 4, 4, 4, 4)),
+    ("mixed", (6, 7, 5), (5, 5, 1, 2, 0, 0)),
+    ("sym", (5, 6, 7), (0, 0, 4, 4, 1, 3)),
+    ("open", (8, 3, 5), (5, 4, 0, 0, 4, 2)),
+    ("wide_x", (70, 4, 5), (5, 5, 4, 2, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("oscillate", (False, True))
+@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("name,shape,faces", NEQ)
+def test_extrapolation_boundaries_match_oracle(emu, Q, name, shape, faces, oscillate):
+    """The fused step followed by the kernel's extrapolation pass (the
+    per-node code of the boundary kernel, run node after node), FP64,
+    random state, wall velocities and face pressures: within 1e-12 of the
+    oracle after 1, 2, 7 and 30 steps."""
+    rng = np.random.default_rng(len(name) + 10 * Q)
+    uw = rng.normal(size=(6, 3)) * 0.02
+    pf = rng.normal(size=6) * 0.01
+    pa = rng.normal(size=6) * 0.005 if oscillate else np.zeros(6)
+    period = 17.0 if oscillate else 0.0
+    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw, nu=0.05,
+                       force=(1e-4, -5e-5, 2e-5), period=13.0, storage="f64")
+    g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw)
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(case.nu)), force=case.force,
+                             period=case.period, p_face=pf, p_amp=pa, p_period=period)
+    u0, p0 = inputs.random_state(case, seed=3)
+    f = oracle.init_equilibrium(g, u0, p0)
+    d = EmuDomain(emu, case)
+    d.put(f, 0)
+    vel = sum(1 << k for k in range(6) if faces[k] == 4)
+    pre = sum(1 << k for k in range(6) if faces[k] == 5)
+    uw_all = np.ascontiguousarray(np.where((np.array(faces) == 4)[:, None] |
+                                           (np.array(faces) == 2)[:, None], uw, 0.0))
+    for k in (1, 1, 5, 23):
+        for _ in range(k):
+            d.step(1)
+            n = d.n
+            amp = np.cos(2 * np.pi * n / case.period)
+            F = np.array(case.force) * amp
+            pb = pf + pa * (np.cos(2 * np.pi * n / period) if period > 0 else 0.0)
+            assert emu.emu_neq(Q, d.A.ctypes.data, *shape, d.per.ctypes.data_as(
+                ctypes.POINTER(ctypes.c_int)), d.moving, d.sym, _d(uw_all), vel, pre,
+                _d(np.ascontiguousarray(pb)), _d(F), n) == 0
+        f = oracle.run(g, prm, f, d.n - k, k, nthreads=1)
+        got = d.get()
+        assert np.max(np.abs(got - f)) <= 1e-12 * np.max(np.abs(f)), (d.n,)
+
+
+SOLID = [
+    # (name, shape, faces, solid fraction): random solid nodes with every
+    # face kind that combines with them, odd and even layouts
+    ("periodic", (9, 7, 6), (0, 0, 0, 0, 0, 0), 0.3),
+    ("walls", (8, 6, 7), (1, 2, 1, 1, 0, 0), 0.2),
+    ("sym", (7, 6, 5), (3, 1, 0, 0, 2, 3), 0.25),
+    ("wide_x", (70, 4, 4), (1, 1, 2, 1, 0, 0), 0.15),
+    ("dense", (6, 6, 6), (0, 0, 1, 1, 3, 3), 0.6),
+]
+
+
+@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("name,shape,faces,frac", SOLID)
+def test_solid_nodes_match_oracle(emu, Q, name, shape, faces, frac):
+    """The kernel's per-cell code with a random solid-node mask (link words
+    built by the device builder's per-cell code) against the oracle's solid
+    mask: FP64, random state, wall velocities and force, 1, 2, 7 and 30
+    steps, fluid and solid nodes alike (solid nodes read zero)."""
+    rng = np.random.default_rng(len(name) + Q)
+    solid = (rng.random(shape[::-1]) < frac).astype(np.uint8)
+    uw = rng.normal(size=(6, 3)) * 0.03
+    case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw, nu=0.05,
+                       force=(1e-4, -2e-4, 5e-5), period=17.0, storage="f64")
+    g = oracle.make_grid(Q, *shape, faces=faces, u_wall=uw, solid=solid)
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(case.nu)), force=case.force,
+                             period=case.period)
+    u0, p0 = inputs.random_state(case, seed=2)
+    f = oracle.init_equilibrium(g, u0, p0)
+    d = EmuDomain(emu, case)
+    links = np.zeros(shape[::-1], dtype=np.uint32)
+    per = int(d.per[0]) | (int(d.per[1]) << 1) | (int(d.per[2]) << 2)
+    assert emu.emu_solid_links(Q, *shape, per, d.sym, solid.ctypes.data, links.ctypes.data) == 0
+    emu.emu_set_solid(links.ctypes.data)
+    try:
+        d.put(f, 0)
+        for k in (1, 1, 5, 23):
+            d.step(k)
+            f = oracle.run(g, prm, f, d.n - k, k, nthreads=1)
+            got = d.get()
+            got[:, solid.astype(bool)] = 0.0  # the read path reports solids as zero
+            assert np.max(np.abs(got - f)) <= 1e-12 * np.max(np.abs(f)), (d.n,)
+    finally:
+        emu.emu_set_solid(None)

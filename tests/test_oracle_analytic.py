@@ -111,7 +111,7 @@ def duct_run(Q, N, nz, nu, umax, steps):
     a = N / 2.0
     G = umax * nu / (an.duct_umax(1, 1, 1, 1) * a * a)
     g = oracle.make_grid(Q, N, N, nz, faces=(W, W, W, W, P, P))
-    prm = oracle.make_params(oracle.rates(Q, 1.0 / (3 * nu + 0.5)), force=(0, 0, G))
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(nu)), force=(0, 0, G))
     f = oracle.run(g, prm, oracle.init_equilibrium(g), 0, steps)
     u, _ = oracle.macroscopic(g, prm, steps, f)
     xs = an.lattice_coords(N)
@@ -148,7 +148,7 @@ def test_pulsatile_gre(Q):
     Y, X = np.meshgrid(xs, xs, indexing="ij")
     Uc = an.pulsatile_amplitude(X, Y, b, b, nu, omega, G)
     g = oracle.make_grid(Q, N, N, 2, faces=(W, W, W, W, P, P))
-    prm = oracle.make_params(oracle.rates(Q, 1.0 / (3 * nu + 0.5)), force=(0, 0, A), period=T)
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(nu)), force=(0, 0, A), period=T)
     u0 = np.zeros((3, 2, N, N))
     u0[2] = np.real(Uc)[None]
     f = oracle.init_equilibrium(g, u0, None)

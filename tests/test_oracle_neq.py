@@ -5,7 +5,9 @@ Pins: the boundary nodes carry exactly the prescribed velocity (velocity
 faces) or pressure (pressure faces); an equilibrium at rest with equal
 pressures is a fixed point; and the whole scheme reproduces the paper's
 Table 1 (GRE_u of the pressure-driven Poiseuille duct at dx = 1/8 and 1/16
-for 1/tau = 0.8, 1.0, 1.3) to the printed digits."""
+for 1/tau = 0.8, 1.0, 1.3) to the printed digits, and Table 3's iD3Q14
+GRE_u of the pressure-driven pulsatile channel at dp = 0.001 to its two
+printed digits."""
 import json
 import os
 
@@ -104,3 +106,45 @@ def test_table1_reproduced(inv_tau, k):
     _, _, _, _, u = steady(case)
     gre = duct_gre(case, u)
     assert abs(gre - printed) <= half_unit_of_last_digit(printed), (gre, printed)
+
+
+def pulsatile_gre(case, u, n, delta_p, period=100.0, length=2.0, a=0.5):
+    """Eq. ed against Eq. wa at t = n dt on the node grid; on the wall nodes
+    the exact solution is the no-slip value 0 (the series only tends to it
+    there, and at the duct's edges its partial sums stay at the core value)."""
+    dx = 2 * a / (case.ny - 1)
+    dt = dx / case.c
+    nu = case.nu * dx * dx / dt
+    ys = -a + dx * np.arange(case.ny)
+    Z, Y = np.meshgrid(ys, ys, indexing="ij")
+    omega = 2 * np.pi / period
+    ua = an.pulsatile_velocity(Y, Z, n * dt, a, a, nu, omega, delta_p / length) / case.c
+    ua[(np.abs(np.abs(Y) - a) < 1e-12) | (np.abs(np.abs(Z) - a) < 1e-12)] = 0.0
+    u_ana = np.zeros_like(u)
+    u_ana[0] = ua[:, :, None]
+    return an.gre_u(u, u_ana)
+
+
+def test_table3_reproduced_smallest_drop():
+    """Table 3, iD3Q14 column, dp = 0.001 (Sec. 4.2: 41x21x21, dt = 0.05,
+    c = 1, tau = 0.9, T = 100): the periodic state (Eq. cr over one period
+    at 6e-14) gives the printed GRE_u at t = T to the last printed digit."""
+    gold = json.load(open(GOLDEN))["table3_gre_u"]
+    dp, printed = gold["delta_p"][0], gold["gre_u"][0]
+    case = inputs.pressure_pulsatile(14, gold["dx"], gold["dt"], gold["tau"], gold["T"], dp)
+    g, prm = oracle_setup(case)
+    steps = int(round(case.p_period))
+    f = oracle.init_equilibrium(g, None, case.init_p)
+    n, u_prev = 0, oracle.macroscopic(g, prm, 0, f)[0]
+    for _ in range(20):
+        f = oracle.run(g, prm, f, n, steps)
+        n += steps
+        u = oracle.macroscopic(g, prm, n, f)[0]
+        done = an.residual_periodic(u[0], u_prev[0]) <= 6e-14
+        u_prev = u
+        if done:
+            break
+    assert done
+    gre = pulsatile_gre(case, u, n, dp)
+    half = 0.5 * 10.0 ** (np.floor(np.log10(printed)) - 1)  # two printed digits
+    assert abs(gre - printed) <= half, (gre, printed)

@@ -156,7 +156,7 @@ def test_couette_profile_linear(Q):
     u_wall[3] = (U, 0.0, 0.0)
     g = oracle.make_grid(Q, 2, ny, 2, faces=(P, P, W, M, P, P), u_wall=u_wall)
     nu = 0.4
-    prm = oracle.make_params(oracle.rates(Q, 1.0 / (3 * nu + 0.5)))
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(nu)))
     f = oracle.init_equilibrium(g)
     f = oracle.run(g, prm, f, 0, 4000, nthreads=1)
     u, _ = oracle.macroscopic(g, prm, 4000, f)

@@ -14,7 +14,7 @@ W, P, M, S = oracle.WALL, oracle.PERIODIC, oracle.MOVING_WALL, oracle.SYMMETRY
 def run(Q, shape, faces, uw, force, steps, u0=None):
     nx, ny, nz = shape
     g = oracle.make_grid(Q, nx, ny, nz, faces=faces, u_wall=uw)
-    prm = oracle.make_params(oracle.rates(Q, 1.0 / (3 * 0.05 + 0.5)), force=force)
+    prm = oracle.make_params(oracle.rates(Q, oracle.s_nu_of(0.05)), force=force)
     f = oracle.run(g, prm, oracle.init_equilibrium(g, u0, None), 0, steps)
     u, p = oracle.macroscopic(g, prm, steps, f)
     return u, p

@@ -53,7 +53,12 @@ class FakeBackend:
         for s, (c, k) in self.slots.items():
             decay = float(c.name.split(":")[1])
             out[s] = FakeStats(k, k - 100 if k > 100 else -1, 10 ** (-k / decay))
+        self.last = out
         return out
+
+    def residual(self, slot):
+        st = self.last[slot]
+        return st.sum_abs_du[0] / st.sum_abs_u[0]
 
 
 class Clock:
