@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--Q", type=int, default=18)
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--storage", default="f32")
+    ap.add_argument("--rounding", default="nearest", choices=("nearest", "stochastic"),
+                    help="16-bit stores of the main workload")
     ap.add_argument("--Re", type=float, default=1000.0)
     ap.add_argument("--residual-interval", type=int, default=1000)
     ap.add_argument("--precision-n", type=int, default=256,
@@ -285,7 +287,9 @@ def run_gpu(a, rank, world, dist):
         case = inputs.cavity(Q, a.n, a.Re, U=0.05, storage=storage)
         h = lbm.lbm_create(Q, case.nx, case.ny, case.nz, storage, sp)
         lbm.lbm_set_geometry(h, case.faces, case.u_wall)
-        lbm.lbm_set_params(h, nu=case.nu, residual_interval=residual_interval)
+        rounding = lbm.LBM_ROUND_STOCHASTIC if a.rounding == "stochastic" else 0
+        lbm.lbm_set_params(h, nu=case.nu, residual_interval=residual_interval,
+                           rounding=rounding)
         lbm.lbm_init_equilibrium(h)
         if a.launch:
             block = tuple(int(v) for v in a.launch.split(","))
@@ -344,7 +348,8 @@ def run_gpu(a, rank, world, dist):
     residual = (lbm.lbm_residual(h, lbm.LBM_RESIDUAL_CAVITY) if stats.prev_step >= 0 else None)
     # the step kernel's own launch duration: back-to-back updates with no
     # reduction in between (the dominant kernel of the step, for the roofline)
-    lbm.lbm_set_params(h, nu=case.nu, residual_interval=0)
+    lbm.lbm_set_params(h, nu=case.nu, residual_interval=0,
+                       rounding=lbm.LBM_ROUND_STOCHASTIC if a.rounding == "stochastic" else 0)
     ku = max(2, a.kernel_updates + (a.kernel_updates & 1))
     e0.record(stream)
     lbm.lbm_step(h, ku)
@@ -527,7 +532,7 @@ def run_gpu(a, rank, world, dist):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": a.storage,
         "data": "synthetic (lid-driven cavity from rest)",
         "config": {"workload": workload_name(a), "grid": [a.n, a.n, a.n], "Q": a.Q,
                    "storage": a.storage, "Re": a.Re, "lid_velocity": 0.05,
