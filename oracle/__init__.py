@@ -73,7 +73,7 @@ def lib():
             ip = ctypes.POINTER(ctypes.c_int)
             L.oracle_velocities.argtypes = [ctypes.c_int, ip]
             L.oracle_weights.argtypes = [ctypes.c_int, dp, dp]
-            L.oracle_transform.argtypes = [ctypes.c_int, ip]
+            L.oracle_transform.argtypes = [ctypes.c_int, dp]
             L.oracle_moment_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
             L.oracle_pressure.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
             L.oracle_feq.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
@@ -114,8 +114,10 @@ def weights(Q: int):
 
 
 def transform(Q: int) -> np.ndarray:
-    out = np.zeros(Q * Q, dtype=np.int32)
-    _check(lib().oracle_transform(Q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    """T (int64): for Q = 14 and 18 as printed, for Q = 26 the Gram-Schmidt
+    rows of Sec. 3's recipe with their denominators cleared."""
+    out = np.zeros(Q * Q)
+    _check(lib().oracle_transform(Q, _dp(out)))
     return out.reshape(Q, Q).astype(np.int64)
 
 

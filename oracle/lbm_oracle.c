@@ -1,6 +1,9 @@
 /*
  * FP64 CPU oracle for the iD3Q14 / iD3Q18 incompressible MRT lattice
- * Boltzmann models (Zhang, Shi & Wang, arXiv:1503.03337).
+ * Boltzmann models (Zhang, Shi & Wang, arXiv:1503.03337), and for the
+ * iD3Q26 model that App. B's closing remark says the same construction
+ * gives (built here by Sec. 3's recipe: moment monomials on the D3Q27 set
+ * without c_0, Gram-Schmidt orthogonalised, m_eq = T f_eq).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
  * CUDA path is checked against.  Only the test suite, the smoke check and the
@@ -13,8 +16,10 @@
  * The update follows the paper's order (Sec. 3, Eq. mrteqvT):
  *   1. P = sum f, j = sum c f                       (Eq. hgl)
  *   2. u = j + F/2, p from P and |u|^2               (Eq. hgl; Guo forcing)
- *   3. m = T f with the printed T                    (Eq. T14 / App. B)
- *   4. m_eq from the printed closed forms            (Eq. meq / App. B)
+ *   3. m = T f with the printed T                    (Eq. T14 / App. B;
+ *                                                      iD3Q26: built T)
+ *   4. m_eq from the printed closed forms            (Eq. meq / App. B;
+ *                                                      iD3Q26: T f_eq)
  *   5. S_F = T Fbar, P row dropped                   (Guo forcing)
  *   6. m* = m - S (m - m_eq) + (I - S/2) S_F         (Eq. mrteqvT, diagonal S)
  *   7. f* = T^-1 m* with T^-1 = T' D^-1              (rows of T are orthogonal)
@@ -52,6 +57,15 @@ static const int C18[18][3] = {
     {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
     {1, 1, 0},  {-1, 1, 0},  {1, -1, 0}, {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1},
     {1, 0, -1}, {-1, 0, -1}, {0, 1, 1},  {0, -1, 1},  {0, 1, -1}, {0, -1, -1}};
+
+/* D3Q26 directions: the D3Q27 set without c_0, ordered as the axes and face
+ * diagonals of D3Q18 followed by the cube diagonals of D3Q14 */
+static const int C26[26][3] = {
+    {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},  {0, 0, 1},   {0, 0, -1},
+    {1, 1, 0},  {-1, 1, 0},  {1, -1, 0},  {-1, -1, 0}, {1, 0, 1},   {-1, 0, 1},
+    {1, 0, -1}, {-1, 0, -1}, {0, 1, 1},   {0, -1, 1},  {0, 1, -1},  {0, -1, -1},
+    {1, 1, 1},  {-1, 1, 1},  {1, -1, 1},  {-1, -1, 1}, {1, 1, -1},  {-1, 1, -1},
+    {1, -1, -1}, {-1, -1, -1}};
 
 /* ---- transformation matrices, as printed ------------------------------ */
 
@@ -98,17 +112,59 @@ static const int T18[18][18] = {
 typedef struct {
   int Q;
   const int (*c)[3];
-  const int *T; /* Q*Q, row-major */
-  double w[18]; /* lattice weights of the directions actually stored */
+  double T[26 * 26]; /* Q*Q, row-major */
+  double w[26]; /* lattice weights of the directions actually stored */
   double w0;    /* weight of the discarded rest direction c_0 */
-  double D[18]; /* D_k = sum_a T_ka^2 (row norms; T T' = diag(D)) */
+  double D[26]; /* D_k = sum_a T_ka^2 (row norms; T T' = diag(D)) */
 } model;
+
+/* The iD3Q26 moment polynomials, in row order: the 18 moments of the iD3Q18
+ * basis (P, e, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww,
+ * p_xy, p_yz, p_xz, t_x, t_y, t_z), then |c|^4, |c|^4 c_x, |c|^4 c_y,
+ * |c|^4 c_z, |c|^2 c_x c_y, |c|^2 c_y c_z, |c|^2 c_x c_z and c_x c_y c_z:
+ * the monomials of Sec. 3's recipe (Eq. transformation_Mbar) for the 26
+ * velocities of D3Q27 without c_0.  c_x^2 c_y^2 c_z^2 is left out: on these
+ * velocities (1 - c_x^2)(1 - c_y^2)(1 - c_z^2) = 0 makes it a combination of
+ * the others, as the paper drops the kinetic-energy-square moment for Q14. */
+static double poly26(int k, const int c[3]) {
+  const double x = c[0], y = c[1], z = c[2];
+  const double n2 = x * x + y * y + z * z;
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return n2;
+    case 2: return x;
+    case 3: return n2 * x;
+    case 4: return y;
+    case 5: return n2 * y;
+    case 6: return z;
+    case 7: return n2 * z;
+    case 8: return 3.0 * x * x - n2;
+    case 9: return n2 * (3.0 * x * x - n2);
+    case 10: return y * y - z * z;
+    case 11: return n2 * (y * y - z * z);
+    case 12: return x * y;
+    case 13: return y * z;
+    case 14: return x * z;
+    case 15: return x * (y * y - z * z);
+    case 16: return y * (z * z - x * x);
+    case 17: return z * (x * x - y * y);
+    case 18: return n2 * n2;
+    case 19: return n2 * n2 * x;
+    case 20: return n2 * n2 * y;
+    case 21: return n2 * n2 * z;
+    case 22: return n2 * x * y;
+    case 23: return n2 * y * z;
+    case 24: return n2 * x * z;
+    case 25: return x * y * z;
+  }
+  return 0.0;
+}
 
 static int model_init(int Q, model *m) {
   if (Q == 14) {
     m->Q = 14;
     m->c = C14;
-    m->T = &T14[0][0];
+    for (int k = 0; k < 14 * 14; ++k) m->T[k] = (double)(&T14[0][0])[k];
     /* The weights printed beside Eq. edf belong to D3Q19; the
      * Q14 equilibria of Eq. meq hold only with the D3Q15 weights
      * w0 = 2/9, 1/9 on the axes and 1/72 on the cube diagonals. */
@@ -117,17 +173,56 @@ static int model_init(int Q, model *m) {
   } else if (Q == 18) {
     m->Q = 18;
     m->c = C18;
-    m->T = &T18[0][0];
+    for (int k = 0; k < 18 * 18; ++k) m->T[k] = (double)(&T18[0][0])[k];
     /* App. B: w_1..6 = 1/18, w_7..18 = 1/36, so w0 = 1/3 */
     m->w0 = 1.0 / 3.0;
     for (int a = 0; a < 18; ++a) m->w[a] = (a < 6) ? 1.0 / 18.0 : 1.0 / 36.0;
+  } else if (Q == 26) {
+    /* iD3Q26 (App. B's closing remark): the D3Q27 weights 8/27, 2/27, 1/54,
+     * 1/216 and the recipe of Sec. 3: the moment polynomials on the velocity
+     * set, Gram-Schmidt orthogonalised in row order (Eq. transformation_Mbar) */
+    m->Q = 26;
+    m->c = C26;
+    m->w0 = 8.0 / 27.0;
+    for (int a = 0; a < 26; ++a)
+      m->w[a] = a < 6 ? 2.0 / 27.0 : (a < 18 ? 1.0 / 54.0 : 1.0 / 216.0);
+    for (int k = 0; k < 26; ++k) {
+      double *row = &m->T[k * 26];
+      for (int a = 0; a < 26; ++a) row[a] = poly26(k, C26[a]);
+      for (int l = 0; l < k; ++l) {
+        const double *prev = &m->T[l * 26];
+        double num = 0.0, den = 0.0;
+        for (int a = 0; a < 26; ++a) {
+          num += row[a] * prev[a];
+          den += prev[a] * prev[a];
+        }
+        for (int a = 0; a < 26; ++a) row[a] -= num / den * prev[a];
+      }
+      /* clear denominators, as the printed T14 and T18 are integer: the
+       * smallest multiple of the row's smallest entry that makes every
+       * entry an integer (the rows are rational with small denominators) */
+      double small = 0.0;
+      for (int a = 0; a < 26; ++a)
+        if (fabs(row[a]) > 1e-9 && (small == 0.0 || fabs(row[a]) < small)) small = fabs(row[a]);
+      int mult = 1;
+      for (; mult <= 720; ++mult) {
+        int ok = 1;
+        for (int a = 0; a < 26 && ok; ++a) {
+          const double v = row[a] * mult / small;
+          ok = fabs(v - nearbyint(v)) < 1e-8;
+        }
+        if (ok) break;
+      }
+      if (mult > 720) return -1;
+      for (int a = 0; a < 26; ++a) row[a] = nearbyint(row[a] * mult / small);
+    }
   } else {
     return -1;
   }
   for (int k = 0; k < m->Q; ++k) {
     double s = 0.0;
     for (int a = 0; a < m->Q; ++a) {
-      double t = (double)m->T[k * m->Q + a];
+      const double t = m->T[k * m->Q + a];
       s += t * t;
     }
     m->D[k] = s;
@@ -147,7 +242,17 @@ static int opposite(const model *m, int a) {
  * Q14: Eq. sD3Q15meaning, (sc,se,sc,sq,sc,sq,sc,sq,snu x5,st).
  * Q18: Eq. sD3Q19, (sc,se,sc,sq,sc,sq,sc,sq,snu,spi,snu,spi,snu,snu,snu,st x3). */
 static void relaxation_diag(const model *m, const oracle_rates *r, double *s) {
-  if (m->Q == 14) {
+  if (m->Q == 26) {
+    /* the paper gives no rates for iD3Q26; the reading extends Eq. sD3Q19:
+     * conserved s_c; e and |c|^4 s_e; the heat fluxes (q and the |c|^4 c
+     * rows) s_q; the stress rows s_nu; the |c|^2-weighted stress rows s_pi;
+     * the third-order rows t and c_x c_y c_z s_t */
+    const double v[26] = {r->sc,  r->se,  r->sc,  r->sq,  r->sc,  r->sq,  r->sc,
+                          r->sq,  r->snu, r->spi, r->snu, r->spi, r->snu, r->snu,
+                          r->snu, r->st,  r->st,  r->st,  r->se,  r->sq,  r->sq,
+                          r->sq,  r->spi, r->spi, r->spi, r->st};
+    memcpy(s, v, sizeof v);
+  } else if (m->Q == 14) {
     const double v[14] = {r->sc,  r->se,  r->sc,  r->sq,  r->sc,  r->sq,  r->sc,
                           r->sq,  r->snu, r->snu, r->snu, r->snu, r->snu, r->st};
     memcpy(s, v, sizeof v);
@@ -161,8 +266,21 @@ static void relaxation_diag(const model *m, const oracle_rates *r, double *s) {
 
 /* Equilibrium moments, printed closed forms.
  * Q14: Eq. meq.  Q18: App. B equilibria. */
+static void feq_cell(const model *m, double p, const double u[3], double *feq);
+
 static void moment_equilibrium(const model *m, double p, const double u[3],
                                double *meq) {
+  if (m->Q == 26) {
+    /* no printed equilibria: m_eq = T f_eq, the definition (Eq. mrteqvT) */
+    double feq[26];
+    feq_cell(m, p, u, feq);
+    for (int k = 0; k < 26; ++k) {
+      double acc = 0.0;
+      for (int a = 0; a < 26; ++a) acc += m->T[k * 26 + a] * feq[a];
+      meq[k] = acc;
+    }
+    return;
+  }
   const double ux = u[0], uy = u[1], uz = u[2];
   const double u2 = ux * ux + uy * uy + uz * uz;
   if (m->Q == 14) {
@@ -226,25 +344,25 @@ static void collide_cell(const model *m, const double *s, const double *f,
   const double p = pressure(m, P, u);
 
   /* m = T f */
-  double mom[18];
+  double mom[26];
   for (int k = 0; k < Q; ++k) {
     double acc = 0.0;
     for (int a = 0; a < Q; ++a) acc += (double)m->T[k * Q + a] * f[a];
     mom[k] = acc;
   }
-  double meq[18];
+  double meq[26];
   moment_equilibrium(m, p, u, meq);
 
   /* Guo source in velocity space, Fbar_a = w_a [3 c.F + 9 (c.u)(c.F) - 3 u.F],
    * projected with T; the P row is dropped. */
-  double Fbar[18];
+  double Fbar[26];
   const double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
   for (int a = 0; a < Q; ++a) {
     const double cF = m->c[a][0] * F[0] + m->c[a][1] * F[1] + m->c[a][2] * F[2];
     const double cu = m->c[a][0] * u[0] + m->c[a][1] * u[1] + m->c[a][2] * u[2];
     Fbar[a] = m->w[a] * (3.0 * cF + 9.0 * cu * cF - 3.0 * uF);
   }
-  double SF[18];
+  double SF[26];
   for (int k = 0; k < Q; ++k) {
     double acc = 0.0;
     for (int a = 0; a < Q; ++a) acc += (double)m->T[k * Q + a] * Fbar[a];
@@ -252,7 +370,7 @@ static void collide_cell(const model *m, const double *s, const double *f,
   }
   SF[0] = 0.0;
 
-  double mpost[18];
+  double mpost[26];
   for (int k = 0; k < Q; ++k)
     mpost[k] = mom[k] - s[k] * (mom[k] - meq[k]) + (1.0 - 0.5 * s[k]) * SF[k];
 
@@ -413,7 +531,7 @@ static void neq_extrapolate(const model *m, const oracle_grid *g, const oracle_p
         double ub[3], pb;
         for (int d = 0; d < 3; ++d) ub[d] = vel_face >= 0 ? g->u_wall[vel_face][d] : uf[d];
         pb = pre_face >= 0 ? face_pressure(prm, pre_face, n) : pf;
-        double eb[18], ef[18];
+        double eb[26], ef[26];
         feq_cell(m, pb, ub, eb);
         feq_cell(m, pf, uf, ef);
         for (int a = 0; a < Q; ++a) f[a * N + ib] = eb[a] + (f[a * N + jf] - ef[a]);
@@ -438,10 +556,10 @@ int oracle_weights(int Q, double *w_out, double *w0_out) {
   return 0;
 }
 
-int oracle_transform(int Q, int *T_out) {
+int oracle_transform(int Q, double *T_out) {
   model m;
   if (model_init(Q, &m)) return -1;
-  memcpy(T_out, m.T, sizeof(int) * Q * Q);
+  memcpy(T_out, m.T, sizeof(double) * Q * Q);
   return 0;
 }
 
@@ -476,7 +594,7 @@ int oracle_collide(int Q, const oracle_rates *r, const double *f,
                    const double *F, double *fpost) {
   model m;
   if (model_init(Q, &m)) return -1;
-  double s[18];
+  double s[26];
   relaxation_diag(&m, r, s);
   collide_cell(&m, s, f, F, fpost, NULL, NULL);
   return 0;
@@ -492,7 +610,7 @@ int oracle_init_equilibrium(const oracle_grid *g, const double *u,
     if (u)
       for (int d = 0; d < 3; ++d) ui[d] = u[d * N + i];
     const double pi = p ? p[i] : 0.0;
-    double feq[18];
+    double feq[26];
     oracle_feq(g->Q, pi, ui, feq);
     const int solid = g->solid && g->solid[i];
     for (int a = 0; a < g->Q; ++a) f[a * N + i] = solid ? 0.0 : feq[a];
@@ -512,9 +630,9 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
       return -3; /* an extrapolation boundary needs an inward neighbour */
   for (int face = 0; face < 6; ++face)
     if (g->solid && is_neq(g->face[face])) return -4; /* not combined */
-  double s[18];
+  double s[26];
   relaxation_diag(&m, &prm->rates, s);
-  int opp[18];
+  int opp[26];
   for (int a = 0; a < Q; ++a) opp[a] = opposite(&m, a);
   const double F[3] = {force_at(prm, n, 0), force_at(prm, n, 1),
                        force_at(prm, n, 2)};
@@ -525,7 +643,7 @@ int oracle_step(const oracle_grid *g, const oracle_params *prm, int64_t n,
 
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
   for (int z = 0; z < nz; ++z) {
-    double fc[18], fp[18];
+    double fc[26], fp[26];
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         const int64_t i = ((int64_t)z * ny + y) * nx + x;

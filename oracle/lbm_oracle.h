@@ -26,7 +26,7 @@ enum {
 };
 
 typedef struct {
-  int Q;              /* 14 or 18 */
+  int Q;              /* 14, 18 or 26 */
   int nx, ny, nz;     /* fluid nodes per axis */
   int face[6];        /* x-, x+, y-, y+, z-, z+ : ORACLE_* kinds */
   double u_wall[6][3];/* wall velocity of each MOVING_WALL face */
@@ -61,7 +61,7 @@ typedef struct {
 
 int oracle_velocities(int Q, int *c_out);           /* Q*3 ints */
 int oracle_weights(int Q, double *w_out, double *w0_out);
-int oracle_transform(int Q, int *T_out);            /* Q*Q ints, row-major */
+int oracle_transform(int Q, double *T_out);         /* Q*Q, row-major */
 int oracle_moment_equilibrium(int Q, double p, const double *u, double *meq);
 int oracle_pressure(int Q, double P, const double *u, double *p);
 int oracle_feq(int Q, double p, const double *u, double *feq);
