@@ -11,7 +11,10 @@
  * Conventions shared by every call:
  *  - Nodes are ordered x fastest: cell = x + nx*(y + ny*z).
  *  - Population arrays are [a][cell], a = 0..Q-1 being the paper's direction
- *    a+1 (Sec. 3 velocity set for Q = 14, App. B for Q = 18).
+ *    a+1 (Sec. 3 velocity set for Q = 14, App. B for Q = 18).  Q = 26 is
+ *    the D3Q27 set without c_0 that App. B's closing remark names: the 18
+ *    directions of Q = 18 in their order, then the 8 cube diagonals in the
+ *    order of Q = 14's directions 7..14.
  *  - Walls sit halfway between the last fluid node and the ghost node beyond
  *    it (halfway bounce-back); a moving wall adds 6 w_a (c_a . u_wall) to the
  *    reflected population.
@@ -100,7 +103,9 @@ enum lbm_rounding { LBM_ROUND_NEAREST = 0, LBM_ROUND_STOCHASTIC = 1 };
 
 /* ---- descriptors -------------------------------------------------------- */
 typedef struct lbm_desc {
-  int32_t Q;       /* 14 (Sec. 3) or 18 (App. B)                           */
+  int32_t Q;       /* 14 (Sec. 3), 18 (App. B) or 26 (App. B's closing
+                      remark: the same construction on D3Q27 without c_0;
+                      single-domain handles only)                         */
   int32_t nx, ny, nz; /* fluid nodes per axis, each >= 1                   */
   int32_t storage; /* enum lbm_storage                                     */
 } lbm_desc;
@@ -127,7 +132,10 @@ typedef struct lbm_geom {
 /* Relaxation rates of the diagonal collision matrix, Eq. sD3Q15meaning
  * (Q14) and Eq. sD3Q19 (Q18).  If nu > 0 then s_nu = 1/(3 nu + 1/2)
  * (Eq. vis) and the s_nu field is ignored.  Sec. 4 uses s_c = 1, s_e = 1.19,
- * s_q = 1.2, s_t = 0.98; s_pi (Q18 only) is not given by the paper.
+ * s_q = 1.2, s_t = 0.98; s_pi (Q18 and Q26) is not given by the paper.
+ * Q26 (no rates in the paper) gives each of its rows beyond the 18 of Q18
+ * the rate of the Q18 row it extends: |c|^4 s_e, the |c|^4 c rows s_q, the
+ * |c|^2 c_x c_y rows s_pi, c_x c_y c_z s_t.
  * Body force F(t_n) = force * cos(2 pi n / force_period) if force_period > 0,
  * else force; it enters as u = j + F/2 and a Guo source in moment space.
  * p_ref shifts the reported pressure: stored populations are
@@ -177,7 +185,7 @@ typedef struct lbm_handle lbm_handle;
  * reduction workspace.  `cuda_stream` is a cudaStream_t (NULL = legacy
  * default stream); it is borrowed, not owned.  Initial state: all walls at
  * rest, Sec. 4 default rates with nu = 1/6, no force, f = 0, step 0.
- * Errors: EINVAL (Q not 14/18, a size < 1, storage unknown, Q*N >= 2^31),
+ * Errors: EINVAL (Q not 14/18/26, a size < 1, storage unknown, Q*N >= 2^31),
  * ENOMEM, ECUDA. */
 int lbm_create(const lbm_desc *desc, void *cuda_stream, lbm_handle **out);
 
@@ -297,7 +305,9 @@ typedef struct lbm_launch {
                                with 2-byte storage instead of 64 B); odd
                                steps run one cell per thread.  Stochastic
                                rounding draws the same random bits for a
-                               cell either way.  Not for FP64 storage.      */
+                               cell either way.  Not for FP64 storage.
+                               Q = 26 accepts 2 and runs one cell per
+                               thread on every step.                        */
 } lbm_launch;
 
 /* Set / read the launch shape.  EINVAL if out of range. */
@@ -383,8 +393,8 @@ int lbm_device_populations(lbm_handle *h, void **ptr, int64_t *bytes);
 /* ---- batches of independent domains -------------------------------------- */
 
 /* A batch advances many independent domains (different sizes, Q, storage,
- * step counters) together.  Grouped mode (default): each step is one launch
- * per group of domains sharing Q, storage, rounding and parity.  Persistent
+ * step counters; Q = 14 or 18) together.  Grouped mode (default): each step
+ * is one launch per group of domains sharing Q, storage, rounding and parity.  Persistent
  * mode: one cooperative launch runs a whole chunk of steps of all domains,
  * with a bounded grid barrier between steps.  The launches of a chunk are
  * captured once in a CUDA graph and replayed.  Each domain computes exactly

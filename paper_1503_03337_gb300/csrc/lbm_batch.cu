@@ -169,7 +169,8 @@ void drop_graph(lbm_batch* b) {
 }
 
 int fill_desc(const lbm_desc* desc, const lbm_geom* g, const lbm_params* p, DomainDesc& dd) {
-  if (desc->Q != 14 && desc->Q != 18) return bfail(LBM_EINVAL, "Q must be 14 or 18");
+  if (desc->Q != 14 && desc->Q != 18)
+    return bfail(LBM_EINVAL, "Q must be 14 or 18 (the batch path has no iD3Q26 kernels)");
   if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
     return bfail(LBM_EINVAL, "grid sizes must be >= 1");
   if (desc->storage != LBM_STORAGE_F32 && desc->storage != LBM_STORAGE_F16 &&

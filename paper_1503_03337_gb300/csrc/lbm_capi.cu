@@ -85,7 +85,7 @@ int apply_params(lbm_handle* h, const lbm_params* p) {
   if (p->nu > 0.0) s[3] = 1.0 / (3.0 * p->nu + 0.5);
   if (!(std::isfinite(p->nu))) return fail(LBM_EINVAL, "nu is not finite");
   for (int k = 0; k < 6; ++k) {
-    if (k == 4 && h->d.Q == 14) continue;  // s_pi exists only for Q18
+    if (k == 4 && h->d.Q == 14) continue;  // s_pi exists only for Q18 and Q26
     if (!(s[k] > 0.0 && s[k] < 2.0))
       return fail(LBM_EINVAL, "relaxation rates must lie in (0, 2)");
   }
@@ -158,7 +158,8 @@ const char* lbm_strerror(int code) {
 int lbm_create(const lbm_desc* desc, void* cuda_stream, lbm_handle** out) {
   if (!desc || !out) return fail(LBM_EINVAL, "null argument");
   *out = nullptr;
-  if (desc->Q != 14 && desc->Q != 18) return fail(LBM_EINVAL, "Q must be 14 or 18");
+  if (desc->Q != 14 && desc->Q != 18 && desc->Q != 26)
+    return fail(LBM_EINVAL, "Q must be 14, 18 or 26");
   if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
     return fail(LBM_EINVAL, "grid sizes must be >= 1");
   const size_t b = storage_bytes(desc->storage);
@@ -607,7 +608,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
     if (e != cudaSuccess) break;
     b.pdl = h->block.pdl;
     if (b.bx * b.cpt > xmax && b.bx > 32) continue;
-    if (b.cpt == 2 && h->d.storage == LBM_STORAGE_F64) continue;
+    if (b.cpt == 2 && (h->d.storage == LBM_STORAGE_F64 || h->d.Q == 26)) continue;
     int64_t n = n0;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->d, n++, b, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);

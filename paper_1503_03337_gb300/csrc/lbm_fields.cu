@@ -420,6 +420,13 @@ cudaError_t dispatch(const DomainDesc& d, Fn&& fn) {
       case LBM_STORAGE_F16: return fn.template operator()<18, __half>();
       case LBM_STORAGE_BF16: return fn.template operator()<18, __nv_bfloat16>();
     }
+  } else if (d.Q == 26) {
+    switch (d.storage) {
+      case LBM_STORAGE_F64: return fn.template operator()<26, double>();
+      case LBM_STORAGE_F32: return fn.template operator()<26, float>();
+      case LBM_STORAGE_F16: return fn.template operator()<26, __half>();
+      case LBM_STORAGE_BF16: return fn.template operator()<26, __nv_bfloat16>();
+    }
   }
   return cudaErrorInvalidValue;
 }

@@ -49,7 +49,7 @@ struct Domain {
   //   pull[a] = abar*N - s(c_a)     (where f_a(x) is read)
   //   push[a] = a*N + s(c_a)        (where f*_a(x) is written)
   // with s(c) = cx + cy*nx + cz*nx*ny.  Filled by fill_offsets().
-  int pull[18], push[18];
+  int pull[26], push[26];
 };
 
 constexpr uint32_t kSolidCell = 0x80000000u;
@@ -249,7 +249,7 @@ __host__ __device__ __forceinline__ void link_of(const Links& L, int& off, bool&
 }
 
 // The population whose velocity is c_A with the components of the axes in
-// `mask` reversed (both lattices are closed under axis reflections).
+// `mask` reversed (every lattice here is closed under axis reflections).
 template <int Q>
 __host__ __device__ constexpr int mirror_of(int a, int mask) {
   int c[3];
@@ -266,7 +266,8 @@ __host__ __device__ constexpr bool mirrors_closed() {
       if (mirror_of<Q>(a, m) < 0) return false;
   return true;
 }
-static_assert(mirrors_closed<14>() && mirrors_closed<18>(), "lattice not closed under mirrors");
+static_assert(mirrors_closed<14>() && mirrors_closed<18>() && mirrors_closed<26>(),
+              "lattice not closed under mirrors");
 
 // mirror_of<Q>(A, mask) for a runtime mask (a select among eight constants)
 template <int Q, int A>

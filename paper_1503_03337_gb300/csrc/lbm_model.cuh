@@ -1,5 +1,7 @@
 // Lattice tables and the per-cell MRT collision of the iD3Q14 (Sec. 3) and
-// iD3Q18 (App. B) incompressible models, written for registers.
+// iD3Q18 (App. B) incompressible models, and of the iD3Q26 model that the
+// same construction gives on the D3Q27 set without c_0 (App. B's closing
+// remark), written for registers.
 //
 // Everything that depends only on the lattice is a constexpr function, so
 // the moment transform m = T f and its inverse f = T' D^-1 m (Eq. mrteqvT)
@@ -68,6 +70,22 @@ struct Lattice<18> {
   }
 };
 
+// iD3Q26: the 26 velocities of D3Q27 without c_0 -- the axes and face
+// diagonals in the order of iD3Q18, then the cube diagonals in the order of
+// iD3Q14 -- with the D3Q27 weights (8/27 for the discarded rest direction,
+// 2/27, 1/54 and 1/216 for the three shells).
+template <>
+struct Lattice<26> {
+  static constexpr int Q = 26;
+  __host__ __device__ static constexpr int c(int a, int d) {
+    return a < 18 ? Lattice<18>::c(a, d) : Lattice<14>::c(a - 12, d);
+  }
+  static constexpr double w0 = 8.0 / 27.0;
+  __host__ __device__ static constexpr double w(int a) {
+    return a < 6 ? 2.0 / 27.0 : (a < 18 ? 1.0 / 54.0 : 1.0 / 216.0);
+  }
+};
+
 template <int Q>
 __host__ __device__ constexpr int opposite(int a) {
   for (int b = 0; b < Q; ++b)
@@ -118,6 +136,55 @@ __host__ __device__ constexpr int phi(int k, int a) {
       case 11: return cy * cz;
       case 12: return cx * cz;
       case 13: return cx * cy * cz;
+    }
+  } else if (Q == 26) {
+    // The monomials 1, |c|^2, c_x, |c|^2 c_x, ..., 3c_x^2 - |c|^2,
+    // |c|^2 (3c_x^2 - |c|^2), c_y^2 - c_z^2, |c|^2 (c_y^2 - c_z^2), c_x c_y,
+    // c_y c_z, c_x c_z, the three t's, |c|^4, |c|^4 c_x, |c|^4 c_y, |c|^4 c_z,
+    // |c|^2 c_x c_y, |c|^2 c_y c_z, |c|^2 c_x c_z and c_x c_y c_z, each
+    // orthogonalised against the ones before it (Sec. 3's recipe) and scaled
+    // to integers.  On this set a function of |c|^2 is a function of the
+    // shell (sizes 6, 12, 8), so orthogonalising a monomial g(|c|^2) h(c)
+    // against the lower ones only changes g, to the quadratic in |c|^2 whose
+    // shell values make it orthogonal with the shell weights of h^2:
+    //   |c|^2       -> 13|c|^2 - 27                     (-14, -1, 12)
+    //   |c|^2 c_x   -> (3|c|^2 - 7) c_x                 (-4, -1, 2)
+    //   |c|^2 (3c_x^2 - |c|^2) -> (3|c|^2 - 5)(...)     (-2, 1, -)
+    //   |c|^4       -> (15|c|^4 - 61|c|^2 + 54) / 2     (4, -4, 3)
+    //   |c|^4 c_x   -> (9|c|^4 - 39|c|^2 + 38) / 2 c_x  (4, -2, 1)
+    //   |c|^2 c_x c_y -> (3|c|^2 - 8) c_x c_y           (-, -2, 1)
+    // The remaining monomials are already orthogonal to the ones before them
+    // (by their parity in each of c_x, c_y, c_z and their cubic symmetry);
+    // basis_ok checks all of it at compile time.  The |c|^6 and
+    // c_x^2 c_y^2 c_z^2 monomials are left out: (1 - c_x^2)(1 - c_y^2)(1 -
+    // c_z^2) = 0 on these velocities makes them dependent on the others.
+    switch (k) {
+      case 0: return 1;
+      case 1: return 13 * n2 - 27;
+      case 2: return cx;
+      case 3: return (3 * n2 - 7) * cx;
+      case 4: return cy;
+      case 5: return (3 * n2 - 7) * cy;
+      case 6: return cz;
+      case 7: return (3 * n2 - 7) * cz;
+      case 8: return 3 * cx * cx - n2;
+      case 9: return (3 * n2 - 5) * (3 * cx * cx - n2);
+      case 10: return cy * cy - cz * cz;
+      case 11: return (3 * n2 - 5) * (cy * cy - cz * cz);
+      case 12: return cx * cy;
+      case 13: return cy * cz;
+      case 14: return cx * cz;
+      case 15: return (cy * cy - cz * cz) * cx;
+      case 16: return (cz * cz - cx * cx) * cy;
+      case 17: return (cx * cx - cy * cy) * cz;
+      case 18: return (15 * n2 * n2 - 61 * n2 + 54) / 2;
+      case 19: return (9 * n2 * n2 - 39 * n2 + 38) / 2 * cx;
+      case 20: return (9 * n2 * n2 - 39 * n2 + 38) / 2 * cy;
+      case 21: return (9 * n2 * n2 - 39 * n2 + 38) / 2 * cz;
+      case 22: return (3 * n2 - 8) * cx * cy;
+      case 23: return (3 * n2 - 8) * cy * cz;
+      case 24: return (3 * n2 - 8) * cx * cz;
+      case 25: return cx * cy * cz;
     }
   } else {
     // P, e, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz,
@@ -189,6 +256,7 @@ __host__ __device__ constexpr bool basis_ok() {
 }
 static_assert(basis_ok<14>(), "iD3Q14 moment basis is inconsistent");
 static_assert(basis_ok<18>(), "iD3Q18 moment basis is inconsistent");
+static_assert(basis_ok<26>(), "iD3Q26 moment basis is inconsistent");
 
 // ---------------------------------------------------------------------------
 // Storage codec: populations live in S, arithmetic runs in R.
@@ -515,12 +583,15 @@ struct Rates {
   // h[K] = (1 - s_K/2) / D_K (for the momentum rows, which carry only the
   // force, h[K] = 1 / D_K).  Filled once per launch by scale_rows, so the
   // collision multiplies each relaxed row once.
-  R k[18], h[18];
+  R k[26], h[26];
 };
 
 // Relaxation rate of row K (Eq. sD3Q15meaning / Eq. sD3Q19): conserved rows
 // s_c, energy s_e, heat flux s_q, the stress rows s_nu (the pi rows of Q18
-// s_pi), the third-order rows s_t.
+// s_pi), the third-order rows s_t.  The paper gives no rates for iD3Q26;
+// its rows take the rate of the iD3Q18 row they extend: |c|^4 that of e,
+// the |c|^4 c rows that of q, the |c|^2 c_x c_y rows that of pi, and
+// c_x c_y c_z that of t.
 template <int Q, typename R>
 __host__ __device__ constexpr R rate_of(const Rates<R>& r, int K) {
   if (K == 0 || K == 2 || K == 4 || K == 6) return r.sc;
@@ -528,12 +599,17 @@ __host__ __device__ constexpr R rate_of(const Rates<R>& r, int K) {
   if (K == 3 || K == 5 || K == 7) return r.sq;
   if (Q == 14) return K == 13 ? r.st : r.snu;
   if (K == 9 || K == 11) return r.spi;
+  if (Q == 26 && K >= 18) {
+    if (K == 18) return r.se;
+    if (K <= 21) return r.sq;
+    return K == 25 ? r.st : r.spi;
+  }
   return K >= 15 ? r.st : r.snu;
 }
 
 template <int Q, typename R>
 __host__ __device__ inline void scale_rows(Rates<R>& r) {
-  for (int K = 0; K < 18; ++K) {
+  for (int K = 0; K < 26; ++K) {
     r.k[K] = R(0);
     r.h[K] = R(0);
   }
@@ -586,8 +662,94 @@ __host__ __device__ constexpr bool accumulators_covered() {
   return true;
 }
 static_assert(accumulators_covered<14, false>() && accumulators_covered<14, true>() &&
-                  accumulators_covered<18, false>() && accumulators_covered<18, true>(),
+                  accumulators_covered<18, false>() && accumulators_covered<18, true>() &&
+                  accumulators_covered<26, false>() && accumulators_covered<26, true>(),
               "a pair accumulator receives no row");
+
+// ---------------------------------------------------------------------------
+// Equilibrium moments from their definition m_eq = T f_eq (Eq. mrteqvT), for
+// a model without printed closed forms (iD3Q26).  With
+//   f_eq,a = w_a [3p + 3 c_a.u + 9/2 (c_a.u)^2 - 3/2 u^2]
+// (the incompressible equilibrium, Eq. edf, c_s^2 = 1/3), row K is
+//   m_eq,K = A_K (3p - 3/2 u^2) + 3 sum_d B_Kd u_d + 9/2 sum_de C_Kde u_d u_e
+// with the compile-time weighted sums A_K = sum_a phi_K w_a,
+// B_Kd = sum_a phi_K w_a c_d and C_Kde = sum_a phi_K w_a c_d c_e.  The Guo
+// source (the projection of w_a [3 c.F + 9 (c.u)(c.F) - 3 u.F]) is the
+// derivative of the same form along F at fixed p:
+//   S_F,K = -3 A_K u.F + 3 sum_d B_Kd F_d + 9 sum_de C_Kde u_d F_e.
+// ---------------------------------------------------------------------------
+template <int Q>
+__host__ __device__ constexpr double eq_a(int K) {
+  double s = 0.0;
+  for (int a = 0; a < Q; ++a) s += phi<Q>(K, a) * Lattice<Q>::w(a);
+  return s;
+}
+template <int Q>
+__host__ __device__ constexpr double eq_b(int K, int d) {
+  double s = 0.0;
+  for (int a = 0; a < Q; ++a) s += phi<Q>(K, a) * Lattice<Q>::w(a) * Lattice<Q>::c(a, d);
+  return s;
+}
+template <int Q>
+__host__ __device__ constexpr double eq_c(int K, int d, int e) {
+  double s = 0.0;
+  for (int a = 0; a < Q; ++a)
+    s += phi<Q>(K, a) * Lattice<Q>::w(a) * Lattice<Q>::c(a, d) * Lattice<Q>::c(a, e);
+  return s;
+}
+
+// acc + C * x, with C a compile-time constant (no instruction when C = 0)
+template <typename V, typename R>
+__host__ __device__ __forceinline__ V add_scaled(V acc, double C, V x) {
+  return C == 0.0 ? acc : fmadd(V(R(C)), x, acc);
+}
+
+// m_eq,K (q3 = 3p - 3/2 u^2; uu = u_x^2, u_y^2, u_z^2, u_x u_y, u_y u_z,
+// u_x u_z)
+template <int Q, int K, typename V, typename R>
+__host__ __device__ __forceinline__ V moment_eq(V q3, V ux, V uy, V uz, const V* uu) {
+  constexpr double A = eq_a<Q>(K);
+  constexpr double Bx = 3.0 * eq_b<Q>(K, 0), By = 3.0 * eq_b<Q>(K, 1), Bz = 3.0 * eq_b<Q>(K, 2);
+  constexpr double Cxx = 4.5 * eq_c<Q>(K, 0, 0), Cyy = 4.5 * eq_c<Q>(K, 1, 1),
+                   Czz = 4.5 * eq_c<Q>(K, 2, 2), Cxy = 9.0 * eq_c<Q>(K, 0, 1),
+                   Cyz = 9.0 * eq_c<Q>(K, 1, 2), Cxz = 9.0 * eq_c<Q>(K, 0, 2);
+  V acc = V(R(0));
+  acc = add_scaled<V, R>(acc, A, q3);
+  acc = add_scaled<V, R>(acc, Bx, ux);
+  acc = add_scaled<V, R>(acc, By, uy);
+  acc = add_scaled<V, R>(acc, Bz, uz);
+  acc = add_scaled<V, R>(acc, Cxx, uu[0]);
+  acc = add_scaled<V, R>(acc, Cyy, uu[1]);
+  acc = add_scaled<V, R>(acc, Czz, uu[2]);
+  acc = add_scaled<V, R>(acc, Cxy, uu[3]);
+  acc = add_scaled<V, R>(acc, Cyz, uu[4]);
+  acc = add_scaled<V, R>(acc, Cxz, uu[5]);
+  return acc;
+}
+
+// S_F,K (uF = u.F; uf = 2 u_x F_x, 2 u_y F_y, 2 u_z F_z, u_x F_y + u_y F_x,
+// u_y F_z + u_z F_y, u_x F_z + u_z F_x)
+template <int Q, int K, typename V, typename R>
+__host__ __device__ __forceinline__ V moment_source(V uF, R Fx, R Fy, R Fz, const V* uf) {
+  constexpr double A = -3.0 * eq_a<Q>(K);
+  constexpr double Bx = 3.0 * eq_b<Q>(K, 0), By = 3.0 * eq_b<Q>(K, 1), Bz = 3.0 * eq_b<Q>(K, 2);
+  constexpr double Cxx = 4.5 * eq_c<Q>(K, 0, 0), Cyy = 4.5 * eq_c<Q>(K, 1, 1),
+                   Czz = 4.5 * eq_c<Q>(K, 2, 2), Cxy = 9.0 * eq_c<Q>(K, 0, 1),
+                   Cyz = 9.0 * eq_c<Q>(K, 1, 2), Cxz = 9.0 * eq_c<Q>(K, 0, 2);
+  R b = R(0);  // the constant part, in the arithmetic type
+  if constexpr (Bx != 0.0) b += R(Bx) * Fx;
+  if constexpr (By != 0.0) b += R(By) * Fy;
+  if constexpr (Bz != 0.0) b += R(Bz) * Fz;
+  V acc = V(b);
+  acc = add_scaled<V, R>(acc, A, uF);
+  acc = add_scaled<V, R>(acc, Cxx, uf[0]);
+  acc = add_scaled<V, R>(acc, Cyy, uf[1]);
+  acc = add_scaled<V, R>(acc, Czz, uf[2]);
+  acc = add_scaled<V, R>(acc, Cxy, uf[3]);
+  acc = add_scaled<V, R>(acc, Cyz, uf[4]);
+  acc = add_scaled<V, R>(acc, Cxz, uf[5]);
+  return acc;
+}
 
 // ---------------------------------------------------------------------------
 // One-cell collision, Eq. mrteqvT:  f* = f - T^-1 [ S (m - m_eq) - (I - S/2) S_F ]
@@ -661,78 +823,108 @@ __host__ __device__ __forceinline__ void collide(V* f, const Rates<R>& s, R Fx, 
     if constexpr (row_even<Q>(K)) return row_sum<Q, K, 0, false>(V(R(0)), ps);
     else return row_sum<Q, K, 0, false>(V(R(0)), pd);
   };
-  V x1;
-  if constexpr (Q == 14) {
-    // e_eq = -7p + u^2 (source 2 u.F)
-    x1 = s.k[1] * (m.template operator()<1>() - (R(-7) * p + u2));
-    if constexpr (FORCE) x1 -= s.h[1] * (R(2) * uF);
+  if constexpr (Q == 26) {
+    // no printed equilibria: every relaxed row from m_eq = T f_eq and the
+    // matching source (moment_eq, moment_source)
+    const V q3 = R(3) * p - R(1.5) * u2;
+    const V uu[6] = {uxx, uyy, uzz, uxy, uyz, uxz};
+    V uf[6] = {V(R(0)), V(R(0)), V(R(0)), V(R(0)), V(R(0)), V(R(0))};
+    if constexpr (FORCE) {
+      uf[0] = R(2) * (ux * Fx);
+      uf[1] = R(2) * (uy * Fy);
+      uf[2] = R(2) * (uz * Fz);
+      uf[3] = sxy;
+      uf[4] = syz;
+      uf[5] = sxz;
+      row.template operator()<2>(V(-Fx * s.h[2]));
+      row.template operator()<4>(V(-Fy * s.h[4]));
+      row.template operator()<6>(V(-Fz * s.h[6]));
+    }
+    auto relax = [&]<int K>() {
+      V xk = s.k[K] * (m.template operator()<K>() - moment_eq<Q, K, V, R>(q3, ux, uy, uz, uu));
+      if constexpr (FORCE) xk -= s.h[K] * moment_source<Q, K, V, R>(uF, Fx, Fy, Fz, uf);
+      row.template operator()<K>(xk);
+    };
+    relax.template operator()<1>();
+    relax.template operator()<3>();
+    relax.template operator()<5>();
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+      (relax.template operator()<K + 7>(), ...);
+    }(std::make_integer_sequence<int, Q - 7>{});
   } else {
-    // e_eq = -p + u^2/2 (source u.F)
-    x1 = s.k[1] * (m.template operator()<1>() - (-p + R(0.5) * u2));
-    if constexpr (FORCE) x1 -= s.h[1] * uF;
-  }
-  row.template operator()<1>(x1);
-  if constexpr (FORCE) {  // momentum rows: s_c (j - u) - (1 - s_c/2) F = -F
-    row.template operator()<2>(V(-Fx * s.h[2]));
-    row.template operator()<4>(V(-Fy * s.h[4]));
-    row.template operator()<6>(V(-Fz * s.h[6]));
-  }
-  // q_eq = -7u/3 (Q14) or -2u/3 (Q18); sources -7F/3 or -2F/3
-  constexpr double cq = Q == 14 ? 7.0 / 3.0 : 2.0 / 3.0;
-  V x3 = s.k[3] * (m.template operator()<3>() + R(cq) * ux);
-  V x5 = s.k[5] * (m.template operator()<5>() + R(cq) * uy);
-  V x7 = s.k[7] * (m.template operator()<7>() + R(cq) * uz);
-  if constexpr (FORCE) {
-    x3 += s.h[3] * (R(cq) * Fx);
-    x5 += s.h[5] * (R(cq) * Fy);
-    x7 += s.h[7] * (R(cq) * Fz);
-  }
-  row.template operator()<3>(x3);
-  row.template operator()<5>(x5);
-  row.template operator()<7>(x7);
-  if constexpr (Q == 14) {
-    V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
-    if constexpr (FORCE) x8 -= s.h[8] * sxx;
-    row.template operator()<8>(x8);
-    V x9 = s.k[9] * (m.template operator()<9>() - pww_eq);
-    if constexpr (FORCE) x9 -= s.h[9] * sww;
-    row.template operator()<9>(x9);
-    V x10 = s.k[10] * (m.template operator()<10>() - uxy);
-    if constexpr (FORCE) x10 -= s.h[10] * sxy;
-    row.template operator()<10>(x10);
-    V x11 = s.k[11] * (m.template operator()<11>() - uyz);
-    if constexpr (FORCE) x11 -= s.h[11] * syz;
-    row.template operator()<11>(x11);
-    V x12 = s.k[12] * (m.template operator()<12>() - uxz);
-    if constexpr (FORCE) x12 -= s.h[12] * sxz;
-    row.template operator()<12>(x12);
-    row.template operator()<13>(s.k[13] * m.template operator()<13>());
-  } else {
-    // 3pi_xx and pi_ww equilibria (and sources) are -1/2 of 3p_xx and p_ww
-    V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
-    if constexpr (FORCE) x8 -= s.h[8] * sxx;
-    row.template operator()<8>(x8);
-    V x9 = s.k[9] * (m.template operator()<9>() + R(0.5) * pxx_eq);
-    if constexpr (FORCE) x9 += s.h[9] * (R(0.5) * sxx);
-    row.template operator()<9>(x9);
-    V x10 = s.k[10] * (m.template operator()<10>() - pww_eq);
-    if constexpr (FORCE) x10 -= s.h[10] * sww;
-    row.template operator()<10>(x10);
-    V x11 = s.k[11] * (m.template operator()<11>() + R(0.5) * pww_eq);
-    if constexpr (FORCE) x11 += s.h[11] * (R(0.5) * sww);
-    row.template operator()<11>(x11);
-    V x12 = s.k[12] * (m.template operator()<12>() - uxy);
-    if constexpr (FORCE) x12 -= s.h[12] * sxy;
-    row.template operator()<12>(x12);
-    V x13 = s.k[13] * (m.template operator()<13>() - uyz);
-    if constexpr (FORCE) x13 -= s.h[13] * syz;
-    row.template operator()<13>(x13);
-    V x14 = s.k[14] * (m.template operator()<14>() - uxz);
-    if constexpr (FORCE) x14 -= s.h[14] * sxz;
-    row.template operator()<14>(x14);
-    row.template operator()<15>(s.k[15] * m.template operator()<15>());
-    row.template operator()<16>(s.k[16] * m.template operator()<16>());
-    row.template operator()<17>(s.k[17] * m.template operator()<17>());
+    V x1;
+    if constexpr (Q == 14) {
+      // e_eq = -7p + u^2 (source 2 u.F)
+      x1 = s.k[1] * (m.template operator()<1>() - (R(-7) * p + u2));
+      if constexpr (FORCE) x1 -= s.h[1] * (R(2) * uF);
+    } else {
+      // e_eq = -p + u^2/2 (source u.F)
+      x1 = s.k[1] * (m.template operator()<1>() - (-p + R(0.5) * u2));
+      if constexpr (FORCE) x1 -= s.h[1] * uF;
+    }
+    row.template operator()<1>(x1);
+    if constexpr (FORCE) {  // momentum rows: s_c (j - u) - (1 - s_c/2) F = -F
+      row.template operator()<2>(V(-Fx * s.h[2]));
+      row.template operator()<4>(V(-Fy * s.h[4]));
+      row.template operator()<6>(V(-Fz * s.h[6]));
+    }
+    // q_eq = -7u/3 (Q14) or -2u/3 (Q18); sources -7F/3 or -2F/3
+    constexpr double cq = Q == 14 ? 7.0 / 3.0 : 2.0 / 3.0;
+    V x3 = s.k[3] * (m.template operator()<3>() + R(cq) * ux);
+    V x5 = s.k[5] * (m.template operator()<5>() + R(cq) * uy);
+    V x7 = s.k[7] * (m.template operator()<7>() + R(cq) * uz);
+    if constexpr (FORCE) {
+      x3 += s.h[3] * (R(cq) * Fx);
+      x5 += s.h[5] * (R(cq) * Fy);
+      x7 += s.h[7] * (R(cq) * Fz);
+    }
+    row.template operator()<3>(x3);
+    row.template operator()<5>(x5);
+    row.template operator()<7>(x7);
+    if constexpr (Q == 14) {
+      V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
+      if constexpr (FORCE) x8 -= s.h[8] * sxx;
+      row.template operator()<8>(x8);
+      V x9 = s.k[9] * (m.template operator()<9>() - pww_eq);
+      if constexpr (FORCE) x9 -= s.h[9] * sww;
+      row.template operator()<9>(x9);
+      V x10 = s.k[10] * (m.template operator()<10>() - uxy);
+      if constexpr (FORCE) x10 -= s.h[10] * sxy;
+      row.template operator()<10>(x10);
+      V x11 = s.k[11] * (m.template operator()<11>() - uyz);
+      if constexpr (FORCE) x11 -= s.h[11] * syz;
+      row.template operator()<11>(x11);
+      V x12 = s.k[12] * (m.template operator()<12>() - uxz);
+      if constexpr (FORCE) x12 -= s.h[12] * sxz;
+      row.template operator()<12>(x12);
+      row.template operator()<13>(s.k[13] * m.template operator()<13>());
+    } else {
+      // 3pi_xx and pi_ww equilibria (and sources) are -1/2 of 3p_xx and p_ww
+      V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
+      if constexpr (FORCE) x8 -= s.h[8] * sxx;
+      row.template operator()<8>(x8);
+      V x9 = s.k[9] * (m.template operator()<9>() + R(0.5) * pxx_eq);
+      if constexpr (FORCE) x9 += s.h[9] * (R(0.5) * sxx);
+      row.template operator()<9>(x9);
+      V x10 = s.k[10] * (m.template operator()<10>() - pww_eq);
+      if constexpr (FORCE) x10 -= s.h[10] * sww;
+      row.template operator()<10>(x10);
+      V x11 = s.k[11] * (m.template operator()<11>() + R(0.5) * pww_eq);
+      if constexpr (FORCE) x11 += s.h[11] * (R(0.5) * sww);
+      row.template operator()<11>(x11);
+      V x12 = s.k[12] * (m.template operator()<12>() - uxy);
+      if constexpr (FORCE) x12 -= s.h[12] * sxy;
+      row.template operator()<12>(x12);
+      V x13 = s.k[13] * (m.template operator()<13>() - uyz);
+      if constexpr (FORCE) x13 -= s.h[13] * syz;
+      row.template operator()<13>(x13);
+      V x14 = s.k[14] * (m.template operator()<14>() - uxz);
+      if constexpr (FORCE) x14 -= s.h[14] * sxz;
+      row.template operator()<14>(x14);
+      row.template operator()<15>(s.k[15] * m.template operator()<15>());
+      row.template operator()<16>(s.k[16] * m.template operator()<16>());
+      row.template operator()<17>(s.k[17] * m.template operator()<17>());
+    }
   }
   // f*_rep = f_rep - (E + O)_rows = E + O, f*_partner = E - O
   [&]<int... I>(std::integer_sequence<int, I...>) {

@@ -70,6 +70,10 @@ cudaError_t launch_neq(const DomainDesc& d, int64_t n, cudaStream_t st) {
     case 181: launch_typed<18, float, float>(d, n, a, st); break;
     case 182: launch_typed<18, __half, float>(d, n, a, st); break;
     case 183: launch_typed<18, __nv_bfloat16, float>(d, n, a, st); break;
+    case 260: launch_typed<26, double, double>(d, n, a, st); break;
+    case 261: launch_typed<26, float, float>(d, n, a, st); break;
+    case 262: launch_typed<26, __half, float>(d, n, a, st); break;
+    case 263: launch_typed<26, __nv_bfloat16, float>(d, n, a, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -28,7 +28,8 @@ cudaError_t launch_solid_links(const DomainDesc& d, const uint8_t* bytes, uint32
   const int64_t blocks64 = (d.N + 255) / 256;
   const int blocks = (int)(blocks64 < 8192 ? blocks64 : 8192);
   if (d.Q == 14) k_solid_links<14><<<blocks, 256, 0, st>>>(d.nx, d.ny, d.nz, per, d.sym, bytes, links);
-  else k_solid_links<18><<<blocks, 256, 0, st>>>(d.nx, d.ny, d.nz, per, d.sym, bytes, links);
+  else if (d.Q == 18) k_solid_links<18><<<blocks, 256, 0, st>>>(d.nx, d.ny, d.nz, per, d.sym, bytes, links);
+  else k_solid_links<26><<<blocks, 256, 0, st>>>(d.nx, d.ny, d.nz, per, d.sym, bytes, links);
   return cudaGetLastError();
 }
 

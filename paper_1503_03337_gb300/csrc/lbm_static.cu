@@ -171,7 +171,8 @@ extern "C" int lbm_reductions_static(const lbm_desc* desc, const lbm_geom* geom,
                                      int64_t prev_step, lbm_stats* out, void* cuda_stream) {
   if (!desc || !geom || !params || !populations || !out)
     return static_fail(LBM_EINVAL, "null argument");
-  if (desc->Q != 14 && desc->Q != 18) return static_fail(LBM_EINVAL, "Q must be 14 or 18");
+  if (desc->Q != 14 && desc->Q != 18 && desc->Q != 26)
+    return static_fail(LBM_EINVAL, "Q must be 14, 18 or 26");
   if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1 || step < 0)
     return static_fail(LBM_EINVAL, "grid sizes must be >= 1 and step >= 0");
   if (desc->storage < LBM_STORAGE_F64 || desc->storage > LBM_STORAGE_BF16)
@@ -223,12 +224,19 @@ extern "C" int lbm_reductions_static(const lbm_desc* desc, const lbm_geom* geom,
       case LBM_STORAGE_F16: launch.template operator()<14, __half>(); break;
       default: launch.template operator()<14, __nv_bfloat16>(); break;
     }
-  } else {
+  } else if (dd.Q == 18) {
     switch (dd.storage) {
       case LBM_STORAGE_F64: launch.template operator()<18, double>(); break;
       case LBM_STORAGE_F32: launch.template operator()<18, float>(); break;
       case LBM_STORAGE_F16: launch.template operator()<18, __half>(); break;
       default: launch.template operator()<18, __nv_bfloat16>(); break;
+    }
+  } else {
+    switch (dd.storage) {
+      case LBM_STORAGE_F64: launch.template operator()<26, double>(); break;
+      case LBM_STORAGE_F32: launch.template operator()<26, float>(); break;
+      case LBM_STORAGE_F16: launch.template operator()<26, __half>(); break;
+      default: launch.template operator()<26, __nv_bfloat16>(); break;
     }
   }
   e = cudaGetLastError();

@@ -1,5 +1,6 @@
 // Single-domain step: descriptor conversion, force time level, default launch
-// shape, and dispatch to the per-Q kernel files (lbm_step_q14.cu / _q18.cu).
+// shape, and dispatch to the per-Q kernel files (lbm_step_q14.cu, _q18.cu,
+// _q26.cu).
 #include <cmath>
 
 #include "lbm_internal.h"
@@ -31,11 +32,13 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]) {
   o.s.spi = R(d.s[4]);
   o.s.st = R(d.s[5]);
   if (d.Q == 14) scale_rows<14>(o.s);
-  else scale_rows<18>(o.s);
+  else if (d.Q == 18) scale_rows<18>(o.s);
+  else scale_rows<26>(o.s);
   for (int k = 0; k < 3; ++k) o.F[k] = R(F[k]);
   o.key = 0;
   if (d.Q == 14) fill_offsets<14>(o);
-  else fill_offsets<18>(o);
+  else if (d.Q == 18) fill_offsets<18>(o);
+  else fill_offsets<26>(o);
   return o;
 }
 template Domain<double> to_domain<double>(const DomainDesc&, const double*);
@@ -97,11 +100,13 @@ BlockShape default_block(int nx, int ny) {
 
 cudaError_t launch_step_q14(const DomainDesc& d, int64_t n, BlockShape b, cudaStream_t st);
 cudaError_t launch_step_q18(const DomainDesc& d, int64_t n, BlockShape b, cudaStream_t st);
+cudaError_t launch_step_q26(const DomainDesc& d, int64_t n, BlockShape b, cudaStream_t st);
 
 cudaError_t launch_step(const DomainDesc& d, int64_t n, BlockShape b, cudaStream_t st) {
   if (d.N == 0) return cudaSuccess;
   if (d.Q == 14) return launch_step_q14(d, n, b, st);
   if (d.Q == 18) return launch_step_q18(d, n, b, st);
+  if (d.Q == 26) return launch_step_q26(d, n, b, st);
   return cudaErrorInvalidValue;
 }
 

@@ -14,8 +14,18 @@ namespace lbm {
 template <typename R>
 Domain<R> to_domain(const DomainDesc& d, const double F[3]);
 
+// Resident 256-thread blocks per SM the register budget is sized for: four
+// (64 registers a thread) for Q = 14 and 18 with 4- or 2-byte storage, two
+// for FP64 and for Q = 26 (whose 26 populations and 13 pair accumulators
+// spill at 64), one for Q = 26 in FP64.
+template <int Q, typename S>
+constexpr int step_min_blocks() {
+  if (Q == 26) return sizeof(S) == 8 ? 1 : 2;
+  return sizeof(S) == 8 ? 2 : 4;
+}
+
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 4) k_step(Domain<R> d) {
+__global__ void __launch_bounds__(256, step_min_blocks<Q, S>()) k_step(Domain<R> d) {
   pdl_release();
   pdl_acquire();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,8 +67,10 @@ template <int Q, typename S, typename R, bool SR>
 void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 block,
                           const BlockShape& b, cudaStream_t st) {
   // two cells per thread: even steps of FP32 / FP16 / BF16 storage with nx
-  // even and no solid nodes; every other step runs one cell per thread
-  if constexpr (sizeof(S) <= 4) {
+  // even and no solid nodes, Q = 14 or 18 (the 52 packed values of a Q = 26
+  // pair would not fit the registers); every other step runs one cell per
+  // thread
+  if constexpr (sizeof(S) <= 4 && Q != 26) {
     if (b.cpt == 2 && !odd && d.nx % 2 == 0 && !d.solid) {
       grid.x = (d.nx / 2 + block.x - 1) / block.x;
       if (force) launch_one(k_step_pair<Q, S, true, SR>, d, grid, block, b.pdl != 0, st);

@@ -11,6 +11,17 @@
 using namespace lbm;
 
 static int g_sr = 0;
+
+// fn.template operator()<Q>() for Q = 14, 18 or 26; -1 for any other Q
+template <typename Fn>
+static int with_q(int Q, Fn&& fn) {
+  switch (Q) {
+    case 14: fn.template operator()<14>(); return 0;
+    case 18: fn.template operator()<18>(); return 0;
+    case 26: fn.template operator()<26>(); return 0;
+  }
+  return -1;
+}
 static const uint32_t* g_solid = nullptr;  // solid-link words (Domain::solid) or null
 
 template <int Q, typename S, typename R>
@@ -98,16 +109,10 @@ template <typename S, typename R>
 static int canon_any(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
                      const double* uw, double* canon, int64_t n, int to_storage) {
   const bool odd = n & 1;
-  if (Q == 14) {
-    if (odd) canonical_typed<14, S, R, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-    else canonical_typed<14, S, R, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-  } else if (Q == 18) {
-    if (odd) canonical_typed<18, S, R, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-    else canonical_typed<18, S, R, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-  } else {
-    return -1;
-  }
-  return 0;
+  return with_q(Q, [&]<int QQ>() {
+    if (odd) canonical_typed<QQ, S, R, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
+    else canonical_typed<QQ, S, R, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
+  });
 }
 
 // The extrapolation pass over every boundary node, on the populations of
@@ -148,41 +153,31 @@ void emu_set_stochastic(int on) { g_sr = on; }
 int emu_solid_links(int Q, int nx, int ny, int nz, int per, int sym, const uint8_t* bytes,
                     uint32_t* out) {
   const int64_t N = (int64_t)nx * ny * nz;
-  for (int64_t i = 0; i < N; ++i)
-    out[i] = Q == 14 ? solid_link_bits<14>(nx, ny, nz, per, sym, bytes, i)
-                     : solid_link_bits<18>(nx, ny, nz, per, sym, bytes, i);
-  return 0;
+  return with_q(Q, [&]<int QQ>() {
+    for (int64_t i = 0; i < N; ++i) out[i] = solid_link_bits<QQ>(nx, ny, nz, per, sym, bytes, i);
+  });
 }
 void emu_set_solid(const uint32_t* links) { g_solid = links; }
 
 int emu_neq(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym,
             const double* uw, int vel, int pre, const double* pb, const double* F, int64_t n) {
   const bool odd = n & 1;
-  if (Q == 14) {
-    if (odd) neq_typed<14, true>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
-    else neq_typed<14, false>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
-  } else if (Q == 18) {
-    if (odd) neq_typed<18, true>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
-    else neq_typed<18, false>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
-  } else {
-    return -1;
-  }
-  return 0;
+  return with_q(Q, [&]<int QQ>() {
+    if (odd) neq_typed<QQ, true>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
+    else neq_typed<QQ, false>(f, nx, ny, nz, per, moving, sym, uw, vel, pre, pb, F);
+  });
 }
 
 // storage: 0 double, 1 float, 2 half, 3 bfloat16
 int emu_step(int Q, int storage, void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
              const double* uw, const double* s, const double* F, int64_t n) {
-  if (Q == 14 && storage == 0) step_typed<14, double, double>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else if (Q == 18 && storage == 0) step_typed<18, double, double>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else if (Q == 14 && storage == 1) step_typed<14, float, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else if (Q == 18 && storage == 1) step_typed<18, float, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else if (Q == 14 && storage == 2) step_typed<14, __half, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else if (Q == 18 && storage == 2) step_typed<18, __half, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else if (Q == 14 && storage == 3) step_typed<14, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else if (Q == 18 && storage == 3) step_typed<18, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
-  else return -1;
-  return 0;
+  if (storage < 0 || storage > 3) return -1;
+  return with_q(Q, [&]<int QQ>() {
+    if (storage == 0) step_typed<QQ, double, double>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+    else if (storage == 1) step_typed<QQ, float, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+    else if (storage == 2) step_typed<QQ, __half, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+    else step_typed<QQ, __nv_bfloat16, float>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, s, F, n);
+  });
 }
 
 // canonical f (FP64) <-> storage layout of parity n (double storage only)
@@ -200,30 +195,16 @@ int emu_canonical_storage(int Q, int storage, void* f, int nx, int ny, int nz, c
 
 int emu_canonical(int Q, void* f, int nx, int ny, int nz, const int* per, int moving, int sym, const int* eaxis, const double* escale,
                   const double* uw, double* canon, int64_t n, int to_storage) {
-  const bool odd = n & 1;
-  if (Q == 14) {
-    if (odd) canonical_typed<14, double, double, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-    else canonical_typed<14, double, double, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-  } else if (Q == 18) {
-    if (odd) canonical_typed<18, double, double, true>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-    else canonical_typed<18, double, double, false>(f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, to_storage);
-  } else {
-    return -1;
-  }
-  return 0;
+  return canon_any<double, double>(Q, f, nx, ny, nz, per, moving, sym, eaxis, escale, uw, canon, n,
+                                   to_storage);
 }
 
 int emu_collide(int Q, const double* s, double* f, const double* F) {
   Rates<double> r{s[0], s[1], s[2], s[3], s[4], s[5], {}, {}};
   double ux, uy, uz;
-  if (Q == 14) {
-    scale_rows<14>(r);
-    collide<14, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
-  } else if (Q == 18) {
-    scale_rows<18>(r);
-    collide<18, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
-  }
-  else return -1;
-  return 0;
+  return with_q(Q, [&]<int QQ>() {
+    scale_rows<QQ>(r);
+    collide<QQ, true>(f, r, F[0], F[1], F[2], ux, uy, uz);
+  });
 }
 }

@@ -66,7 +66,7 @@ def neq_case(Q, name, shape, faces, storage, oscillate):
 @pytest.mark.parametrize("oscillate", (False, True))
 @pytest.mark.parametrize("steps", (1, 2, 37))
 @pytest.mark.parametrize("name,shape,faces", CASES)
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_parity(Q, name, shape, faces, steps, oscillate):
     """FP64 storage, random state, random wall velocities and face
     pressures, body force: populations and velocity within 1e-12 relative of
@@ -77,7 +77,7 @@ def test_fp64_parity(Q, name, shape, faces, steps, oscillate):
     assert rel_max(g["u"], o["u"]) <= 1e-12
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_parity_1000_steps(Q):
     """The Sec. 4.1 duct at dx = 1/8 from rest, 1000 steps: 1e-12."""
     case = inputs.pressure_duct(Q, 1.0 / 8, 1.0)
@@ -86,7 +86,7 @@ def test_fp64_parity_1000_steps(Q):
     assert rel_max(g["u"], o["u"]) <= 1e-12
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_reduced_storage_parity(Q):
     """The Sec. 4.1 duct at dx = 1/16 from rest, 1000 steps, populations
     stored as deviations from the mean pressure: FP32 storage within 1e-5 U

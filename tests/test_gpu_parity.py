@@ -1,4 +1,5 @@
-"""CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+"""CUDA path (through the C-ABI) against the FP64 oracle, element by element,
+for the iD3Q14, iD3Q18 and iD3Q26 models.
 
 Bounds: FP64 build <= 1e-12 relative after 1000 steps; FP32 storage
 <= 1e-5 U; FP16 storage <= 1e-3 U (U the case's velocity scale)."""
@@ -28,7 +29,7 @@ def both(case, steps):
     return gpu_run(case, steps), oracle_run(case, steps)
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_duct_1000_steps(Q):
     """Duct 16x16x32 (x,y walls, z periodic, body force), FP64, 1000 steps."""
     case = inputs.duct(Q, 16, 32, nu=0.1, u_max=0.02, storage="f64")
@@ -38,7 +39,7 @@ def test_fp64_duct_1000_steps(Q):
     assert rel_max(g["p"], o["p"]) <= 1e-11
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_cavity_1000_steps(Q):
     """Lid-driven cube 24^3 at Re 100, FP64, 1000 steps."""
     case = inputs.cavity(Q, 24, 100.0, storage="f64")
@@ -47,7 +48,7 @@ def test_fp64_cavity_1000_steps(Q):
     assert rel_max(g["f"], o["f"]) <= 1e-12
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_pulsatile_odd_steps(Q):
     """Oscillating force (period 100), ends on an odd step count."""
     case = inputs.pulsatile(Q, 16, 4, 100, 4.0, 2e-4, storage="f64")
@@ -79,7 +80,7 @@ def seed(*key):
     return zlib.crc32(repr(key).encode())
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces", EDGE)
 @pytest.mark.parametrize("steps", (1, 2, 37))
 def test_fp64_edge_cases(Q, name, shape, faces, steps):
@@ -125,11 +126,12 @@ def test_two_cells_per_thread(Q, name, shape, faces, storage):
 
 
 @pytest.mark.parametrize("launch", ((32, 2, 2), (64, 1, 2), (32, 1, 1), (64, 2, 1)))
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces", PAIR_CASES)
 def test_fp32_launch_shapes(Q, name, shape, faces, launch):
-    """Every launch shape, including two cells per thread, against the
-    oracle from a seeded random state (odd step count)."""
+    """Every launch shape, including two cells per thread (which Q26 accepts
+    and runs one cell per thread), against the oracle from a seeded random
+    state (odd step count)."""
     rng = np.random.default_rng(seed(name, Q))
     uw = rng.normal(size=(6, 3)) * 0.03
     case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
@@ -141,7 +143,7 @@ def test_fp32_launch_shapes(Q, name, shape, faces, launch):
     assert np.max(np.abs(g["u"] - o["u"])) <= 1e-5 * case.u_ref
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp32_cavity(Q):
     case = inputs.cavity(Q, 32, 400.0, storage="f32")
     g, o = both(case, 1000)
@@ -149,7 +151,7 @@ def test_fp32_cavity(Q):
     assert err <= 1e-5 * case.u_ref, err
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp32_duct(Q):
     case = inputs.duct(Q, 16, 32, nu=0.1, u_max=0.02, storage="f32")
     g, o = both(case, 1000)
@@ -158,7 +160,7 @@ def test_fp32_duct(Q):
 
 
 @pytest.mark.parametrize("launch", ((64, 1, 2), (64, 1, 1)))
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp16_pulsatile_stochastic_within_1e3(Q, launch):
     """FP16 storage with stochastic rounding on the oscillating-force channel,
     two cells per thread on even steps (the benchmarked launch) and one:
@@ -190,7 +192,7 @@ RMS_BOUND = {"f16": 3e-4, "bf16": 3e-3}
     ("f16", "nearest", (64, 1, 2)), ("f16", "stochastic", (64, 1, 2)),
     ("f16", "stochastic", (64, 1, 1)), ("bf16", "stochastic", (64, 1, 2)),
     ("bf16", "nearest", (64, 1, 1))])
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_reduced_precision_cavity(Q, storage, rounding, launch):
     case = inputs.cavity(Q, 32, 400.0, storage="f64")
     o = oracle_run(case, 1000)
@@ -209,7 +211,7 @@ def test_reduced_precision_cavity(Q, storage, rounding, launch):
     assert erms <= RMS_BOUND[storage] * U, erms / U
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_lbgk_special_case(Q):
     """S = (1/tau) I (every rate equal): the GPU path runs the LBGK special
     case of the model (pinned against the LBGK step in the oracle tests) and

@@ -48,7 +48,7 @@ def solid_case(Q, name, shape, faces, frac, storage):
 @pytest.mark.parametrize("launch", ((64, 1, 1), (32, 4, 1), (128, 2, 1)))
 @pytest.mark.parametrize("steps", (1, 2, 37))
 @pytest.mark.parametrize("name,shape,faces,frac", CASES)
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_parity(Q, name, shape, faces, frac, steps, launch):
     """FP64, random solid nodes with every face kind they combine with: the
     populations (zero at solid nodes) and velocity within 1e-12 of the
@@ -60,7 +60,7 @@ def test_fp64_parity(Q, name, shape, faces, frac, steps, launch):
     assert np.all(g["u"][:, case.solid.astype(bool)] == 0.0)
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_reduced_storage_porous_channel(Q):
     """A channel with random obstacles (periodic, body force), from rest,
     500 steps: FP32 storage within 1e-5 U of the oracle (U = max |u|); FP16
@@ -89,7 +89,7 @@ def test_reduced_storage_porous_channel(Q):
     assert err["f16"] <= max(1e-3 * U, 3.0 * 2.0 ** 13 * err["f32"])
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_reductions_checkpoint_and_clear(Q):
     """Reductions sum the fluid nodes only (against the oracle's fields);
     a checkpoint written back at an odd step restores the run bit for bit;

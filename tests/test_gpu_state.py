@@ -48,7 +48,7 @@ def test_checkpoint_restore_bit_exact(storage, split):
     np.testing.assert_array_equal(fa, fb)
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_reductions_match_fields(Q):
     """FP64 reductions (residual numerators/denominators, mass, flux, max)
     against sums of the read-back oracle fields."""
@@ -83,7 +83,7 @@ def test_reductions_match_fields(Q):
     assert abs(r - np.abs(ub[2] - ua[2]).sum() / np.abs(ub[2]).sum()) < 1e-12
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_residual_criteria_match_oracle_fields(Q):
     """lbm_residual (Eq. sc, Eq. cr, Eq. cavity_creterion) on the GPU's FP64
     reductions against the oracle's residual forms of the oracle's velocity
@@ -141,7 +141,7 @@ def test_residual_criteria_match_oracle_fields(Q):
         lbm.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_residual_resolves_1e14(Q):
     """Eq. cavity_creterion's 1e-14 (Sec. 4.3) is resolvable: a FP64 duct
     (the storage whose reductions run in FP64) converging from rest drives
@@ -201,7 +201,7 @@ def test_unstable_run_reported():
         lbm.lbm_destroy(h)
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_full_size_single_steps(Q):
     """128^3 FP32 cavity in the benchmark's launch configuration: from a
     seeded random state, each of an even and an odd step matches one oracle
@@ -299,7 +299,7 @@ def test_overlap_does_not_change_results(storage):
 
 @pytest.mark.parametrize("sym", (False, True))
 @pytest.mark.parametrize("storage", ("f32", "f16", "bf16"))
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_pair_reductions_match_fields(Q, storage, sym):
     """The 32- and 16-bit storage reductions (FP32 pair arithmetic) against
     FP64 sums of the read-back fields, on an odd and an even step, with a

@@ -32,7 +32,7 @@ def full_of(half):
     return c
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_half_cavity_equals_full_cavity(Q):
     """FP64 half cavity 17 x 17 x 9 on the GPU, 301 steps (odd), against
     the lower half of the oracle's full 17 x 17 x 18 box: populations and
@@ -50,7 +50,7 @@ def test_fp64_half_cavity_equals_full_cavity(Q):
 
 @pytest.mark.parametrize("launch", ((64, 1, 1), (64, 2, 2)))
 @pytest.mark.parametrize("storage,tol", (("f32", 1e-5), ("f16", 1e-2), ("bf16", 6e-2)))
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_half_cavity_equals_full_box(Q, storage, tol, launch):
     """32- and 16-bit storage: the half cavity 48 x 48 x 24 and the lower
     half of the full 48 x 48 x 48 box on the GPU, both at the same
@@ -67,7 +67,7 @@ def test_half_cavity_equals_full_box(Q, storage, tol, launch):
     assert np.max(np.abs(h["u"])) > 0.1 * half.u_ref
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_half_duct_with_two_symmetry_faces(Q):
     """A quarter of the square duct (symmetry faces at x+ and y+, walls at
     x- and y-, z periodic, body force), FP64, 400 steps, against the oracle's
@@ -96,7 +96,7 @@ EDGE_CASES = [
 
 @pytest.mark.parametrize("steps", (1, 2, 37))
 @pytest.mark.parametrize("name,shape,faces,edge", EDGE_CASES)
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_fp64_edge_profiles(Q, name, shape, faces, edge, steps):
     """Moving faces with edge profiles (the lid corner velocities of Sec.
     4.3), FP64, from a seeded random state, against the oracle to 1e-12."""
@@ -110,7 +110,7 @@ def test_fp64_edge_profiles(Q, name, shape, faces, edge, steps):
     assert rel_max(g["u"], o["u"]) <= 1e-12
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_ku_half_cavity_fp64_and_fp32(Q):
     """The Sec. 4.3 setup: half cavity 25 x 25 x 13, lid 0.1 with the corner
     velocities, Re 400, 401 steps.  FP64 against the oracle to 1e-12; FP32

@@ -55,7 +55,7 @@ def _d(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_collide_matches_oracle(emu, Q):
     rng = np.random.default_rng(21)
     for _ in range(50):
@@ -144,7 +144,7 @@ EDGE = [
 ]
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces,edge", EDGE)
 def test_step_matches_oracle(emu, Q, name, shape, faces, edge):
     rng = np.random.default_rng(5)
@@ -168,7 +168,7 @@ def test_step_matches_oracle(emu, Q, name, shape, faces, edge):
         assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (d.n,)
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 def test_restore_at_odd_parity(emu, Q):
     """Canonical populations written at an odd step read back unchanged."""
     faces = (1, 2, 0, 0, 2, 1)
@@ -180,7 +180,7 @@ def test_restore_at_odd_parity(emu, Q):
 
 
 @pytest.mark.parametrize("storage,dtype,tol", ((1, np.float32, 2e-6), (2, np.float16, 3e-3)))
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces,edge", [e for e in EDGE if e[0] in
                                                    ("sym_lid", "sym_corner", "edge_multi",
                                                     "sym_wide_x")])
@@ -227,7 +227,7 @@ NEQ = [
 
 
 @pytest.mark.parametrize("oscillate", (False, True))
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces", NEQ)
 def test_extrapolation_boundaries_match_oracle(emu, Q, name, shape, faces, oscillate):
     """The fused step followed by the kernel's extrapolation pass (the
@@ -278,7 +278,7 @@ SOLID = [
 ]
 
 
-@pytest.mark.parametrize("Q", (14, 18))
+@pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces,frac", SOLID)
 def test_solid_nodes_match_oracle(emu, Q, name, shape, faces, frac):
     """The kernel's per-cell code with a random solid-node mask (link words

@@ -90,6 +90,8 @@ WIDE_CASES = {
     # symmetry face on z+, moving lid on y+ with the corner edge profile
     "half_cavity": lambda st: inputs.half_cavity(18, 17, 200.0, U=0.05, storage=st,
                                                  ku_lid=True),
+    # the iD3Q26 model on the lid-driven cube
+    "cavity_q26": lambda st: inputs.cavity(26, 13, 100.0, storage=st),
 }
 
 
