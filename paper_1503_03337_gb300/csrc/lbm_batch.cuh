@@ -1,7 +1,8 @@
 // Device side of the batched stepping (lbm_batch.cu): the descriptor table
 // entry, the bounded grid barrier, the per-tile update and the grouped
-// kernels.  The grouped kernels are instantiated per Q in lbm_batch_g14.cu /
-// lbm_batch_g18.cu so that their variants compile in parallel.
+// kernels.  The grouped and solo kernels are instantiated per Q in
+// lbm_batch_g14.cu / _g18.cu and lbm_batch_s14.cu / _s18.cu so that their
+// variants compile in parallel.
 #pragma once
 
 #include <cuda_runtime.h>

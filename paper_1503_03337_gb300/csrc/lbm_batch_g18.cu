@@ -1,4 +1,5 @@
-// Grouped and solo batch kernels for Q = 18 (see lbm_batch.cuh).
+// Grouped batch kernels for Q = 18 (see lbm_batch.cuh); the solo kernels
+// are in lbm_batch_s18.cu, so the two compile in parallel.
 #include "lbm_batch.cuh"
 
 namespace lbm {
@@ -6,10 +7,6 @@ namespace batchk {
 
 cudaError_t launch_group_q18(const GroupLaunch& g) {
   return launch_by_storage<18, GroupLaunch, GroupOp>(g);
-}
-
-cudaError_t launch_solo_q18(const SoloLaunch& g) {
-  return launch_by_storage<18, SoloLaunch, SoloOp>(g);
 }
 
 int group_blocks_per_sm(int threads) {
