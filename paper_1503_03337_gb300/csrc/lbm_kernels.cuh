@@ -17,7 +17,7 @@
 // Each update therefore moves exactly 2Q stored values.
 #pragma once
 
-#include "lbm_model.cuh"
+#include "lbm_collide.cuh"
 
 namespace lbm {
 

@@ -505,18 +505,20 @@ __host__ __device__ __forceinline__ float fmadd(float a, float b, float c) { ret
 __host__ __device__ __forceinline__ double fmadd(double a, double b, double c) {
   return a * b + c;
 }
+// integer form, for compile-time checks of the transforms
+__host__ __device__ constexpr int fmadd(int a, int b, int c) { return a * b + c; }
 
 // ---------------------------------------------------------------------------
 // Unrolled transforms over pairs
 // ---------------------------------------------------------------------------
 template <int C, typename V>
-__host__ __device__ __forceinline__ V term_first(V x) {
+__host__ __device__ __forceinline__ constexpr V term_first(V x) {
   if constexpr (C == 1) return x;
   else if constexpr (C == -1) return -x;
   else return V(C) * x;
 }
 template <int C, typename V>
-__host__ __device__ __forceinline__ V term_add(V acc, V x) {
+__host__ __device__ __forceinline__ constexpr V term_add(V acc, V x) {
   if constexpr (C == 1) return acc + x;
   else if constexpr (C == -1) return acc - x;
   else return fmadd(V(C), x, acc);
@@ -579,11 +581,12 @@ __host__ __device__ __forceinline__ void back_transform(const R* x, R* f) {
 template <typename R>
 struct Rates {
   R sc, se, sq, snu, spi, st;
-  // Per row K of T, with D_K its norm: k[K] = s_K / D_K and
+  // Per row K of T, with D_K its norm: k[K] = s_K / D_K,
   // h[K] = (1 - s_K/2) / D_K (for the momentum rows, which carry only the
-  // force, h[K] = 1 / D_K).  Filled once per launch by scale_rows, so the
-  // collision multiplies each relaxed row once.
-  R k[26], h[26];
+  // force, h[K] = 1 / D_K) and g[K] = (1 - s_K) / D_K, so that the
+  // post-collision row over its norm is g m + k m_eq + h S_F.  Filled once
+  // per launch by scale_rows, so the collision multiplies each row once.
+  R k[26], h[26], g[26];
 };
 
 // Relaxation rate of row K (Eq. sD3Q15meaning / Eq. sD3Q19): conserved rows
@@ -612,12 +615,14 @@ __host__ __device__ inline void scale_rows(Rates<R>& r) {
   for (int K = 0; K < 26; ++K) {
     r.k[K] = R(0);
     r.h[K] = R(0);
+    r.g[K] = R(0);
   }
   for (int K = 0; K < Q; ++K) {
     const R inv = R(1.0 / row_norm<Q>(K));
     const R sk = rate_of<Q>(r, K);
     r.k[K] = sk * inv;
     r.h[K] = (K == 2 || K == 4 || K == 6) ? inv : (R(1) - R(0.5) * sk) * inv;
+    r.g[K] = (R(1) - sk) * inv;
   }
 }
 
@@ -749,187 +754,6 @@ __host__ __device__ __forceinline__ V moment_source(V uF, R Fx, R Fy, R Fz, cons
   acc = add_scaled<V, R>(acc, Cyz, uf[4]);
   acc = add_scaled<V, R>(acc, Cxz, uf[5]);
   return acc;
-}
-
-// ---------------------------------------------------------------------------
-// One-cell collision, Eq. mrteqvT:  f* = f - T^-1 [ S (m - m_eq) - (I - S/2) S_F ]
-//
-// u = j + F/2 and p from Eq. hgl.  The Guo source S_F is the derivative of
-// the equilibrium moments along F at fixed p (the first-order rows give F,
-// the quadratic ones 2 B(u, F) for m_eq = B(u, u)); its P row is zero, so P
-// stays a collision invariant.  Because p is computed from P, P - P_eq = 0
-// exactly and j - u = -F/2, so the conserved rows contribute only -F to the
-// momentum rows whatever s_c is.
-// On return f holds f*, and (ux,uy,uz) the velocity of the pre-collision state.
-// ---------------------------------------------------------------------------
-// V is the value type (float, double, or pf2 for two cells at once) and R
-// the scalar type of rates, force and constants.
-template <int Q, bool FORCE, typename V, typename R>
-__host__ __device__ __forceinline__ void collide(V* f, const Rates<R>& s, R Fx, R Fy,
-                                                 R Fz, V& ux, V& uy, V& uz) {
-  constexpr int NP = Q / 2;
-  V ps[NP], pd[NP];
-  // pair sums and differences; f itself is not needed again
-  [&]<int... I>(std::integer_sequence<int, I...>) {
-    ((ps[I] = f[pair_rep<Q>(I)] + f[opposite<Q>(pair_rep<Q>(I))],
-      pd[I] = f[pair_rep<Q>(I)] - f[opposite<Q>(pair_rep<Q>(I))]),
-     ...);
-  }(std::make_integer_sequence<int, NP>{});
-
-  // conserved moments, velocity (Eq. hgl with the force half step), pressure
-  const V P = row_sum<Q, 0, 0, false>(V(R(0)), ps);
-  const V jx = row_sum<Q, 2, 0, false>(V(R(0)), pd);
-  const V jy = row_sum<Q, 4, 0, false>(V(R(0)), pd);
-  const V jz = row_sum<Q, 6, 0, false>(V(R(0)), pd);
-  if constexpr (FORCE) {
-    ux = jx + R(0.5) * Fx;
-    uy = jy + R(0.5) * Fy;
-    uz = jz + R(0.5) * Fz;
-  } else {
-    ux = jx;
-    uy = jy;
-    uz = jz;
-  }
-  const V uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
-  const V u2 = uxx + uyy + uzz;
-  constexpr double cs2 = 1.0 / 3.0;
-  constexpr double w0 = Lattice<Q>::w0;
-  const V p = R(cs2 / (1.0 - w0)) * (P - R(w0 / (2.0 * cs2)) * u2);
-
-  const V uxy = ux * uy, uyz = uy * uz, uxz = ux * uz;
-  const V pxx_eq = R(3) * uxx - u2;  // 3 p_xx
-  const V pww_eq = uyy - uzz;
-  // force terms: derivative along F of the quadratic equilibria
-  V uF = V(R(0)), sxx = V(R(0)), sww = V(R(0)), sxy = V(R(0)), syz = V(R(0)), sxz = V(R(0));
-  if constexpr (FORCE) {
-    uF = ux * Fx + uy * Fy + uz * Fz;
-    sxx = R(6) * ux * Fx - R(2) * uF;
-    sww = R(2) * (uy * Fy - uz * Fz);
-    sxy = ux * Fy + uy * Fx;
-    syz = uy * Fz + uz * Fy;
-    sxz = ux * Fz + uz * Fx;
-  }
-
-  // x_K = (S (m - m_eq) - (I - S/2) S_F)_K / D_K, streamed into the pair
-  // accumulators E = s/2 - sum_even phi x and O = d/2 - sum_odd phi x, so
-  // that f*_rep = E + O and f*_partner = E - O at the end
-  V E[NP], O[NP];
-  [&]<int... I>(std::integer_sequence<int, I...>) {
-    ((E[I] = R(0.5) * ps[I], O[I] = R(0.5) * pd[I]), ...);
-  }(std::make_integer_sequence<int, NP>{});
-  // xk arrives divided by D_K (the factors of s.k and s.h)
-  auto row = [&]<int K>(V xk) { add_row<Q, FORCE, K>(xk, E, O); };
-  auto m = [&]<int K>() {
-    if constexpr (row_even<Q>(K)) return row_sum<Q, K, 0, false>(V(R(0)), ps);
-    else return row_sum<Q, K, 0, false>(V(R(0)), pd);
-  };
-  if constexpr (Q == 26) {
-    // no printed equilibria: every relaxed row from m_eq = T f_eq and the
-    // matching source (moment_eq, moment_source)
-    const V q3 = R(3) * p - R(1.5) * u2;
-    const V uu[6] = {uxx, uyy, uzz, uxy, uyz, uxz};
-    V uf[6] = {V(R(0)), V(R(0)), V(R(0)), V(R(0)), V(R(0)), V(R(0))};
-    if constexpr (FORCE) {
-      uf[0] = R(2) * (ux * Fx);
-      uf[1] = R(2) * (uy * Fy);
-      uf[2] = R(2) * (uz * Fz);
-      uf[3] = sxy;
-      uf[4] = syz;
-      uf[5] = sxz;
-      row.template operator()<2>(V(-Fx * s.h[2]));
-      row.template operator()<4>(V(-Fy * s.h[4]));
-      row.template operator()<6>(V(-Fz * s.h[6]));
-    }
-    auto relax = [&]<int K>() {
-      V xk = s.k[K] * (m.template operator()<K>() - moment_eq<Q, K, V, R>(q3, ux, uy, uz, uu));
-      if constexpr (FORCE) xk -= s.h[K] * moment_source<Q, K, V, R>(uF, Fx, Fy, Fz, uf);
-      row.template operator()<K>(xk);
-    };
-    relax.template operator()<1>();
-    relax.template operator()<3>();
-    relax.template operator()<5>();
-    [&]<int... K>(std::integer_sequence<int, K...>) {
-      (relax.template operator()<K + 7>(), ...);
-    }(std::make_integer_sequence<int, Q - 7>{});
-  } else {
-    V x1;
-    if constexpr (Q == 14) {
-      // e_eq = -7p + u^2 (source 2 u.F)
-      x1 = s.k[1] * (m.template operator()<1>() - (R(-7) * p + u2));
-      if constexpr (FORCE) x1 -= s.h[1] * (R(2) * uF);
-    } else {
-      // e_eq = -p + u^2/2 (source u.F)
-      x1 = s.k[1] * (m.template operator()<1>() - (-p + R(0.5) * u2));
-      if constexpr (FORCE) x1 -= s.h[1] * uF;
-    }
-    row.template operator()<1>(x1);
-    if constexpr (FORCE) {  // momentum rows: s_c (j - u) - (1 - s_c/2) F = -F
-      row.template operator()<2>(V(-Fx * s.h[2]));
-      row.template operator()<4>(V(-Fy * s.h[4]));
-      row.template operator()<6>(V(-Fz * s.h[6]));
-    }
-    // q_eq = -7u/3 (Q14) or -2u/3 (Q18); sources -7F/3 or -2F/3
-    constexpr double cq = Q == 14 ? 7.0 / 3.0 : 2.0 / 3.0;
-    V x3 = s.k[3] * (m.template operator()<3>() + R(cq) * ux);
-    V x5 = s.k[5] * (m.template operator()<5>() + R(cq) * uy);
-    V x7 = s.k[7] * (m.template operator()<7>() + R(cq) * uz);
-    if constexpr (FORCE) {
-      x3 += s.h[3] * (R(cq) * Fx);
-      x5 += s.h[5] * (R(cq) * Fy);
-      x7 += s.h[7] * (R(cq) * Fz);
-    }
-    row.template operator()<3>(x3);
-    row.template operator()<5>(x5);
-    row.template operator()<7>(x7);
-    if constexpr (Q == 14) {
-      V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
-      if constexpr (FORCE) x8 -= s.h[8] * sxx;
-      row.template operator()<8>(x8);
-      V x9 = s.k[9] * (m.template operator()<9>() - pww_eq);
-      if constexpr (FORCE) x9 -= s.h[9] * sww;
-      row.template operator()<9>(x9);
-      V x10 = s.k[10] * (m.template operator()<10>() - uxy);
-      if constexpr (FORCE) x10 -= s.h[10] * sxy;
-      row.template operator()<10>(x10);
-      V x11 = s.k[11] * (m.template operator()<11>() - uyz);
-      if constexpr (FORCE) x11 -= s.h[11] * syz;
-      row.template operator()<11>(x11);
-      V x12 = s.k[12] * (m.template operator()<12>() - uxz);
-      if constexpr (FORCE) x12 -= s.h[12] * sxz;
-      row.template operator()<12>(x12);
-      row.template operator()<13>(s.k[13] * m.template operator()<13>());
-    } else {
-      // 3pi_xx and pi_ww equilibria (and sources) are -1/2 of 3p_xx and p_ww
-      V x8 = s.k[8] * (m.template operator()<8>() - pxx_eq);
-      if constexpr (FORCE) x8 -= s.h[8] * sxx;
-      row.template operator()<8>(x8);
-      V x9 = s.k[9] * (m.template operator()<9>() + R(0.5) * pxx_eq);
-      if constexpr (FORCE) x9 += s.h[9] * (R(0.5) * sxx);
-      row.template operator()<9>(x9);
-      V x10 = s.k[10] * (m.template operator()<10>() - pww_eq);
-      if constexpr (FORCE) x10 -= s.h[10] * sww;
-      row.template operator()<10>(x10);
-      V x11 = s.k[11] * (m.template operator()<11>() + R(0.5) * pww_eq);
-      if constexpr (FORCE) x11 += s.h[11] * (R(0.5) * sww);
-      row.template operator()<11>(x11);
-      V x12 = s.k[12] * (m.template operator()<12>() - uxy);
-      if constexpr (FORCE) x12 -= s.h[12] * sxy;
-      row.template operator()<12>(x12);
-      V x13 = s.k[13] * (m.template operator()<13>() - uyz);
-      if constexpr (FORCE) x13 -= s.h[13] * syz;
-      row.template operator()<13>(x13);
-      V x14 = s.k[14] * (m.template operator()<14>() - uxz);
-      if constexpr (FORCE) x14 -= s.h[14] * sxz;
-      row.template operator()<14>(x14);
-      row.template operator()<15>(s.k[15] * m.template operator()<15>());
-      row.template operator()<16>(s.k[16] * m.template operator()<16>());
-      row.template operator()<17>(s.k[17] * m.template operator()<17>());
-    }
-  }
-  // f*_rep = f_rep - (E + O)_rows = E + O, f*_partner = E - O
-  [&]<int... I>(std::integer_sequence<int, I...>) {
-    ((f[pair_rep<Q>(I)] = E[I] + O[I], f[opposite<Q>(pair_rep<Q>(I))] = E[I] - O[I]), ...);
-  }(std::make_integer_sequence<int, NP>{});
 }
 
 }  // namespace lbm

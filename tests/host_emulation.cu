@@ -200,7 +200,7 @@ int emu_canonical(int Q, void* f, int nx, int ny, int nz, const int* per, int mo
 }
 
 int emu_collide(int Q, const double* s, double* f, const double* F) {
-  Rates<double> r{s[0], s[1], s[2], s[3], s[4], s[5], {}, {}};
+  Rates<double> r{s[0], s[1], s[2], s[3], s[4], s[5], {}, {}, {}};
   double ux, uy, uz;
   return with_q(Q, [&]<int QQ>() {
     scale_rows<QQ>(r);

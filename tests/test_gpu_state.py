@@ -89,7 +89,7 @@ def test_residual_criteria_match_oracle_fields(Q):
     reductions against the oracle's residual forms of the oracle's velocity
     fields at the same two steps: 1e-12 relative.  The batch form
     (lbm_batch_residual) gives the same numbers for FP32 storage against the
-    single-domain handle."""
+    single-domain handle; the batch rejects Q = 26."""
     from oracle import analytic
     case = inputs.cavity(Q, 12, 100.0, storage="f64")
     h = gpu_open(case)
@@ -118,8 +118,17 @@ def test_residual_criteria_match_oracle_fields(Q):
 
     import torch
     c32 = inputs.cavity(Q, 12, 100.0, storage="f32")
-    h = gpu_open(c32)
     b = lbm.lbm_batch_create(2, 0, torch.cuda.current_stream().cuda_stream)
+    if Q == 26:  # single-domain handles only
+        try:
+            with pytest.raises(lbm.LBMError) as ei:
+                lbm.lbm_batch_add(b, Q, c32.nx, c32.ny, c32.nz, "f32", c32.faces, c32.u_wall,
+                                  nu=c32.nu)
+            assert ei.value.code == lbm.LBM_EINVAL
+        finally:
+            lbm.lbm_batch_destroy(b)
+        return
+    h = gpu_open(c32)
     try:
         slot = lbm.lbm_batch_add(b, Q, c32.nx, c32.ny, c32.nz, "f32", c32.faces, c32.u_wall,
                                  nu=c32.nu)

@@ -40,7 +40,9 @@ def close(a, b):
 def same_stats(s, r, with_du, cells=0):
     for k in range(3):
         assert close(s.sum_abs_u[k], r.sum_abs_u[k])
-        assert close(s.sum_u[k], r.sum_u[k])
+        # a signed sum that nearly cancels (the net flow of a closed cavity)
+        # is accurate relative to the sum of its terms' magnitudes
+        assert abs(s.sum_u[k] - r.sum_u[k]) <= TOL * max(s.sum_abs_u[k], r.sum_abs_u[k]) + 1e-300
         if with_du:
             assert close(s.sum_abs_du[k], r.sum_abs_du[k])
             assert close(s.sum_abs_u_prev[k], r.sum_abs_u_prev[k])
