@@ -361,10 +361,10 @@ int lbm_autotune(lbm_handle *h, int32_t trials, lbm_launch *chosen, double *ms_p
  * Limits: N = nx*ny*nz <= 2,097,152 cells (128^3); larger domains are
  * rejected with LBM_EINVAL and a message naming the limit.
  * The first call on a device looks up the static array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The looked-up address is kept for the life of
- * the process: after a cudaDeviceReset of that device it is stale, so the
- * entry point must not be called on a device that has been reset.  Every call on a device shares the same static
+ * (cudaGetSymbolAddress) with that device current.  The looked-up address
+ * is kept for the life of the process: after a cudaDeviceReset of that
+ * device it is stale, so the entry point must not be called on a device
+ * that has been reset.  Every call on a device shares the same static
  * array: each call overwrites everything it reads, so nothing needs
  * clearing, but calls whose GPU work overlaps (e.g. on two streams at once)
  * race on it and must be serialised by the caller.
