@@ -179,7 +179,8 @@ def kernel_source_hash():
     h = hashlib.sha256()
     for name in ("lbm_model.cuh", "lbm_factored.cuh", "lbm_collide.cuh", "lbm_kernels.cuh",
                  "lbm_launch.cuh", "lbm_step.cu", "lbm_step_impl.cuh", "lbm_step_q14.cu",
-                 "lbm_step_q18.cu"):
+                 "lbm_step_q18.cu", "lbm_step_q14h.cu", "lbm_step_q18h.cu", "lbm_step_q14b.cu",
+                 "lbm_step_q18b.cu"):
         p = os.path.join(ROOT, "paper_1503_03337_gb300", "csrc", name)
         with open(p, "rb") as fh:
             h.update(os.path.basename(p).encode())

@@ -1,14 +1,18 @@
-// Step kernels for Q = 18 (see lbm_step_impl.cuh).
+// Step kernels for Q = 18 with FP64 and FP32 storage (see lbm_step_impl.cuh);
+// the 2-byte storage types are in lbm_step_q18h.cu, so the two compile in
+// parallel.
 #include "lbm_step_impl.cuh"
 
 namespace lbm {
+
+cudaError_t launch_step_q18_half(const DomainDesc& d, int64_t n, BlockShape b, cudaStream_t st);
 
 cudaError_t launch_step_q18(const DomainDesc& d, int64_t n, BlockShape b, cudaStream_t st) {
   switch (d.storage) {
     case LBM_STORAGE_F64: return launch_typed<18, double, double>(d, n, b, st);
     case LBM_STORAGE_F32: return launch_typed<18, float, float>(d, n, b, st);
-    case LBM_STORAGE_F16: return launch_typed<18, __half, float>(d, n, b, st);
-    case LBM_STORAGE_BF16: return launch_typed<18, __nv_bfloat16, float>(d, n, b, st);
+    case LBM_STORAGE_F16:
+    case LBM_STORAGE_BF16: return launch_step_q18_half(d, n, b, st);
   }
   return cudaErrorInvalidValue;
 }
