@@ -169,33 +169,27 @@ __host__ __device__ __forceinline__ void collide_factored(V* f, const Rates<R>& 
   }(std::make_integer_sequence<int, NP>{});
 }
 
-// Any model, row by row from the phi basis (used for iD3Q26): each relaxed
-// row x_K is subtracted from the per-pair accumulators E (even rows) and O
-// (odd rows) as soon as it is known, so no moment array stays live, and the
-// equilibrium moments come from their definition m_eq = T f_eq.
+// Any model, row by row from the phi basis (used for iD3Q26): every moment
+// m_K as its own row sum, every post-collision row y_K = m*_K / D_K with the
+// equilibrium moments from their definition m_eq = T f_eq (moment_eq,
+// moment_source), then f* = T' D^-1 m* column by column.  As in
+// collide_factored, the pair sums are dead once the moments are known.
 template <int Q, bool FORCE, typename V, typename R>
 __host__ __device__ __forceinline__ void collide_rows(V* f, const Rates<R>& s, R Fx, R Fy, R Fz,
                                                       V& ux, V& uy, V& uz) {
   constexpr int NP = Q / 2;
-  V ps[NP], pd[NP];
-  pair_split<Q>(f, ps, pd);
-  const CellState<Q, FORCE, V, R> c(
-      row_sum<Q, 0, 0, false>(V(R(0)), ps), row_sum<Q, 2, 0, false>(V(R(0)), pd),
-      row_sum<Q, 4, 0, false>(V(R(0)), pd), row_sum<Q, 6, 0, false>(V(R(0)), pd), Fx, Fy, Fz);
+  V m[Q];
+  {
+    V ps[NP], pd[NP];
+    pair_split<Q>(f, ps, pd);
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+      ((m[K] = row_sum<Q, K, 0, false>(V(R(0)), row_even<Q>(K) ? ps : pd)), ...);
+    }(std::make_integer_sequence<int, Q>{});
+  }
+  const CellState<Q, FORCE, V, R> c(m[0], m[2], m[4], m[6], Fx, Fy, Fz);
   ux = c.ux;
   uy = c.uy;
   uz = c.uz;
-  // E = s/2 - sum_even phi x and O = d/2 - sum_odd phi x, so that
-  // f*_rep = E + O and f*_opp = E - O at the end
-  V E[NP], O[NP];
-  [&]<int... I>(std::integer_sequence<int, I...>) {
-    ((E[I] = R(0.5) * ps[I], O[I] = R(0.5) * pd[I]), ...);
-  }(std::make_integer_sequence<int, NP>{});
-  auto row = [&]<int K>(V xk) { add_row<Q, FORCE, K>(xk, E, O); };
-  auto m = [&]<int K>() {
-    if constexpr (row_even<Q>(K)) return row_sum<Q, K, 0, false>(V(R(0)), ps);
-    else return row_sum<Q, K, 0, false>(V(R(0)), pd);
-  };
   const V q3 = R(3) * c.p - R(1.5) * c.u2;
   const V uu[6] = {c.uxx, c.uyy, c.uzz, c.uxy, c.uyz, c.uxz};
   V uf[6] = {V(R(0)), V(R(0)), V(R(0)), V(R(0)), V(R(0)), V(R(0))};
@@ -206,14 +200,22 @@ __host__ __device__ __forceinline__ void collide_rows(V* f, const Rates<R>& s, R
     uf[3] = c.sxy;
     uf[4] = c.syz;
     uf[5] = c.sxz;
-    row.template operator()<2>(V(-Fx * s.h[2]));  // momentum rows: -F
-    row.template operator()<4>(V(-Fy * s.h[4]));
-    row.template operator()<6>(V(-Fz * s.h[6]));
+  }
+  V* y = m;  // y_K replaces m_K
+  y[0] = R(1.0 / row_norm<Q>(0)) * m[0];
+  if constexpr (FORCE) {  // m*_j = j + F (see collide_factored)
+    y[2] = R(1.0 / row_norm<Q>(2)) * (m[2] + Fx);
+    y[4] = R(1.0 / row_norm<Q>(4)) * (m[4] + Fy);
+    y[6] = R(1.0 / row_norm<Q>(6)) * (m[6] + Fz);
+  } else {
+    y[2] = R(1.0 / row_norm<Q>(2)) * m[2];
+    y[4] = R(1.0 / row_norm<Q>(4)) * m[4];
+    y[6] = R(1.0 / row_norm<Q>(6)) * m[6];
   }
   auto relax = [&]<int K>() {
-    V xk = s.k[K] * (m.template operator()<K>() - moment_eq<Q, K, V, R>(q3, c.ux, c.uy, c.uz, uu));
-    if constexpr (FORCE) xk -= s.h[K] * moment_source<Q, K, V, R>(c.uF, Fx, Fy, Fz, uf);
-    row.template operator()<K>(xk);
+    V v = fmadd(V(s.k[K]), moment_eq<Q, K, V, R>(q3, c.ux, c.uy, c.uz, uu), s.g[K] * m[K]);
+    if constexpr (FORCE) v = fmadd(V(s.h[K]), moment_source<Q, K, V, R>(c.uF, Fx, Fy, Fz, uf), v);
+    y[K] = v;
   };
   relax.template operator()<1>();
   relax.template operator()<3>();
@@ -222,7 +224,14 @@ __host__ __device__ __forceinline__ void collide_rows(V* f, const Rates<R>& s, R
     (relax.template operator()<K + 7>(), ...);
   }(std::make_integer_sequence<int, Q - 7>{});
   [&]<int... I>(std::integer_sequence<int, I...>) {
-    ((f[pair_rep<Q>(I)] = E[I] + O[I], f[opposite<Q>(pair_rep<Q>(I))] = E[I] - O[I]), ...);
+    (
+        [&] {
+          const V E = col_sum<Q, I, 0, true, false>(V(R(0)), y);
+          const V O = col_sum<Q, I, 0, false, false>(V(R(0)), y);
+          f[pair_rep<Q>(I)] = E + O;
+          f[opposite<Q>(pair_rep<Q>(I))] = E - O;
+        }(),
+        ...);
   }(std::make_integer_sequence<int, NP>{});
 }
 

@@ -3,6 +3,7 @@
 and indexing mistakes in the kernel source before it reaches a GPU; the GPU
 parity tests then check the device build itself."""
 import ctypes
+import glob
 import os
 import subprocess
 
@@ -22,8 +23,7 @@ def emu():
     out_dir = os.path.join(ROOT, "_build")
     os.makedirs(out_dir, exist_ok=True)
     lib = os.path.join(out_dir, "libhost_emulation.so")
-    deps = [SRC] + [os.path.join(ROOT, "paper_1503_03337_gb300", "csrc", f)
-                    for f in ("lbm_model.cuh", "lbm_kernels.cuh", "lbm_neq.cuh")]
+    deps = [SRC] + glob.glob(os.path.join(ROOT, "paper_1503_03337_gb300", "csrc", "*.cuh"))
     if not os.path.exists(lib) or os.path.getmtime(lib) < max(map(os.path.getmtime, deps)):
         tmp = lib + ".tmp%d" % os.getpid()
         subprocess.run([pkg_build.nvcc(), "-std=c++20", "-O2", "--expt-relaxed-constexpr",
