@@ -16,11 +16,12 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]);
 
 // Resident 256-thread blocks per SM the register budget is sized for: four
 // (64 registers a thread) for Q = 14 and 18 with 4- or 2-byte storage, two
-// for FP64 and for Q = 26 (whose 26 populations and 13 pair accumulators
-// spill at 64), one for Q = 26 in FP64.
+// for their FP64.  Q = 26 needs more: three for FP32 (80 registers, a few
+// dozen bytes spilled, measured faster at 256^3 than two: 29.3 vs 28.2
+// GLUPS), two for FP16 / BF16 (34.8 at three vs 36.2 at two), one for FP64.
 template <int Q, typename S>
 constexpr int step_min_blocks() {
-  if (Q == 26) return sizeof(S) == 8 ? 1 : 2;
+  if (Q == 26) return sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 2);
   return sizeof(S) == 8 ? 2 : 4;
 }
 
