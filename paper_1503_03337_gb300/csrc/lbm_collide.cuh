@@ -8,9 +8,9 @@
 // exactly and j - u = -F/2, so the conserved rows contribute only -F to the
 // momentum rows whatever s_c is.
 //
-// iD3Q14 and iD3Q18 use the factored transforms of lbm_factored.cuh and the
-// printed closed-form equilibria; iD3Q26 evaluates its rows one by one from
-// the phi basis (row_sum / add_row) with m_eq = T f_eq (moment_eq).
+// Every model uses the factored transforms of lbm_factored.cuh; iD3Q14 and
+// iD3Q18 the printed closed-form equilibria, iD3Q26 m_eq = T f_eq
+// (moment_eq).
 // On return f holds f*, and (ux,uy,uz) the velocity of the pre-collision
 // state.  V is the value type (float, double, or pf2 for two cells at once)
 // and R the scalar type of rates, force and constants.
@@ -169,22 +169,19 @@ __host__ __device__ __forceinline__ void collide_factored(V* f, const Rates<R>& 
   }(std::make_integer_sequence<int, NP>{});
 }
 
-// Any model, row by row from the phi basis (used for iD3Q26): every moment
-// m_K as its own row sum, every post-collision row y_K = m*_K / D_K with the
-// equilibrium moments from their definition m_eq = T f_eq (moment_eq,
-// moment_source), then f* = T' D^-1 m* column by column.  As in
-// collide_factored, the pair sums are dead once the moments are known.
+// A model without printed equilibria (iD3Q26): the factored transforms, and
+// every post-collision row y_K = m*_K / D_K with the equilibrium moments and
+// sources from their definition m_eq = T f_eq (moment_eq, moment_source).
+// As in collide_factored, the pair sums are dead once the moments are known.
 template <int Q, bool FORCE, typename V, typename R>
-__host__ __device__ __forceinline__ void collide_rows(V* f, const Rates<R>& s, R Fx, R Fy, R Fz,
-                                                      V& ux, V& uy, V& uz) {
+__host__ __device__ __forceinline__ void collide_teq(V* f, const Rates<R>& s, R Fx, R Fy, R Fz,
+                                                     V& ux, V& uy, V& uz) {
   constexpr int NP = Q / 2;
   V m[Q];
   {
     V ps[NP], pd[NP];
     pair_split<Q>(f, ps, pd);
-    [&]<int... K>(std::integer_sequence<int, K...>) {
-      ((m[K] = row_sum<Q, K, 0, false>(V(R(0)), row_even<Q>(K) ? ps : pd)), ...);
-    }(std::make_integer_sequence<int, Q>{});
+    Factored<Q>::moments(ps, pd, m);
   }
   const CellState<Q, FORCE, V, R> c(m[0], m[2], m[4], m[6], Fx, Fy, Fz);
   ux = c.ux;
@@ -223,15 +220,11 @@ __host__ __device__ __forceinline__ void collide_rows(V* f, const Rates<R>& s, R
   [&]<int... K>(std::integer_sequence<int, K...>) {
     (relax.template operator()<K + 7>(), ...);
   }(std::make_integer_sequence<int, Q - 7>{});
+  V C[NP], D[NP];
+  Factored<Q>::cols_even(y, C);
+  Factored<Q>::cols_odd(y, D);
   [&]<int... I>(std::integer_sequence<int, I...>) {
-    (
-        [&] {
-          const V E = col_sum<Q, I, 0, true, false>(V(R(0)), y);
-          const V O = col_sum<Q, I, 0, false, false>(V(R(0)), y);
-          f[pair_rep<Q>(I)] = E + O;
-          f[opposite<Q>(pair_rep<Q>(I))] = E - O;
-        }(),
-        ...);
+    ((f[pair_rep<Q>(I)] = C[I] + D[I], f[opposite<Q>(pair_rep<Q>(I))] = C[I] - D[I]), ...);
   }(std::make_integer_sequence<int, NP>{});
 }
 
@@ -239,7 +232,7 @@ template <int Q, bool FORCE, typename V, typename R>
 __host__ __device__ __forceinline__ void collide(V* f, const Rates<R>& s, R Fx, R Fy, R Fz,
                                                  V& ux, V& uy, V& uz) {
   if constexpr (Q == 14 || Q == 18) collide_factored<Q, FORCE>(f, s, Fx, Fy, Fz, ux, uy, uz);
-  else collide_rows<Q, FORCE>(f, s, Fx, Fy, Fz, ux, uy, uz);
+  else collide_teq<Q, FORCE>(f, s, Fx, Fy, Fz, ux, uy, uz);
 }
 
 }  // namespace lbm

@@ -1,14 +1,14 @@
-// Lattice tables and the per-cell MRT collision of the iD3Q14 (Sec. 3) and
-// iD3Q18 (App. B) incompressible models, and of the iD3Q26 model that the
-// same construction gives on the D3Q27 set without c_0 (App. B's closing
-// remark), written for registers.
+// Lattice tables, moment basis, rates, storage codecs and arithmetic
+// helpers of the iD3Q14 (Sec. 3) and iD3Q18 (App. B) incompressible models,
+// and of the iD3Q26 model that the same construction gives on the D3Q27 set
+// without c_0 (App. B's closing remark).
 //
-// Everything that depends only on the lattice is a constexpr function, so
-// the moment transform m = T f and its inverse f = T' D^-1 m (Eq. mrteqvT)
-// unroll at compile time into adds and constant multiply-adds; no matrix is
-// stored anywhere.  The rows of T are the orthogonal basis vectors phi_k of
-// Sec. 3 (Eq. m, after orthogonalisation) and App. B (Eq. appendix_m18),
-// evaluated on the velocity set.
+// Everything that depends only on the lattice is a constexpr function: the
+// rows of T are the orthogonal basis vectors phi_k of Sec. 3 (Eq. m, after
+// orthogonalisation) and App. B (Eq. appendix_m18), evaluated on the
+// velocity set, and no matrix is stored anywhere.  The transform itself is
+// in lbm_factored.cuh, checked against phi at compile time, and the
+// collision in lbm_collide.cuh.
 //
 // Every direction a has an opposite abar (Q is even and there is no rest
 // direction), and every row of T is either even (T_k,abar = T_k,a: P, e and
@@ -508,9 +508,8 @@ __host__ __device__ __forceinline__ double fmadd(double a, double b, double c) {
 // integer form, for compile-time checks of the transforms
 __host__ __device__ constexpr int fmadd(int a, int b, int c) { return a * b + c; }
 
-// ---------------------------------------------------------------------------
-// Unrolled transforms over pairs
-// ---------------------------------------------------------------------------
+// acc + C x (term_add) and C x (term_first) for a compile-time integer C: an
+// add or subtract for C = +-1, else one multiply(-add).
 template <int C, typename V>
 __host__ __device__ __forceinline__ constexpr V term_first(V x) {
   if constexpr (C == 1) return x;
@@ -522,60 +521,6 @@ __host__ __device__ __forceinline__ constexpr V term_add(V acc, V x) {
   if constexpr (C == 1) return acc + x;
   else if constexpr (C == -1) return acc - x;
   else return fmadd(V(C), x, acc);
-}
-
-// m_K = sum_i phi_K(rep_i) v_i, with v = pair sums (even K) or differences.
-template <int Q, int K, int I, bool STARTED, typename R>
-__host__ __device__ __forceinline__ R row_sum(R acc, const R* v) {
-  if constexpr (I == Q / 2) {
-    if constexpr (STARTED) return acc;
-    else return R(0);
-  } else {
-    constexpr int C = phi<Q>(K, pair_rep<Q>(I));
-    if constexpr (C == 0) return row_sum<Q, K, I + 1, STARTED>(acc, v);
-    else if constexpr (!STARTED)
-      return row_sum<Q, K, I + 1, true>(term_first<C>(v[I]), v);
-    else return row_sum<Q, K, I + 1, true>(term_add<C>(acc, v[I]), v);
-  }
-}
-
-// Back-transform share of pair I: sum over rows K of the given parity of
-// phi_K(rep_I) * x_K.
-template <int Q, int I, int K, bool EVEN, bool STARTED, typename R>
-__host__ __device__ __forceinline__ R col_sum(R acc, const R* x) {
-  if constexpr (K == Q) {
-    if constexpr (STARTED) return acc;
-    else return R(0);
-  } else {
-    constexpr int C = (row_even<Q>(K) == EVEN) ? phi<Q>(K, pair_rep<Q>(I)) : 0;
-    if constexpr (C == 0) return col_sum<Q, I, K + 1, EVEN, STARTED>(acc, x);
-    else if constexpr (!STARTED)
-      return col_sum<Q, I, K + 1, EVEN, true>(term_first<C>(x[K]), x);
-    else return col_sum<Q, I, K + 1, EVEN, true>(term_add<C>(acc, x[K]), x);
-  }
-}
-
-template <int Q, int K = 0, typename R>
-__host__ __device__ __forceinline__ void moments(const R* s, const R* d, R* m) {
-  if constexpr (K < Q) {
-    if constexpr (row_even<Q>(K)) m[K] = row_sum<Q, K, 0, false>(R(0), s);
-    else m[K] = row_sum<Q, K, 0, false>(R(0), d);
-    moments<Q, K + 1>(s, d, m);
-  }
-}
-
-// f*_rep = f_rep - (E + O), f*_partner = f_partner - (E - O)
-template <int Q, int I = 0, typename R>
-__host__ __device__ __forceinline__ void back_transform(const R* x, R* f) {
-  if constexpr (I < Q / 2) {
-    constexpr int a = pair_rep<Q>(I);
-    constexpr int b = opposite<Q>(a);
-    const R E = col_sum<Q, I, 0, true, false>(R(0), x);
-    const R O = col_sum<Q, I, 0, false, false>(R(0), x);
-    f[a] = f[a] - (E + O);
-    f[b] = f[b] - (E - O);
-    back_transform<Q, I + 1>(x, f);
-  }
 }
 
 template <typename R>
@@ -625,51 +570,6 @@ __host__ __device__ inline void scale_rows(Rates<R>& r) {
     r.g[K] = (R(1) - sk) * inv;
   }
 }
-
-// ---------------------------------------------------------------------------
-// Streaming back-transform: a relaxed row x_K (already divided by D_K) is
-// subtracted from the per-pair accumulators E (even rows) or O (odd rows) as
-// soon as it is known, so no moment array stays live.  Row 0 (P) never
-// contributes and rows 2, 4, 6 (j) contribute only with a force.
-// ---------------------------------------------------------------------------
-template <int Q, bool FORCE>
-__host__ __device__ constexpr bool row_active(int k) {
-  return k != 0 && (FORCE || (k != 2 && k != 4 && k != 6));
-}
-
-template <int Q, bool FORCE>
-__host__ __device__ constexpr bool touched(int I, int K, bool even) {
-  for (int k = 0; k < K; ++k)
-    if (row_active<Q, FORCE>(k) && row_even<Q>(k) == even &&
-        phi<Q>(k, pair_rep<Q>(I)) != 0)
-      return true;
-  return false;
-}
-
-template <int Q, bool FORCE, int K, int I = 0, typename R>
-__host__ __device__ __forceinline__ void add_row(R xk, R* E, R* O) {
-  if constexpr (I < Q / 2) {
-    constexpr int C = phi<Q>(K, pair_rep<Q>(I));
-    constexpr bool EV = row_even<Q>(K);
-    if constexpr (C != 0) {
-      R& acc = EV ? E[I] : O[I];
-      acc = term_add<-C>(acc, xk);
-    }
-    add_row<Q, FORCE, K, I + 1>(xk, E, O);
-  }
-}
-
-// every accumulator receives at least one row (else it would stay unset)
-template <int Q, bool FORCE>
-__host__ __device__ constexpr bool accumulators_covered() {
-  for (int I = 0; I < Q / 2; ++I)
-    if (!touched<Q, FORCE>(I, Q, true) || !touched<Q, FORCE>(I, Q, false)) return false;
-  return true;
-}
-static_assert(accumulators_covered<14, false>() && accumulators_covered<14, true>() &&
-                  accumulators_covered<18, false>() && accumulators_covered<18, true>() &&
-                  accumulators_covered<26, false>() && accumulators_covered<26, true>(),
-              "a pair accumulator receives no row");
 
 // ---------------------------------------------------------------------------
 // Equilibrium moments from their definition m_eq = T f_eq (Eq. mrteqvT), for
