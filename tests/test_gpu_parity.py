@@ -235,3 +235,33 @@ def test_fp64_lbgk_special_case(Q):
         lbm.lbm_destroy(h)
     assert rel_max(u, u_o) <= 1e-12
     assert rel_max(fg, f.reshape(fg.shape)) <= 1e-12
+
+
+@pytest.mark.parametrize("Q", (14, 18, 26))
+def test_fp64_random_rates(Q):
+    """Every relaxation rate drawn at random in (0.3, 1.9), one per class
+    (s_c, s_e, s_q, s_nu, s_pi, s_t), through lbm_set_params: the device's
+    per-row rate tables (k, h and g of every row) against the oracle's
+    diagonal S, FP64, moving lid, body force, odd step count."""
+    import oracle
+    rng = np.random.default_rng(seed("rates", Q))
+    sc, se, sq, snu, spi, st = rng.uniform(0.3, 1.9, size=6)
+    case = inputs.cavity(Q, 12, 100.0, storage="f64")
+    force = (1e-4, -2e-4, 5e-5)
+    g_or = oracle.make_grid(Q, case.nx, case.ny, case.nz, case.faces, case.u_wall)
+    prm = oracle.make_params(oracle.rates(Q, snu, sc=sc, se=se, sq=sq, st=st, spi=spi),
+                             force=force)
+    u0, p0 = inputs.random_state(case, seed=9)
+    f0 = oracle.init_equilibrium(g_or, u0, p0)
+    f = oracle.run(g_or, prm, f0, 0, 37)
+    h = lbm.lbm_create(Q, case.nx, case.ny, case.nz, "f64", None)
+    try:
+        lbm.lbm_set_geometry(h, case.faces, case.u_wall)
+        lbm.lbm_set_params(h, nu=0.0, s_c=sc, s_e=se, s_q=sq, s_nu=snu, s_pi=spi, s_t=st,
+                           force=force)
+        lbm.lbm_init_equilibrium(h, np.ascontiguousarray(u0), np.ascontiguousarray(p0), 0)
+        lbm.lbm_step(h, 37)
+        fg = lbm.read_populations(h, Q, case.nx, case.ny, case.nz)
+    finally:
+        lbm.lbm_destroy(h)
+    assert rel_max(fg, f.reshape(fg.shape)) <= 1e-12
