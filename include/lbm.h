@@ -185,7 +185,11 @@ typedef struct lbm_handle lbm_handle;
  * reduction workspace.  `cuda_stream` is a cudaStream_t (NULL = legacy
  * default stream); it is borrowed, not owned.  Initial state: all walls at
  * rest, Sec. 4 default rates with nu = 1/6, no force, f = 0, step 0.
- * Errors: EINVAL (Q not 14/18/26, a size < 1, storage unknown, Q*N >= 2^31),
+ * Domains of up to 2^31 - 1 cells (D3Q18 FP32: 154 GB); where Q*N >= 2^31
+ * the step runs one cell per thread with 64-bit population offsets
+ * (cells_per_thread = 2 is accepted and has no effect there).
+ * Errors: EINVAL (Q not 14/18/26, a size < 1, storage unknown,
+ * nx*ny*nz >= 2^31, nz > 65535),
  * ENOMEM, ECUDA. */
 int lbm_create(const lbm_desc *desc, void *cuda_stream, lbm_handle **out);
 

@@ -165,8 +165,10 @@ int lbm_create(const lbm_desc* desc, void* cuda_stream, lbm_handle** out) {
   const size_t b = storage_bytes(desc->storage);
   if (!b) return fail(LBM_EINVAL, "unknown storage type");
   const int64_t N = (int64_t)desc->nx * desc->ny * desc->nz;
-  if (N * desc->Q >= (int64_t(1) << 31) || desc->nz > 65535)
-    return fail(LBM_EINVAL, "domain too large (Q*N must be < 2^31, nz <= 65535)");
+  // cell indices are 32-bit; population offsets a*N + i are 64-bit where
+  // Q*N >= 2^31 (the step's wide kernels)
+  if (N >= (int64_t(1) << 31) || desc->nz > 65535)
+    return fail(LBM_EINVAL, "domain too large (nx*ny*nz must be < 2^31, nz <= 65535)");
 
   lbm_handle* h = new (std::nothrow) lbm_handle();
   if (!h) return fail(LBM_ENOMEM, "host allocation failed");
@@ -608,7 +610,9 @@ int lbm_autotune(lbm_handle* h, int32_t trials, lbm_launch* chosen, double* ms) 
     if (e != cudaSuccess) break;
     b.pdl = h->block.pdl;
     if (b.bx * b.cpt > xmax && b.bx > 32) continue;
-    if (b.cpt == 2 && (h->d.storage == LBM_STORAGE_F64 || h->d.Q == 26)) continue;
+    if (b.cpt == 2 && (h->d.storage == LBM_STORAGE_F64 || h->d.Q == 26 ||
+                       (int64_t)h->d.Q * h->d.N >= (int64_t(1) << 31)))
+      continue;
     int64_t n = n0;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = launch_step(h->d, n++, b, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);

@@ -263,7 +263,7 @@ __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __
                                              const double (&es)[6][2],
                                              PairSum& sP, PairSum (&sj)[3]) {
   const int i = x + d.nx * (y + d.ny * z);
-  const int N = (int)d.N;
+  const int64_t N = d.N;
   Links L{};
   if constexpr (ODD) L = make_links(d, x, y, z);
   [&]<int... A>(std::integer_sequence<int, A...>) {
@@ -271,7 +271,7 @@ __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __
         [&] {
           constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
                         cz = Lattice<Q>::c(A, 2);
-          int idx = A * N + i;
+          int64_t idx = A * N + i;
           if constexpr (ODD) {
             int off, mirror;
             bool ghost;
@@ -321,12 +321,13 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d,
   PairSum sdu[3], su_abs[3], sup_abs[3], su[3], sPt, umax;
   int nonfinite = 0;
   const PairSum Fh[3] = {Fh0, Fh1, Fh2};
-  const int N = (int)d.N;
+  const int64_t N = d.N;
   float2* snap = reinterpret_cast<float2*>(a.u_prev);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const int x = i % d.nx;
-    const int r = i / d.nx;
-    const int y = r % d.ny, z = r / d.ny;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % d.nx);
+    const int64_t r = i / d.nx;
+    const int y = (int)(r % d.ny), z = (int)(r / d.ny);
     if (d.solid && (d.solid[i] & kSolidCell)) {  // no flow: zero in every sum
       if (a.u_prev)
         for (int k = 0; k < 3; ++k) snap[(int64_t)k * N + i] = make_float2(0.0f, 0.0f);

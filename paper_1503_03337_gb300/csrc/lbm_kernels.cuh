@@ -48,9 +48,28 @@ struct Domain {
   // on odd steps:
   //   pull[a] = abar*N - s(c_a)     (where f_a(x) is read)
   //   push[a] = a*N + s(c_a)        (where f*_a(x) is written)
-  // with s(c) = cx + cy*nx + cz*nx*ny.  Filled by fill_offsets().
+  // with s(c) = cx + cy*nx + cz*nx*ny.  Filled by fill_offsets().  pull and
+  // push hold them while Q*N < 2^31; pull64 / push64 always, for the wide
+  // kernels of larger domains (cell indices stay 32-bit: N < 2^31).
   int pull[26], push[26];
+  int64_t pull64[26], push64[26];
 };
+
+// Index type of population offsets a*N + i: 32-bit while Q*N < 2^31, else
+// 64-bit (the WIDE kernel variants).
+template <bool WIDE>
+using PopIndex = std::conditional_t<WIDE, int64_t, int>;
+
+template <bool WIDE, typename R>
+__host__ __device__ __forceinline__ PopIndex<WIDE> pull_offset(const Domain<R>& d, int a) {
+  if constexpr (WIDE) return d.pull64[a];
+  else return d.pull[a];
+}
+template <bool WIDE, typename R>
+__host__ __device__ __forceinline__ PopIndex<WIDE> push_offset(const Domain<R>& d, int a) {
+  if constexpr (WIDE) return d.push64[a];
+  else return d.push[a];
+}
 
 constexpr uint32_t kSolidCell = 0x80000000u;
 
@@ -91,11 +110,13 @@ __host__ __device__ inline uint32_t step_key(int64_t n) {
 
 template <int Q, typename R>
 __host__ __device__ inline void fill_offsets(Domain<R>& d) {
-  const int N = (int)d.N, sy = d.nx, sz = d.nx * d.ny;
+  const int64_t N = d.N, sy = d.nx, sz = (int64_t)d.nx * d.ny;
   for (int a = 0; a < Q; ++a) {
-    const int s = Lattice<Q>::c(a, 0) + Lattice<Q>::c(a, 1) * sy + Lattice<Q>::c(a, 2) * sz;
-    d.pull[a] = opposite<Q>(a) * N - s;
-    d.push[a] = a * N + s;
+    const int64_t s = Lattice<Q>::c(a, 0) + Lattice<Q>::c(a, 1) * sy + Lattice<Q>::c(a, 2) * sz;
+    d.pull64[a] = opposite<Q>(a) * N - s;
+    d.push64[a] = a * N + s;
+    d.pull[a] = (int)d.pull64[a];  // exact while Q*N < 2^31
+    d.push[a] = (int)d.push64[a];
   }
 }
 
@@ -342,10 +363,11 @@ __host__ __device__ __forceinline__ void add_pull_wall_terms(const Domain<R>& d,
 // Pre-collision populations f^n of cell i into fv (CG: L2-only loads; SYM:
 // the domain may have symmetry faces).
 template <int Q, typename S, typename R, bool ODD, bool CG = false, bool SYM = true,
-          bool SOLID = true>
+          bool SOLID = true, bool WIDE = false>
 __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __restrict__ f,
                                                 int i, const Links& L, R* fv) {
-  const int N = (int)d.N;
+  using Ix = PopIndex<WIDE>;
+  const Ix N = (Ix)d.N;
   const S* __restrict__ fc = f + i;
   if constexpr (!ODD) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
@@ -353,7 +375,7 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
     }(std::make_integer_sequence<int, Q>{});
   } else if (L.interior) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
-      ((fv[A] = load_pop<S, R, CG>(fc + d.pull[A])), ...);
+      ((fv[A] = load_pop<S, R, CG>(fc + pull_offset<WIDE>(d, A))), ...);
     }(std::make_integer_sequence<int, Q>{});
   } else {
     // f_a(x) = A[abar][x - c_a], or A[a][x] if x - c_a is a wall ghost;
@@ -364,7 +386,7 @@ __host__ __device__ __forceinline__ void gather(const Domain<R>& d, const S* __r
             int off, mirror;
             bool ghost;
             link_of<Q, A, -1, SYM, SOLID>(L, off, ghost, mirror);
-            const int idx =
+            const Ix idx =
                 ghost ? (A * N + i) : (opposite_mirror_rt<Q, A>(mirror) * N + i + off);
             fv[A] = load_pop<S, R, CG>(f + idx);
           }(),
@@ -424,16 +446,17 @@ __host__ __device__ __forceinline__ void store_cell(const R* fv, uint32_t h, Add
 // Post-collision populations f* of cell i from fv into storage (`key`: the
 // step's stochastic-rounding key; SYM as in gather).
 template <int Q, typename S, typename R, bool ODD, bool SR = false, bool SYM = true,
-          bool SOLID = true>
+          bool SOLID = true, bool WIDE = false>
 __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restrict__ f,
                                                  int i, const Links& L, R* fv, uint32_t key) {
-  const int N = (int)d.N;
+  using Ix = PopIndex<WIDE>;
+  const Ix N = (Ix)d.N;
   const uint32_t h = SR ? sr_cell_hash(i, key) : 0u;
   S* __restrict__ fc = f + i;
   if constexpr (!ODD) {
     store_cell<Q, S, R, SR>(fv, h, [&]<int A>() { return fc + (size_t)opposite<Q>(A) * d.N; });
   } else if (L.interior) {
-    store_cell<Q, S, R, SR>(fv, h, [&]<int A>() { return fc + d.push[A]; });
+    store_cell<Q, S, R, SR>(fv, h, [&]<int A>() { return fc + push_offset<WIDE>(d, A); });
   } else {
     if (d.moving && touches_moving(d, L)) {
       [&]<int... A>(std::integer_sequence<int, A...>) {
@@ -455,23 +478,23 @@ __host__ __device__ __forceinline__ void scatter(const Domain<R>& d, S* __restri
       int off, mirror;
       bool ghost;
       link_of<Q, A, 1, SYM, SOLID>(L, off, ghost, mirror);
-      const int idx = ghost ? (opposite<Q>(A) * N + i) : (mirror_rt<Q, A>(mirror) * N + i + off);
+      const Ix idx = ghost ? (opposite<Q>(A) * N + i) : (mirror_rt<Q, A>(mirror) * N + i + off);
       return f + idx;
     });
   }
 }
 
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR, bool CG = false,
-          bool SYM = true, bool SOLID = false>
+          bool SYM = true, bool SOLID = false, bool WIDE = false>
 __host__ __device__ __forceinline__ void update_with_links(const Domain<R>& d,
                                                            S* __restrict__ f, int i,
                                                            const Links& L, const R* F,
                                                            const uint32_t* key) {
   R fv[Q];
-  gather<Q, S, R, ODD, CG, SYM, SOLID>(d, f, i, L, fv);
+  gather<Q, S, R, ODD, CG, SYM, SOLID, WIDE>(d, f, i, L, fv);
   R ux, uy, uz;
   collide<Q, FORCE>(fv, d.s, F[0], F[1], F[2], ux, uy, uz);
-  scatter<Q, S, R, ODD, SR, SYM, SOLID>(d, f, i, L, fv, SR ? *key : 0u);
+  scatter<Q, S, R, ODD, SR, SYM, SOLID, WIDE>(d, f, i, L, fv, SR ? *key : 0u);
 }
 
 // Does any active lane of the warp hold a nonzero v (every lane on the
@@ -495,7 +518,7 @@ __host__ __device__ __forceinline__ bool warp_any(bool v) {
 // where they are used (F and key may live outside the descriptor);
 // update_cell takes them from the descriptor.
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false,
-          bool CG = false>
+          bool CG = false, bool WIDE = false>
 __host__ __device__ __forceinline__ void update_cell_at(const Domain<R>& d, S* __restrict__ f,
                                                         const R* F, const uint32_t* key, int x,
                                                         int y, int z, int x_lo, int x_hi) {
@@ -503,7 +526,7 @@ __host__ __device__ __forceinline__ void update_cell_at(const Domain<R>& d, S* _
   if constexpr (!ODD) {
     if (d.solid && (d.solid[i] & kSolidCell)) return;  // solid cells hold no flow
     Links L{};
-    update_with_links<Q, S, R, false, FORCE, SR, CG>(d, f, i, L, F, key);
+    update_with_links<Q, S, R, false, FORCE, SR, CG, true, false, WIDE>(d, f, i, L, F, key);
   } else {
     if (d.solid) {
       // a warp with any solid-touching link takes the full addressing with
@@ -512,40 +535,40 @@ __host__ __device__ __forceinline__ void update_cell_at(const Domain<R>& d, S* _
       if (warp_any(sm != 0u)) {
         if (sm & kSolidCell) return;
         if (d.sym)
-          update_with_links<Q, S, R, true, FORCE, SR, CG, true, true>(
+          update_with_links<Q, S, R, true, FORCE, SR, CG, true, true, WIDE>(
               d, f, i, make_links(d, x, y, z), F, key);
         else
-          update_with_links<Q, S, R, true, FORCE, SR, CG, false, true>(
+          update_with_links<Q, S, R, true, FORCE, SR, CG, false, true, WIDE>(
               d, f, i, make_links(d, x, y, z), F, key);
         return;
       }
     }
     if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
       if (x_lo > 0 && x_hi < d.nx - 1)
-        update_with_links<Q, S, R, true, FORCE, SR, CG>(d, f, i, make_links_interior(d), F,
+        update_with_links<Q, S, R, true, FORCE, SR, CG, true, false, WIDE>(d, f, i, make_links_interior(d), F,
                                                         key);
       else if (d.sym)
-        update_with_links<Q, S, R, true, FORCE, SR, CG, true>(d, f, i, make_links_x(d, x), F,
+        update_with_links<Q, S, R, true, FORCE, SR, CG, true, false, WIDE>(d, f, i, make_links_x(d, x), F,
                                                               key);
       else
-        update_with_links<Q, S, R, true, FORCE, SR, CG, false>(d, f, i, make_links_x(d, x), F,
+        update_with_links<Q, S, R, true, FORCE, SR, CG, false, false, WIDE>(d, f, i, make_links_x(d, x), F,
                                                                key);
     } else if (d.sym) {
-      update_with_links<Q, S, R, true, FORCE, SR, CG, true>(d, f, i, make_links(d, x, y, z), F,
+      update_with_links<Q, S, R, true, FORCE, SR, CG, true, false, WIDE>(d, f, i, make_links(d, x, y, z), F,
                                                             key);
     } else {
-      update_with_links<Q, S, R, true, FORCE, SR, CG, false>(d, f, i, make_links(d, x, y, z), F,
+      update_with_links<Q, S, R, true, FORCE, SR, CG, false, false, WIDE>(d, f, i, make_links(d, x, y, z), F,
                                                              key);
     }
   }
 }
 
 template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR = false,
-          bool CG = false>
+          bool CG = false, bool WIDE = false>
 __host__ __device__ __forceinline__ void update_cell(const Domain<R>& d, S* __restrict__ f,
                                                      int x, int y, int z, int x_lo = -1,
                                                      int x_hi = -1) {
-  update_cell_at<Q, S, R, ODD, FORCE, SR, CG>(d, f, d.F, &d.key, x, y, z, x_lo, x_hi);
+  update_cell_at<Q, S, R, ODD, FORCE, SR, CG, WIDE>(d, f, d.F, &d.key, x, y, z, x_lo, x_hi);
 }
 
 // Two storage values of x-adjacent cells as one word (8 bytes for FP32,
@@ -622,11 +645,13 @@ __device__ __forceinline__ void update_pair_even(const Domain<float>& d, S* __re
 }
 
 // Inverse of gather: put canonical pre-collision values fv of cell (x,y,z)
-// where the step parity keeps them (checkpoint restore / init).
+// where the step parity keeps them (checkpoint restore / init).  These two
+// helpers serve the kernels off the step path (init, read-back, writes,
+// reductions, extrapolation faces) and always index with 64 bits.
 template <int Q, typename S, typename R, bool ODD>
 __host__ __device__ __forceinline__ void put_canonical(const Domain<R>& d, S* __restrict__ f,
                                                        int x, int y, int z, const R* fv) {
-  const int N = (int)d.N;
+  const int64_t N = d.N;
   const int i = x + d.nx * (y + d.ny * z);
   if constexpr (!ODD) {
     [&]<int... A>(std::integer_sequence<int, A...>) {
@@ -646,7 +671,7 @@ __host__ __device__ __forceinline__ void put_canonical(const Domain<R>& d, S* __
               v -= R(6.0 * Lattice<Q>::w(A)) *
                    ghost_dot(d, L.edge, faces, Lattice<Q>::c(A, 0), Lattice<Q>::c(A, 1),
                              Lattice<Q>::c(A, 2));
-            const int idx =
+            const int64_t idx =
                 ghost ? (A * N + i) : (opposite_mirror_rt<Q, A>(mirror) * N + i + off);
             Codec<S, R>::store(f + idx, v);
           }(),
@@ -662,9 +687,9 @@ __host__ __device__ __forceinline__ void get_canonical(const Domain<R>& d, const
   const int i = x + d.nx * (y + d.ny * z);
   if constexpr (!ODD) {
     Links L{};
-    gather<Q, S, R, false>(d, f, i, L, fv);
+    gather<Q, S, R, false, false, true, true, true>(d, f, i, L, fv);
   } else {
-    gather<Q, S, R, true>(d, f, i, make_links(d, x, y, z), fv);
+    gather<Q, S, R, true, false, true, true, true>(d, f, i, make_links(d, x, y, z), fv);
   }
 }
 

@@ -19,14 +19,18 @@ Domain<R> to_domain(const DomainDesc& d, const double F[3]);
 // for their FP64.  Q = 26 needs more: three for FP32 (80 registers, a few
 // dozen bytes spilled, measured faster at 256^3 than two: 29.3 vs 28.2
 // GLUPS), two for FP16 / BF16 (34.8 at three vs 36.2 at two), one for FP64.
-template <int Q, typename S>
+// The wide kernels (64-bit offsets, Q*N >= 2^31) of Q = 14 and 18 take
+// three blocks (80 registers): at four they spill 150-180 bytes.
+template <int Q, typename S, bool WIDE = false>
 constexpr int step_min_blocks() {
   if (Q == 26) return sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 3 : 2);
+  if (WIDE && sizeof(S) <= 4) return 3;
   return sizeof(S) == 8 ? 2 : 4;
 }
 
-template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR>
-__global__ void __launch_bounds__(256, step_min_blocks<Q, S>()) k_step(Domain<R> d) {
+// WIDE: 64-bit population offsets, for domains with Q*N >= 2^31.
+template <int Q, typename S, typename R, bool ODD, bool FORCE, bool SR, bool WIDE = false>
+__global__ void __launch_bounds__(256, step_min_blocks<Q, S, WIDE>()) k_step(Domain<R> d) {
   pdl_release();
   pdl_acquire();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -37,7 +41,8 @@ __global__ void __launch_bounds__(256, step_min_blocks<Q, S>()) k_step(Domain<R>
   // blockDim.x is a multiple of 32 (then the path choice is warp-uniform)
   const int x_lo = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   const int x_hi = x_lo + 31;
-  update_cell<Q, S, R, ODD, FORCE, SR>(d, static_cast<S*>(d.f), x, y, z, x_lo, x_hi);
+  update_cell<Q, S, R, ODD, FORCE, SR, false, WIDE>(d, static_cast<S*>(d.f), x, y, z, x_lo,
+                                                    x_hi);
 }
 
 // Even steps with two x-adjacent cells per thread (see update_pair_even; nx
@@ -65,8 +70,19 @@ void launch_one(void (*kernel)(Domain<R>), const Domain<R>& d, dim3 grid, dim3 b
 }
 
 template <int Q, typename S, typename R, bool SR>
-void launch_parity(const Domain<R>& d, bool odd, bool force, dim3 grid, dim3 block,
-                          const BlockShape& b, cudaStream_t st) {
+void launch_parity(const Domain<R>& d, bool odd, bool force, bool wide, dim3 grid, dim3 block,
+                   const BlockShape& b, cudaStream_t st) {
+  // Q*N >= 2^31: one cell per thread with 64-bit population offsets
+  if (wide) {
+    if (odd) {
+      if (force) launch_one(k_step<Q, S, R, true, true, SR, true>, d, grid, block, b.pdl != 0, st);
+      else launch_one(k_step<Q, S, R, true, false, SR, true>, d, grid, block, b.pdl != 0, st);
+    } else {
+      if (force) launch_one(k_step<Q, S, R, false, true, SR, true>, d, grid, block, b.pdl != 0, st);
+      else launch_one(k_step<Q, S, R, false, false, SR, true>, d, grid, block, b.pdl != 0, st);
+    }
+    return;
+  }
   // two cells per thread: even steps of FP32 / FP16 / BF16 storage with nx
   // even and no solid nodes, Q = 14 or 18 (the 52 packed values of a Q = 26
   // pair would not fit the registers); every other step runs one cell per
@@ -101,13 +117,14 @@ cudaError_t launch_typed(const DomainDesc& dd, int64_t n, BlockShape b,
   dim3 block(b.bx, b.by, 1);
   dim3 grid((dd.nx + b.bx - 1) / b.bx, (dd.ny + b.by - 1) / b.by, dd.nz);
   const bool odd = (n & 1) != 0;
+  const bool wide = (int64_t)dd.Q * dd.N >= (int64_t(1) << 31);
   if constexpr (Stochastic<S>::enabled) {
     if (dd.rounding == LBM_ROUND_STOCHASTIC) {
-      launch_parity<Q, S, R, true>(d, odd, force, grid, block, b, st);
+      launch_parity<Q, S, R, true>(d, odd, force, wide, grid, block, b, st);
       return cudaGetLastError();
     }
   }
-  launch_parity<Q, S, R, false>(d, odd, force, grid, block, b, st);
+  launch_parity<Q, S, R, false>(d, odd, force, wide, grid, block, b, st);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 using namespace lbm;
 
 static int g_sr = 0;
+static int g_wide = 0;  // the step's 64-bit-offset (WIDE) instantiations
 
 // fn.template operator()<Q>() for Q = 14, 18 or 26; -1 for any other Q
 template <typename Fn>
@@ -49,25 +50,31 @@ static void step_typed(void* f, int nx, int ny, int nz, const int* per, int movi
   d.key = mix32(0x5eedu ^ uint32_t(n) * 0x632be5abu);
   fill_offsets<Q>(d);
   const bool force = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0;
+  // one cell of the step kernel: parity, force and rounding as launched
+  auto cell = [&]<bool WIDE>(int x, int y, int z, int xl, int xh) {
+    S* fs = static_cast<S*>(f);
+    if constexpr (Stochastic<S>::enabled) {
+      if (g_sr) {
+        if (n & 1) update_cell<Q, S, R, true, true, true, false, WIDE>(d, fs, x, y, z, xl, xh);
+        else update_cell<Q, S, R, false, true, true, false, WIDE>(d, fs, x, y, z, xl, xh);
+        return;
+      }
+    }
+    if (n & 1) {
+      if (force) update_cell<Q, S, R, true, true, false, false, WIDE>(d, fs, x, y, z, xl, xh);
+      else update_cell<Q, S, R, true, false, false, false, WIDE>(d, fs, x, y, z, xl, xh);
+    } else {
+      if (force) update_cell<Q, S, R, false, true, false, false, WIDE>(d, fs, x, y, z, xl, xh);
+      else update_cell<Q, S, R, false, false, false, false, WIDE>(d, fs, x, y, z, xl, xh);
+    }
+  };
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         // the 32-wide x-range a warp of a 32-multiple-wide block would cover
         const int xl = x & ~31, xh = xl + 31;
-        if constexpr (Stochastic<S>::enabled) {
-          if (g_sr) {
-            if (n & 1) update_cell<Q, S, R, true, true, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
-            else update_cell<Q, S, R, false, true, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
-            continue;
-          }
-        }
-        if (n & 1) {
-          if (force) update_cell<Q, S, R, true, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
-          else update_cell<Q, S, R, true, false>(d, static_cast<S*>(f), x, y, z, xl, xh);
-        } else {
-          if (force) update_cell<Q, S, R, false, true>(d, static_cast<S*>(f), x, y, z, xl, xh);
-          else update_cell<Q, S, R, false, false>(d, static_cast<S*>(f), x, y, z, xl, xh);
-        }
+        if (g_wide) cell.template operator()<true>(x, y, z, xl, xh);
+        else cell.template operator()<false>(x, y, z, xl, xh);
       }
 }
 
@@ -148,6 +155,7 @@ static void neq_typed(void* f, int nx, int ny, int nz, const int* per, int movin
 
 extern "C" {
 void emu_set_stochastic(int on) { g_sr = on; }
+void emu_set_wide(int on) { g_wide = on; }
 
 // Solid-link words of a byte mask (the device builder's per-cell code).
 int emu_solid_links(int Q, int nx, int ny, int nz, int per, int sym, const uint8_t* bytes,

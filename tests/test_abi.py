@@ -57,7 +57,10 @@ def test_strerror_and_argument_errors(library):
     assert library.lbm_create(ctypes.byref(bad), None, ctypes.byref(out)) == lbm.LBM_EINVAL
     bad = lbm.lbm_desc(18, 8, 8, 8, 9)
     assert library.lbm_create(ctypes.byref(bad), None, ctypes.byref(out)) == lbm.LBM_EINVAL
-    big = lbm.lbm_desc(18, 1024, 1024, 1024, lbm.LBM_STORAGE_F32)
+    big = lbm.lbm_desc(18, 2048, 1024, 1024, lbm.LBM_STORAGE_F16)  # 2^31 cells
     assert library.lbm_create(ctypes.byref(big), None, ctypes.byref(out)) == lbm.LBM_EINVAL
+    assert b"2^31" in library.lbm_last_error()
+    tall = lbm.lbm_desc(14, 4, 4, 65536, lbm.LBM_STORAGE_F32)  # grid z limit
+    assert library.lbm_create(ctypes.byref(tall), None, ctypes.byref(out)) == lbm.LBM_EINVAL
     assert library.lbm_step(None, 1) == lbm.LBM_EINVAL
     library.lbm_destroy(None)

@@ -45,6 +45,7 @@ def emu():
     L.emu_solid_links.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, vp, vp]
     L.emu_set_solid.argtypes = [vp]
+    L.emu_set_wide.argtypes = [ctypes.c_int]
     L.emu_neq.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip,
                           ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp,
                           ctypes.c_int64]
@@ -144,9 +145,20 @@ EDGE = [
 ]
 
 
+@pytest.mark.parametrize("wide", (False, True))
 @pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces,edge", EDGE)
-def test_step_matches_oracle(emu, Q, name, shape, faces, edge):
+def test_step_matches_oracle(emu, Q, name, shape, faces, edge, wide):
+    """The step's per-cell code, with 32-bit and with 64-bit (WIDE)
+    population offsets, against the oracle."""
+    emu.emu_set_wide(int(wide))
+    try:
+        _step_matches_oracle(emu, Q, name, shape, faces, edge)
+    finally:
+        emu.emu_set_wide(0)
+
+
+def _step_matches_oracle(emu, Q, name, shape, faces, edge):
     rng = np.random.default_rng(5)
     uw = rng.normal(size=(6, 3)) * 0.03
     case = inputs.Case(name, Q, shape[0], shape[1], shape[2], tuple(faces), uw,
@@ -184,8 +196,9 @@ def test_restore_at_odd_parity(emu, Q):
 @pytest.mark.parametrize("name,shape,faces,edge", [e for e in EDGE if e[0] in
                                                    ("sym_lid", "sym_corner", "edge_multi",
                                                     "sym_wide_x")])
+@pytest.mark.parametrize("wide", (False, True))
 def test_reduced_storage_step_matches_oracle(emu, Q, name, shape, faces, edge, storage, dtype,
-                                             tol):
+                                             tol, wide):
     """FP32 and FP16 storage (FP32 arithmetic) of the kernel's per-cell code
     with symmetry faces and edge profiles: 7 steps from a seeded state
     against the FP64 oracle, to the storage precision."""
@@ -203,11 +216,15 @@ def test_reduced_storage_step_matches_oracle(emu, Q, name, shape, faces, edge, s
     canon = np.ascontiguousarray(f0, dtype=np.float64)
     assert emu.emu_canonical_storage(Q, storage, A.ctypes.data, *shape, *d._geom(), _d(canon),
                                      0, 1) == 0
-    for n in range(7):
-        amp = np.cos(2 * np.pi * n / case.period)
-        F = np.array(case.force, dtype=np.float64) * amp
-        assert emu.emu_step(Q, storage, A.ctypes.data, *shape, *d._geom(), _d(d.s), _d(F),
-                            n) == 0
+    emu.emu_set_wide(int(wide))
+    try:
+        for n in range(7):
+            amp = np.cos(2 * np.pi * n / case.period)
+            F = np.array(case.force, dtype=np.float64) * amp
+            assert emu.emu_step(Q, storage, A.ctypes.data, *shape, *d._geom(), _d(d.s),
+                                _d(F), n) == 0
+    finally:
+        emu.emu_set_wide(0)
     out = np.zeros_like(canon)
     assert emu.emu_canonical_storage(Q, storage, A.ctypes.data, *shape, *d._geom(), _d(out),
                                      7, 0) == 0
@@ -278,9 +295,10 @@ SOLID = [
 ]
 
 
+@pytest.mark.parametrize("wide", (False, True))
 @pytest.mark.parametrize("Q", (14, 18, 26))
 @pytest.mark.parametrize("name,shape,faces,frac", SOLID)
-def test_solid_nodes_match_oracle(emu, Q, name, shape, faces, frac):
+def test_solid_nodes_match_oracle(emu, Q, name, shape, faces, frac, wide):
     """The kernel's per-cell code with a random solid-node mask (link words
     built by the device builder's per-cell code) against the oracle's solid
     mask: FP64, random state, wall velocities and force, 1, 2, 7 and 30
@@ -300,6 +318,7 @@ def test_solid_nodes_match_oracle(emu, Q, name, shape, faces, frac):
     per = int(d.per[0]) | (int(d.per[1]) << 1) | (int(d.per[2]) << 2)
     assert emu.emu_solid_links(Q, *shape, per, d.sym, solid.ctypes.data, links.ctypes.data) == 0
     emu.emu_set_solid(links.ctypes.data)
+    emu.emu_set_wide(int(wide))
     try:
         d.put(f, 0)
         for k in (1, 1, 5, 23):
@@ -310,3 +329,4 @@ def test_solid_nodes_match_oracle(emu, Q, name, shape, faces, frac):
             assert np.max(np.abs(got - f)) <= 1e-12 * np.max(np.abs(f)), (d.n,)
     finally:
         emu.emu_set_solid(None)
+        emu.emu_set_wide(0)
