@@ -57,6 +57,9 @@ def parse():
                     help="cube side of the storage-precision comparison (0: skip); its "
                          "buffers are several times larger than L2, so steps run back to back")
     ap.add_argument("--precision-steps", type=int, default=200)
+    ap.add_argument("--large-n", type=int, default=1024,
+                    help="cube side of the large-domain timing (D3Q18 FP16, Q*N >= 2^31, the "
+                         "step's 64-bit-offset kernels; 0: skip)")
     ap.add_argument("--porous-n", type=int, default=256,
                     help="cube side of the solid-node (porous medium) timing (0: skip)")
     ap.add_argument("--reduction-n", type=int, default=256,
@@ -464,6 +467,34 @@ def run_gpu(a, rank, world, dist):
                                 2 * 14 * a.precision_n ** 3 >> 20,
                                 4 * 26 * a.precision_n ** 3 >> 20))
 
+    # --- one large domain: Q*N >= 2^31, the step's 64-bit-offset kernels ------------
+    large = {}
+    if a.large_n > 0 and rank == 0:
+        cl = inputs.cavity(18, a.large_n, a.Re, U=0.05, storage="f16")
+        hl = lbm.lbm_create(18, cl.nx, cl.ny, cl.nz, "f16", sp)
+        try:
+            lbm.lbm_set_geometry(hl, cl.faces, cl.u_wall)
+            lbm.lbm_set_params(hl, nu=cl.nu, residual_interval=0)
+            lbm.lbm_init_equilibrium(hl)
+            bl, _ = lbm.lbm_autotune(hl, 2)
+            lbm.lbm_step(hl, 4)
+            kl = 20
+            e0.record(stream)
+            lbm.lbm_step(hl, kl)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tl = e0.elapsed_time(e1) / kl
+        finally:
+            lbm.lbm_destroy(hl)
+        lbytes = 2 * 18 * 2 * cl.cells
+        large = {"workload": "lid-driven cavity %d^3 D3Q18 FP16 (%.1f GB of populations, "
+                             "Q*N = %.3g >= 2^31)" % (a.large_n, 18 * 2 * cl.cells / 1e9,
+                                                      18.0 * cl.cells),
+                 "launch": list(bl), "steps": kl,
+                 "glups": round(cl.cells / (tl * 1e-3) / 1e9, 3),
+                 "hbm_gbs": round(lbytes / (tl * 1e-3) / 1e9, 1),
+                 "frac_of_measured_hbm": round(lbytes / (tl * 1e-3) / 1e9 / peak, 4)}
+
     # --- solid nodes: a porous medium of random spheres, 256^3 --------------------
     porous = {}
     if a.porous_n > 0 and rank == 0:
@@ -566,6 +597,7 @@ def run_gpu(a, rank, world, dist):
         "precision": precision,
         "reductions": reductions,
         "solid_nodes": porous,
+        "large_domain": large,
         "flushed_per_step": flushed,
     }
     return res
