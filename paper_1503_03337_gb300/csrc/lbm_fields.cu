@@ -325,9 +325,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d,
   float2* snap = reinterpret_cast<float2*>(a.u_prev);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % d.nx);
-    const int64_t r = i / d.nx;
-    const int y = (int)(r % d.ny), z = (int)(r / d.ny);
+    // a cell index (N < 2^31): 32-bit division, far cheaper than 64-bit
+    const int c = (int)i;
+    const int x = c % d.nx;
+    const int r = c / d.nx;
+    const int y = r % d.ny, z = r / d.ny;
     if (d.solid && (d.solid[i] & kSolidCell)) {  // no flow: zero in every sum
       if (a.u_prev)
         for (int k = 0; k < 3; ++k) snap[(int64_t)k * N + i] = make_float2(0.0f, 0.0f);
