@@ -257,13 +257,14 @@ __device__ __forceinline__ bool greater(PairSum a, PairSum b) {
 // whose source is a ghost beyond a moving face, evaluated in FP64 from the
 // FP64 wall velocities and added as pairs (the same canonical values that
 // the FP64 path of get_canonical forms).
-template <int Q, typename S, bool ODD>
+template <int Q, typename S, bool ODD, bool WIDE>
 __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __restrict__ f,
                                              int x, int y, int z, const double (&uw)[6][3],
                                              const double (&es)[6][2],
                                              PairSum& sP, PairSum (&sj)[3]) {
+  using Ix = PopIndex<WIDE>;  // 64-bit offsets only where Q*N >= 2^31
   const int i = x + d.nx * (y + d.ny * z);
-  const int64_t N = d.N;
+  const Ix N = (Ix)d.N;
   Links L{};
   if constexpr (ODD) L = make_links(d, x, y, z);
   [&]<int... A>(std::integer_sequence<int, A...>) {
@@ -271,7 +272,7 @@ __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __
         [&] {
           constexpr int cx = Lattice<Q>::c(A, 0), cy = Lattice<Q>::c(A, 1),
                         cz = Lattice<Q>::c(A, 2);
-          int64_t idx = A * N + i;
+          Ix idx = A * N + i;
           if constexpr (ODD) {
             int off, mirror;
             bool ghost;
@@ -312,8 +313,9 @@ __device__ __forceinline__ void cell_moments(const Domain<float>& d, const S* __
 // k_reduce for FP32 / FP16 / BF16 storage on PairSum arithmetic (see
 // above); the statistics are those of k_reduce.  The snapshot holds each u
 // component as its (hi, lo) pair in the 8 bytes of its FP64 slot.  Cells
-// are numbered with 32-bit arithmetic (Q*N < 2^31).
-template <int Q, typename S, bool ODD>
+// are numbered with 32-bit arithmetic; population offsets are 32-bit too
+// unless Q*N >= 2^31 (WIDE).
+template <int Q, typename S, bool ODD, bool WIDE>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d, ReduceArgs a,
                                                                  PairSum Fh0, PairSum Fh1,
                                                                  PairSum Fh2, PairSum Pref) {
@@ -321,11 +323,14 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d,
   PairSum sdu[3], su_abs[3], sup_abs[3], su[3], sPt, umax;
   int nonfinite = 0;
   const PairSum Fh[3] = {Fh0, Fh1, Fh2};
-  const int64_t N = d.N;
+  // the loop counter is 64-bit only where Q*N >= 2^31 (it may pass 2^31 on
+  // its last increment there); the cell index itself is below 2^31, so the
+  // coordinates come from a 32-bit division
+  using Ix = PopIndex<WIDE>;
+  const Ix N = (Ix)d.N;
   float2* snap = reinterpret_cast<float2*>(a.u_prev);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    // a cell index (N < 2^31): 32-bit division, far cheaper than 64-bit
+  for (Ix i = blockIdx.x * (Ix)blockDim.x + threadIdx.x; i < N;
+       i += (Ix)gridDim.x * blockDim.x) {
     const int c = (int)i;
     const int x = c % d.nx;
     const int r = c / d.nx;
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_pair(Domain<float> d,
       continue;
     }
     PairSum sP, sj[3];
-    cell_moments<Q, S, ODD>(d, static_cast<const S*>(d.f), x, y, z, a.uw, a.edge_scale, sP,
+    cell_moments<Q, S, ODD, WIDE>(d, static_cast<const S*>(d.f), x, y, z, a.uw, a.edge_scale, sP,
                             sj);
     PairSum u[3];
     bool finite = isfinite(sP.hi) && isfinite(sP.lo);
@@ -512,8 +517,10 @@ cudaError_t launch_reduce(const DomainDesc& dd, int64_t n, double* u_prev, int h
       const PairSum f0 = pair_of(0.5 * F[0]), f1 = pair_of(0.5 * F[1]),
                     f2 = pair_of(0.5 * F[2]);
       const PairSum pr = pair_of(3.0 * (1.0 - Lattice<Q>::w0) * dd.p_ref);
-      if (odd) k_reduce_pair<Q, S, true><<<(int)g, kReduceThreads, 0, st>>>(df, a, f0, f1, f2, pr);
-      else k_reduce_pair<Q, S, false><<<(int)g, kReduceThreads, 0, st>>>(df, a, f0, f1, f2, pr);
+      const bool wide = (int64_t)dd.Q * dd.N >= (int64_t(1) << 31);
+      auto kernel = wide ? (odd ? k_reduce_pair<Q, S, true, true> : k_reduce_pair<Q, S, false, true>)
+                         : (odd ? k_reduce_pair<Q, S, true, false> : k_reduce_pair<Q, S, false, false>);
+      kernel<<<(int)g, kReduceThreads, 0, st>>>(df, a, f0, f1, f2, pr);
     } else {
       if (odd) k_reduce<Q, S, true><<<(int)g, kReduceThreads, 0, st>>>(d, a);
       else k_reduce<Q, S, false><<<(int)g, kReduceThreads, 0, st>>>(d, a);
