@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the iD3Q14 / iD3Q18 incompressible MRT LBM.
+"""FP64 CPU oracle for the iD3Q14 / iD3Q18 incompressible MRT LBM, and for
+the iD3Q26 model built by the same construction (App. B's closing remark).
 
 TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the CPU
 baseline leg of the benchmark are the only callers.  The product path (the
